@@ -1,0 +1,309 @@
+"""Benchmark of the FMM force solve on GB300.
+
+A step is one pass of the whole hot path over one box of synthetic particles: Morton keys,
+radix sort, radix tree, upward pass, checklist walk with local expansions, PP, PC and L2P
+evaluation (fmm_compute_forces), then one kick-drift substep on rung 0 (fmm_kick_drift).
+The default workload is the 128^3 clustered NFW box (30% uniform background, 70% in 200 NFW
+halos, eps = 1/50 of the mean separation, theta = 0.55, buckets of 16, groups of 64).
+
+metric: interactions/s = (PP pairs + PC pairs) of one solve / seconds per step, over the
+whole job (all ranks).  Inputs are resident in HBM when the timed region starts; the box is
+larger than L2 for the tree-build phase and every step rebuilds the tree from the drifted
+positions, so no state is reused across steps.  ``e2e`` repeats the measurement through
+fmm_compute_forces_host with host buffers (copies inside the timed region).
+
+``--impl reference`` times the CPU oracle (plain FP64 FMM, OpenMP) on a bounded sample of
+the same workload and prints the same JSON line with "impl": "reference".
+
+Under torchrun each rank solves an independent box (its own seed): weak scaling, no
+collective on the data path; rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP32 FMA peak of the part: SMs x lanes x 2 flops x max SM clock (TFLOP/s)
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul, 3 fma, 1 add)
+
+# DRAM traffic per launch of the dominant kernel from an ncu capture (bytes), or None.
+# Filled from the committed profile summary of the current kernel; reset to None whenever the
+# kernel changes.
+NCU_TRAFFIC = {"k_pc": None, "k_pp": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="nfw2m", choices=["nfw2m", "plummer4096", "rungs16m"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
+    return ap.parse_args()
+
+
+def workload(name, rank):
+    from paper_1609_08621_gb300 import synth
+
+    w = synth.WORKLOADS[name]
+    seed = w["seed"] + 1000 * rank
+    pos, mass = synth.make(w["kind"], w["n"], seed)
+    return pos, mass, w["eps"], w["theta"]
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons in the background during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.rows.append([x.strip() for x in ln.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 8:
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
+    """The oracle's plain FP64 FMM on a bounded sample: the full tree, forces for a random
+    subset of active sinks.  Returns interactions/s over the sample."""
+    import oracle
+
+    n = mass.size
+    rng = np.random.default_rng(123)
+    if frac is None:
+        frac = min(1.0, 4096.0 / n)
+    act = (rng.random(n) < frac).astype(np.uint8)
+    t0 = time.perf_counter()
+    f = oracle.FMM(pos, mass, eps, theta, active=act)
+    f.forces()
+    dt = time.perf_counter() - t0
+    c = f.counts()
+    inter = c["pp_pairs"] + c["pc_pairs"]
+    return {"value": inter / dt, "unit": "interactions/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"N={n} tree + walk + FP64 PP/PC/local for {int(act.sum())} random active sinks "
+                      f"({frac:.4f} of N); {inter} interactions in {dt:.2f} s",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pos, mass, eps, theta = workload(args.workload, 0)
+    vals = []
+    for _ in range(max(args.warmup, 0) and 0 or 0):
+        pass
+    steps = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(pos, mass, eps, theta, frac=args.cpu_sample or min(1.0, 1024.0 / mass.size))
+        if k >= args.warmup:
+            steps.append(r)
+    v = float(np.mean([s["value"] for s in steps]))
+    sec = float(np.mean([s["seconds"] for s in steps]))
+    line = {"impl": "reference", "metric": "interactions/s (PP + PC) per force solve", "value": v,
+            "unit": "interactions/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": int(mass.size), "eps": eps, "theta": theta},
+            "cpu_baseline": {k: steps[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    line["cpu_baseline"]["value"] = v
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    from paper_1609_08621_gb300 import binding
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    pos, mass, eps, theta = workload(args.workload, rank)
+    n = mass.size
+    tpos0 = torch.from_numpy(pos.reshape(-1).copy()).to(dev)
+    tpos = tpos0.clone()
+    tmass = torch.from_numpy(mass).to(dev)
+    vel = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+    acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+    pot = torch.zeros(n, dtype=torch.float32, device=dev)
+    rung = torch.zeros(n, dtype=torch.uint8, device=dev)
+    act_next = torch.zeros(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(local, stream)
+    dt0 = 1e-5  # tiny base step: the box barely changes, so every step solves the same workload
+
+    def step(k):
+        ctx.compute_forces(tpos, tmass, eps, theta, acc, pot)
+        ctx.kick_drift(tpos, vel, acc, rung, act_next, eps, dt0, 0, 0, 1 if k > 0 else 0)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    kt = {"pp": 0.0, "pc": 0.0, "tree": 0.0, "walk": 0.0, "l2p": 0.0}
+    inter = []
+    launches = 0
+    e0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k)
+        st = ctx.stats()
+        for key in kt:
+            kt[key] += st["ms_" + key]
+        inter.append(st["n_pp_pairs"] + st["n_pc_pairs"])
+        launches += st["n_launches"] + 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(np.mean(inter))], device=dev, dtype=torch.float64)
+        dist.all_reduce(tot)
+        inter_job = float(tot.item())
+    else:
+        inter_job = float(np.mean(inter))
+    value = inter_job / (ms * 1e-3)
+    st = ctx.stats()
+    # roofline of the dominant kernel (FP32 ALU bound)
+    pp_ms, pc_ms = kt["pp"] / args.steps, kt["pc"] / args.steps
+    flops_pc = st["kernel_flops_pc"]
+    flops_pp = st["kernel_flops_pp"]
+    dom = "k_pc" if pc_ms >= pp_ms else "k_pp"
+    dom_ms = pc_ms if dom == "k_pc" else pp_ms
+    dom_flops = flops_pc if dom == "k_pc" else flops_pp
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+            "pp_pc_frac": ((flops_pp + flops_pc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
+            if pp_ms + pc_ms > 0 else 0.0}
+    line = {"metric": "interactions/s (PP + PC) per force solve", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": int(n), "eps": eps, "theta": theta, "bucket": 16,
+                       "group": 64, "l2": "inputs and tree larger than L2 are rebuilt every step"},
+            "phase_ms": {k: v / args.steps for k, v in kt.items()},
+            "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
+            "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
+            "roofline": roof, "clocks": ck, "gpu_launches": launches}
+    # end to end through the host-buffer entry point
+    if not args.no_e2e:
+        hpos = torch.from_numpy(pos.reshape(-1).copy()).pin_memory().numpy()
+        hmass = torch.from_numpy(mass.copy()).pin_memory().numpy()
+        hacc = torch.zeros(3 * n, dtype=torch.float32).pin_memory().numpy()
+        hpot = torch.zeros(n, dtype=torch.float32).pin_memory().numpy()
+        for _ in range(2):
+            ctx.compute_forces_host(hpos, hmass, eps, theta, hacc, hpot)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.compute_forces_host(hpos, hmass, eps, theta, hacc, hpot)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": inter_job / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
+                       "h2d_bytes_per_step": int(hpos.nbytes + hmass.nbytes),
+                       "d2h_bytes_per_step": int(hacc.nbytes + hpot.nbytes)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(pos, mass, eps, theta, args.cpu_sample).items()
+                                if k != "seconds"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * fmm.h -- C ABI of the GB300 (sm_103a) FMM gravity force solve.
+ *
+ * The library computes softened gravitational accelerations and potentials of N
+ * particles in the isolated unit box with the fast multipole method of PKDGRAV3
+ * (Potter, Stadel & Teyssier, arXiv:1609.08621):
+ *   - a Morton-ordered binary tree whose leaves ("buckets") hold at most b
+ *     particles (Sec. 3.1, "Leaf cells of our tree contain up to b particles");
+ *   - order-4 multipoles about each cell's centre of mass and the opening
+ *     radius R_O = b_max / theta (Sec. 3.1);
+ *   - a checklist walk that sorts each source into cell-cell / cell-particle
+ *     (local expansion), particle-cell, particle-particle, "stay on the
+ *     checklist" or "open" (Sec. 3.1), stopping at groups of at most g
+ *     particles;
+ *   - PP, PC and local-expansion (order 5) evaluation for each group (Sec. 3.1,
+ *     Sec. 3.3);
+ *   - kick-drift-kick on individual time-step rungs (Sec. 3.2).
+ *
+ * Physics conventions (all entry points): G = 1, Plummer softening,
+ *     a_i   =  sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2)
+ *     phi_i = -sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^(1/2)
+ * which the method approximates.  Positions must lie in [0,1)^3 (isolated box,
+ * no periodic replicas), masses must be finite and > 0, eps > 0, 0 < theta <= 1.
+ *
+ * Memory and ownership:
+ *   - "device" arguments are CUDA device pointers on the context's device;
+ *     "host" arguments are host pointers (pinned memory is faster, pageable
+ *     works).  The caller owns every pointer it passes; the library never
+ *     frees or retains them beyond the call.
+ *   - Positions are structure-of-arrays doubles: x[0..N), then y, then z
+ *     (3N values).  Accelerations likewise (3N floats).  Outputs are in the
+ *     caller's particle order.
+ *   - Everything behind an fmm_ctx (tree, lists, scratch, events) is owned by
+ *     the library and released by fmm_destroy.
+ *
+ * Streams and synchronisation: all device work of a context runs on the CUDA
+ * stream given to fmm_create (0 = the legacy default stream).  fmm_kick_drift and
+ * fmm_assign_rungs are asynchronous with respect to the host.  fmm_build_tree and
+ * fmm_compute_forces read sizes back to the host (cell counts, per-level frontier
+ * sizes of the walk) and return after their work has completed on the stream.
+ *
+ * Errors: every entry point returns an fmm_status.  A message for the last
+ * failure on the calling thread is returned by fmm_last_error().  Device-side
+ * failures (a bounded wait that gave up, capacity exhausted, invalid input
+ * detected by a kernel) are reported through a device status word that the
+ * library reads at its next synchronisation point; kernels never trap.
+ * After FMM_ERR_CUDA the context should be destroyed.
+ */
+#ifndef FMM_GB300_H
+#define FMM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_ctx fmm_ctx;
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,     /* invalid argument (pointer, size, range, parameter) */
+    FMM_ERR_OOM = -2,     /* device or host allocation failed */
+    FMM_ERR_CUDA = -3,    /* a CUDA runtime call failed */
+    FMM_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up */
+    FMM_ERR_STATE = -5,   /* call order violated (e.g. export before any solve) */
+    FMM_ERR_NUMERIC = -6  /* non-finite input or output detected */
+} fmm_status;
+
+/* Solver parameters.  Obtain defaults from fmm_default_params. */
+typedef struct fmm_params {
+    double theta;          /* opening angle, 0 < theta <= 1 (Sec. 3.1; default 0.55, Sec. 4.2) */
+    double eps;            /* Plummer softening length, > 0 (Sec. 3.1: 1/50 of the mean separation) */
+    int bucket;            /* b: maximum particles per leaf, 1..16 (Sec. 3.1: ~16; default 16) */
+    int group;             /* g: sink group size, bucket..64 (Sec. 3.1: 64 = 4 b; default 64) */
+    int criterion;         /* 0: fixed theta (Sec. 3.1); 1: learned (MLP, requires fmm_mlp_load) */
+    int accumulate;        /* 0: FP32 partial sums; 1: compensated (double-float) accumulation */
+    int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion; default 7 */
+    int reserved;          /* must be 0 */
+    long long spin_limit;  /* iteration cap of any device-side wait (default 1<<26) */
+} fmm_params;
+
+/* Per-solve statistics of the last fmm_compute_forces on a context. */
+typedef struct fmm_stats {
+    long long n;            /* particles */
+    long long n_active;     /* active particles (forces computed) */
+    long long n_cells;      /* tree cells */
+    long long n_buckets;    /* leaf buckets */
+    long long n_groups;     /* sink groups walked to the end */
+    long long n_levels;     /* walk levels (tree depth reached by the walk + 1) */
+    long long n_pp_pairs;   /* particle-particle interactions (sink x source particle) */
+    long long n_pc_pairs;   /* particle-cell interactions (sink x source cell) */
+    long long n_cc;         /* cell-cell (multipole -> local) interactions */
+    long long n_cp;         /* cell-particle (particle -> local) interactions */
+    long long n_pp_entries; /* PP list entries (buckets or particles) */
+    long long n_pc_entries; /* PC list entries (cells) */
+    double ms_tree;         /* keys, sort, tree, upward pass (CUDA events) */
+    double ms_walk;         /* checklist walk + local expansions */
+    double ms_pp;           /* PP kernel */
+    double ms_pc;           /* PC kernel */
+    double ms_l2p;          /* local expansion at particles + output */
+    double ms_total;        /* whole solve */
+    double paper_flops;     /* paper-equivalent flops: 53 PP + 215 PC + 479 CC + 213 CP (Sec. 4.6) */
+    double kernel_flops_pp; /* FP32 flops performed by the PP kernel (19 per pair) */
+    double kernel_flops_pc; /* FP32 flops performed by the PC kernel (per pair count, see fmm_flops_per_pc) */
+    int retries;            /* walk restarts after a capacity grow */
+    int n_launches;         /* kernels launched by the solve */
+} fmm_stats;
+
+/* Fill *p with the defaults: theta 0.55, eps 1e-3, bucket 16, group 64, criterion 0,
+ * accumulate 0, terms 7, spin_limit 1<<26.  Returns FMM_ERR_ARG for p == NULL. */
+fmm_status fmm_default_params(fmm_params *p);
+
+/* Create a context on CUDA device `device`, enqueuing all work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  *out receives the
+ * context.  FMM_ERR_CUDA if the device cannot be used, FMM_ERR_OOM on allocation
+ * failure.  The context's parameters start at fmm_default_params. */
+fmm_status fmm_create(fmm_ctx **out, int device, void *cuda_stream);
+
+/* Release the context and all device memory it owns.  NULL is accepted. */
+void fmm_destroy(fmm_ctx *ctx);
+
+/* Replace the context's parameters (validated; FMM_ERR_ARG leaves them unchanged). */
+fmm_status fmm_set_params(fmm_ctx *ctx, const fmm_params *p);
+fmm_status fmm_get_params(const fmm_ctx *ctx, fmm_params *p);
+
+/* Build the tree of N particles: Morton keys, radix sort, binary radix tree with
+ * buckets of <= bucket particles, and the upward pass (mass, centre of mass,
+ * bounding box, exact b_max, order-4 moments) -- Sec. 3.1.
+ *   pos    device, 3N doubles, SoA x|y|z, each in [0,1)
+ *   mass   device, N floats, > 0
+ *   active device, N bytes (non-zero = active) or NULL for all active
+ *   n      1 <= n < 2^31
+ *   p      parameters (bucket is used) or NULL for the context's
+ * Returns after the tree is built (the cell count is read back to size the upward
+ * pass).  Invalid positions or masses are reported as FMM_ERR_ARG. */
+fmm_status fmm_build_tree(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,
+                          long long n, const fmm_params *p);
+
+/* Full force solve (Sec. 3.1): build the tree, walk it with the context's
+ * criterion, evaluate PP, PC and local expansions for every group that holds an
+ * active particle, and write the results in the caller's order.
+ *   pos, mass, active, n   as for fmm_build_tree
+ *   eps, theta             softening (> 0) and opening angle (0 < theta <= 1);
+ *                          they override the context's parameters for this call
+ *   acc    device, 3N floats SoA out (ax|ay|az); entries of inactive particles
+ *          are left unchanged
+ *   pot    device, N floats out, or NULL
+ * Returns after completion (see Streams).  Statistics via fmm_get_stats. */
+fmm_status fmm_compute_forces(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,
+                              long long n, double eps, double theta, float *acc, float *pot);
+
+/* Same as fmm_compute_forces with HOST buffers: pos (3N doubles), mass (N floats),
+ * active (N bytes or NULL) are copied to device memory owned by the context, and
+ * acc (3N floats) / pot (N floats or NULL) are copied back before returning. */
+fmm_status fmm_compute_forces_host(fmm_ctx *ctx, const double *pos, const float *mass,
+                                   const unsigned char *active, long long n, double eps, double theta, float *acc,
+                                   float *pot);
+
+/* One substep of the hierarchical kick-drift-kick leapfrog on time-step rungs
+ * (Sec. 3.2, Fig. KDK).  The base step dt0 is cut into 2^max_rung substeps of
+ * h = dt0 / 2^max_rung; particle i sits on rung r_i (step dt0 / 2^r_i) and is active at
+ * substep s when s is a multiple of 2^(max_rung - r_i).  For substep s this call does,
+ * for the particles active at s:
+ *   1. if closing != 0, the closing half kick v += a dt0 / 2^(r_i + 1) of the step that
+ *      ends at s (pass closing = 0 for the very first substep of a run),
+ *   2. rung reassignment from Delta T = 0.2 sqrt(eps / |a|) (Sec. 3.2): the target rung
+ *      is the smallest r in [0, max_rung] with dt0 / 2^r <= Delta T; a particle moves
+ *      to a coarser rung only at a substep where that rung is synchronised,
+ *   3. the opening half kick v += a dt0 / 2^(r_i + 1) with the new rung;
+ * then drifts every particle, x += v h (FP64), and marks in active_next the particles
+ * active at substep s + 1, whose forces the caller computes next (for example with
+ * fmm_compute_forces(..., active_next, ...)).
+ *   pos   device, 3N doubles SoA, updated in place (must stay in [0,1): a particle that
+ *         leaves the box is reported as FMM_ERR_ARG by the next synchronising call)
+ *   vel   device, 3N doubles SoA, updated in place
+ *   acc   device, 3N floats SoA: accelerations at substep s of the active particles
+ *   rung  device, N bytes in [0, max_rung], updated in place
+ *   active_next  device, N bytes out
+ *   eps > 0, dt0 > 0, 0 <= max_rung <= 30, 0 <= substep < 2^max_rung.
+ * Asynchronous. */
+fmm_status fmm_kick_drift(fmm_ctx *ctx, double *pos, double *vel, const float *acc, unsigned char *rung,
+                          unsigned char *active_next, long long n, double eps, double dt0, int max_rung,
+                          int substep, int closing);
+
+/* Assign rungs from accelerations: the smallest r in [0, max_rung] with dt0 / 2^r <= Delta T,
+ * Delta T = 0.2 sqrt(eps / |a|) (Sec. 3.2).  acc device 3N floats SoA, rung device N bytes out.
+ * Asynchronous. */
+fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung, long long n, double eps,
+                            double dt0, int max_rung);
+
+/* Statistics of the last solve.  Synchronises the context's stream. */
+fmm_status fmm_get_stats(const fmm_ctx *ctx, fmm_stats *out);
+
+/* Message of the last error on the calling thread ("" if none). Never NULL. */
+const char *fmm_last_error(void);
+
+/* FP32 flops per particle-cell interaction performed by the PC kernel (a constant of the build). */
+double fmm_flops_per_pc(void);
+
+/* ---------------- introspection (stage-by-stage parity; synchronise the stream) ----------------
+ * All outputs are HOST buffers sized from fmm_tree_info.  Valid after fmm_build_tree
+ * (tree exports) or fmm_compute_forces (list and local exports); FMM_ERR_STATE otherwise.
+ * Cells are numbered by the library; a cell is identified across implementations by its
+ * particle range [first, first + count) in the sorted (Morton) order, which is the
+ * stable sort of the keys by (key, input index). */
+fmm_status fmm_tree_info(const fmm_ctx *ctx, long long *n_cells, long long *n_groups, long long *n_pp_entries,
+                         long long *n_pc_entries, long long *n_local_entries);
+
+/* perm[i] = input index of the i-th particle in sorted order; keys[i] its 63-bit Morton key
+ * (level l of the tree bisects axis l mod 3 in the order x, y, z; 21 bits per axis). */
+fmm_status fmm_export_order(const fmm_ctx *ctx, unsigned int *perm, unsigned long long *keys);
+
+/* Per cell: first, count, parent (-1 for the root), child (2 per cell, -1 for leaves),
+ * number of active particles, mass, centre of mass (3), bounding box lo (3) / hi (3),
+ * b_max, and the moment record (44 floats: M, M2 (6), M3 (10), M4 (15) about the centre of
+ * mass, then the traces trM2, trM3 (3), trM4 (6), trtrM4, 0).  Any pointer may be NULL. */
+fmm_status fmm_export_cells(const fmm_ctx *ctx, int *first, int *count, int *parent, int *child, int *nact,
+                            double *mass, double *com, double *lo, double *hi, double *bmax, float *moments);
+
+/* Interaction lists of the last solve.  kind: 0 PP, 1 PC, 2 CC, 3 CP.  For every entry:
+ * the sink cell and the source's particle range (a single particle has count 1).
+ * PP and PC entries belong to groups; CC and CP entries to any walked sink cell. */
+fmm_status fmm_export_lists(const fmm_ctx *ctx, int kind, long long *n_entries, int *sink, int *src_first,
+                            int *src_count, long long capacity);
+
+/* Local expansions of the groups: group_cell[i] and 56 coefficients L_k = D^k Phi at the
+ * group's centre of mass, in the order of fmm_multi_index. */
+fmm_status fmm_export_locals(const fmm_ctx *ctx, int *group_cell, float *L, long long capacity);
+
+/* The 56 multi-indices (a, b, c) of the local coefficients in storage order (168 ints),
+ * and the 32 multi-indices of the moment slots (96 ints).  Either may be NULL. */
+fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_GB300_H */

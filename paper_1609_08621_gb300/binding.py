@@ -1,0 +1,284 @@
+"""ctypes binding of the C ABI in ``include/fmm.h`` (argument marshalling only).
+
+Every computation happens in the CUDA library ``_build/libfmm_gb300.so``; if it is
+missing and cannot be built, loading raises -- there is no CPU fallback.  PyTorch is
+used only for device memory and streams: tensors are passed by their data pointers
+after their dtype, device, shape and contiguity are checked.
+
+The functions keep the C names (``fmm_create``, ``fmm_compute_forces``, ...);
+:class:`Context` is a small owner of one ``fmm_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FMM_OK = 0
+STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_TIMEOUT",
+          -5: "FMM_ERR_STATE", -6: "FMM_ERR_NUMERIC"}
+KIND = {"pp": 0, "pc": 1, "cc": 2, "cp": 3}
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fmm_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("bucket", C.c_int), ("group", C.c_int),
+                ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("reserved", C.c_int),
+                ("spin_limit", C.c_longlong)]
+
+
+class fmm_stats(C.Structure):
+    _fields_ = [(k, C.c_longlong) for k in ("n", "n_active", "n_cells", "n_buckets", "n_groups", "n_levels",
+                                             "n_pp_pairs", "n_pc_pairs", "n_cc", "n_cp", "n_pp_entries",
+                                             "n_pc_entries")] + \
+               [(k, C.c_double) for k in ("ms_tree", "ms_walk", "ms_pp", "ms_pc", "ms_l2p", "ms_total",
+                                          "paper_flops", "kernel_flops_pp", "kernel_flops_pc")] + \
+               [("retries", C.c_int), ("n_launches", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    vp, ll, d, i = C.c_void_p, C.c_longlong, C.c_double, C.c_int
+    sig = {
+        "fmm_default_params": (i, [C.POINTER(fmm_params)]),
+        "fmm_create": (i, [C.POINTER(vp), i, vp]),
+        "fmm_destroy": (None, [vp]),
+        "fmm_set_params": (i, [vp, C.POINTER(fmm_params)]),
+        "fmm_get_params": (i, [vp, C.POINTER(fmm_params)]),
+        "fmm_build_tree": (i, [vp, vp, vp, vp, ll, C.POINTER(fmm_params)]),
+        "fmm_compute_forces": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
+        "fmm_compute_forces_host": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
+        "fmm_kick_drift": (i, [vp, vp, vp, vp, vp, vp, ll, d, d, i, i, i]),
+        "fmm_assign_rungs": (i, [vp, vp, vp, ll, d, d, i]),
+        "fmm_get_stats": (i, [vp, C.POINTER(fmm_stats)]),
+        "fmm_last_error": (C.c_char_p, []),
+        "fmm_flops_per_pc": (d, []),
+        "fmm_tree_info": (i, [vp, C.POINTER(ll), C.POINTER(ll), C.POINTER(ll), C.POINTER(ll), C.POINTER(ll)]),
+        "fmm_export_order": (i, [vp, vp, vp]),
+        "fmm_export_cells": (i, [vp] + [vp] * 11),
+        "fmm_export_lists": (i, [vp, i, C.POINTER(ll), vp, vp, vp, ll]),
+        "fmm_export_locals": (i, [vp, vp, vp, ll]),
+        "fmm_multi_index": (i, [vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(st):
+    if st != FMM_OK:
+        raise FmmError(st, load().fmm_last_error().decode())
+
+
+def _ptr(t, dtype, n=None, name="tensor", allow_none=False):
+    """Data pointer of a contiguous CUDA tensor of the given torch dtype."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} must not be None")
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _hptr(a, dtype, n=None, name="array", allow_none=False):
+    if a is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} must not be None")
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{name} must be a C-contiguous numpy array of {dtype}")
+    if n is not None and a.size != n:
+        raise ValueError(f"{name} must have {n} elements, got {a.size}")
+    return a.ctypes.data
+
+
+def fmm_default_params() -> fmm_params:
+    p = fmm_params()
+    _check(load().fmm_default_params(C.byref(p)))
+    return p
+
+
+def fmm_flops_per_pc() -> float:
+    return float(load().fmm_flops_per_pc())
+
+
+def fmm_multi_index():
+    loc = np.zeros(56 * 3, np.int32)
+    mom = np.zeros(32 * 3, np.int32)
+    _check(load().fmm_multi_index(loc.ctypes.data, mom.ctypes.data))
+    return loc.reshape(56, 3), mom.reshape(32, 3)
+
+
+class Context:
+    """One fmm_ctx on a CUDA device, bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, device: int = 0, stream=None, **params):
+        import torch
+
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(load().fmm_create(C.byref(h), self.device, C.c_void_p(stream.cuda_stream)))
+        self.h = h
+        if params:
+            self.set_params(**params)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- parameters
+    def get_params(self) -> fmm_params:
+        p = fmm_params()
+        _check(load().fmm_get_params(self.h, C.byref(p)))
+        return p
+
+    def set_params(self, **kw):
+        p = self.get_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _check(load().fmm_set_params(self.h, C.byref(p)))
+
+    # -- solve
+    def build_tree(self, pos, mass, active=None, params=None):
+        import torch
+
+        n = mass.numel()
+        pp = C.byref(params) if params is not None else None
+        _check(load().fmm_build_tree(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                     _ptr(mass, torch.float32, n, "mass"),
+                                     _ptr(active, torch.uint8, n, "active", True), n, pp))
+
+    def compute_forces(self, pos, mass, eps, theta, acc, pot=None, active=None):
+        """pos (3N float64 SoA), mass (N float32), acc out (3N float32), pot out (N float32) -- CUDA tensors."""
+        import torch
+
+        n = mass.numel()
+        _check(load().fmm_compute_forces(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                         _ptr(mass, torch.float32, n, "mass"),
+                                         _ptr(active, torch.uint8, n, "active", True), n, float(eps), float(theta),
+                                         _ptr(acc, torch.float32, 3 * n, "acc"),
+                                         _ptr(pot, torch.float32, n, "pot", True)))
+
+    def compute_forces_host(self, pos, mass, eps, theta, acc, pot=None, active=None):
+        """Host (numpy) buffers; copies happen inside the library call."""
+        n = mass.size
+        _check(load().fmm_compute_forces_host(self.h, _hptr(pos, np.float64, 3 * n, "pos"),
+                                              _hptr(mass, np.float32, n, "mass"),
+                                              _hptr(active, np.uint8, n, "active", True), n, float(eps),
+                                              float(theta), _hptr(acc, np.float32, 3 * n, "acc"),
+                                              _hptr(pot, np.float32, n, "pot", True)))
+
+    def kick_drift(self, pos, vel, acc, rung, active_next, eps, dt0, max_rung, substep, closing):
+        import torch
+
+        n = rung.numel()
+        _check(load().fmm_kick_drift(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                     _ptr(vel, torch.float64, 3 * n, "vel"), _ptr(acc, torch.float32, 3 * n, "acc"),
+                                     _ptr(rung, torch.uint8, n, "rung"),
+                                     _ptr(active_next, torch.uint8, n, "active_next"), n, float(eps), float(dt0),
+                                     int(max_rung), int(substep), int(closing)))
+
+    def assign_rungs(self, acc, rung, eps, dt0, max_rung):
+        import torch
+
+        n = rung.numel()
+        _check(load().fmm_assign_rungs(self.h, _ptr(acc, torch.float32, 3 * n, "acc"),
+                                       _ptr(rung, torch.uint8, n, "rung"), n, float(eps), float(dt0),
+                                       int(max_rung)))
+
+    def stats(self) -> dict:
+        s = fmm_stats()
+        _check(load().fmm_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    # -- introspection (host numpy outputs)
+    def tree_info(self):
+        v = [C.c_longlong() for _ in range(5)]
+        _check(load().fmm_tree_info(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("cells", "groups", "pp", "pc", "local"), (x.value for x in v)))
+
+    def export_order(self, n):
+        perm = np.zeros(n, np.uint32)
+        keys = np.zeros(n, np.uint64)
+        _check(load().fmm_export_order(self.h, perm.ctypes.data, keys.ctypes.data))
+        return perm, keys
+
+    def export_cells(self):
+        nc = self.tree_info()["cells"]
+        d = dict(first=np.zeros(nc, np.int32), count=np.zeros(nc, np.int32), parent=np.zeros(nc, np.int32),
+                 child=np.zeros(2 * nc, np.int32), nact=np.zeros(nc, np.int32), mass=np.zeros(nc),
+                 com=np.zeros(3 * nc), lo=np.zeros(3 * nc), hi=np.zeros(3 * nc), bmax=np.zeros(nc),
+                 moments=np.zeros(44 * nc, np.float32))
+        keys = ("first", "count", "parent", "child", "nact", "mass", "com", "lo", "hi", "bmax", "moments")
+        _check(load().fmm_export_cells(self.h, *[d[k].ctypes.data for k in keys]))
+        d["child"] = d["child"].reshape(nc, 2)
+        for k in ("com", "lo", "hi"):
+            d[k] = d[k].reshape(nc, 3)
+        d["moments"] = d["moments"].reshape(nc, 44)
+        return d
+
+    def export_lists(self, kind):
+        k = KIND[kind]
+        n = C.c_longlong()
+        _check(load().fmm_export_lists(self.h, k, C.byref(n), None, None, None, 0))
+        m = n.value
+        sink, first, count = (np.zeros(max(m, 1), np.int32) for _ in range(3))
+        _check(load().fmm_export_lists(self.h, k, C.byref(n), sink.ctypes.data, first.ctypes.data,
+                                       count.ctypes.data, m))
+        return sink[:m], first[:m], count[:m]
+
+    def export_locals(self):
+        g = self.tree_info()["groups"]
+        cell = np.zeros(max(g, 1), np.int32)
+        L = np.zeros(max(g, 1) * 56, np.float32)
+        _check(load().fmm_export_locals(self.h, cell.ctypes.data, L.ctypes.data, g))
+        return cell[:g], L[:g * 56].reshape(g, 56)

@@ -1,0 +1,734 @@
+// C ABI and host orchestration of the force solve (see include/fmm.h).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "expansions.cuh"
+#include "fmm_internal.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+fmm_status fail(fmm_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    } while (0)
+
+template <typename T>
+cudaError_t grow(T** p, long long* cap, long long need)
+{
+    if (need <= *cap && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (need < 1) need = 1;
+    cudaError_t e = cudaMalloc((void**)p, (size_t)need * sizeof(T));
+    if (e == cudaSuccess) *cap = need;
+    return e;
+}
+
+template <typename T>
+cudaError_t alloc(T** p, long long need)
+{
+    long long cap = 0;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return grow(p, &cap, need);
+}
+
+}  // namespace
+
+struct fmm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    fmm_params params;
+    DevTree t;
+    DevWalk w;
+    DevCounters* ctr = nullptr;       // device
+    DevCounters* ctr_h = nullptr;     // pinned mirror
+    unsigned int* totals = nullptr;   // device: [cells, buckets]
+    unsigned int* totals_h = nullptr; // pinned
+    unsigned int* seed = nullptr;     // device: root frontier / checklist constants
+    cudaEvent_t ev[8] = {};
+    fmm_stats stats;
+    bool have_tree = false, have_solve = false;
+    int launches = 0;  // kernels launched by the current solve
+    float theta_nodes = -1.0f;
+    // staging for the host-buffer entry point
+    double* hpos = nullptr;
+    float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
+    unsigned char* hact = nullptr;
+    long long hcap = 0;
+};
+
+static fmm_status check_params(const fmm_params* p)
+{
+    if (!p) return fail(FMM_ERR_ARG, "params is NULL");
+    if (!(p->theta > 0.0 && p->theta <= 1.0)) return fail(FMM_ERR_ARG, "theta must be in (0, 1], got %g", p->theta);
+    if (!(p->eps > 0.0) || !(p->eps < 1.0)) return fail(FMM_ERR_ARG, "eps must be in (0, 1), got %g", p->eps);
+    if (p->bucket < 1 || p->bucket > 16) return fail(FMM_ERR_ARG, "bucket must be in [1, 16], got %d", p->bucket);
+    if (p->group < p->bucket || p->group > 64)
+        return fail(FMM_ERR_ARG, "group must be in [bucket, 64], got %d", p->group);
+    if (p->criterion != 0) return fail(FMM_ERR_ARG, "criterion %d is not available", p->criterion);
+    if (p->accumulate != 0) return fail(FMM_ERR_ARG, "accumulate %d is not available", p->accumulate);
+    if (p->terms < 0 || p->terms > 7) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4, got %d", p->terms);
+    if (p->reserved != 0) return fail(FMM_ERR_ARG, "reserved must be 0");
+    if (p->spin_limit < 1) return fail(FMM_ERR_ARG, "spin_limit must be >= 1");
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_default_params(fmm_params* p)
+{
+    if (!p) return fail(FMM_ERR_ARG, "params is NULL");
+    memset(p, 0, sizeof *p);
+    p->theta = 0.55;
+    p->eps = 1e-3;
+    p->bucket = 16;
+    p->group = 64;
+    p->criterion = 0;
+    p->accumulate = 0;
+    p->terms = 7;
+    p->spin_limit = 1LL << 26;
+    return FMM_OK;
+}
+
+extern "C" const char* fmm_last_error(void) { return g_err.c_str(); }
+
+extern "C" double fmm_flops_per_pc(void) { return (double)FMM_FLOPS_PC; }
+
+static void free_all(fmm_ctx* c)
+{
+    DevTree& t = c->t;
+    void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
+                  t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
+                  t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
+                  t.L, t.scan_part, t.hist};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    DevWalk& w = c->w;
+    void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.f_ccoff,
+                  w.f_cclen, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
+    for (void* p : qs)
+        if (p) cudaFree(p);
+    if (c->ctr) cudaFree(c->ctr);
+    if (c->totals) cudaFree(c->totals);
+    if (c->seed) cudaFree(c->seed);
+    if (c->ctr_h) cudaFreeHost(c->ctr_h);
+    if (c->totals_h) cudaFreeHost(c->totals_h);
+    void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact};
+    for (void* p : hs)
+        if (p) cudaFree(p);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return fail(FMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(FMM_ERR_ARG, "device %d out of range (%d devices)", device, ndev);
+    CK(cudaSetDevice(device));
+    fmm_ctx* c = new fmm_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    fmm_default_params(&c->params);
+    memset(&c->stats, 0, sizeof c->stats);
+    cudaError_t e = cudaMalloc(&c->ctr, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->ctr_h, sizeof(DevCounters));
+    if (e == cudaSuccess) e = cudaMalloc(&c->totals, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->totals_h, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->seed, 8 * sizeof(unsigned int));
+    for (auto& ev : c->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e == cudaSuccess) e = cudaMemset(c->seed, 0, 8 * sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(e == cudaErrorMemoryAllocation ? FMM_ERR_OOM : FMM_ERR_CUDA, "fmm_create: %s",
+                    cudaGetErrorString(e));
+    }
+    c->w.n_warps = fmm_walk_warps(device);
+    *out = c;
+    return FMM_OK;
+}
+
+extern "C" void fmm_destroy(fmm_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+extern "C" fmm_status fmm_set_params(fmm_ctx* c, const fmm_params* p)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    fmm_status st = check_params(p);
+    if (st != FMM_OK) return st;
+    c->params = *p;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_get_params(const fmm_ctx* c, fmm_params* p)
+{
+    if (!c || !p) return fail(FMM_ERR_ARG, "NULL argument");
+    *p = c->params;
+    return FMM_OK;
+}
+
+static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket)
+{
+    DevTree& t = c->t;
+    if (n > t.cap_n) {
+        long long cap = n;
+        CK(alloc(&t.key, cap));
+        CK(alloc(&t.key_alt, cap));
+        CK(alloc(&t.idx, cap));
+        CK(alloc(&t.idx_alt, cap));
+        CK(alloc(&t.sx, cap));
+        CK(alloc(&t.sy, cap));
+        CK(alloc(&t.sz, cap));
+        CK(alloc(&t.sm, cap));
+        CK(alloc(&t.sact, cap));
+        CK(alloc(&t.posf, cap));
+        CK(alloc(&t.off, cap));
+        CK(alloc(&t.accs, cap));
+        CK(alloc(&t.bucket_of, cap));
+        CK(alloc(&t.bflag, cap));
+        CK(alloc(&t.ifirst, cap));
+        CK(alloc(&t.ilast, cap));
+        CK(alloc(&t.ileft, cap));
+        CK(alloc(&t.iright, cap));
+        CK(alloc(&t.nparent, 2 * cap));
+        CK(alloc(&t.keep, 2 * cap));
+        t.cap_n = cap;
+    }
+    long long need_cells = 6 * n / (bucket + 1) + 8;
+    if (need_cells > 2 * n + 1) need_cells = 2 * n + 1;
+    if (need_cells > t.cap_cells) {
+        long long cap = need_cells;
+        CK(alloc(&t.cfirst, cap));
+        CK(alloc(&t.ccount, cap));
+        CK(alloc(&t.cparent, cap));
+        CK(alloc(&t.cchild, 2 * cap));
+        CK(alloc(&t.cnact, cap));
+        CK(alloc(&t.bucket_cell, cap));
+        CK(alloc(&t.arrive, cap));
+        CK(alloc(&t.com, cap));
+        CK(alloc(&t.clo, 3 * cap));
+        CK(alloc(&t.chi, 3 * cap));
+        CK(alloc(&t.bmax, cap));
+        CK(alloc(&t.rec, (long long)FMM_NREC * cap));
+        CK(alloc(&t.node, cap));
+        CK(alloc(&t.L, (long long)FMM_NL * cap));
+        t.cap_cells = cap;
+    }
+    CK(fmm_sort_ensure(t, n));
+    return FMM_OK;
+}
+
+static fmm_status read_status(fmm_ctx* c, const char* where)
+{
+    unsigned int st = c->ctr_h->status;
+    if (st & FMM_DEV_ERR_ARG)
+        return fail(FMM_ERR_ARG, "%s: a position outside [0,1), or a mass that is not finite and > 0", where);
+    if (st & FMM_DEV_ERR_TIMEOUT) return fail(FMM_ERR_TIMEOUT, "%s: a bounded device wait gave up", where);
+    if (st & FMM_DEV_ERR_NUMERIC) return fail(FMM_ERR_NUMERIC, "%s: non-finite result", where);
+    return FMM_OK;
+}
+
+static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
+                             long long n, int bucket)
+{
+    DevTree& t = c->t;
+    cudaStream_t s = c->stream;
+    fmm_status st = ensure_tree(c, n, bucket);
+    if (st != FMM_OK) return st;
+    c->have_tree = false;
+    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
+    CK(fmm_radix_sort(t, n, s));
+    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s));
+    CK(fmm_launch_radix_tree(t, n, bucket, s));
+    CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
+    CK(cudaMemsetAsync(t.bflag, 0, sizeof(unsigned int) * (size_t)n, s));
+    CK(fmm_launch_cells(t, n, bucket, s));
+    // bucket ids: exclusive scan of the bucket start flags into keep[] (free after k_cells)
+    CK(fmm_scan_exclusive(t.bflag, t.keep, n, c->totals + 1, t, s));
+    CK(fmm_launch_bucket_index(t, n, s));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = read_status(c, "fmm_build_tree");
+    if (st != FMM_OK) return st;
+    t.n = n;
+    t.n_cells = c->totals_h[0];
+    t.n_buckets = c->totals_h[1];
+    if (t.n_cells > t.cap_cells) return fail(FMM_ERR_CUDA, "internal: %lld cells exceed capacity", t.n_cells);
+    CK(fmm_launch_upward(t, n, bucket, c->ctr, s));
+    // keys, 8 x (histogram, 3-kernel scan, scatter), gather, radix tree + keep, scan, cells, scan,
+    // bucket index, bucket cells, upward, exact b_max
+    c->launches += 1 + 8 * 5 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 3;
+    c->have_tree = true;
+    c->theta_nodes = -1.0f;
+    return FMM_OK;
+}
+
+static fmm_status check_common(fmm_ctx* c, const double* pos, const float* mass, long long n)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!pos || !mass) return fail(FMM_ERR_ARG, "pos and mass must not be NULL");
+    if (n < 1 || n >= (1LL << 31)) return fail(FMM_ERR_ARG, "n must be in [1, 2^31), got %lld", n);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(FMM_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_build_tree(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
+                                     long long n, const fmm_params* p)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    const fmm_params* q = p ? p : &c->params;
+    st = check_params(q);
+    if (st != FMM_OK) return st;
+    c->have_solve = false;
+    return build_tree(c, pos, mass, active, n, q->bucket);
+}
+
+static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
+{
+    DevWalk& w = c->w;
+    long long cells = c->t.cap_cells;
+    long long need_front = cells;
+    long long need_cl = (long long)scale * 16 * n + 4096;
+    long long need_pp = (long long)scale * 8 * n + 4096;
+    long long need_pc = (long long)scale * 16 * n + 4096;
+    long long need_cc = (long long)scale * 16 * n + 4096;
+    long long need_scr = 8192LL * scale;
+    if (need_front > w.cap_front) {
+        for (int i = 0; i < 2; i++) {
+            CK(alloc(&w.f_cell[i], need_front));
+            CK(alloc(&w.f_cloff[i], need_front));
+            CK(alloc(&w.f_cllen[i], need_front));
+        }
+        CK(alloc(&w.f_ccoff, need_front));
+        CK(alloc(&w.f_cclen, need_front));
+        CK(alloc(&w.groups, need_front));
+        w.cap_front = need_front;
+        w.cap_groups = need_front;
+    }
+    if (need_cl > w.cap_cl) {
+        CK(alloc(&w.cl[0], need_cl));
+        CK(alloc(&w.cl[1], need_cl));
+        w.cap_cl = need_cl;
+    }
+    if (need_pp > w.cap_pp) {
+        CK(alloc(&w.pp, need_pp));
+        w.cap_pp = need_pp;
+    }
+    if (need_pc > w.cap_pc) {
+        CK(alloc(&w.pc, need_pc));
+        w.cap_pc = need_pc;
+    }
+    if (need_cc > w.cap_cc) {
+        CK(alloc(&w.cc, need_cc));
+        CK(alloc(&w.cc_sink, need_cc));
+        w.cap_cc = need_cc;
+    }
+    if (need_scr > w.cap_scratch) {
+        CK(alloc(&w.scratch, (long long)w.n_warps * 5 * need_scr));
+        w.cap_scratch = need_scr;
+    }
+    return FMM_OK;
+}
+
+static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int group)
+{
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    cudaStream_t s = c->stream;
+    WalkArgs a;
+    float e2 = (float)(2.0 * eps);
+    a.four_eps2 = e2 * e2;
+    a.eps2 = (float)(eps * eps);
+    a.bucket = bucket;
+    a.group = group;
+    int scale = 1;
+    for (int attempt = 0;; attempt++) {
+        fmm_status st = ensure_walk(c, n, scale);
+        if (st != FMM_OK) return st;
+        // reset the list counters; keep the build status bits
+        CK(cudaMemsetAsync(&c->ctr->n_front_next, 0, sizeof(DevCounters) - offsetof(DevCounters, n_front_next), s));
+        CK(cudaMemsetAsync(&c->ctr->status, 0, sizeof(unsigned int), s));
+        CK(fmm_launch_walk_seed(w, s));
+        c->launches += 1;
+        unsigned long long n_front = c->stats.n_active > 0 ? 1 : 0;
+        int parity = 0;
+        long long levels = 0;
+        bool overflow = false;
+        while (n_front > 0) {
+            CK(cudaMemsetAsync(&c->ctr->work_ctr, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(&c->ctr->n_front_next, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(&c->ctr->cl_next_len, 0, sizeof(unsigned long long), s));
+            a.level_parity = parity;
+            CK(fmm_launch_walk_level(t, w, c->ctr, n_front, a, s));
+            CK(fmm_launch_local_level(t, w, c->ctr, n_front, a, s));
+            c->launches += 2;
+            CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            levels++;
+            if (c->ctr_h->status & FMM_DEV_ERR_OVERFLOW) {
+                overflow = true;
+                break;
+            }
+            n_front = c->ctr_h->n_front_next;
+            parity ^= 1;
+            if (levels > 4096) return fail(FMM_ERR_STATE, "walk did not terminate");
+        }
+        if (!overflow) {
+            w.n_levels = levels;
+            w.n_groups = (long long)c->ctr_h->n_groups;
+            w.pp_len = (long long)c->ctr_h->pp_len;
+            w.pc_len = (long long)c->ctr_h->pc_len;
+            w.cc_len = (long long)c->ctr_h->cc_len;
+            c->stats.retries = attempt;
+            return FMM_OK;
+        }
+        if (attempt >= 6) return fail(FMM_ERR_OOM, "walk lists keep overflowing after %d grows", attempt);
+        scale *= 4;
+    }
+}
+
+static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
+                        double eps, double theta, float* acc, float* pot)
+{
+    fmm_params q = c->params;
+    q.eps = eps;
+    q.theta = theta;
+    fmm_status st = check_params(&q);
+    if (st != FMM_OK) return st;
+    if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
+    cudaStream_t s = c->stream;
+    c->have_solve = false;
+    memset(&c->stats, 0, sizeof c->stats);
+    c->launches = 0;
+    CK(cudaEventRecord(c->ev[0], s));
+    st = build_tree(c, pos, mass, active, n, q.bucket);
+    if (st != FMM_OK) return st;
+    c->stats.n_active = (long long)c->ctr_h->n_active;
+    CK(fmm_launch_nodes(c->t, theta, s));
+    c->launches += 1;
+    CK(cudaEventRecord(c->ev[1], s));
+    st = run_walk(c, n, eps, q.bucket, q.group);
+    if (st != FMM_OK) return st;
+    CK(cudaEventRecord(c->ev[2], s));
+    InteractArgs ia;
+    ia.eps2 = (float)(eps * eps);
+    ia.terms = q.terms;
+    ia.accumulate = q.accumulate;
+    if (c->w.n_groups > 0) {
+        CK(fmm_launch_pp(c->t, c->w, c->ctr, ia, s));
+        CK(cudaEventRecord(c->ev[3], s));
+        CK(fmm_launch_pc(c->t, c->w, c->ctr, ia, s));
+        CK(cudaEventRecord(c->ev[4], s));
+        CK(fmm_launch_l2p_out(c->t, c->w, c->ctr, ia, acc, pot, n, s));
+        c->launches += (q.terms & 2) ? 3 : 2;
+    } else {
+        CK(cudaEventRecord(c->ev[3], s));
+        CK(cudaEventRecord(c->ev[4], s));
+    }
+    CK(cudaEventRecord(c->ev[5], s));
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = read_status(c, "fmm_compute_forces");
+    if (st != FMM_OK) return st;
+    fmm_stats& S = c->stats;
+    S.n = n;
+    S.n_cells = c->t.n_cells;
+    S.n_buckets = c->t.n_buckets;
+    S.n_groups = c->w.n_groups;
+    S.n_levels = c->w.n_levels;
+    S.n_pp_pairs = (long long)c->ctr_h->n_pp_pairs;
+    S.n_pc_pairs = (long long)c->ctr_h->n_pc_pairs;
+    S.n_cc = (long long)c->ctr_h->n_cc;
+    S.n_cp = (long long)c->ctr_h->n_cp;
+    S.n_pp_entries = c->w.pp_len;
+    S.n_pc_entries = c->w.pc_len;
+    float ms;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    S.ms_tree = ms;
+    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+    S.ms_walk = ms;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    S.ms_pp = ms;
+    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
+    S.ms_pc = ms;
+    cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+    S.ms_l2p = ms;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]);
+    S.ms_total = ms;
+    S.paper_flops = 53.0 * S.n_pp_pairs + 215.0 * S.n_pc_pairs + 479.0 * S.n_cc + 213.0 * S.n_cp;
+    S.kernel_flops_pp = 19.0 * S.n_pp_pairs;
+    S.kernel_flops_pc = (double)FMM_FLOPS_PC * S.n_pc_pairs;
+    S.n_launches = c->launches;
+    c->have_solve = true;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_compute_forces(fmm_ctx* c, const double* pos, const float* mass,
+                                         const unsigned char* active, long long n, double eps, double theta,
+                                         float* acc, float* pot)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    return solve(c, pos, mass, active, n, eps, theta, acc, pot);
+}
+
+extern "C" fmm_status fmm_compute_forces_host(fmm_ctx* c, const double* pos, const float* mass,
+                                              const unsigned char* active, long long n, double eps, double theta,
+                                              float* acc, float* pot)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
+    cudaStream_t s = c->stream;
+    if (n > c->hcap) {
+        CK(alloc(&c->hpos, 3 * n));
+        CK(alloc(&c->hmass, n));
+        CK(alloc(&c->hacc, 3 * n));
+        CK(alloc(&c->hpot, n));
+        CK(alloc(&c->hact, n));
+        c->hcap = n;
+    }
+    CK(cudaMemcpyAsync(c->hpos, pos, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->hmass, mass, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s));
+    if (active) CK(cudaMemcpyAsync(c->hact, active, (size_t)n, cudaMemcpyHostToDevice, s));
+    if (active) {
+        // entries of inactive particles keep the caller's values
+        CK(cudaMemcpyAsync(c->hacc, acc, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
+        if (pot) CK(cudaMemcpyAsync(c->hpot, pot, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s));
+    }
+    st = solve(c, c->hpos, c->hmass, active ? c->hact : nullptr, n, eps, theta, c->hacc, pot ? c->hpot : nullptr);
+    if (st != FMM_OK) return st;
+    CK(cudaMemcpyAsync(acc, c->hacc, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToHost, s));
+    if (pot) CK(cudaMemcpyAsync(pot, c->hpot, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_kick_drift(fmm_ctx* c, double* pos, double* vel, const float* acc, unsigned char* rung,
+                                     unsigned char* active_next, long long n, double eps, double dt0, int max_rung,
+                                     int substep, int closing)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!pos || !vel || !acc || !rung || !active_next) return fail(FMM_ERR_ARG, "NULL array");
+    if (n < 1 || n >= (1LL << 31)) return fail(FMM_ERR_ARG, "n must be in [1, 2^31)");
+    if (!(eps > 0.0) || !(dt0 > 0.0)) return fail(FMM_ERR_ARG, "eps and dt0 must be > 0");
+    if (max_rung < 0 || max_rung > 30) return fail(FMM_ERR_ARG, "max_rung must be in [0, 30]");
+    if (substep < 0 || substep >= (1 << max_rung)) return fail(FMM_ERR_ARG, "substep out of range");
+    CK(cudaSetDevice(c->device));
+    CK(fmm_launch_kick_drift(pos, vel, acc, rung, active_next, n, eps, dt0, max_rung, substep, closing ? 1 : 0,
+                             c->ctr, c->stream));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_assign_rungs(fmm_ctx* c, const float* acc, unsigned char* rung, long long n, double eps,
+                                       double dt0, int max_rung)
+{
+    if (!c || !acc || !rung) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 1 || n >= (1LL << 31)) return fail(FMM_ERR_ARG, "n must be in [1, 2^31)");
+    if (!(eps > 0.0) || !(dt0 > 0.0)) return fail(FMM_ERR_ARG, "eps and dt0 must be > 0");
+    if (max_rung < 0 || max_rung > 30) return fail(FMM_ERR_ARG, "max_rung must be in [0, 30]");
+    CK(cudaSetDevice(c->device));
+    CK(fmm_launch_assign_rungs(acc, rung, n, eps, dt0, max_rung, c->stream));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_get_stats(const fmm_ctx* c, fmm_stats* out)
+{
+    if (!c || !out) return fail(FMM_ERR_ARG, "NULL argument");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = c->stats;
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------- introspection
+
+template <typename T>
+static cudaError_t d2h(T* dst, const T* src, long long n, cudaStream_t s)
+{
+    if (!dst || n <= 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, s);
+}
+
+extern "C" fmm_status fmm_tree_info(const fmm_ctx* c, long long* n_cells, long long* n_groups, long long* n_pp,
+                                    long long* n_pc, long long* n_local)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!c->have_tree) return fail(FMM_ERR_STATE, "no tree built yet");
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_cells) *n_cells = c->t.n_cells;
+    if (n_groups) *n_groups = c->have_solve ? c->w.n_groups : 0;
+    if (n_pp) *n_pp = c->have_solve ? c->w.pp_len : 0;
+    if (n_pc) *n_pc = c->have_solve ? c->w.pc_len : 0;
+    if (n_local) *n_local = c->have_solve ? c->w.cc_len : 0;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_order(const fmm_ctx* c, unsigned int* perm, unsigned long long* keys)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!c->have_tree) return fail(FMM_ERR_STATE, "no tree built yet");
+    CK(cudaSetDevice(c->device));
+    CK(d2h(perm, c->t.idx, c->t.n, c->stream));
+    CK(d2h(keys, c->t.key, c->t.n, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_cells(const fmm_ctx* c, int* first, int* count, int* parent, int* child, int* nact,
+                                       double* mass, double* com, double* lo, double* hi, double* bmax,
+                                       float* moments)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!c->have_tree) return fail(FMM_ERR_STATE, "no tree built yet");
+    CK(cudaSetDevice(c->device));
+    const DevTree& t = c->t;
+    long long nc = t.n_cells;
+    cudaStream_t s = c->stream;
+    CK(d2h(first, t.cfirst, nc, s));
+    CK(d2h(count, t.ccount, nc, s));
+    CK(d2h(parent, t.cparent, nc, s));
+    CK(d2h(child, t.cchild, 2 * nc, s));
+    CK(d2h(nact, t.cnact, nc, s));
+    CK(d2h(lo, t.clo, 3 * nc, s));
+    CK(d2h(hi, t.chi, 3 * nc, s));
+    CK(d2h(bmax, t.bmax, nc, s));
+    CK(d2h(moments, t.rec, (long long)FMM_NREC * nc, s));
+    std::vector<Com4> cm;
+    if (mass || com) {
+        cm.resize((size_t)nc);
+        CK(d2h(cm.data(), t.com, nc, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    for (long long i = 0; i < (long long)cm.size(); i++) {
+        if (mass) mass[i] = cm[i].w;
+        if (com) {
+            com[3 * i] = cm[i].x;
+            com[3 * i + 1] = cm[i].y;
+            com[3 * i + 2] = cm[i].z;
+        }
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_lists(const fmm_ctx* c, int kind, long long* n_entries, int* sink, int* src_first,
+                                       int* src_count, long long capacity)
+{
+    if (!c || !n_entries) return fail(FMM_ERR_ARG, "NULL argument");
+    if (kind < 0 || kind > 3) return fail(FMM_ERR_ARG, "kind must be 0..3");
+    if (!c->have_solve) return fail(FMM_ERR_STATE, "no solve yet");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    const DevTree& t = c->t;
+    const DevWalk& w = c->w;
+    long long nc = t.n_cells;
+    std::vector<int> cf((size_t)nc), cn((size_t)nc);
+    CK(d2h(cf.data(), t.cfirst, nc, s));
+    CK(d2h(cn.data(), t.ccount, nc, s));
+    std::vector<long long> out_sink, out_first, out_count;
+    auto push = [&](int sk, unsigned int e) {
+        if (e & FMM_PARTICLE_BIT) {
+            out_sink.push_back(sk);
+            out_first.push_back((int)(e & ~FMM_PARTICLE_BIT));
+            out_count.push_back(1);
+        } else {
+            out_sink.push_back(sk);
+            out_first.push_back(cf[e]);
+            out_count.push_back(cn[e]);
+        }
+    };
+    if (kind <= 1) {
+        std::vector<Group> g((size_t)w.n_groups);
+        CK(d2h(g.data(), w.groups, w.n_groups, s));
+        long long len = kind == 0 ? w.pp_len : w.pc_len;
+        std::vector<unsigned int> L((size_t)len);
+        CK(d2h(L.data(), kind == 0 ? w.pp : w.pc, len, s));
+        CK(cudaStreamSynchronize(s));
+        for (const Group& G : g) {
+            unsigned long long o = kind == 0 ? G.pp_off : G.pc_off;
+            int l = kind == 0 ? G.pp_len : G.pc_len;
+            for (int i = 0; i < l; i++) push(G.cell, L[o + i]);
+        }
+    } else {
+        std::vector<unsigned int> L((size_t)w.cc_len);
+        std::vector<int> sk((size_t)w.cc_len);
+        CK(d2h(L.data(), w.cc, w.cc_len, s));
+        CK(d2h(sk.data(), w.cc_sink, w.cc_len, s));
+        CK(cudaStreamSynchronize(s));
+        for (long long i = 0; i < w.cc_len; i++) {
+            unsigned int e = L[i];
+            bool pointlike = (e & FMM_PARTICLE_BIT) || cn[e] == 1;
+            if ((kind == 3) == pointlike) push(sk[i], e);
+        }
+    }
+    *n_entries = (long long)out_sink.size();
+    if (capacity < *n_entries) return FMM_OK;  // size query
+    for (long long i = 0; i < *n_entries; i++) {
+        if (sink) sink[i] = (int)out_sink[i];
+        if (src_first) src_first[i] = (int)out_first[i];
+        if (src_count) src_count[i] = (int)out_count[i];
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_locals(const fmm_ctx* c, int* group_cell, float* L, long long capacity)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!c->have_solve) return fail(FMM_ERR_STATE, "no solve yet");
+    if (capacity < c->w.n_groups) return fail(FMM_ERR_ARG, "capacity %lld < %lld groups", capacity, c->w.n_groups);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    std::vector<Group> g((size_t)c->w.n_groups);
+    CK(d2h(g.data(), c->w.groups, c->w.n_groups, s));
+    std::vector<float> Lall((size_t)c->t.n_cells * FMM_NL);
+    CK(d2h(Lall.data(), c->t.L, c->t.n_cells * FMM_NL, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < g.size(); i++) {
+        if (group_cell) group_cell[i] = g[i].cell;
+        if (L) memcpy(L + i * FMM_NL, &Lall[(size_t)g[i].cell * FMM_NL], FMM_NL * sizeof(float));
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_multi_index(int* local_idx, int* moment_idx)
+{
+    if (local_idx) memcpy(local_idx, fmm_multi_index_table, sizeof(fmm_multi_index_table));
+    if (moment_idx) memcpy(moment_idx, fmm_moment_index_table, sizeof(fmm_moment_index_table));
+    return FMM_OK;
+}

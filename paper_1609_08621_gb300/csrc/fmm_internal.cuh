@@ -1,0 +1,186 @@
+// Internal definitions shared by the CUDA translation units of the FMM library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fmm.h"
+
+#define FMM_FULL_MASK 0xffffffffu
+#define FMM_PARTICLE_BIT 0x80000000u  // checklist / list entry is a particle index
+
+// device status word bits
+#define FMM_DEV_ERR_ARG 1u        // invalid position or mass seen by a kernel
+#define FMM_DEV_ERR_OVERFLOW 2u   // a list or scratch capacity was exceeded (host grows and retries)
+#define FMM_DEV_ERR_TIMEOUT 4u    // a bounded wait gave up
+#define FMM_DEV_ERR_NUMERIC 8u    // non-finite output
+
+// Centre of mass (x, y, z) and mass (w) of a cell, double precision, one 32-byte load.
+struct __align__(32) Com4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ Com4 make_com4(double x, double y, double z, double w)
+{
+    Com4 r;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+    r.w = w;
+    return r;
+}
+
+// One tree cell as the walk reads it: 64 bytes, four aligned 16-byte loads.
+//   a = (centre of mass, single precision, and R_O = b_max / theta)
+//   b = (bounding box lo, single precision, and b_max)
+//   c = (bounding box hi, single precision, and unused)
+//   d = (child0, child1, first, count); child0 = -1 for a bucket
+struct __align__(16) WalkNode {
+    float4 a, b, c;
+    int4 d;
+};
+
+// A sink group after the walk.
+struct __align__(16) Group {
+    int cell;
+    int first;
+    int count;
+    int pad;
+    unsigned long long pp_off, pc_off;
+    int pp_len, pc_len;
+};
+
+// Device-side counters and status, one per context.
+struct DevCounters {
+    unsigned int status;
+    unsigned int pad0;
+    unsigned long long n_front_next;   // frontier size of the next walk level
+    unsigned long long n_groups;
+    unsigned long long cl_next_len;    // entries written to the next checklist buffer
+    unsigned long long pp_len, pc_len, cc_len;
+    unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
+    unsigned long long work_ctr;       // persistent-kernel work counter
+    unsigned long long n_active;
+};
+
+// Device buffers of a context.  Capacities are in elements.
+struct DevTree {
+    long long n = 0, cap_n = 0;
+    long long n_cells = 0, cap_cells = 0, n_buckets = 0;
+    // sorting
+    unsigned long long *key = nullptr, *key_alt = nullptr;
+    unsigned int *idx = nullptr, *idx_alt = nullptr;
+    // sorted particles
+    double *sx = nullptr, *sy = nullptr, *sz = nullptr;
+    float *sm = nullptr;
+    unsigned char *sact = nullptr;
+    float4 *posf = nullptr;  // single-precision position for the walk's decisions
+    float4 *off = nullptr;   // (x - com_bucket) in single precision, mass
+    int *bucket_of = nullptr;
+    float4 *accs = nullptr;  // accumulator in sorted order (ax, ay, az, pot)
+    // radix tree (nodes 0..n-2 internal, leaf p is node n-1+p)
+    int *ifirst = nullptr, *ilast = nullptr, *ileft = nullptr, *iright = nullptr;  // child node ids
+    int *nparent = nullptr;  // parent internal node of every node (2n-1)
+    unsigned int *keep = nullptr;  // 2n-1 flags, scanned to cell ids
+    unsigned int *bflag = nullptr; // n flags, scanned to bucket ids
+    // cells
+    int *cfirst = nullptr, *ccount = nullptr, *cparent = nullptr, *cchild = nullptr, *cnact = nullptr;
+    int *bucket_cell = nullptr;
+    unsigned int *arrive = nullptr;
+    Com4 *com = nullptr;      // centre of mass + mass
+    double *clo = nullptr, *chi = nullptr;  // 3 per cell
+    double *bmax = nullptr;
+    float *rec = nullptr;        // FMM_NREC per cell
+    WalkNode *node = nullptr;
+    float *L = nullptr;          // FMM_NL per cell (walked cells)
+    // scan scratch
+    unsigned int *scan_part = nullptr;
+    long long cap_scan_part = 0;
+    unsigned int *hist = nullptr;
+    long long cap_hist = 0;
+};
+
+struct DevWalk {
+    long long cap_front = 0, cap_cl = 0, cap_pp = 0, cap_pc = 0, cap_cc = 0, cap_groups = 0;
+    long long cap_scratch = 0;  // entries per list per warp
+    int n_warps = 0;
+    int *f_cell[2] = {nullptr, nullptr};
+    unsigned long long *f_cloff[2] = {nullptr, nullptr};
+    int *f_cllen[2] = {nullptr, nullptr};
+    unsigned long long *f_ccoff = nullptr;
+    int *f_cclen = nullptr;
+    unsigned int *cl[2] = {nullptr, nullptr};
+    unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
+    int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry, for export
+    Group *groups = nullptr;
+    unsigned int *scratch = nullptr;
+    // levels kept for export of the local lists
+    long long n_groups = 0, pp_len = 0, pc_len = 0, cc_len = 0, n_levels = 0;
+};
+
+// ---------------------------------------------------------------- launchers (host)
+
+// scan.cu / sort.cu
+cudaError_t fmm_scan_exclusive(const unsigned int* in, unsigned int* out, long long n, unsigned int* total_dev,
+                               DevTree& t, cudaStream_t s);
+cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s);
+cudaError_t fmm_sort_ensure(DevTree& t, long long n);
+
+// tree.cu
+cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
+                            cudaStream_t s);
+cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
+                              long long n, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_bucket_index(DevTree& t, long long n, cudaStream_t s);
+cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStream_t s);
+cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s);
+cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s);
+
+// walk.cu
+struct WalkArgs {
+    int level_parity;
+    int bucket, group;
+    float four_eps2;
+    float eps2;
+};
+cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
+                                  const WalkArgs& a, cudaStream_t s);
+cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
+                                   const WalkArgs& a, cudaStream_t s);
+cudaError_t fmm_launch_walk_seed(DevWalk& w, cudaStream_t s);
+int fmm_walk_warps(int device);
+
+// interact.cu
+struct InteractArgs {
+    float eps2;
+    int terms;
+    int accumulate;
+};
+cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
+cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
+cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,
+                               float* pot, long long n, cudaStream_t s);
+int fmm_interact_blocks(int device);
+
+// kdk.cu
+cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, unsigned char* rung,
+                                  unsigned char* active_next, long long n, double eps, double dt0, int max_rung,
+                                  int substep, int closing, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_assign_rungs(const float* acc, unsigned char* rung, long long n, double eps, double dt0,
+                                    int max_rung, cudaStream_t s);
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ unsigned int fmm_lanemask_lt()
+{
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int fmm_lane() { return threadIdx.x & 31; }
+
+template <typename T>
+__device__ __forceinline__ T fmm_ldcg(const T* p) { return __ldcg(p); }
+
+__host__ __device__ __forceinline__ long long fmm_ceil_div(long long a, long long b) { return (a + b - 1) / b; }

@@ -1,0 +1,97 @@
+// Individual time steps on rungs with the hierarchical kick-drift-kick leapfrog (Sec. 3.2).
+//
+// Particle i sits on rung r_i with step dt0 / 2^r_i (Sec. 3.2: time steps restricted to
+// 2^-l of the base step).  The base step is cut into 2^R substeps of h = dt0 / 2^R; a
+// particle is active at substep s when s is a multiple of 2^(R - r_i), i.e. where its
+// kicks line up with those of the coarser rungs (Fig. KDK).  At substep s, for active
+// particles: closing half kick with the force just computed, rung reassignment from
+// Delta T_i = 0.2 sqrt(eps / |a_i|) (Sec. 3.2), opening half kick of the new step; then
+// every particle drifts by h.  All of it in FP64.
+//
+// Rung choice is an integer decided by floating point, made reproducible by avoiding
+// log2: r = the smallest r in [0, R] with dt0 <= Delta T * 2^r (scaling by 2^r is exact),
+// with |a| = sqrt((ax^2 + ay^2) + az^2) and Delta T computed step by step without fused
+// operations.  A particle may move to a coarser rung only at a substep where that rung
+// is synchronised.
+#include <math.h>
+
+#include "fmm_internal.cuh"
+
+__device__ __forceinline__ int target_rung(float ax, float ay, float az, double eps, double dt0, int R)
+{
+    double x = ax, y = ay, z = az;
+    double a2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+    double am = __dsqrt_rn(a2);
+    if (!(am > 0.0)) return 0;
+    double dt = __dmul_rn(0.2, __dsqrt_rn(__ddiv_rn(eps, am)));
+    int r = 0;
+    while (r < R && dt0 > ldexp(dt, r)) r++;
+    return r;
+}
+
+__global__ void k_assign_rungs(const float* __restrict__ acc, unsigned char* __restrict__ rung, long long n,
+                               double eps, double dt0, int R)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rung[i] = (unsigned char)target_rung(acc[i], acc[n + i], acc[2 * n + i], eps, dt0, R);
+}
+
+__global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel, const float* __restrict__ acc,
+                             unsigned char* __restrict__ rung, unsigned char* __restrict__ active_next, long long n,
+                             double eps, double dt0, int R, long long s, int closing, unsigned int* __restrict__ status)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = rung[i];
+    double vx = vel[i], vy = vel[n + i], vz = vel[2 * n + i];
+    if ((s & ((1LL << (R - r)) - 1)) == 0) {
+        float fx = acc[i], fy = acc[n + i], fz = acc[2 * n + i];
+        double ax = fx, ay = fy, az = fz;
+        if (closing) {
+            double hk = ldexp(dt0, -r - 1);
+            vx += ax * hk;
+            vy += ay * hk;
+            vz += az * hk;
+        }
+        int rt = target_rung(fx, fy, fz, eps, dt0, R);
+        int rn = rt;
+        if (rt < r) {
+            rn = rt;
+            while (rn < r && (s & ((1LL << (R - rn)) - 1)) != 0) rn++;
+        }
+        r = rn;
+        rung[i] = (unsigned char)r;
+        double hk = ldexp(dt0, -r - 1);
+        vx += ax * hk;
+        vy += ay * hk;
+        vz += az * hk;
+        vel[i] = vx;
+        vel[n + i] = vy;
+        vel[2 * n + i] = vz;
+    }
+    double h = ldexp(dt0, -R);
+    double x = pos[i] + vx * h, y = pos[n + i] + vy * h, z = pos[2 * n + i] + vz * h;
+    if (!(x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0)) atomicOr(status, FMM_DEV_ERR_ARG);
+    pos[i] = x;
+    pos[n + i] = y;
+    pos[2 * n + i] = z;
+    long long s1 = s + 1;
+    active_next[i] = ((s1 & ((1LL << (R - r)) - 1)) == 0) ? 1 : 0;
+}
+
+cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, unsigned char* rung,
+                                  unsigned char* active_next, long long n, double eps, double dt0, int max_rung,
+                                  int substep, int closing, DevCounters* ctr, cudaStream_t s)
+{
+    k_kick_drift<<<(unsigned)fmm_ceil_div(n, 256), 256, 0, s>>>(pos, vel, acc, rung, active_next, n, eps, dt0,
+                                                                max_rung, substep, closing, &ctr->status);
+    return cudaGetLastError();
+}
+
+cudaError_t fmm_launch_assign_rungs(const float* acc, unsigned char* rung, long long n, double eps, double dt0,
+                                    int max_rung, cudaStream_t s)
+{
+    k_assign_rungs<<<(unsigned)fmm_ceil_div(n, 256), 256, 0, s>>>(acc, rung, n, eps, dt0, max_rung);
+    return cudaGetLastError();
+}

@@ -1,0 +1,450 @@
+// Tree build: Morton keys, sorted particle arrays, binary radix tree, bucket cells and the
+// upward pass (Sec. 3.1).
+//
+// Geometry.  Level l of the tree bisects axis l mod 3 (x, y, z) of the unit box; on a cube
+// this is the paper's longest-axis equal-volume bisection with ties broken x, y, z.  The
+// tree is the binary radix tree of the sorted 63-bit keys (Karras 2012 construction):
+// every internal node splits its range at the highest key bit in which its first and last
+// keys differ (runs of identical keys split on the highest differing bit of the
+// positions), so empty children never exist and one-child chains are collapsed.  Nodes
+// holding <= b particles whose parent holds more become the buckets (Sec. 3.1, leaf cells
+// of up to b particles); nodes below them are dropped.
+//
+// Upward pass.  Per cell: mass and centre of mass (FP64), bounding box (FP64),
+// b_max = distance from the centre of mass to the farthest particle (Sec. 3.1), exact in
+// FP64, and moments M_n = sum m y^n to order 4 about the centre of mass (FP32; Sec. 3.1
+// "4th order moments").  Buckets take moments from FP64 offsets rounded to FP32; parents
+// shift their children's moments (M2M).  A thread per bucket walks up with an arrival
+// counter per cell; the second child to arrive computes the parent.
+#include <math.h>
+
+#include "expansions.cuh"
+#include "fmm_internal.cuh"
+
+#define TB 256
+
+// ---------------------------------------------------------------- keys
+
+__device__ __forceinline__ unsigned long long spread3(unsigned int v)
+{
+    // place the 21 bits of v at every third bit position
+    unsigned long long x = v & 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ unsigned int quantise21(double v)
+{
+    double s = v * 2097152.0;  // 2^21, exact
+    if (!(s >= 0.0)) s = 0.0;
+    unsigned int u = (unsigned int)s;
+    return u > 2097151u ? 2097151u : u;
+}
+
+__global__ void k_keys(const double* __restrict__ pos, const float* __restrict__ mass, long long n,
+                       unsigned long long* __restrict__ key, unsigned int* __restrict__ idx,
+                       unsigned int* __restrict__ status)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
+    float m = mass[i];
+    bool ok = (x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0 && m > 0.0f && isfinite(m));
+    if (!ok) atomicOr(status, FMM_DEV_ERR_ARG);
+    // axis x owns the highest bit of each level triple: key bit 62 - l for level l
+    key[i] = (spread3(quantise21(x)) << 2) | (spread3(quantise21(y)) << 1) | spread3(quantise21(z));
+    idx[i] = (unsigned int)i;
+}
+
+cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
+                            cudaStream_t s)
+{
+    k_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, mass, n, t.key, t.idx, &ctr->status);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather(const double* __restrict__ pos, const float* __restrict__ mass,
+                         const unsigned char* __restrict__ active, long long n, const unsigned int* __restrict__ idx,
+                         double* __restrict__ sx, double* __restrict__ sy, double* __restrict__ sz,
+                         float* __restrict__ sm, unsigned char* __restrict__ sact, float4* __restrict__ posf,
+                         unsigned long long* __restrict__ n_active)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = false;
+    if (i < n) {
+        unsigned int p = idx[i];
+        double x = pos[p], y = pos[n + p], z = pos[2 * n + p];
+        sx[i] = x;
+        sy[i] = y;
+        sz[i] = z;
+        float m = mass[p];
+        sm[i] = m;
+        act = active ? (active[p] != 0) : true;
+        sact[i] = act ? 1 : 0;
+        posf[i] = make_float4(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z), m);
+    }
+    unsigned int b = __ballot_sync(FMM_FULL_MASK, act);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, (unsigned long long)__popc(b));
+}
+
+cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
+                              long long n, DevCounters* ctr, cudaStream_t s)
+{
+    k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, mass, active, n, t.idx, t.sx, t.sy, t.sz, t.sm,
+                                                           t.sact, t.posf, &ctr->n_active);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix tree
+
+// length of the common prefix of the augmented keys (key, position); -1 outside [0, n)
+__device__ __forceinline__ int delta(const unsigned long long* __restrict__ k, int n, int i, long long j)
+{
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = k[i], b = k[j];
+    if (a != b) return __clzll(a ^ b);
+    return 64 + __clz((unsigned int)(i ^ (int)j));
+}
+
+__global__ void k_radix_tree(const unsigned long long* __restrict__ key, int n, int* __restrict__ ifirst,
+                             int* __restrict__ ilast, int* __restrict__ ileft, int* __restrict__ iright,
+                             int* __restrict__ nparent)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(key, n, i, i + 1) - delta(key, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = delta(key, n, i, i - d);
+    long long lmax = 2;
+    while (delta(key, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    long long l = 0;
+    for (long long t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(key, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = (int)(i + l * d);
+    int dnode = delta(key, n, i, j);
+    long long s = 0;
+    for (long long div = 2;; div <<= 1) {
+        long long t = (l + div - 1) / div;
+        if (delta(key, n, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+    }
+    int gamma = (int)(i + s * d + (d < 0 ? -1 : 0));
+    int first = min(i, j), last = max(i, j);
+    // node ids: internal g -> g, leaf p -> n - 1 + p
+    int left = (first == gamma) ? (n - 1 + gamma) : gamma;
+    int right = (last == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
+    ifirst[i] = first;
+    ilast[i] = last;
+    ileft[i] = left;
+    iright[i] = right;
+    nparent[left] = i;
+    nparent[right] = i;
+    if (i == 0) nparent[0] = -1;
+}
+
+__device__ __forceinline__ int node_count(const int* ifirst, const int* ilast, int n, int x)
+{
+    return x < n - 1 ? ilast[x] - ifirst[x] + 1 : 1;
+}
+
+__global__ void k_keep(const int* __restrict__ ifirst, const int* __restrict__ ilast, const int* __restrict__ nparent,
+                       int n, int bucket, unsigned int* __restrict__ keep)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= 2 * n - 1) return;
+    unsigned int k;
+    if (n == 1) {
+        k = 1;
+    } else {
+        int p = nparent[x];
+        k = (p < 0) ? 1u : (node_count(ifirst, ilast, n, p) > bucket ? 1u : 0u);
+    }
+    keep[x] = k;
+}
+
+// keep[] has been turned into exclusive cell ids in place; kept marks whether node x is kept
+__global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ ilast, const int* __restrict__ ileft,
+                        const int* __restrict__ iright, const int* __restrict__ nparent,
+                        const unsigned int* __restrict__ cid, int n, int bucket, int* __restrict__ cfirst,
+                        int* __restrict__ ccount, int* __restrict__ cparent, int* __restrict__ cchild,
+                        unsigned int* __restrict__ bflag)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= 2 * n - 1) return;
+    bool kept;
+    if (n == 1) {
+        kept = true;
+    } else {
+        int p = nparent[x];
+        kept = (p < 0) || node_count(ifirst, ilast, n, p) > bucket;
+    }
+    if (!kept) return;
+    int c = (int)cid[x];
+    int first = x < n - 1 ? ifirst[x] : x - (n - 1);
+    int count = node_count(ifirst, ilast, n, x);
+    cfirst[c] = first;
+    ccount[c] = count;
+    int p = n == 1 ? -1 : nparent[x];
+    cparent[c] = p < 0 ? -1 : (int)cid[p];
+    if (count > bucket) {
+        cchild[2 * c] = (int)cid[ileft[x]];
+        cchild[2 * c + 1] = (int)cid[iright[x]];
+    } else {
+        cchild[2 * c] = -1;
+        cchild[2 * c + 1] = -1;
+        bflag[first] = 1u;
+    }
+}
+
+__global__ void k_bucket_index(const unsigned int* __restrict__ bscan, const unsigned int* __restrict__ bflag_raw,
+                               long long n, int* __restrict__ bucket_of)
+{
+    // bscan is the exclusive scan of the start flags; bucket id of particle i is the
+    // number of bucket starts at or before i, minus one
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bucket_of[i] = (int)(bscan[i] + bflag_raw[i]) - 1;
+}
+
+__global__ void k_bucket_cells(const int* __restrict__ cfirst, const int* __restrict__ cchild, int ncell,
+                               const int* __restrict__ bucket_of, int* __restrict__ bucket_cell)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    if (cchild[2 * c] < 0) bucket_cell[bucket_of[cfirst[c]]] = c;
+}
+
+cudaError_t fmm_launch_bucket_index(DevTree& t, long long n, cudaStream_t s)
+{
+    k_bucket_index<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(t.keep, t.bflag, n, t.bucket_of);
+    return cudaGetLastError();
+}
+
+cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStream_t s)
+{
+    int ni = (int)n;
+    if (ni > 1)
+        k_radix_tree<<<(unsigned)fmm_ceil_div(ni - 1, TB), TB, 0, s>>>(t.key, ni, t.ifirst, t.ilast, t.ileft,
+                                                                       t.iright, t.nparent);
+    k_keep<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.nparent, ni, bucket, t.keep);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- upward pass
+
+__device__ __forceinline__ Com4 ldcg_d4(const Com4* p)
+{
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_com4(a.x, a.y, b.x, b.y);
+}
+
+__device__ void write_record(float* __restrict__ rec, const float* M)
+{
+    float R[FMM_NREC];
+#pragma unroll
+    for (int i = 0; i < FMM_NMOM; i++) R[i] = M[i];
+    fmm_moment_traces(R);
+    float4* dst = reinterpret_cast<float4*>(rec);
+#pragma unroll
+    for (int i = 0; i < FMM_NREC / 4; i++) dst[i] = make_float4(R[4 * i], R[4 * i + 1], R[4 * i + 2], R[4 * i + 3]);
+}
+
+__device__ __forceinline__ double dist2_ordered(double dx, double dy, double dz)
+{
+    // ((dx*dx + dy*dy) + dz*dz), correctly rounded step by step, no fused multiply-add
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ bucket_cell,
+                                                const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                                                const int* __restrict__ cparent, const int* __restrict__ cchild,
+                                                const double* __restrict__ sx, const double* __restrict__ sy,
+                                                const double* __restrict__ sz, const float* __restrict__ sm,
+                                                const unsigned char* __restrict__ sact, Com4* com, double* clo,
+                                                double* chi, double* bmax, int* cnact, float* rec,
+                                                float4* __restrict__ off, unsigned int* arrive)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    int c = bucket_cell[b];
+    int f = cfirst[c], cnt = ccount[c];
+    double M = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int na = 0;
+    for (int j = f; j < f + cnt; j++) {
+        double m = (double)sm[j], x = sx[j], y = sy[j], z = sz[j];
+        M += m;
+        mx += m * x;
+        my += m * y;
+        mz += m * z;
+        lo[0] = fmin(lo[0], x);
+        hi[0] = fmax(hi[0], x);
+        lo[1] = fmin(lo[1], y);
+        hi[1] = fmax(hi[1], y);
+        lo[2] = fmin(lo[2], z);
+        hi[2] = fmax(hi[2], z);
+        na += sact[j] ? 1 : 0;
+    }
+    double cx = mx / M, cy = my / M, cz = mz / M;
+    double b2 = 0.0;
+    float Mo[FMM_NMOM];
+#pragma unroll
+    for (int i = 0; i < FMM_NMOM; i++) Mo[i] = 0.0f;
+    for (int j = f; j < f + cnt; j++) {
+        double dx = sx[j] - cx, dy = sy[j] - cy, dz = sz[j] - cz;
+        b2 = fmax(b2, dist2_ordered(dx, dy, dz));
+        float m = sm[j];
+        float fx = __double2float_rn(dx), fy = __double2float_rn(dy), fz = __double2float_rn(dz);
+        fmm_p2m_acc(m, fx, fy, fz, Mo);
+        off[j] = make_float4(fx, fy, fz, m);
+    }
+    com[c] = make_com4(cx, cy, cz, M);
+    for (int a = 0; a < 3; a++) {
+        clo[3 * c + a] = lo[a];
+        chi[3 * c + a] = hi[a];
+    }
+    bmax[c] = __dsqrt_rn(b2);
+    cnact[c] = na;
+    write_record(rec + (long long)c * FMM_NREC, Mo);
+    // climb: the second child to arrive at a parent computes it
+    int p = cparent[c];
+    while (p >= 0) {
+        __threadfence();
+        unsigned int old = atomicAdd(&arrive[p], 1u);
+        if (old == 0u) return;
+        __threadfence();
+        int c0 = cchild[2 * p], c1 = cchild[2 * p + 1];
+        Com4 a0 = ldcg_d4(&com[c0]), a1 = ldcg_d4(&com[c1]);
+        double Mp = a0.w + a1.w;
+        double px = (a0.w * a0.x + a1.w * a1.x) / Mp;
+        double py = (a0.w * a0.y + a1.w * a1.y) / Mp;
+        double pz = (a0.w * a0.z + a1.w * a1.z) / Mp;
+        float Mq[FMM_NMOM];
+#pragma unroll
+        for (int i = 0; i < FMM_NMOM; i++) Mq[i] = 0.0f;
+        double bound = 0.0;
+        for (int h = 0; h < 2; h++) {
+            int ch = h ? c1 : c0;
+            Com4 ac = h ? a1 : a0;
+            float Mc[FMM_NMOM];
+            const float* src = rec + (long long)ch * FMM_NREC;
+#pragma unroll
+            for (int i = 0; i < FMM_NMOM; i++) Mc[i] = __ldcg(src + i);
+            double tx = ac.x - px, ty = ac.y - py, tz = ac.z - pz;
+            fmm_m2m_acc(Mc, __double2float_rn(tx), __double2float_rn(ty), __double2float_rn(tz), Mq);
+            bound = fmax(bound, sqrt(tx * tx + ty * ty + tz * tz) + __ldcg(&bmax[ch]));
+        }
+        com[p] = make_com4(px, py, pz, Mp);
+        for (int a = 0; a < 3; a++) {
+            clo[3 * p + a] = fmin(__ldcg(&clo[3 * c0 + a]), __ldcg(&clo[3 * c1 + a]));
+            chi[3 * p + a] = fmax(__ldcg(&chi[3 * c0 + a]), __ldcg(&chi[3 * c1 + a]));
+        }
+        bmax[p] = bound;  // upper bound; replaced by the exact value in k_bmax_exact
+        cnact[p] = __ldcg(&cnact[c0]) + __ldcg(&cnact[c1]);
+        write_record(rec + (long long)p * FMM_NREC, Mq);
+        p = cparent[p];
+    }
+}
+
+// Exact b_max of every internal cell: the farthest particle from the centre of mass.
+// A bucket can hold it only if |com_b - com| + b_max(b) reaches the largest |com_b - com|
+// (a lower bound of the answer, since a bucket's centre of mass lies in the convex hull
+// of its particles); only those buckets are scanned particle by particle.
+__global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __restrict__ cfirst,
+                                                    const int* __restrict__ ccount, const int* __restrict__ cchild,
+                                                    const int* __restrict__ bucket_of,
+                                                    const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                                    const double* __restrict__ sx, const double* __restrict__ sy,
+                                                    const double* __restrict__ sz, double* __restrict__ bmax)
+{
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int c = wid; c < ncell; c += nw) {
+        if (cchild[2 * c] < 0) continue;  // buckets are exact already
+        const Com4 cc = com[c];
+        const int f = cfirst[c], cnt = ccount[c];
+        const int b0 = bucket_of[f], b1 = bucket_of[f + cnt - 1];
+        double lb2 = 0.0;
+        for (int b = b0 + lane; b <= b1; b += 32) {
+            Com4 cb = com[bucket_cell[b]];
+            lb2 = fmax(lb2, dist2_ordered(cb.x - cc.x, cb.y - cc.y, cb.z - cc.z));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lb2 = fmax(lb2, __shfl_xor_sync(FMM_FULL_MASK, lb2, o));
+        const double lb = sqrt(lb2) * (1.0 - 1e-12);
+        double best = 0.0;
+        for (int b = b0 + lane; b <= b1; b += 32) {
+            int bc = bucket_cell[b];
+            Com4 cb = com[bc];
+            double d = sqrt(dist2_ordered(cb.x - cc.x, cb.y - cc.y, cb.z - cc.z));
+            if (d + bmax[bc] < lb) continue;
+            int pf = cfirst[bc], pn = ccount[bc];
+            for (int j = pf; j < pf + pn; j++) best = fmax(best, dist2_ordered(sx[j] - cc.x, sy[j] - cc.y, sz[j] - cc.z));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
+        if (lane == 0) bmax[c] = __dsqrt_rn(best);
+    }
+}
+
+cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s)
+{
+    int ni = (int)n;
+    k_cells<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.ileft, t.iright, t.nparent,
+                                                                  t.keep, ni, bucket, t.cfirst, t.ccount, t.cparent,
+                                                                  t.cchild, t.bflag);
+    return cudaGetLastError();
+}
+
+cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s)
+{
+    (void)bucket;
+    (void)ctr;
+    int nc = (int)t.n_cells, nb = (int)t.n_buckets;
+    k_bucket_cells<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.cfirst, t.cchild, nc, t.bucket_of, t.bucket_cell);
+    cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)nc, s);
+    k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
+                                                              t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact, t.com, t.clo,
+                                                              t.chi, t.bmax, t.cnact, t.rec, t.off, t.arrive);
+    int blocks = (int)fmm_ceil_div((long long)nc * 32, 128);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
+    k_bmax_exact<<<blocks, 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.bucket_of, t.bucket_cell, t.com, t.sx,
+                                        t.sy, t.sz, t.bmax);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- walk nodes (depend on theta)
+
+__global__ void k_nodes(int ncell, float theta, const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                        const int* __restrict__ cchild, const Com4* __restrict__ com, const double* __restrict__ clo,
+                        const double* __restrict__ chi, const double* __restrict__ bmax, WalkNode* __restrict__ node)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    Com4 cm = com[c];
+    float bm = __double2float_rn(bmax[c]);
+    int cnt = ccount[c];
+    float ro = (cnt == 1) ? 0.0f : __fdiv_rn(bm, theta);
+    WalkNode w;
+    w.a = make_float4(__double2float_rn(cm.x), __double2float_rn(cm.y), __double2float_rn(cm.z), ro);
+    w.b = make_float4(__double2float_rn(clo[3 * c]), __double2float_rn(clo[3 * c + 1]),
+                      __double2float_rn(clo[3 * c + 2]), bm);
+    w.c = make_float4(__double2float_rn(chi[3 * c]), __double2float_rn(chi[3 * c + 1]),
+                      __double2float_rn(chi[3 * c + 2]), 0.0f);
+    w.d = make_int4(cchild[2 * c], cchild[2 * c + 1], cfirst[c], cnt);
+    node[c] = w;
+}
+
+cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s)
+{
+    int nc = (int)t.n_cells;
+    k_nodes<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(nc, (float)theta, t.cfirst, t.ccount, t.cchild, t.com,
+                                                          t.clo, t.chi, t.bmax, t.node);
+    return cudaGetLastError();
+}

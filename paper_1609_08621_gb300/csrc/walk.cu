@@ -1,0 +1,371 @@
+// Checklist walk and local expansions (Sec. 3.1).
+//
+// Sink cells are walked top-down, one tree level per launch.  A warp owns one sink cell k
+// and its checklist: the sources its parent left on the checklist ("remain on the
+// checklist for further consideration by the children of the sink cell") plus, for the
+// root, the root itself.  Each lane takes one entry, evaluates the opening criterion and
+// the warp appends the entry to one of five places with ballot/popc ranks:
+//   accept  -> k's local-expansion list (CC for a cell, CP for a particle)
+//   defer   -> the checklist handed to k's children
+//   PC, PP  -> the group's interaction lists (k a group: <= g particles)
+//   open    -> its two children, or for a bucket its particles with R_O = 0, are
+//              appended to k's own queue and examined in turn.
+// The criterion (single precision, fixed operation order, no fused multiply-add):
+//   d = |com_k - com_s|, R_O = b_max / theta (0 for a particle or a one-particle cell)
+//   accept if d > 1.5 R_O(k) + R_O(s) and the bounding boxes are >= 2 eps apart
+//   k not a group: defer if s is point-like or R_O(s) <= R_O(k), else open
+//   k a group:     PP if s is point-like; PC if d > R_O(s) + b_max(k); PP if s is a
+//                  bucket; else open.
+// Outputs are staged in per-warp scratch and copied to contiguous per-cell ranges, so each
+// cell's lists are in a deterministic order whatever the scheduling.
+//
+// The local expansion of a walked cell is L_k = L2L(L_parent) + sum of M2L (CC) and P2L
+// (CP) terms, computed by a second kernel per level after the walk kernel of that level.
+#include "expansions.cuh"
+#include "fmm_internal.cuh"
+
+#define WALK_WPB 4
+#define WALK_THREADS (WALK_WPB * 32)
+
+enum { OUT_NONE = 0, OUT_ACCEPT = 1, OUT_DEFER = 2, OUT_PC = 3, OUT_PP = 4, OUT_OPEN = 5 };
+
+__device__ __forceinline__ float d2_ordered(float dx, float dy, float dz)
+{
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ float gap_axis(float lo_s, float hi_s, float lo_k, float hi_k)
+{
+    float g1 = __fsub_rn(lo_s, hi_k), g2 = __fsub_rn(lo_k, hi_s);
+    float g = g1 > g2 ? g1 : g2;
+    return g > 0.0f ? g : 0.0f;
+}
+
+__global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
+    const WalkNode* __restrict__ node, const float4* __restrict__ posf, const int* __restrict__ cnact,
+    const int* __restrict__ f_cell, const unsigned long long* __restrict__ f_cloff, const int* __restrict__ f_cllen,
+    unsigned long long n_front, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
+    unsigned long long* __restrict__ f_cloff_next, int* __restrict__ f_cllen_next, long long cap_front,
+    unsigned int* __restrict__ cl_next, long long cap_cl, unsigned long long* __restrict__ f_ccoff,
+    int* __restrict__ f_cclen, unsigned int* __restrict__ pp, long long cap_pp, unsigned int* __restrict__ pc,
+    long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
+    Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
+    DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    unsigned int* Q = scratch + gw * 5 * cap_scr;
+    unsigned int* D = Q + cap_scr;
+    unsigned int* A = Q + 2 * cap_scr;
+    unsigned int* P = Q + 3 * cap_scr;
+    unsigned int* C = Q + 4 * cap_scr;
+    const unsigned int lt = fmm_lanemask_lt();
+
+    for (;;) {
+        unsigned long long fi = 0;
+        if (lane == 0) fi = atomicAdd(&ctr->work_ctr, 1ull);
+        fi = __shfl_sync(FMM_FULL_MASK, fi, 0);
+        if (fi >= n_front) break;
+        const int k = f_cell[fi];
+        const WalkNode K = node[k];
+        const bool kg = K.d.w <= group;
+        const float rk = K.a.w, bk = K.b.w;
+        const unsigned long long cl0 = f_cloff[fi];
+        const long long ncl = f_cllen[fi];
+        long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
+        bool overflow = false;
+        for (long long base = 0; base < ncl + nq; base += 32) {
+            const long long vi = base + lane;
+            const bool valid = vi < ncl + nq;
+            unsigned int e = 0;
+            if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
+            int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1;
+            bool sleaf = false;
+            if (valid) {
+                float cx, cy, cz, ro, lox, loy, loz, hix, hiy, hiz;
+                bool pointlike;
+                if (e & FMM_PARTICLE_BIT) {
+                    float4 p = posf[e & ~FMM_PARTICLE_BIT];
+                    cx = lox = hix = p.x;
+                    cy = loy = hiy = p.y;
+                    cz = loz = hiz = p.z;
+                    ro = 0.0f;
+                    pointlike = true;
+                } else {
+                    const WalkNode S = node[e];
+                    cx = S.a.x; cy = S.a.y; cz = S.a.z; ro = S.a.w;
+                    lox = S.b.x; loy = S.b.y; loz = S.b.z;
+                    hix = S.c.x; hiy = S.c.y; hiz = S.c.z;
+                    pointlike = S.d.w == 1;
+                    sleaf = S.d.w <= bucket;
+                    c0 = S.d.x;
+                    c1 = S.d.y;
+                    sfirst = S.d.z;
+                    nadd = sleaf ? S.d.w : 2;
+                }
+                const float d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
+                const float thr = __fadd_rn(__fmul_rn(1.5f, rk), ro);
+                const float gx = gap_axis(lox, hix, K.b.x, K.c.x);
+                const float gy = gap_axis(loy, hiy, K.b.y, K.c.y);
+                const float gz = gap_axis(loz, hiz, K.b.z, K.c.z);
+                const float gap2 = d2_ordered(gx, gy, gz);
+                if (d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2) {
+                    out = OUT_ACCEPT;
+                } else if (!kg) {
+                    out = (pointlike || ro <= rk) ? OUT_DEFER : OUT_OPEN;
+                } else if (pointlike) {
+                    out = OUT_PP;
+                } else {
+                    const float u = __fadd_rn(ro, bk);
+                    if (d2 > __fmul_rn(u, u)) out = OUT_PC;
+                    else out = sleaf ? OUT_PP : OUT_OPEN;
+                }
+                if (out != OUT_OPEN) nadd = 0;
+            }
+            const unsigned int mA = __ballot_sync(FMM_FULL_MASK, out == OUT_ACCEPT);
+            const unsigned int mD = __ballot_sync(FMM_FULL_MASK, out == OUT_DEFER);
+            const unsigned int mC = __ballot_sync(FMM_FULL_MASK, out == OUT_PC);
+            const unsigned int mP = __ballot_sync(FMM_FULL_MASK, out == OUT_PP);
+            int incl = nadd;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int tot = __shfl_sync(FMM_FULL_MASK, incl, 31);
+            if (na + __popc(mA) > cap_scr || nd + __popc(mD) > cap_scr || npc + __popc(mC) > cap_scr ||
+                npp + __popc(mP) > cap_scr || nq + tot > cap_scr) {
+                overflow = true;
+                break;
+            }
+            if (out == OUT_ACCEPT) A[na + __popc(mA & lt)] = e;
+            if (out == OUT_DEFER) D[nd + __popc(mD & lt)] = e;
+            if (out == OUT_PC) C[npc + __popc(mC & lt)] = e;
+            if (out == OUT_PP) P[npp + __popc(mP & lt)] = e;
+            if (out == OUT_OPEN) {
+                long long pos = nq + incl - nadd;
+                if (sleaf) {
+                    for (int j = 0; j < nadd; j++) Q[pos + j] = (unsigned int)(sfirst + j) | FMM_PARTICLE_BIT;
+                } else {
+                    Q[pos] = (unsigned int)c0;
+                    Q[pos + 1] = (unsigned int)c1;
+                }
+            }
+            na += __popc(mA);
+            nd += __popc(mD);
+            npc += __popc(mC);
+            npp += __popc(mP);
+            nq += tot;
+            __syncwarp();
+        }
+        if (overflow) {
+            if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+            continue;
+        }
+        __syncwarp();
+        // local-expansion entries of this sink
+        unsigned long long off = 0;
+        if (lane == 0) off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
+        off = __shfl_sync(FMM_FULL_MASK, off, 0);
+        if ((long long)(off + na) > cap_cc) {
+            if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+            continue;
+        }
+        for (long long i = lane; i < na; i += 32) {
+            cc[off + i] = A[i];
+            cc_sink[off + i] = k;
+        }
+        if (lane == 0) {
+            f_ccoff[fi] = off;
+            f_cclen[fi] = (int)na;
+        }
+        if (kg) {
+            unsigned long long po = 0, co = 0, gi = 0;
+            if (lane == 0) {
+                po = atomicAdd(&ctr->pp_len, (unsigned long long)npp);
+                co = atomicAdd(&ctr->pc_len, (unsigned long long)npc);
+                gi = atomicAdd(&ctr->n_groups, 1ull);
+            }
+            po = __shfl_sync(FMM_FULL_MASK, po, 0);
+            co = __shfl_sync(FMM_FULL_MASK, co, 0);
+            gi = __shfl_sync(FMM_FULL_MASK, gi, 0);
+            if ((long long)(po + npp) > cap_pp || (long long)(co + npc) > cap_pc || (long long)gi >= cap_groups) {
+                if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                continue;
+            }
+            for (long long i = lane; i < npp; i += 32) pp[po + i] = P[i];
+            for (long long i = lane; i < npc; i += 32) pc[co + i] = C[i];
+            if (lane == 0) {
+                Group g;
+                g.cell = k;
+                g.first = K.d.z;
+                g.count = K.d.w;
+                g.pad = 0;
+                g.pp_off = po;
+                g.pc_off = co;
+                g.pp_len = (int)npp;
+                g.pc_len = (int)npc;
+                groups[gi] = g;
+            }
+        } else {
+            unsigned long long doff = 0;
+            if (lane == 0) doff = atomicAdd(&ctr->cl_next_len, (unsigned long long)nd);
+            doff = __shfl_sync(FMM_FULL_MASK, doff, 0);
+            if ((long long)(doff + nd) > cap_cl) {
+                if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                continue;
+            }
+            for (long long i = lane; i < nd; i += 32) cl_next[doff + i] = D[i];
+            if (lane < 2) {
+                int c = lane == 0 ? K.d.x : K.d.y;
+                if (cnact[c] > 0) {
+                    unsigned long long fj = atomicAdd(&ctr->n_front_next, 1ull);
+                    if ((long long)fj < cap_front) {
+                        f_cell_next[fj] = c;
+                        f_cloff_next[fj] = doff;
+                        f_cllen_next[fj] = (int)nd;
+                    } else {
+                        atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                    }
+                }
+            }
+        }
+    }
+}
+
+#define LOCAL_WPB 2
+#define LOCAL_THREADS (LOCAL_WPB * 32)
+
+// L_k = L2L(L_parent, com_k - com_parent) + sum over k's local list of M2L / P2L.
+// One warp per sink cell; lanes take list entries; partial sums are reduced in shared memory.
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local_level(
+    const int* __restrict__ f_cell, unsigned long long n_front, const unsigned long long* __restrict__ f_ccoff,
+    const int* __restrict__ f_cclen, const unsigned int* __restrict__ cc, const int* __restrict__ cparent,
+    const Com4* __restrict__ com, const double* __restrict__ sx, const double* __restrict__ sy,
+    const double* __restrict__ sz, const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ L,
+    float eps2, DevCounters* __restrict__ ctr)
+{
+    __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
+    __shared__ float lsum[LOCAL_WPB][FMM_NL];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long fi = gw; fi < (long long)n_front; fi += nw) {
+        const int k = f_cell[fi];
+        const unsigned long long off = f_ccoff[fi];
+        const int len = f_cclen[fi];
+        const Com4 ck = com[k];
+        float acc[FMM_NL];
+#pragma unroll
+        for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
+        int ncc = 0, ncp = 0;
+        for (int i = lane; i < len; i += 32) {
+            unsigned int e = cc[off + i];
+            if (e & FMM_PARTICLE_BIT) {
+                unsigned int j = e & ~FMM_PARTICLE_BIT;
+                float rx = __double2float_rn(ck.x - sx[j]);
+                float ry = __double2float_rn(ck.y - sy[j]);
+                float rz = __double2float_rn(ck.z - sz[j]);
+                fmm_p2l_acc(sm[j], rx, ry, rz, eps2, acc);
+                ncp++;
+            } else {
+                const Com4 cs = com[e];
+                float M[FMM_NMOM];
+                const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)e * FMM_NREC);
+#pragma unroll
+                for (int q = 0; q < FMM_NMOM / 4; q++) {
+                    float4 v = r4[q];
+                    M[4 * q] = v.x;
+                    M[4 * q + 1] = v.y;
+                    M[4 * q + 2] = v.z;
+                    M[4 * q + 3] = v.w;
+                }
+                fmm_m2l_acc(M, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
+                            __double2float_rn(ck.z - cs.z), eps2, acc);
+                ncc++;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
+        __syncwarp();
+        for (int c = lane; c < FMM_NL; c += 32) {
+            float s = 0.0f;
+            for (int r = 0; r < 32; r++) s += red[wl][r][c];
+            lsum[wl][c] = s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ncc += __shfl_xor_sync(FMM_FULL_MASK, ncc, o);
+            ncp += __shfl_xor_sync(FMM_FULL_MASK, ncp, o);
+        }
+        __syncwarp();
+        const int p = cparent[k];
+        if (lane == 0) {
+            float out[FMM_NL];
+            if (p >= 0) {
+                const Com4 cp = com[p];
+                fmm_l2l(L + (long long)p * FMM_NL, __double2float_rn(ck.x - cp.x), __double2float_rn(ck.y - cp.y),
+                        __double2float_rn(ck.z - cp.z), out);
+            } else {
+#pragma unroll
+                for (int i = 0; i < FMM_NL; i++) out[i] = 0.0f;
+            }
+            float* Lk = L + (long long)k * FMM_NL;
+#pragma unroll
+            for (int i = 0; i < FMM_NL; i++) Lk[i] = out[i] + lsum[wl][i];
+            if (ncc) atomicAdd(&ctr->n_cc, (unsigned long long)ncc);
+            if (ncp) atomicAdd(&ctr->n_cp, (unsigned long long)ncp);
+        }
+        __syncwarp();
+    }
+}
+
+// level 0 of the walk: the root as the only sink, with the root on its checklist
+__global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl)
+{
+    f_cell[0] = 0;
+    f_cloff[0] = 0;
+    f_cllen[0] = 1;
+    cl[0] = 0u;
+}
+
+cudaError_t fmm_launch_walk_seed(DevWalk& w, cudaStream_t s)
+{
+    k_walk_seed<<<1, 1, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0]);
+    return cudaGetLastError();
+}
+
+int fmm_walk_warps(int device)
+{
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms * 16;  // 4 blocks of 4 warps per SM
+}
+
+cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
+                                  const WalkArgs& a, cudaStream_t s)
+{
+    const int cur = a.level_parity, nxt = cur ^ 1;
+    long long warps = (long long)n_front < w.n_warps ? (long long)n_front : w.n_warps;
+    int blocks = (int)fmm_ceil_div(warps, WALK_WPB);
+    if (blocks < 1) blocks = 1;
+    k_walk_level<<<blocks, WALK_THREADS, 0, s>>>(
+        t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], n_front, w.cl[cur], w.f_cell[nxt],
+        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.f_ccoff, w.f_cclen, w.pp, w.cap_pp, w.pc,
+        w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, a.bucket, a.group,
+        a.four_eps2);
+    return cudaGetLastError();
+}
+
+cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
+                                   const WalkArgs& a, cudaStream_t s)
+{
+    const int cur = a.level_parity;
+    long long blocks = fmm_ceil_div((long long)n_front, LOCAL_WPB);
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    if (blocks < 1) blocks = 1;
+    k_local_level<<<(unsigned)blocks, LOCAL_THREADS, 0, s>>>(w.f_cell[cur], n_front, w.f_ccoff, w.f_cclen, w.cc,
+                                                             t.cparent, t.com, t.sx, t.sy, t.sz, t.sm, t.rec, t.L,
+                                                             a.eps2, ctr);
+    return cudaGetLastError();
+}
