@@ -74,9 +74,14 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
         const long long ncl = f_cllen[fi];
         long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
         bool overflow = false;
-        for (long long base = 0; base < ncl + nq; base += 32) {
+        long long base = 0;
+        while (base < ncl + nq) {
+            // entries appended while this batch runs get indices >= ncl + nq (batch start), so the
+            // next batch begins right after the entries that were actually available here
+            const long long avail = ncl + nq - base;
             const long long vi = base + lane;
-            const bool valid = vi < ncl + nq;
+            const bool valid = lane < avail;
+            base += avail < 32 ? avail : 32;
             unsigned int e = 0;
             if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
             int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1;
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local_level(
     const int* __restrict__ f_cell, unsigned long long n_front, const unsigned long long* __restrict__ f_ccoff,
     const int* __restrict__ f_cclen, const unsigned int* __restrict__ cc, const int* __restrict__ cparent,
-    const Com4* __restrict__ com, const double* __restrict__ sx, const double* __restrict__ sy,
+    const int* __restrict__ ccount, const Com4* __restrict__ com, const double* __restrict__ sx, const double* __restrict__ sy,
     const double* __restrict__ sz, const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ L,
     float eps2, DevCounters* __restrict__ ctr)
 {
@@ -267,6 +272,12 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_level(
                 float ry = __double2float_rn(ck.y - sy[j]);
                 float rz = __double2float_rn(ck.z - sz[j]);
                 fmm_p2l_acc(sm[j], rx, ry, rz, eps2, acc);
+                ncp++;
+            } else if (ccount[e] == 1) {
+                // a one-particle cell: its particle -> local expansion
+                const Com4 cs = com[e];
+                fmm_p2l_acc((float)cs.w, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
+                            __double2float_rn(ck.z - cs.z), eps2, acc);
                 ncp++;
             } else {
                 const Com4 cs = com[e];
@@ -365,7 +376,7 @@ cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, uns
     if (blocks > 152LL * 64) blocks = 152LL * 64;
     if (blocks < 1) blocks = 1;
     k_local_level<<<(unsigned)blocks, LOCAL_THREADS, 0, s>>>(w.f_cell[cur], n_front, w.f_ccoff, w.f_cclen, w.cc,
-                                                             t.cparent, t.com, t.sx, t.sy, t.sz, t.sm, t.rec, t.L,
+                                                             t.cparent, t.ccount, t.com, t.sx, t.sy, t.sz, t.sm, t.rec, t.L,
                                                              a.eps2, ctr);
     return cudaGetLastError();
 }
