@@ -56,16 +56,21 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
+    ap.add_argument("--n", type=int, default=None,
+                    help="particle count override (profiling a smaller box of the same structure)")
     return ap.parse_args()
 
 
-def workload(name, rank):
+def workload(name, rank, n=None):
     from paper_1609_08621_gb300 import synth
 
     w = synth.WORKLOADS[name]
     seed = w["seed"] + 1000 * rank
-    pos, mass = synth.make(w["kind"], w["n"], seed)
-    return pos, mass, w["eps"], w["theta"]
+    if n is None:
+        pos, mass = synth.make(w["kind"], w["n"], seed)
+        return pos, mass, w["eps"], w["theta"]
+    pos, mass = synth.make(w["kind"], n, seed)
+    return pos, mass, (w["eps"] if w["eps"] == 1e-3 else synth.paper_softening(n)), w["theta"]
 
 
 class Clocks:
@@ -145,10 +150,7 @@ def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    pos, mass, eps, theta = workload(args.workload, 0)
-    vals = []
-    for _ in range(max(args.warmup, 0) and 0 or 0):
-        pass
+    pos, mass, eps, theta = workload(args.workload, 0, args.n)
     steps = []
     for k in range(args.warmup + args.steps):
         r = cpu_baseline(pos, mass, eps, theta, frac=args.cpu_sample or min(1.0, 1024.0 / mass.size))
@@ -186,7 +188,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    pos, mass, eps, theta = workload(args.workload, rank)
+    pos, mass, eps, theta = workload(args.workload, rank, args.n)
     n = mass.size
     tpos0 = torch.from_numpy(pos.reshape(-1).copy()).to(dev)
     tpos = tpos0.clone()

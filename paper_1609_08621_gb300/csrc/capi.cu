@@ -125,8 +125,8 @@ static void free_all(fmm_ctx* c)
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
-    void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.f_ccoff,
-                  w.f_cclen, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
+    void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off,
+                  w.lcc_len, w.lcells, w.Lg, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
     for (void* p : qs)
         if (p) cudaFree(p);
     if (c->ctr) cudaFree(c->ctr);
@@ -278,6 +278,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     // bucket ids: exclusive scan of the bucket start flags into keep[] (free after k_cells)
     CK(fmm_scan_exclusive(t.bflag, t.keep, n, c->totals + 1, t, s));
     CK(fmm_launch_bucket_index(t, n, s));
+    CK(fmm_launch_depth(t, c->totals, c->ctr, s));
     CK(cudaMemcpyAsync(c->totals_h, c->totals, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -290,7 +291,8 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     CK(fmm_launch_upward(t, n, bucket, c->ctr, s));
     // keys, 8 x (histogram, 3-kernel scan, scatter), gather, radix tree + keep, scan, cells, scan,
     // bucket index, bucket cells, upward, exact b_max
-    c->launches += 1 + 8 * 5 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 3;
+    c->launches += 1 + 8 * 5 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
+    t.depth = (int)c->ctr_h->depth;
     c->have_tree = true;
     c->theta_nodes = -1.0f;
     return FMM_OK;
@@ -334,9 +336,11 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
             CK(alloc(&w.f_cloff[i], need_front));
             CK(alloc(&w.f_cllen[i], need_front));
         }
-        CK(alloc(&w.f_ccoff, need_front));
-        CK(alloc(&w.f_cclen, need_front));
+        CK(alloc(&w.lcc_off, need_front));
+        CK(alloc(&w.lcc_len, need_front));
+        CK(alloc(&w.lcells, need_front));
         CK(alloc(&w.groups, need_front));
+        CK(alloc(&w.Lg, (long long)FMM_NL * need_front));
         w.cap_front = need_front;
         w.cap_groups = need_front;
     }
@@ -376,40 +380,32 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     a.eps2 = (float)(eps * eps);
     a.bucket = bucket;
     a.group = group;
+    // groups sit at most at the deepest cell level: depth + 1 levels, no host round trip between them
+    const int levels = t.depth + 1;
+    if (levels + 1 > FMM_MAX_LEVELS) return fail(FMM_ERR_STATE, "tree depth %d exceeds the walk's levels", t.depth);
     int scale = 1;
     for (int attempt = 0;; attempt++) {
         fmm_status st = ensure_walk(c, n, scale);
         if (st != FMM_OK) return st;
-        // reset the list counters; keep the build status bits
-        CK(cudaMemsetAsync(&c->ctr->n_front_next, 0, sizeof(DevCounters) - offsetof(DevCounters, n_front_next), s));
-        CK(cudaMemsetAsync(&c->ctr->status, 0, sizeof(unsigned int), s));
-        CK(fmm_launch_walk_seed(w, s));
+        CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
+        CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
+        CK(fmm_launch_walk_seed(t, w, c->ctr, s));
         c->launches += 1;
-        unsigned long long n_front = c->stats.n_active > 0 ? 1 : 0;
-        int parity = 0;
-        long long levels = 0;
-        bool overflow = false;
-        while (n_front > 0) {
-            CK(cudaMemsetAsync(&c->ctr->work_ctr, 0, sizeof(unsigned long long), s));
-            CK(cudaMemsetAsync(&c->ctr->n_front_next, 0, sizeof(unsigned long long), s));
-            CK(cudaMemsetAsync(&c->ctr->cl_next_len, 0, sizeof(unsigned long long), s));
-            a.level_parity = parity;
-            CK(fmm_launch_walk_level(t, w, c->ctr, n_front, a, s));
-            CK(fmm_launch_local_level(t, w, c->ctr, n_front, a, s));
-            c->launches += 2;
-            CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            levels++;
-            if (c->ctr_h->status & FMM_DEV_ERR_OVERFLOW) {
-                overflow = true;
-                break;
-            }
-            n_front = c->ctr_h->n_front_next;
-            parity ^= 1;
-            if (levels > 4096) return fail(FMM_ERR_STATE, "walk did not terminate");
+        for (int L = 0; L < levels; L++) {
+            a.level = L;
+            a.level_parity = L & 1;
+            CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
+            c->launches += 1;
         }
-        if (!overflow) {
-            w.n_levels = levels;
+        CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
+        c->launches += 2;
+        CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!c->ctr_h->overflow) {
+            if (c->ctr_h->lv_front[levels] != 0) return fail(FMM_ERR_STATE, "walk went below the deepest cell");
+            long long used = 0;
+            while (used < levels && c->ctr_h->lv_front[used] > 0) used++;
+            w.n_levels = used;
             w.n_groups = (long long)c->ctr_h->n_groups;
             w.pp_len = (long long)c->ctr_h->pp_len;
             w.pc_len = (long long)c->ctr_h->pc_len;
@@ -716,13 +712,10 @@ extern "C" fmm_status fmm_export_locals(const fmm_ctx* c, int* group_cell, float
     cudaStream_t s = c->stream;
     std::vector<Group> g((size_t)c->w.n_groups);
     CK(d2h(g.data(), c->w.groups, c->w.n_groups, s));
-    std::vector<float> Lall((size_t)c->t.n_cells * FMM_NL);
-    CK(d2h(Lall.data(), c->t.L, c->t.n_cells * FMM_NL, s));
+    CK(d2h(L, c->w.Lg, c->w.n_groups * FMM_NL, s));
     CK(cudaStreamSynchronize(s));
-    for (size_t i = 0; i < g.size(); i++) {
+    for (size_t i = 0; i < g.size(); i++)
         if (group_cell) group_cell[i] = g[i].cell;
-        if (L) memcpy(L + i * FMM_NL, &Lall[(size_t)g[i].cell * FMM_NL], FMM_NL * sizeof(float));
-    }
     return FMM_OK;
 }
 

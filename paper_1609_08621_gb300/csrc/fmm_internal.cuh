@@ -11,7 +11,6 @@
 
 // device status word bits
 #define FMM_DEV_ERR_ARG 1u        // invalid position or mass seen by a kernel
-#define FMM_DEV_ERR_OVERFLOW 2u   // a list or scratch capacity was exceeded (host grows and retries)
 #define FMM_DEV_ERR_TIMEOUT 4u    // a bounded wait gave up
 #define FMM_DEV_ERR_NUMERIC 8u    // non-finite output
 
@@ -49,23 +48,31 @@ struct __align__(16) Group {
     int pp_len, pc_len;
 };
 
+#define FMM_MAX_LEVELS 192  // walk levels: tree depth + 1 (63 key bits + 31 position bits at most)
+
 // Device-side counters and status, one per context.
 struct DevCounters {
-    unsigned int status;
+    unsigned int status;    // FMM_DEV_ERR_* bits of invalid input or failed waits
+    unsigned int overflow;  // a walk list or scratch capacity was exceeded (host grows and retries)
+    unsigned int depth;     // deepest cell level
     unsigned int pad0;
-    unsigned long long n_front_next;   // frontier size of the next walk level
-    unsigned long long n_groups;
-    unsigned long long cl_next_len;    // entries written to the next checklist buffer
+    unsigned long long n_active;
+    // walk totals
+    unsigned long long n_groups, n_lcells;
     unsigned long long pp_len, pc_len, cc_len;
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
-    unsigned long long work_ctr;       // persistent-kernel work counter
-    unsigned long long n_active;
+    // per walk level: frontier size, work counters of the walk and local kernels, and the
+    // number of checklist entries handed to that level
+    unsigned long long lv_front[FMM_MAX_LEVELS];
+    unsigned long long lv_work[FMM_MAX_LEVELS];
+    unsigned long long lv_cl[FMM_MAX_LEVELS];
 };
 
 // Device buffers of a context.  Capacities are in elements.
 struct DevTree {
     long long n = 0, cap_n = 0;
     long long n_cells = 0, cap_cells = 0, n_buckets = 0;
+    int depth = 0;
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;
     unsigned int *idx = nullptr, *idx_alt = nullptr;
@@ -91,7 +98,7 @@ struct DevTree {
     double *bmax = nullptr;
     float *rec = nullptr;        // FMM_NREC per cell
     WalkNode *node = nullptr;
-    float *L = nullptr;          // FMM_NL per cell (walked cells)
+    float *L = nullptr;          // FMM_NL per cell: own local expansion of walked cells
     // scan scratch
     unsigned int *scan_part = nullptr;
     long long cap_scan_part = 0;
@@ -106,8 +113,10 @@ struct DevWalk {
     int *f_cell[2] = {nullptr, nullptr};
     unsigned long long *f_cloff[2] = {nullptr, nullptr};
     int *f_cllen[2] = {nullptr, nullptr};
-    unsigned long long *f_ccoff = nullptr;
-    int *f_cclen = nullptr;
+    unsigned long long *lcc_off = nullptr;  // per cell: its local (CC/CP) list
+    int *lcc_len = nullptr;
+    int *lcells = nullptr;                  // cells with a non-empty local list
+    float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
     unsigned int *cl[2] = {nullptr, nullptr};
     unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
     int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry, for export
@@ -135,19 +144,19 @@ cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStrea
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s);
+cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s);
 
 // walk.cu
 struct WalkArgs {
+    int level;
     int level_parity;
     int bucket, group;
     float four_eps2;
     float eps2;
 };
-cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
-                                  const WalkArgs& a, cudaStream_t s);
-cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
-                                   const WalkArgs& a, cudaStream_t s);
-cudaError_t fmm_launch_walk_seed(DevWalk& w, cudaStream_t s);
+cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
+cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s);
+cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s);
 int fmm_walk_warps(int device);
 
 // interact.cu

@@ -2,8 +2,7 @@
 // particle-cell (PC) and the group's local expansion at its particles (L2P), then the
 // results are written back in the caller's order.
 //
-// One warp per group; lane l holds sinks l and l + 32 (g <= 64) in registers.  All
-// coordinates are single precision offsets from the group's centre of mass c_g
+// All coordinates are single precision offsets from the group's centre of mass c_g
 // (Sec. 3.1: interactions in single precision):
 //   sink     u_i = fl(com_bucket(i) - c_g) + fl(x_i - com_bucket(i))
 //   source   s_j = fl(com_bucket(j) - c_g) + fl(x_j - com_bucket(j))
@@ -11,6 +10,12 @@
 // where the differences of double-precision centres are formed in FP64 and rounded once
 // per bucket or cell (never per interaction: FP64 issue is 1/64 of FP32 on this GPU),
 // and fl(x - com_bucket) is stored per particle by the upward pass.
+//
+// One warp per group.  The warp's 32 lanes are laid out as Q list splits of 32/Q lanes,
+// each lane holding R sinks (slots lane%S, +S, ...): a group of n <= R*32/Q sinks uses
+// the (R, Q) of the smallest such slot count, so few lanes idle whatever the group size
+// (groups hold <= g particles, typically 30-64).  Each split takes every Q-th source; the
+// splits' partial sums are added with warp shuffles.
 //
 // PP: a_i += m_j (s_j - u_i) / (|s_j - u_i|^2 + eps^2)^(3/2), phi_i -= m_j / (...)^(1/2)
 // over every particle of every PP source, the sink itself included: its force term is
@@ -26,40 +31,19 @@
 #define IW 4  // warps per block
 #define ITHREADS (IW * 32)
 #define PP_TILE 512
+#define PC_CHUNK 32
 
-struct SinkPair {
-    float ux0, uy0, uz0, ux1, uy1, uz1;
-    float m0, m1;
-    int s0, s1;
-    bool v0, v1;
-};
-
-__device__ __forceinline__ void load_sinks(const Group& G, const Com4& ck, const int* __restrict__ bucket_of,
-                                           const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
-                                           const float4* __restrict__ off, int lane, SinkPair& S)
+// one sink's offset from the group centre and its mass
+__device__ __forceinline__ void load_sink(int s, const Com4& ck, const int* __restrict__ bucket_of,
+                                          const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                          const float4* __restrict__ off, float& ux, float& uy, float& uz, float& m)
 {
-    S.s0 = G.first + lane;
-    S.s1 = G.first + lane + 32;
-    S.v0 = lane < G.count;
-    S.v1 = lane + 32 < G.count;
-    S.ux0 = S.uy0 = S.uz0 = S.ux1 = S.uy1 = S.uz1 = 0.0f;
-    S.m0 = S.m1 = 0.0f;
-    if (S.v0) {
-        Com4 cb = com[bucket_cell[bucket_of[S.s0]]];
-        float4 o = off[S.s0];
-        S.ux0 = __double2float_rn(cb.x - ck.x) + o.x;
-        S.uy0 = __double2float_rn(cb.y - ck.y) + o.y;
-        S.uz0 = __double2float_rn(cb.z - ck.z) + o.z;
-        S.m0 = o.w;
-    }
-    if (S.v1) {
-        Com4 cb = com[bucket_cell[bucket_of[S.s1]]];
-        float4 o = off[S.s1];
-        S.ux1 = __double2float_rn(cb.x - ck.x) + o.x;
-        S.uy1 = __double2float_rn(cb.y - ck.y) + o.y;
-        S.uz1 = __double2float_rn(cb.z - ck.z) + o.z;
-        S.m1 = o.w;
-    }
+    const Com4 cb = com[bucket_cell[bucket_of[s]]];
+    const float4 o = off[s];
+    ux = __double2float_rn(cb.x - ck.x) + o.x;
+    uy = __double2float_rn(cb.y - ck.y) + o.y;
+    uz = __double2float_rn(cb.z - ck.z) + o.z;
+    m = o.w;
 }
 
 __device__ __forceinline__ void pp_pair(float ux, float uy, float uz, float4 s, float eps2, float& ax, float& ay,
@@ -74,6 +58,123 @@ __device__ __forceinline__ void pp_pair(float ux, float uy, float uz, float4 s, 
     ay = fmaf(mir3, dy, ay);
     az = fmaf(mir3, dz, az);
     ph -= mir;
+}
+
+template <int R, int Q>
+struct Sinks {
+    static constexpr int S = 32 / Q;
+    float ux[R], uy[R], uz[R], m[R];
+    float ax[R], ay[R], az[R], ph[R];
+    int idx[R];
+    bool v[R];
+    int split;
+
+    __device__ __forceinline__ void load(const Group& G, const Com4& ck, const int* __restrict__ bucket_of,
+                                         const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                         const float4* __restrict__ off, int lane)
+    {
+        split = lane / S;
+        const int slot = lane % S;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int i = slot + r * S;
+            v[r] = i < G.count;
+            idx[r] = G.first + i;
+            ux[r] = uy[r] = uz[r] = m[r] = 0.0f;
+            ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
+            if (v[r]) load_sink(idx[r], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m[r]);
+        }
+    }
+
+    // add the partial sums of the Q splits (lanes l, l ^ S, l ^ 2S, ...)
+    __device__ __forceinline__ void reduce()
+    {
+#pragma unroll
+        for (int o = S; o < 32; o <<= 1)
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                ax[r] += __shfl_xor_sync(FMM_FULL_MASK, ax[r], o);
+                ay[r] += __shfl_xor_sync(FMM_FULL_MASK, ay[r], o);
+                az[r] += __shfl_xor_sync(FMM_FULL_MASK, az[r], o);
+                ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
+            }
+    }
+};
+
+template <int R, int Q>
+__device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, const unsigned int* __restrict__ pp,
+                                              const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                                              const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                              const int* __restrict__ bucket_cell, const float4* __restrict__ off,
+                                              float4* __restrict__ accs, float4* T, float eps2, int enabled,
+                                              int lane)
+{
+    Sinks<R, Q> K;
+    K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
+    long long nsrc = 0;
+    if (enabled) {
+        for (int base = 0; base < G.pp_len; base += 32) {
+            const int ne = min(32, G.pp_len - base);
+            int first = 0, cnt = 0;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            if (lane < ne) {
+                const unsigned int e = pp[G.pp_off + base + lane];
+                int bc;
+                if (e & FMM_PARTICLE_BIT) {
+                    first = (int)(e & ~FMM_PARTICLE_BIT);
+                    cnt = 1;
+                    bc = bucket_cell[bucket_of[first]];
+                } else {
+                    first = cfirst[e];
+                    cnt = ccount[e];
+                    bc = (int)e;
+                }
+                const Com4 cb = com[bc];
+                dx = __double2float_rn(cb.x - ck.x);
+                dy = __double2float_rn(cb.y - ck.y);
+                dz = __double2float_rn(cb.z - ck.z);
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int total = __shfl_sync(FMM_FULL_MASK, incl, 31);
+            const int excl = incl - cnt;
+            for (int j = 0; j < ne; j++) {
+                const int fj = __shfl_sync(FMM_FULL_MASK, first, j);
+                const int nj = __shfl_sync(FMM_FULL_MASK, cnt, j);
+                const int pj = __shfl_sync(FMM_FULL_MASK, excl, j);
+                const float ex = __shfl_sync(FMM_FULL_MASK, dx, j);
+                const float ey = __shfl_sync(FMM_FULL_MASK, dy, j);
+                const float ez = __shfl_sync(FMM_FULL_MASK, dz, j);
+                if (lane < nj) {
+                    const float4 o = off[fj + lane];
+                    T[pj + lane] = make_float4(ex + o.x, ey + o.y, ez + o.z, o.w);
+                }
+            }
+            __syncwarp();
+            for (int t = K.split; t < total; t += Q) {
+                const float4 s = T[t];
+#pragma unroll
+                for (int r = 0; r < R; r++) pp_pair(K.ux[r], K.uy[r], K.uz[r], s, eps2, K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+            }
+            nsrc += total;
+            __syncwarp();
+        }
+        K.reduce();
+        // remove the self term of the potential (the force term is exactly zero)
+        const float ie = rsqrtf(eps2);
+#pragma unroll
+        for (int r = 0; r < R; r++) K.ph[r] += K.m[r] * ie;
+    }
+    if (K.split == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (K.v[r]) accs[K.idx[r]] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+    }
+    return nsrc;
 }
 
 __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ groups, long long n_groups,
@@ -93,74 +194,65 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
     for (long long gi = gw; gi < n_groups; gi += nw) {
         const Group G = groups[gi];
         const Com4 ck = com[G.cell];
-        SinkPair S;
-        load_sinks(G, ck, bucket_of, bucket_cell, com, off, lane, S);
-        float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, p0 = 0.f, ax1 = 0.f, ay1 = 0.f, az1 = 0.f, p1 = 0.f;
-        long long nsrc = 0;
-        if (enabled) {
-            for (int base = 0; base < G.pp_len; base += 32) {
-                const int ne = min(32, G.pp_len - base);
-                int first = 0, cnt = 0;
-                float dx = 0.f, dy = 0.f, dz = 0.f;
-                if (lane < ne) {
-                    unsigned int e = pp[G.pp_off + base + lane];
-                    int bc;
-                    if (e & FMM_PARTICLE_BIT) {
-                        first = (int)(e & ~FMM_PARTICLE_BIT);
-                        cnt = 1;
-                        bc = bucket_cell[bucket_of[first]];
-                    } else {
-                        first = cfirst[e];
-                        cnt = ccount[e];
-                        bc = (int)e;
-                    }
-                    Com4 cb = com[bc];
-                    dx = __double2float_rn(cb.x - ck.x);
-                    dy = __double2float_rn(cb.y - ck.y);
-                    dz = __double2float_rn(cb.z - ck.z);
-                }
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int total = __shfl_sync(FMM_FULL_MASK, incl, 31);
-                const int excl = incl - cnt;
-                for (int j = 0; j < ne; j++) {
-                    const int fj = __shfl_sync(FMM_FULL_MASK, first, j);
-                    const int nj = __shfl_sync(FMM_FULL_MASK, cnt, j);
-                    const int pj = __shfl_sync(FMM_FULL_MASK, excl, j);
-                    const float ex = __shfl_sync(FMM_FULL_MASK, dx, j);
-                    const float ey = __shfl_sync(FMM_FULL_MASK, dy, j);
-                    const float ez = __shfl_sync(FMM_FULL_MASK, dz, j);
-                    if (lane < nj) {
-                        float4 o = off[fj + lane];
-                        T[pj + lane] = make_float4(ex + o.x, ey + o.y, ez + o.z, o.w);
-                    }
-                }
-                __syncwarp();
-                for (int t = 0; t < total; t++) {
-                    const float4 s = T[t];
-                    pp_pair(S.ux0, S.uy0, S.uz0, s, eps2, ax0, ay0, az0, p0);
-                    pp_pair(S.ux1, S.uy1, S.uz1, s, eps2, ax1, ay1, az1, p1);
-                }
-                nsrc += total;
-                __syncwarp();
-            }
-            // remove the self term of the potential (the force term is exactly zero)
-            const float ie = rsqrtf(eps2);
-            p0 += S.m0 * ie;
-            p1 += S.m1 * ie;
-        }
-        if (S.v0) accs[S.s0] = make_float4(ax0, ay0, az0, p0);
-        if (S.v1) accs[S.s1] = make_float4(ax1, ay1, az1, p1);
+        const int n = G.count;
+        long long nsrc;
+#define PP_CALL(R, Q) pp_group<R, Q>(G, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, accs, T, eps2, enabled, lane)
+        if (n <= 8) nsrc = PP_CALL(1, 4);
+        else if (n <= 16) nsrc = PP_CALL(1, 2);
+        else if (n <= 24) nsrc = PP_CALL(3, 4);
+        else if (n <= 32) nsrc = PP_CALL(1, 1);
+        else if (n <= 48) nsrc = PP_CALL(3, 2);
+        else nsrc = PP_CALL(2, 1);
+#undef PP_CALL
         if (lane == 0) pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nsrc;
     }
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pp_pairs, pairs);
 }
 
-#define PC_CHUNK 32
+template <int R, int Q>
+__device__ __forceinline__ void pc_group(const Group& G, const Com4& ck, const unsigned int* __restrict__ pc,
+                                         const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                         const int* __restrict__ bucket_cell, const float4* __restrict__ off,
+                                         const float4* __restrict__ rec4, float4* __restrict__ accs, float4* R4,
+                                         float4* Z, int* ids, float eps2, int lane)
+{
+    Sinks<R, Q> K;
+    K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
+    for (int base = 0; base < G.pc_len; base += PC_CHUNK) {
+        const int ne = min(PC_CHUNK, G.pc_len - base);
+        if (lane < ne) {
+            const unsigned int c = pc[G.pc_off + base + lane];
+            const Com4 cs = com[c];
+            ids[lane] = (int)c;
+            Z[lane] = make_float4(__double2float_rn(cs.x - ck.x), __double2float_rn(cs.y - ck.y),
+                                  __double2float_rn(cs.z - ck.z), 0.0f);
+        }
+        __syncwarp();
+        const int nv = ne * (FMM_NREC / 4);
+        for (int i = lane; i < nv; i += 32) {
+            const int cl = i / (FMM_NREC / 4), part = i - cl * (FMM_NREC / 4);
+            R4[i] = rec4[(long long)ids[cl] * (FMM_NREC / 4) + part];
+        }
+        __syncwarp();
+        for (int j = K.split; j < ne; j += Q) {
+            const float* Rj = reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]);
+            const float4 z = Z[j];
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                fmm_pc_acc(Rj, K.ux[r] - z.x, K.uy[r] - z.y, K.uz[r] - z.z, eps2, K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+        }
+        __syncwarp();
+    }
+    K.reduce();
+    if (K.split == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (K.v[r]) {
+                const float4 a = accs[K.idx[r]];
+                accs[K.idx[r]] = make_float4(a.x + K.ax[r], a.y + K.ay[r], a.z + K.az[r], a.w + K.ph[r]);
+            }
+    }
+}
 
 __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, long long n_groups,
                                                  const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
@@ -169,9 +261,9 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
                                                  const float* __restrict__ rec, float4* __restrict__ accs, float eps2,
                                                  DevCounters* __restrict__ ctr)
 {
-    __shared__ float4 R4[IW][PC_CHUNK * FMM_NREC / 4];
-    __shared__ float4 Z[IW][PC_CHUNK];
-    __shared__ int ids[IW][PC_CHUNK];
+    __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
+    __shared__ float4 Zs[IW][PC_CHUNK];
+    __shared__ int idss[IW][PC_CHUNK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -181,41 +273,15 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         const Group G = groups[gi];
         if (G.pc_len == 0) continue;
         const Com4 ck = com[G.cell];
-        SinkPair S;
-        load_sinks(G, ck, bucket_of, bucket_cell, com, off, lane, S);
-        float ax0 = 0.f, ay0 = 0.f, az0 = 0.f, p0 = 0.f, ax1 = 0.f, ay1 = 0.f, az1 = 0.f, p1 = 0.f;
-        for (int base = 0; base < G.pc_len; base += PC_CHUNK) {
-            const int ne = min(PC_CHUNK, G.pc_len - base);
-            if (lane < ne) {
-                unsigned int c = pc[G.pc_off + base + lane];
-                Com4 cs = com[c];
-                ids[wl][lane] = (int)c;
-                Z[wl][lane] = make_float4(__double2float_rn(cs.x - ck.x), __double2float_rn(cs.y - ck.y),
-                                          __double2float_rn(cs.z - ck.z), 0.0f);
-            }
-            __syncwarp();
-            const int nv = ne * (FMM_NREC / 4);
-            for (int i = lane; i < nv; i += 32) {
-                int cl = i / (FMM_NREC / 4), part = i - cl * (FMM_NREC / 4);
-                R4[wl][i] = rec4[(long long)ids[wl][cl] * (FMM_NREC / 4) + part];
-            }
-            __syncwarp();
-            for (int j = 0; j < ne; j++) {
-                const float* Rj = reinterpret_cast<const float*>(&R4[wl][j * (FMM_NREC / 4)]);
-                const float4 z = Z[wl][j];
-                fmm_pc_acc(Rj, S.ux0 - z.x, S.uy0 - z.y, S.uz0 - z.z, eps2, ax0, ay0, az0, p0);
-                fmm_pc_acc(Rj, S.ux1 - z.x, S.uy1 - z.y, S.uz1 - z.z, eps2, ax1, ay1, az1, p1);
-            }
-            __syncwarp();
-        }
-        if (S.v0) {
-            float4 a = accs[S.s0];
-            accs[S.s0] = make_float4(a.x + ax0, a.y + ay0, a.z + az0, a.w + p0);
-        }
-        if (S.v1) {
-            float4 a = accs[S.s1];
-            accs[S.s1] = make_float4(a.x + ax1, a.y + ay1, a.z + az1, a.w + p1);
-        }
+        const int n = G.count;
+#define PC_CALL(R, Q) pc_group<R, Q>(G, ck, pc, com, bucket_of, bucket_cell, off, rec4, accs, R4s[wl], Zs[wl], idss[wl], eps2, lane)
+        if (n <= 8) PC_CALL(1, 4);
+        else if (n <= 16) PC_CALL(1, 2);
+        else if (n <= 24) PC_CALL(3, 4);
+        else if (n <= 32) PC_CALL(1, 1);
+        else if (n <= 48) PC_CALL(3, 2);
+        else PC_CALL(2, 1);
+#undef PC_CALL
         if (lane == 0) pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)G.pc_len;
     }
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pc_pairs, pairs);
@@ -225,7 +291,7 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
                                                       const Com4* __restrict__ com,
                                                       const int* __restrict__ bucket_of,
                                                       const int* __restrict__ bucket_cell,
-                                                      const float4* __restrict__ off, const float* __restrict__ L,
+                                                      const float4* __restrict__ off, const float* __restrict__ Lg,
                                                       const float4* __restrict__ accs,
                                                       const unsigned char* __restrict__ sact,
                                                       const unsigned int* __restrict__ perm, long long n,
@@ -238,19 +304,14 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
     for (long long gi = gw; gi < n_groups; gi += nw) {
         const Group G = groups[gi];
         const Com4 ck = com[G.cell];
-        SinkPair S;
-        load_sinks(G, ck, bucket_of, bucket_cell, com, off, lane, S);
-        for (int i = lane; i < FMM_NL; i += 32) Ls[wl][i] = L[(long long)G.cell * FMM_NL + i];
+        for (int i = lane; i < FMM_NL; i += 32) Ls[wl][i] = Lg[gi * FMM_NL + i];
         __syncwarp();
-        for (int h = 0; h < 2; h++) {
-            const bool v = h ? S.v1 : S.v0;
-            if (!v) continue;
-            const int s = h ? S.s1 : S.s0;
+        for (int i = lane; i < G.count; i += 32) {
+            const int s = G.first + i;
+            float ux, uy, uz, m;
+            load_sink(s, ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
             float4 a = accs[s];
-            if (use_local) {
-                if (h) fmm_l2p_acc(Ls[wl], S.ux1, S.uy1, S.uz1, a.x, a.y, a.z, a.w);
-                else fmm_l2p_acc(Ls[wl], S.ux0, S.uy0, S.uz0, a.x, a.y, a.z, a.w);
-            }
+            if (use_local) fmm_l2p_acc(Ls[wl], ux, uy, uz, a.x, a.y, a.z, a.w);
             if (sact[s]) {
                 const unsigned int p = perm[s];
                 acc[p] = a.x;
@@ -298,7 +359,7 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
 {
     (void)ctr;
     k_l2p_out<<<grid_for(w.n_groups), ITHREADS, 0, s>>>(w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell,
-                                                        t.off, t.L, t.accs, t.sact, t.idx, n, acc, pot,
+                                                        t.off, w.Lg, t.accs, t.sact, t.idx, n, acc, pot,
                                                         (a.terms & 4) ? 1 : 0);
     return cudaGetLastError();
 }

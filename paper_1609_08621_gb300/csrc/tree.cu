@@ -350,46 +350,70 @@ __global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ 
     }
 }
 
-// Exact b_max of every internal cell: the farthest particle from the centre of mass.
-// A bucket can hold it only if |com_b - com| + b_max(b) reaches the largest |com_b - com|
-// (a lower bound of the answer, since a bucket's centre of mass lies in the convex hull
-// of its particles); only those buckets are scanned particle by particle.
+// Exact b_max of every internal cell: the distance from its centre of mass p to the farthest
+// of its particles, in FP64 (the same operations as a brute-force scan, so the value is the
+// exact one).  One thread per cell runs a branch-and-bound descent of the cell's subtree:
+//   lb = a lower bound of the answer: 0.999998 x any FP32 distance from p to a sub-cell's
+//        centre of mass (inside the hull of the particles) or to a particle;
+//   a sub-cell is skipped when (FP32 distance to its centre + its b_max bound) x 1.000002 < lb;
+//   a particle of a visited bucket gets its FP64 distance only if its FP32 distance could
+//   reach lb.
+// FP32 distances are formed from fl(com_node - p) (FP64 difference, rounded) plus the
+// particle's stored offset from its bucket centre, so their relative error is below 1e-6 of
+// the cell's b_max; the 2e-6 margins therefore never discard the farthest particle.  Only a
+// handful of buckets per cell reach the FP64 stage (FP64 issue is 1/64 of FP32 here).
+// bmax[] holds exact values for buckets and the upward pass's upper bounds for internal cells;
+// threads may read either a bound or an exact value of another cell, both valid bounds.
+#define BMAX_STACK 128
+
 __global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __restrict__ cfirst,
                                                     const int* __restrict__ ccount, const int* __restrict__ cchild,
-                                                    const int* __restrict__ bucket_of,
-                                                    const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                                    const Com4* __restrict__ com, const float4* __restrict__ off,
                                                     const double* __restrict__ sx, const double* __restrict__ sy,
-                                                    const double* __restrict__ sz, double* __restrict__ bmax)
+                                                    const double* __restrict__ sz, double* bmax,
+                                                    unsigned int* __restrict__ status)
 {
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int c = wid; c < ncell; c += nw) {
-        if (cchild[2 * c] < 0) continue;  // buckets are exact already
-        const Com4 cc = com[c];
-        const int f = cfirst[c], cnt = ccount[c];
-        const int b0 = bucket_of[f], b1 = bucket_of[f + cnt - 1];
-        double lb2 = 0.0;
-        for (int b = b0 + lane; b <= b1; b += 32) {
-            Com4 cb = com[bucket_cell[b]];
-            lb2 = fmax(lb2, dist2_ordered(cb.x - cc.x, cb.y - cc.y, cb.z - cc.z));
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    if (cchild[2 * c] < 0) return;  // buckets are exact already
+    const Com4 p = com[c];
+    int stack[BMAX_STACK];
+    int sp = 0;
+    stack[sp++] = cchild[2 * c];
+    stack[sp++] = cchild[2 * c + 1];
+    float lb = 0.0f;
+    double best2 = 0.0;
+    while (sp > 0) {
+        const int nd = stack[--sp];
+        const Com4 cm = com[nd];
+        const float dx = __double2float_rn(cm.x - p.x), dy = __double2float_rn(cm.y - p.y),
+                    dz = __double2float_rn(cm.z - p.z);
+        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+        lb = fmaxf(lb, d * (1.0f - 2e-6f));
+        const float ub = d + __double2float_ru(bmax[nd]);
+        if (ub * (1.0f + 2e-6f) < lb) continue;
+        const int c0 = cchild[2 * nd];
+        if (c0 < 0) {
+            const int f = cfirst[nd], cnt = ccount[nd];
+            for (int j = f; j < f + cnt; j++) {
+                const float4 o = off[j];
+                const float vx = dx + o.x, vy = dy + o.y, vz = dz + o.z;
+                const float dj = sqrtf(vx * vx + vy * vy + vz * vz);
+                if (dj * (1.0f + 2e-6f) >= lb) {
+                    best2 = fmax(best2, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
+                    lb = fmaxf(lb, dj * (1.0f - 2e-6f));
+                }
+            }
+        } else {
+            if (sp + 2 > BMAX_STACK) {  // deeper than any 63-bit radix tree with 31-bit positions
+                atomicOr(status, FMM_DEV_ERR_NUMERIC);
+                return;
+            }
+            stack[sp++] = c0;
+            stack[sp++] = cchild[2 * nd + 1];
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) lb2 = fmax(lb2, __shfl_xor_sync(FMM_FULL_MASK, lb2, o));
-        const double lb = sqrt(lb2) * (1.0 - 1e-12);
-        double best = 0.0;
-        for (int b = b0 + lane; b <= b1; b += 32) {
-            int bc = bucket_cell[b];
-            Com4 cb = com[bc];
-            double d = sqrt(dist2_ordered(cb.x - cc.x, cb.y - cc.y, cb.z - cc.z));
-            if (d + bmax[bc] < lb) continue;
-            int pf = cfirst[bc], pn = ccount[bc];
-            for (int j = pf; j < pf + pn; j++) best = fmax(best, dist2_ordered(sx[j] - cc.x, sy[j] - cc.y, sz[j] - cc.z));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
-        if (lane == 0) bmax[c] = __dsqrt_rn(best);
     }
+    bmax[c] = __dsqrt_rn(best2);
 }
 
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s)
@@ -404,18 +428,14 @@ cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s)
 {
     (void)bucket;
-    (void)ctr;
     int nc = (int)t.n_cells, nb = (int)t.n_buckets;
     k_bucket_cells<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.cfirst, t.cchild, nc, t.bucket_of, t.bucket_cell);
     cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)nc, s);
     k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
                                                               t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact, t.com, t.clo,
                                                               t.chi, t.bmax, t.cnact, t.rec, t.off, t.arrive);
-    int blocks = (int)fmm_ceil_div((long long)nc * 32, 128);
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    if (blocks < 1) blocks = 1;
-    k_bmax_exact<<<blocks, 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.bucket_of, t.bucket_cell, t.com, t.sx,
-                                        t.sy, t.sz, t.bmax);
+    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.com, t.off, t.sx,
+                                                                  t.sy, t.sz, t.bmax, &ctr->status);
     return cudaGetLastError();
 }
 
@@ -446,5 +466,23 @@ cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s)
     int nc = (int)t.n_cells;
     k_nodes<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(nc, (float)theta, t.cfirst, t.ccount, t.cchild, t.com,
                                                           t.clo, t.chi, t.bmax, t.node);
+    return cudaGetLastError();
+}
+
+// deepest level of any cell (the walk needs at most depth + 1 levels)
+__global__ void k_depth(const unsigned int* __restrict__ ncell, const int* __restrict__ cparent,
+                        DevCounters* __restrict__ ctr)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (int)*ncell) return;
+    unsigned int d = 0;
+    for (int p = cparent[c]; p >= 0; p = cparent[p]) d++;
+    atomicMax(&ctr->depth, d);
+}
+
+// ncell_dev: device copy of the cell count (the grid covers the cell capacity)
+cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s)
+{
+    k_depth<<<(unsigned)fmm_ceil_div(t.cap_cells, TB), TB, 0, s>>>(ncell_dev, t.cparent, ctr);
     return cudaGetLastError();
 }

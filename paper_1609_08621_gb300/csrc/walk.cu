@@ -41,13 +41,14 @@ __device__ __forceinline__ float gap_axis(float lo_s, float hi_s, float lo_k, fl
     return g > 0.0f ? g : 0.0f;
 }
 
-__global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
+__global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
     const WalkNode* __restrict__ node, const float4* __restrict__ posf, const int* __restrict__ cnact,
     const int* __restrict__ f_cell, const unsigned long long* __restrict__ f_cloff, const int* __restrict__ f_cllen,
-    unsigned long long n_front, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
+    int level, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
     unsigned long long* __restrict__ f_cloff_next, int* __restrict__ f_cllen_next, long long cap_front,
-    unsigned int* __restrict__ cl_next, long long cap_cl, unsigned long long* __restrict__ f_ccoff,
-    int* __restrict__ f_cclen, unsigned int* __restrict__ pp, long long cap_pp, unsigned int* __restrict__ pc,
+    unsigned int* __restrict__ cl_next, long long cap_cl, unsigned long long* __restrict__ lcc_off,
+    int* __restrict__ lcc_len, int* __restrict__ lcells, unsigned int* __restrict__ pp, long long cap_pp,
+    unsigned int* __restrict__ pc,
     long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
     Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
     DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2)
@@ -60,10 +61,11 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
     unsigned int* P = Q + 3 * cap_scr;
     unsigned int* C = Q + 4 * cap_scr;
     const unsigned int lt = fmm_lanemask_lt();
+    const unsigned long long n_front = *(volatile unsigned long long*)&ctr->lv_front[level];
 
     for (;;) {
         unsigned long long fi = 0;
-        if (lane == 0) fi = atomicAdd(&ctr->work_ctr, 1ull);
+        if (lane == 0) fi = atomicAdd(&ctr->lv_work[level], 1ull);
         fi = __shfl_sync(FMM_FULL_MASK, fi, 0);
         if (fi >= n_front) break;
         const int k = f_cell[fi];
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
             __syncwarp();
         }
         if (overflow) {
-            if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+            if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
         }
         __syncwarp();
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
         if (lane == 0) off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
         off = __shfl_sync(FMM_FULL_MASK, off, 0);
         if ((long long)(off + na) > cap_cc) {
-            if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+            if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
         }
         for (long long i = lane; i < na; i += 32) {
@@ -181,8 +183,9 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
             cc_sink[off + i] = k;
         }
         if (lane == 0) {
-            f_ccoff[fi] = off;
-            f_cclen[fi] = (int)na;
+            lcc_off[k] = off;
+            lcc_len[k] = (int)na;
+            if (na > 0) lcells[atomicAdd(&ctr->n_lcells, 1ull)] = k;
         }
         if (kg) {
             unsigned long long po = 0, co = 0, gi = 0;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
             co = __shfl_sync(FMM_FULL_MASK, co, 0);
             gi = __shfl_sync(FMM_FULL_MASK, gi, 0);
             if ((long long)(po + npp) > cap_pp || (long long)(co + npc) > cap_pc || (long long)gi >= cap_groups) {
-                if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                if (lane == 0) atomicOr(&ctr->overflow, 1u);
                 continue;
             }
             for (long long i = lane; i < npp; i += 32) pp[po + i] = P[i];
@@ -214,23 +217,23 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
             }
         } else {
             unsigned long long doff = 0;
-            if (lane == 0) doff = atomicAdd(&ctr->cl_next_len, (unsigned long long)nd);
+            if (lane == 0) doff = atomicAdd(&ctr->lv_cl[level + 1], (unsigned long long)nd);
             doff = __shfl_sync(FMM_FULL_MASK, doff, 0);
             if ((long long)(doff + nd) > cap_cl) {
-                if (lane == 0) atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                if (lane == 0) atomicOr(&ctr->overflow, 1u);
                 continue;
             }
             for (long long i = lane; i < nd; i += 32) cl_next[doff + i] = D[i];
             if (lane < 2) {
                 int c = lane == 0 ? K.d.x : K.d.y;
                 if (cnact[c] > 0) {
-                    unsigned long long fj = atomicAdd(&ctr->n_front_next, 1ull);
+                    unsigned long long fj = atomicAdd(&ctr->lv_front[level + 1], 1ull);
                     if ((long long)fj < cap_front) {
                         f_cell_next[fj] = c;
                         f_cloff_next[fj] = doff;
                         f_cllen_next[fj] = (int)nd;
                     } else {
-                        atomicOr(&ctr->status, FMM_DEV_ERR_OVERFLOW);
+                        atomicOr(&ctr->overflow, 1u);
                     }
                 }
             }
@@ -241,37 +244,37 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_level(
 #define LOCAL_WPB 2
 #define LOCAL_THREADS (LOCAL_WPB * 32)
 
-// L_k = L2L(L_parent, com_k - com_parent) + sum over k's local list of M2L / P2L.
-// One warp per sink cell; lanes take list entries; partial sums are reduced in shared memory.
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local_level(
-    const int* __restrict__ f_cell, unsigned long long n_front, const unsigned long long* __restrict__ f_ccoff,
-    const int* __restrict__ f_cclen, const unsigned int* __restrict__ cc, const int* __restrict__ cparent,
-    const int* __restrict__ ccount, const Com4* __restrict__ com, const double* __restrict__ sx, const double* __restrict__ sy,
-    const double* __restrict__ sz, const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ L,
-    float eps2, DevCounters* __restrict__ ctr)
+// Own local expansion of every walked cell with a non-empty local list: the sum of the M2L
+// (CC) and P2L (CP) terms of that cell's list, about its centre of mass.  One warp per cell,
+// lanes take list entries, partial sums are reduced in shared memory.  All cells are done in
+// one launch after the walk.
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local_own(
+    const int* __restrict__ lcells, const unsigned long long* __restrict__ lcc_off, const int* __restrict__ lcc_len,
+    const unsigned int* __restrict__ cc, const int* __restrict__ ccount, const Com4* __restrict__ com,
+    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
+    const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ Lown, float eps2,
+    DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
-    __shared__ float lsum[LOCAL_WPB][FMM_NL];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long fi = gw; fi < (long long)n_front; fi += nw) {
-        const int k = f_cell[fi];
-        const unsigned long long off = f_ccoff[fi];
-        const int len = f_cclen[fi];
+    const long long ncells = (long long)*(volatile unsigned long long*)&ctr->n_lcells;
+    int ncc = 0, ncp = 0;
+    for (long long li = gw; li < ncells; li += nw) {
+        const int k = lcells[li];
+        const unsigned long long off = lcc_off[k];
+        const int len = lcc_len[k];
         const Com4 ck = com[k];
         float acc[FMM_NL];
 #pragma unroll
         for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
-        int ncc = 0, ncp = 0;
         for (int i = lane; i < len; i += 32) {
             unsigned int e = cc[off + i];
             if (e & FMM_PARTICLE_BIT) {
                 unsigned int j = e & ~FMM_PARTICLE_BIT;
-                float rx = __double2float_rn(ck.x - sx[j]);
-                float ry = __double2float_rn(ck.y - sy[j]);
-                float rz = __double2float_rn(ck.z - sz[j]);
-                fmm_p2l_acc(sm[j], rx, ry, rz, eps2, acc);
+                fmm_p2l_acc(sm[j], __double2float_rn(ck.x - sx[j]), __double2float_rn(ck.y - sy[j]),
+                            __double2float_rn(ck.z - sz[j]), eps2, acc);
                 ncp++;
             } else if (ccount[e] == 1) {
                 // a one-particle cell: its particle -> local expansion
@@ -299,50 +302,97 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_level(
 #pragma unroll
         for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
         __syncwarp();
+        float* Lk = Lown + (long long)k * FMM_NL;
         for (int c = lane; c < FMM_NL; c += 32) {
-            float s = 0.0f;
-            for (int r = 0; r < 32; r++) s += red[wl][r][c];
-            lsum[wl][c] = s;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ncc += __shfl_xor_sync(FMM_FULL_MASK, ncc, o);
-            ncp += __shfl_xor_sync(FMM_FULL_MASK, ncp, o);
+            float sum = 0.0f;
+            for (int r = 0; r < 32; r++) sum += red[wl][r][c];
+            Lk[c] = sum;
         }
         __syncwarp();
-        const int p = cparent[k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ncc += __shfl_xor_sync(FMM_FULL_MASK, ncc, o);
+        ncp += __shfl_xor_sync(FMM_FULL_MASK, ncp, o);
+    }
+    if (lane == 0) {
+        if (ncc) atomicAdd(&ctr->n_cc, (unsigned long long)ncc);
+        if (ncp) atomicAdd(&ctr->n_cp, (unsigned long long)ncp);
+    }
+}
+
+// Local expansion of each group about its centre of mass: the own expansions of the group and
+// of all its ancestors, each re-expanded (L2L) at the group's centre.  A local expansion is a
+// polynomial of degree 5, so one re-expansion from an ancestor equals the chain of L2L steps
+// down the tree.  One warp per group, lanes take ancestors.
+#define LG_MAX_ANC FMM_MAX_LEVELS
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
+    const Group* __restrict__ groups, const int* __restrict__ cparent, const int* __restrict__ lcc_len,
+    const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg,
+    DevCounters* __restrict__ ctr)
+{
+    __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
+    __shared__ int anc[LOCAL_WPB][LG_MAX_ANC];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long ng = (long long)*(volatile unsigned long long*)&ctr->n_groups;
+    for (long long gi = gw; gi < ng; gi += nw) {
+        const int g = groups[gi].cell;
+        int na = 0;
         if (lane == 0) {
-            float out[FMM_NL];
-            if (p >= 0) {
-                const Com4 cp = com[p];
-                fmm_l2l(L + (long long)p * FMM_NL, __double2float_rn(ck.x - cp.x), __double2float_rn(ck.y - cp.y),
-                        __double2float_rn(ck.z - cp.z), out);
+            for (int a = g; a >= 0 && na < LG_MAX_ANC; a = cparent[a])
+                if (lcc_len[a] > 0) anc[wl][na++] = a;
+        }
+        na = __shfl_sync(FMM_FULL_MASK, na, 0);
+        __syncwarp();
+        const Com4 cg = com[g];
+        float acc[FMM_NL];
+#pragma unroll
+        for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
+        for (int i = lane; i < na; i += 32) {
+            const int a = anc[wl][i];
+            const float* La = Lown + (long long)a * FMM_NL;
+            if (a == g) {
+#pragma unroll
+                for (int q = 0; q < FMM_NL; q++) acc[q] += La[q];
             } else {
+                const Com4 ca = com[a];
+                float Lo[FMM_NL];
+                fmm_l2l(La, __double2float_rn(cg.x - ca.x), __double2float_rn(cg.y - ca.y),
+                        __double2float_rn(cg.z - ca.z), Lo);
 #pragma unroll
-                for (int i = 0; i < FMM_NL; i++) out[i] = 0.0f;
+                for (int q = 0; q < FMM_NL; q++) acc[q] += Lo[q];
             }
-            float* Lk = L + (long long)k * FMM_NL;
+        }
 #pragma unroll
-            for (int i = 0; i < FMM_NL; i++) Lk[i] = out[i] + lsum[wl][i];
-            if (ncc) atomicAdd(&ctr->n_cc, (unsigned long long)ncc);
-            if (ncp) atomicAdd(&ctr->n_cp, (unsigned long long)ncp);
+        for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
+        __syncwarp();
+        float* out = Lg + gi * FMM_NL;
+        for (int c = lane; c < FMM_NL; c += 32) {
+            float sum = 0.0f;
+            for (int r = 0; r < 32; r++) sum += red[wl][r][c];
+            out[c] = sum;
         }
         __syncwarp();
     }
 }
 
-// level 0 of the walk: the root as the only sink, with the root on its checklist
-__global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl)
+// level 0 of the walk: the root as the only sink, with the root on its checklist (no sink
+// at all when no particle is active)
+__global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl,
+                            const int* __restrict__ cnact, DevCounters* ctr)
 {
     f_cell[0] = 0;
     f_cloff[0] = 0;
     f_cllen[0] = 1;
     cl[0] = 0u;
+    ctr->lv_front[0] = cnact[0] > 0 ? 1ull : 0ull;
 }
 
-cudaError_t fmm_launch_walk_seed(DevWalk& w, cudaStream_t s)
+cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s)
 {
-    k_walk_seed<<<1, 1, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0]);
+    k_walk_seed<<<1, 1, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0], t.cnact, ctr);
     return cudaGetLastError();
 }
 
@@ -350,33 +400,27 @@ int fmm_walk_warps(int device)
 {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return sms * 16;  // 4 blocks of 4 warps per SM
+    return sms * 24;  // 6 resident blocks of 4 warps per SM
 }
 
-cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
-                                  const WalkArgs& a, cudaStream_t s)
+cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s)
 {
     const int cur = a.level_parity, nxt = cur ^ 1;
-    long long warps = (long long)n_front < w.n_warps ? (long long)n_front : w.n_warps;
-    int blocks = (int)fmm_ceil_div(warps, WALK_WPB);
-    if (blocks < 1) blocks = 1;
+    // persistent grid: every warp owns a scratch slot; idle warps exit after one atomic
+    const int blocks = w.n_warps / WALK_WPB;
     k_walk_level<<<blocks, WALK_THREADS, 0, s>>>(
-        t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], n_front, w.cl[cur], w.f_cell[nxt],
-        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.f_ccoff, w.f_cclen, w.pp, w.cap_pp, w.pc,
-        w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, a.bucket, a.group,
-        a.four_eps2);
+        t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],
+        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,
+        w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr,
+        a.bucket, a.group, a.four_eps2);
     return cudaGetLastError();
 }
 
-cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, unsigned long long n_front,
-                                   const WalkArgs& a, cudaStream_t s)
+cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s)
 {
-    const int cur = a.level_parity;
-    long long blocks = fmm_ceil_div((long long)n_front, LOCAL_WPB);
-    if (blocks > 152LL * 64) blocks = 152LL * 64;
-    if (blocks < 1) blocks = 1;
-    k_local_level<<<(unsigned)blocks, LOCAL_THREADS, 0, s>>>(w.f_cell[cur], n_front, w.f_ccoff, w.f_cclen, w.cc,
-                                                             t.cparent, t.ccount, t.com, t.sx, t.sy, t.sz, t.sm, t.rec, t.L,
-                                                             a.eps2, ctr);
+    const int blocks = w.n_warps / LOCAL_WPB;
+    k_local_own<<<blocks, LOCAL_THREADS, 0, s>>>(w.lcells, w.lcc_off, w.lcc_len, w.cc, t.ccount, t.com, t.sx, t.sy,
+                                                  t.sz, t.sm, t.rec, t.L, eps2, ctr);
+    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, ctr);
     return cudaGetLastError();
 }
