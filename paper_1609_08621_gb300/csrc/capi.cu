@@ -126,7 +126,7 @@ static void free_all(fmm_ctx* c)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
     void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off,
-                  w.lcc_len, w.lcells, w.Lg, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
+                  w.lcc_len, w.lcells, w.Lg, w.order_pp, w.order_pc, w.gkey, w.gkey_alt, w.gval, w.gval_alt, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
     for (void* p : qs)
         if (p) cudaFree(p);
     if (c->ctr) cudaFree(c->ctr);
@@ -341,6 +341,12 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
         CK(alloc(&w.lcells, need_front));
         CK(alloc(&w.groups, need_front));
         CK(alloc(&w.Lg, (long long)FMM_NL * need_front));
+        CK(alloc(&w.order_pp, need_front));
+        CK(alloc(&w.order_pc, need_front));
+        CK(alloc(&w.gkey, need_front));
+        CK(alloc(&w.gkey_alt, need_front));
+        CK(alloc(&w.gval, need_front));
+        CK(alloc(&w.gval_alt, need_front));
         w.cap_front = need_front;
         w.cap_groups = need_front;
     }
@@ -446,6 +452,8 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     ia.terms = q.terms;
     ia.accumulate = q.accumulate;
     if (c->w.n_groups > 0) {
+        CK(fmm_launch_group_order(c->t, c->w, s));
+        c->launches += 1 + 2 * 5;
         CK(fmm_launch_pp(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[3], s));
         CK(fmm_launch_pc(c->t, c->w, c->ctr, ia, s));

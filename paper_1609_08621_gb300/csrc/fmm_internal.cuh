@@ -43,7 +43,7 @@ struct __align__(16) Group {
     int cell;
     int first;
     int count;
-    int pad;
+    int pp_src;  // source particles in the PP list
     unsigned long long pp_off, pc_off;
     int pp_len, pc_len;
 };
@@ -61,6 +61,7 @@ struct DevCounters {
     unsigned long long n_groups, n_lcells;
     unsigned long long pp_len, pc_len, cc_len;
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
+    unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     // per walk level: frontier size, work counters of the walk and local kernels, and the
     // number of checklist entries handed to that level
     unsigned long long lv_front[FMM_MAX_LEVELS];
@@ -117,6 +118,10 @@ struct DevWalk {
     int *lcc_len = nullptr;
     int *lcells = nullptr;                  // cells with a non-empty local list
     float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
+    // group orders for the interaction kernels (most expensive first) and sort scratch
+    unsigned int *order_pp = nullptr, *order_pc = nullptr;
+    unsigned long long *gkey = nullptr, *gkey_alt = nullptr;
+    unsigned int *gval = nullptr, *gval_alt = nullptr;
     unsigned int *cl[2] = {nullptr, nullptr};
     unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
     int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry, for export
@@ -132,6 +137,8 @@ struct DevWalk {
 cudaError_t fmm_scan_exclusive(const unsigned int* in, unsigned int* out, long long n, unsigned int* total_dev,
                                DevTree& t, cudaStream_t s);
 cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s);
+cudaError_t fmm_radix_sort_kv(unsigned long long* ka, unsigned long long* kb, unsigned int* va, unsigned int* vb,
+                              long long n, int passes, DevTree& t, cudaStream_t s);
 cudaError_t fmm_sort_ensure(DevTree& t, long long n);
 
 // tree.cu
@@ -165,6 +172,7 @@ struct InteractArgs {
     int terms;
     int accumulate;
 };
+cudaError_t fmm_launch_group_order(DevTree& t, DevWalk& w, cudaStream_t s);
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,

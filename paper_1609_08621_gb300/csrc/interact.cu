@@ -101,13 +101,22 @@ struct Sinks {
     }
 };
 
+// Source particles of 32 PP entries staged in shared memory: entry j contributes cnt_j
+// particles at tile positions [excl_j, excl_j + cnt_j); each lane fills tile slots
+// lane, lane + 32, ... independently (entry found by binary search over the prefix), so the
+// particle loads of the whole chunk are in flight together.
+struct PPChunk {
+    int first[32], excl[33];
+    float dx[32], dy[32], dz[32];
+};
+
 template <int R, int Q>
 __device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, const unsigned int* __restrict__ pp,
                                               const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                               const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                               const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                              float4* __restrict__ accs, float4* T, float eps2, int enabled,
-                                              int lane)
+                                              float4* __restrict__ accs, float4* T, PPChunk& E, float eps2,
+                                              int enabled, int lane)
 {
     Sinks<R, Q> K;
     K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
@@ -141,20 +150,26 @@ __device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, co
                 if (lane >= o) incl += t;
             }
             const int total = __shfl_sync(FMM_FULL_MASK, incl, 31);
-            const int excl = incl - cnt;
-            for (int j = 0; j < ne; j++) {
-                const int fj = __shfl_sync(FMM_FULL_MASK, first, j);
-                const int nj = __shfl_sync(FMM_FULL_MASK, cnt, j);
-                const int pj = __shfl_sync(FMM_FULL_MASK, excl, j);
-                const float ex = __shfl_sync(FMM_FULL_MASK, dx, j);
-                const float ey = __shfl_sync(FMM_FULL_MASK, dy, j);
-                const float ez = __shfl_sync(FMM_FULL_MASK, dz, j);
-                if (lane < nj) {
-                    const float4 o = off[fj + lane];
-                    T[pj + lane] = make_float4(ex + o.x, ey + o.y, ez + o.z, o.w);
+            E.first[lane] = first;
+            E.excl[lane] = incl - cnt;
+            E.dx[lane] = dx;
+            E.dy[lane] = dy;
+            E.dz[lane] = dz;
+            if (lane == 31) E.excl[32] = total;
+            __syncwarp();
+            for (int t = lane; t < total; t += 32) {
+                // largest j with excl[j] <= t (entries with cnt 0 never occur)
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (E.excl[mid] <= t) lo = mid;
+                    else hi = mid - 1;
                 }
+                const float4 o = off[E.first[lo] + (t - E.excl[lo])];
+                T[t] = make_float4(E.dx[lo] + o.x, E.dy[lo] + o.y, E.dz[lo] + o.z, o.w);
             }
             __syncwarp();
+#pragma unroll 4
             for (int t = K.split; t < total; t += Q) {
                 const float4 s = T[t];
 #pragma unroll
@@ -177,26 +192,30 @@ __device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, co
     return nsrc;
 }
 
-__global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ groups, long long n_groups,
-                                                 const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
-                                                 const int* __restrict__ ccount, const int* __restrict__ cnact,
-                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
-                                                 const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                                 float4* __restrict__ accs, float eps2, int enabled,
-                                                 DevCounters* __restrict__ ctr)
+// Persistent: each warp takes the next group of the cost-sorted order until none is left.
+__global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ groups, const unsigned int* __restrict__ order,
+                                                 long long n_groups, const unsigned int* __restrict__ pp,
+                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                                                 const int* __restrict__ cnact, const Com4* __restrict__ com,
+                                                 const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
+                                                 const float4* __restrict__ off, float4* __restrict__ accs, float eps2,
+                                                 int enabled, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 tile[IW][PP_TILE];
+    __shared__ PPChunk chunk[IW];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     float4* T = tile[wl];
     unsigned long long pairs = 0;
-    for (long long gi = gw; gi < n_groups; gi += nw) {
-        const Group G = groups[gi];
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(&ctr->pp_work, 1ull);
+        i = __shfl_sync(FMM_FULL_MASK, i, 0);
+        if ((long long)i >= n_groups) break;
+        const Group G = groups[order[i]];
         const Com4 ck = com[G.cell];
         const int n = G.count;
         long long nsrc;
-#define PP_CALL(R, Q) pp_group<R, Q>(G, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, accs, T, eps2, enabled, lane)
+#define PP_CALL(R, Q) pp_group<R, Q>(G, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, accs, T, chunk[wl], eps2, enabled, lane)
         if (n <= 8) nsrc = PP_CALL(1, 4);
         else if (n <= 16) nsrc = PP_CALL(1, 2);
         else if (n <= 24) nsrc = PP_CALL(3, 4);
@@ -209,15 +228,29 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pp_pairs, pairs);
 }
 
-template <int R, int Q>
-__device__ __forceinline__ void pc_group(const Group& G, const Com4& ck, const unsigned int* __restrict__ pc,
+// PC for one group with a runtime sink layout (R sinks per lane, Q list splits): the sinks
+// are taken one after another against each staged chunk of cell records, so a single copy of
+// the (large) particle-cell body serves every layout.
+#define PC_RMAX 3
+__device__ __forceinline__ void pc_group(const Group& G, int R, int Q, const Com4& ck, const unsigned int* __restrict__ pc,
                                          const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                          const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                          const float4* __restrict__ rec4, float4* __restrict__ accs, float4* R4,
                                          float4* Z, int* ids, float eps2, int lane)
 {
-    Sinks<R, Q> K;
-    K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
+    const int S = 32 / Q, split = lane / S, slot = lane % S;
+    float ux[PC_RMAX], uy[PC_RMAX], uz[PC_RMAX];
+    float ax[PC_RMAX], ay[PC_RMAX], az[PC_RMAX], ph[PC_RMAX];
+#pragma unroll
+    for (int r = 0; r < PC_RMAX; r++) {
+        ux[r] = uy[r] = uz[r] = 0.0f;
+        ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
+        const int i = slot + r * S;
+        if (r < R && i < G.count) {
+            float m;
+            load_sink(G.first + i, ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
+        }
+    }
     for (int base = 0; base < G.pc_len; base += PC_CHUNK) {
         const int ne = min(PC_CHUNK, G.pc_len - base);
         if (lane < ne) {
@@ -234,54 +267,72 @@ __device__ __forceinline__ void pc_group(const Group& G, const Com4& ck, const u
             R4[i] = rec4[(long long)ids[cl] * (FMM_NREC / 4) + part];
         }
         __syncwarp();
-        for (int j = K.split; j < ne; j += Q) {
-            const float* Rj = reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]);
-            const float4 z = Z[j];
 #pragma unroll
-            for (int r = 0; r < R; r++)
-                fmm_pc_acc(Rj, K.ux[r] - z.x, K.uy[r] - z.y, K.uz[r] - z.z, eps2, K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+        for (int r = 0; r < PC_RMAX; r++) {
+            if (r >= R) break;
+            float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+            const float sx = ux[r], sy = uy[r], sz = uz[r];
+#pragma unroll 1
+            for (int j = split; j < ne; j += Q) {
+                const float4 z = Z[j];
+                fmm_pc_acc(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]), sx - z.x, sy - z.y, sz - z.z,
+                           eps2, bx, by, bz, bp);
+            }
+            ax[r] += bx;
+            ay[r] += by;
+            az[r] += bz;
+            ph[r] += bp;
         }
         __syncwarp();
     }
-    K.reduce();
-    if (K.split == 0) {
 #pragma unroll
-        for (int r = 0; r < R; r++)
-            if (K.v[r]) {
-                const float4 a = accs[K.idx[r]];
-                accs[K.idx[r]] = make_float4(a.x + K.ax[r], a.y + K.ay[r], a.z + K.az[r], a.w + K.ph[r]);
-            }
+    for (int r = 0; r < PC_RMAX; r++) {
+        if (r >= R) break;
+        for (int o = S; o < 32; o <<= 1) {
+            ax[r] += __shfl_xor_sync(FMM_FULL_MASK, ax[r], o);
+            ay[r] += __shfl_xor_sync(FMM_FULL_MASK, ay[r], o);
+            az[r] += __shfl_xor_sync(FMM_FULL_MASK, az[r], o);
+            ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
+        }
+        const int i = slot + r * S;
+        if (split == 0 && i < G.count) {
+            const int s = G.first + i;
+            const float4 a = accs[s];
+            accs[s] = make_float4(a.x + ax[r], a.y + ay[r], a.z + az[r], a.w + ph[r]);
+        }
     }
 }
 
-__global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, long long n_groups,
-                                                 const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
-                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
-                                                 const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                                 const float* __restrict__ rec, float4* __restrict__ accs, float eps2,
-                                                 DevCounters* __restrict__ ctr)
+__global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ order,
+                                                 long long n_groups, const unsigned int* __restrict__ pc,
+                                                 const int* __restrict__ cnact, const Com4* __restrict__ com,
+                                                 const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
+                                                 const float4* __restrict__ off, const float* __restrict__ rec,
+                                                 float4* __restrict__ accs, float eps2, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
     __shared__ int idss[IW][PC_CHUNK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
     unsigned long long pairs = 0;
-    for (long long gi = gw; gi < n_groups; gi += nw) {
-        const Group G = groups[gi];
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(&ctr->pc_work, 1ull);
+        i = __shfl_sync(FMM_FULL_MASK, i, 0);
+        if ((long long)i >= n_groups) break;
+        const Group G = groups[order[i]];
         if (G.pc_len == 0) continue;
         const Com4 ck = com[G.cell];
         const int n = G.count;
-#define PC_CALL(R, Q) pc_group<R, Q>(G, ck, pc, com, bucket_of, bucket_cell, off, rec4, accs, R4s[wl], Zs[wl], idss[wl], eps2, lane)
-        if (n <= 8) PC_CALL(1, 4);
-        else if (n <= 16) PC_CALL(1, 2);
-        else if (n <= 24) PC_CALL(3, 4);
-        else if (n <= 32) PC_CALL(1, 1);
-        else if (n <= 48) PC_CALL(3, 2);
-        else PC_CALL(2, 1);
-#undef PC_CALL
+        int R, Q;
+        if (n <= 8) { R = 1; Q = 4; }
+        else if (n <= 16) { R = 1; Q = 2; }
+        else if (n <= 24) { R = 3; Q = 4; }
+        else if (n <= 32) { R = 1; Q = 1; }
+        else if (n <= 48) { R = 3; Q = 2; }
+        else { R = 2; Q = 1; }
+        pc_group(G, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, accs, R4s[wl], Zs[wl], idss[wl], eps2, lane);
         if (lane == 0) pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)G.pc_len;
     }
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pc_pairs, pairs);
@@ -338,19 +389,57 @@ static unsigned grid_for(long long n_groups)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
+// resident blocks of a kernel on the whole GPU (persistent grids)
+template <typename K>
+static int persistent_blocks(K kernel)
+{
+    int per_sm = 1, sms = 152, device = 0;
+    cudaGetDevice(&device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ITHREADS, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return (per_sm < 1 ? 1 : per_sm) * sms;
+}
+
+// One order for both interaction kernels, most expensive group first (longest-processing-time
+// first for the persistent grids): the key is 16 bits of log2 of the group's FP32 flops
+// (19 per PP pair, FMM_FLOPS_PC per PC pair), descending; two 8-bit radix passes.
+__global__ void k_group_costs(const Group* __restrict__ groups, long long ng, unsigned long long* __restrict__ key,
+                              unsigned int* __restrict__ val)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    const Group G = groups[i];
+    const float flops = (float)G.count * (19.0f * (float)G.pp_src + (float)FMM_FLOPS_PC * (float)G.pc_len) + 1.0f;
+    const float q = fminf(__log2f(flops) * 1024.0f, 65535.0f);  // log2(flops) < 64
+    key[i] = 65535ull - (unsigned long long)q;
+    val[i] = (unsigned int)i;
+}
+
+cudaError_t fmm_launch_group_order(DevTree& t, DevWalk& w, cudaStream_t s)
+{
+    const long long ng = w.n_groups;
+    k_group_costs<<<(unsigned)fmm_ceil_div(ng, 256), 256, 0, s>>>(w.groups, ng, w.gkey, w.order_pp);
+    return fmm_radix_sort_kv(w.gkey, w.gkey_alt, w.order_pp, w.gval_alt, ng, 2, t, s);
+}
+
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s)
 {
-    k_pp<<<grid_for(w.n_groups), ITHREADS, 0, s>>>(w.groups, w.n_groups, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
-                                                   t.bucket_of, t.bucket_cell, t.off, t.accs, a.eps2, a.terms & 1,
-                                                   ctr);
+    static int blocks = 0;
+    if (!blocks) blocks = persistent_blocks(k_pp);
+    cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
+    k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.order_pp, w.n_groups, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
+                                     t.bucket_of, t.bucket_cell, t.off, t.accs, a.eps2, a.terms & 1, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s)
 {
     if (!(a.terms & 2)) return cudaSuccess;
-    k_pc<<<grid_for(w.n_groups), ITHREADS, 0, s>>>(w.groups, w.n_groups, w.pc, t.cnact, t.com, t.bucket_of,
-                                                   t.bucket_cell, t.off, t.rec, t.accs, a.eps2, ctr);
+    static int blocks = 0;
+    if (!blocks) blocks = persistent_blocks(k_pc);
+    cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
+    k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.order_pp, w.n_groups, w.pc, t.cnact, t.com, t.bucket_of,
+                                     t.bucket_cell, t.off, t.rec, t.accs, a.eps2, ctr);
     return cudaGetLastError();
 }
 

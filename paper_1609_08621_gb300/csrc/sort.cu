@@ -242,16 +242,16 @@ cudaError_t fmm_sort_ensure(DevTree& t, long long n)
     return cudaSuccess;
 }
 
-// sorts t.key / t.idx (n elements) in place, using key_alt / idx_alt as ping-pong buffers
-cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s)
+// Stable LSD sort of n (key, value) pairs on the low 8 * passes key bits (passes even): the
+// result is back in ka / va; kb / vb are scratch of the same size.
+cudaError_t fmm_radix_sort_kv(unsigned long long* ka, unsigned long long* kb, unsigned int* va, unsigned int* vb,
+                              long long n, int passes, DevTree& t, cudaStream_t s)
 {
     if (n <= 1) return cudaSuccess;
     cudaError_t e = fmm_sort_ensure(t, n);
     if (e != cudaSuccess) return e;
     int nblk = (int)fmm_ceil_div(n, RS_TILE);
-    unsigned long long *ka = t.key, *kb = t.key_alt;
-    unsigned int *va = t.idx, *vb = t.idx_alt;
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < passes; pass++) {
         int shift = 8 * pass;
         k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ka, n, shift, t.hist, nblk);
         e = fmm_scan_exclusive(t.hist, t.hist, 256LL * nblk, nullptr, t, s);
@@ -264,5 +264,11 @@ cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s)
         va = vb;
         vb = tv;
     }
-    return cudaGetLastError();  // 8 passes: result is back in t.key / t.idx
+    return cudaGetLastError();
+}
+
+// sorts t.key / t.idx (n elements) on all 64 key bits
+cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s)
+{
+    return fmm_radix_sort_kv(t.key, t.key_alt, t.idx, t.idx_alt, n, 8, t, s);
 }

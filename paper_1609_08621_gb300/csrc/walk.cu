@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
         const unsigned long long cl0 = f_cloff[fi];
         const long long ncl = f_cllen[fi];
         long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
+        int srcpp = 0;  // this lane's PP source particles
         bool overflow = false;
         long long base = 0;
         while (base < ncl + nq) {
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             base += avail < 32 ? avail : 32;
             unsigned int e = 0;
             if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
-            int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1;
+            int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1, nsrc_cell = 0;
             bool sleaf = false;
             if (valid) {
                 float cx, cy, cz, ro, lox, loy, loz, hix, hiy, hiz;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
                     c0 = S.d.x;
                     c1 = S.d.y;
                     sfirst = S.d.z;
+                    nsrc_cell = S.d.w;
                     nadd = sleaf ? S.d.w : 2;
                 }
                 const float d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
@@ -148,7 +150,10 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             if (out == OUT_ACCEPT) A[na + __popc(mA & lt)] = e;
             if (out == OUT_DEFER) D[nd + __popc(mD & lt)] = e;
             if (out == OUT_PC) C[npc + __popc(mC & lt)] = e;
-            if (out == OUT_PP) P[npp + __popc(mP & lt)] = e;
+            if (out == OUT_PP) {
+                P[npp + __popc(mP & lt)] = e;
+                srcpp += (e & FMM_PARTICLE_BIT) ? 1 : nsrc_cell;
+            }
             if (out == OUT_OPEN) {
                 long long pos = nq + incl - nadd;
                 if (sleaf) {
@@ -188,6 +193,8 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             if (na > 0) lcells[atomicAdd(&ctr->n_lcells, 1ull)] = k;
         }
         if (kg) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) srcpp += __shfl_xor_sync(FMM_FULL_MASK, srcpp, o);
             unsigned long long po = 0, co = 0, gi = 0;
             if (lane == 0) {
                 po = atomicAdd(&ctr->pp_len, (unsigned long long)npp);
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
                 g.cell = k;
                 g.first = K.d.z;
                 g.count = K.d.w;
-                g.pad = 0;
+                g.pp_src = srcpp;
                 g.pp_off = po;
                 g.pc_off = co;
                 g.pp_len = (int)npp;
