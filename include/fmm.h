@@ -228,6 +228,12 @@ fmm_status fmm_export_lists(const fmm_ctx *ctx, int kind, long long *n_entries, 
  * group's centre of mass, in the order of fmm_multi_index. */
 fmm_status fmm_export_locals(const fmm_ctx *ctx, int *group_cell, float *L, long long capacity);
 
+/* Per walk level of the last solve (the root is level 0), for l < min(*n_levels, capacity):
+ * counts[3l] = sink cells walked, counts[3l+1] = checklist entries they examined (opened
+ * entries included), counts[3l+2] = the largest number examined by one sink.  Any of the
+ * three may be used; counts must hold 3 * capacity values. */
+fmm_status fmm_export_walk_levels(const fmm_ctx *ctx, long long *counts, int capacity, int *n_levels);
+
 /* The 56 multi-indices (a, b, c) of the local coefficients in storage order (168 ints),
  * and the 32 multi-indices of the moment slots (96 ints).  Either may be NULL. */
 fmm_status fmm_multi_index(int *local_idx, int *moment_idx);

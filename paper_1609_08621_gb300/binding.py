@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
         "fmm_export_lists": (i, [vp, i, C.POINTER(ll), vp, vp, vp, ll]),
         "fmm_export_locals": (i, [vp, vp, vp, ll]),
         "fmm_multi_index": (i, [vp, vp]),
+        "fmm_export_walk_levels": (i, [vp, vp, i, C.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,6 +276,12 @@ class Context:
         _check(load().fmm_export_lists(self.h, k, C.byref(n), sink.ctypes.data, first.ctypes.data,
                                        count.ctypes.data, m))
         return sink[:m], first[:m], count[:m]
+
+    def export_walk_levels(self):
+        counts = np.zeros(3 * 256, np.int64)
+        nl = C.c_int()
+        _check(load().fmm_export_walk_levels(self.h, counts.ctypes.data, 256, C.byref(nl)))
+        return counts[:3 * nl.value].reshape(-1, 3)
 
     def export_locals(self):
         g = self.tree_info()["groups"]

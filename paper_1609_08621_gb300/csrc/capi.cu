@@ -126,7 +126,7 @@ static void free_all(fmm_ctx* c)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
     void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off,
-                  w.lcc_len, w.lcells, w.Lg, w.order_pp, w.order_pc, w.gkey, w.gkey_alt, w.gval, w.gval_alt, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
+                  w.lcc_len, w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
     for (void* p : qs)
         if (p) cudaFree(p);
     if (c->ctr) cudaFree(c->ctr);
@@ -341,12 +341,10 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
         CK(alloc(&w.lcells, need_front));
         CK(alloc(&w.groups, need_front));
         CK(alloc(&w.Lg, (long long)FMM_NL * need_front));
-        CK(alloc(&w.order_pp, need_front));
-        CK(alloc(&w.order_pc, need_front));
-        CK(alloc(&w.gkey, need_front));
-        CK(alloc(&w.gkey_alt, need_front));
-        CK(alloc(&w.gval, need_front));
-        CK(alloc(&w.gval_alt, need_front));
+        CK(alloc(&w.cnt_pp, need_front));
+        CK(alloc(&w.cnt_pc, need_front));
+        CK(alloc(&w.base_pp, need_front));
+        CK(alloc(&w.base_pc, need_front));
         w.cap_front = need_front;
         w.cap_groups = need_front;
     }
@@ -452,14 +450,28 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     ia.terms = q.terms;
     ia.accumulate = q.accumulate;
     if (c->w.n_groups > 0) {
-        CK(fmm_launch_group_order(c->t, c->w, s));
-        c->launches += 1 + 2 * 5;
+        // work items: at most one partial chunk per group beyond the full chunks
+        DevWalk& w = c->w;
+        long long need_pp = w.pp_len / FMM_PP_CHUNK + w.n_groups + 1;
+        long long need_pc = w.pc_len / FMM_PC_CHUNK + w.n_groups + 1;
+        if (need_pp > w.cap_item_pp) {
+            CK(alloc(&w.item_pp, need_pp));
+            CK(alloc(&w.part_pp, need_pp * FMM_GMAX));
+            w.cap_item_pp = need_pp;
+        }
+        if (need_pc > w.cap_item_pc) {
+            CK(alloc(&w.item_pc, need_pc));
+            CK(alloc(&w.part_pc, need_pc * FMM_GMAX));
+            w.cap_item_pc = need_pc;
+        }
+        CK(fmm_launch_items(c->t, w, c->ctr, s));
+        c->launches += 2 + 2 * 3;
         CK(fmm_launch_pp(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[3], s));
         CK(fmm_launch_pc(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[4], s));
         CK(fmm_launch_l2p_out(c->t, c->w, c->ctr, ia, acc, pot, n, s));
-        c->launches += (q.terms & 2) ? 3 : 2;
+        c->launches += ((q.terms & 1) ? 1 : 0) + ((q.terms & 2) ? 1 : 0) + 1;
     } else {
         CK(cudaEventRecord(c->ev[3], s));
         CK(cudaEventRecord(c->ev[4], s));
@@ -724,6 +736,19 @@ extern "C" fmm_status fmm_export_locals(const fmm_ctx* c, int* group_cell, float
     CK(cudaStreamSynchronize(s));
     for (size_t i = 0; i < g.size(); i++)
         if (group_cell) group_cell[i] = g[i].cell;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_walk_levels(const fmm_ctx* c, long long* counts, int capacity, int* n_levels)
+{
+    if (!c || !n_levels) return fail(FMM_ERR_ARG, "NULL argument");
+    if (!c->have_solve) return fail(FMM_ERR_STATE, "no solve yet");
+    *n_levels = (int)c->w.n_levels;
+    for (int l = 0; l < capacity && l < (int)c->w.n_levels; l++) {
+        counts[3 * l] = (long long)c->ctr_h->lv_front[l];
+        counts[3 * l + 1] = (long long)c->ctr_h->lv_entries[l];
+        counts[3 * l + 2] = (long long)c->ctr_h->lv_max_entries[l];
+    }
     return FMM_OK;
 }
 

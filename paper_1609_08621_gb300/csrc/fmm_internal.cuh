@@ -48,6 +48,9 @@ struct __align__(16) Group {
     int pp_len, pc_len;
 };
 
+#define FMM_PP_CHUNK 64   // PP list entries per work item
+#define FMM_PC_CHUNK 64   // PC list entries per work item
+#define FMM_GMAX 64       // sink slots per group
 #define FMM_MAX_LEVELS 192  // walk levels: tree depth + 1 (63 key bits + 31 position bits at most)
 
 // Device-side counters and status, one per context.
@@ -62,11 +65,14 @@ struct DevCounters {
     unsigned long long pp_len, pc_len, cc_len;
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
+    unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
     // per walk level: frontier size, work counters of the walk and local kernels, and the
     // number of checklist entries handed to that level
     unsigned long long lv_front[FMM_MAX_LEVELS];
     unsigned long long lv_work[FMM_MAX_LEVELS];
     unsigned long long lv_cl[FMM_MAX_LEVELS];
+    unsigned long long lv_entries[FMM_MAX_LEVELS];      // checklist entries examined (incl. opened)
+    unsigned long long lv_max_entries[FMM_MAX_LEVELS];  // largest per-sink count
 };
 
 // Device buffers of a context.  Capacities are in elements.
@@ -118,10 +124,13 @@ struct DevWalk {
     int *lcc_len = nullptr;
     int *lcells = nullptr;                  // cells with a non-empty local list
     float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
-    // group orders for the interaction kernels (most expensive first) and sort scratch
-    unsigned int *order_pp = nullptr, *order_pc = nullptr;
-    unsigned long long *gkey = nullptr, *gkey_alt = nullptr;
-    unsigned int *gval = nullptr, *gval_alt = nullptr;
+    // work items of the interaction kernels: group g's PP list is cut into chunks of
+    // FMM_PP_CHUNK entries (items base_pp[g] ..), its PC list into chunks of FMM_PC_CHUNK cells;
+    // every item writes one partial result per sink slot, summed per sink in item order
+    unsigned int *cnt_pp = nullptr, *cnt_pc = nullptr, *base_pp = nullptr, *base_pc = nullptr;
+    unsigned int *item_pp = nullptr, *item_pc = nullptr;
+    float4 *part_pp = nullptr, *part_pc = nullptr;
+    long long cap_item_pp = 0, cap_item_pc = 0;
     unsigned int *cl[2] = {nullptr, nullptr};
     unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
     int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry, for export
@@ -172,7 +181,7 @@ struct InteractArgs {
     int terms;
     int accumulate;
 };
-cudaError_t fmm_launch_group_order(DevTree& t, DevWalk& w, cudaStream_t s);
+cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,

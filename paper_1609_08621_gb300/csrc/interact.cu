@@ -11,7 +11,13 @@
 // per bucket or cell (never per interaction: FP64 issue is 1/64 of FP32 on this GPU),
 // and fl(x - com_bucket) is stored per particle by the upward pass.
 //
-// One warp per group.  The warp's 32 lanes are laid out as Q list splits of 32/Q lanes,
+// Work items: each group's PP list is cut into chunks of FMM_PP_CHUNK entries and its PC list
+// into chunks of FMM_PC_CHUNK cells; a persistent grid of warps takes items from an atomic
+// counter, so a group with a very long list no longer sets the kernel's duration.  Each item
+// writes one partial (ax, ay, az, phi) per sink slot; the output kernel adds a sink's
+// partials in item order (deterministic), then the local expansion.
+//
+// One warp per item.  The warp's 32 lanes are laid out as Q list splits of 32/Q lanes,
 // each lane holding R sinks (slots lane%S, +S, ...): a group of n <= R*32/Q sinks uses
 // the (R, Q) of the smallest such slot count, so few lanes idle whatever the group size
 // (groups hold <= g particles, typically 30-64).  Each split takes every Q-th source; the
@@ -111,19 +117,20 @@ struct PPChunk {
 };
 
 template <int R, int Q>
-__device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, const unsigned int* __restrict__ pp,
-                                              const int* __restrict__ cfirst, const int* __restrict__ ccount,
-                                              const Com4* __restrict__ com, const int* __restrict__ bucket_of,
-                                              const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                              float4* __restrict__ accs, float4* T, PPChunk& E, float eps2,
-                                              int enabled, int lane)
+__device__ __forceinline__ long long pp_item(const Group& G, int chunk, const Com4& ck,
+                                             const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
+                                             const int* __restrict__ ccount, const Com4* __restrict__ com,
+                                             const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
+                                             const float4* __restrict__ off, float4* __restrict__ part, float4* T,
+                                             PPChunk& E, float eps2, int lane)
 {
     Sinks<R, Q> K;
     K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
     long long nsrc = 0;
-    if (enabled) {
-        for (int base = 0; base < G.pp_len; base += 32) {
-            const int ne = min(32, G.pp_len - base);
+    const int e0 = chunk * FMM_PP_CHUNK, e1 = min(e0 + FMM_PP_CHUNK, G.pp_len);
+    {
+        for (int base = e0; base < e1; base += 32) {
+            const int ne = min(32, e1 - base);
             int first = 0, cnt = 0;
             float dx = 0.f, dy = 0.f, dz = 0.f;
             if (lane < ne) {
@@ -179,43 +186,49 @@ __device__ __forceinline__ long long pp_group(const Group& G, const Com4& ck, co
             __syncwarp();
         }
         K.reduce();
-        // remove the self term of the potential (the force term is exactly zero)
-        const float ie = rsqrtf(eps2);
+        // remove the self term of the potential (the force term is exactly zero), once per sink
+        if (chunk == 0) {
+            const float ie = rsqrtf(eps2);
 #pragma unroll
-        for (int r = 0; r < R; r++) K.ph[r] += K.m[r] * ie;
+            for (int r = 0; r < R; r++) K.ph[r] += K.m[r] * ie;
+        }
     }
     if (K.split == 0) {
 #pragma unroll
         for (int r = 0; r < R; r++)
-            if (K.v[r]) accs[K.idx[r]] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+            if (K.v[r]) part[K.idx[r] - G.first] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
     }
     return nsrc;
 }
 
-// Persistent: each warp takes the next group of the cost-sorted order until none is left.
-__global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ groups, const unsigned int* __restrict__ order,
-                                                 long long n_groups, const unsigned int* __restrict__ pp,
-                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
-                                                 const int* __restrict__ cnact, const Com4* __restrict__ com,
-                                                 const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
-                                                 const float4* __restrict__ off, float4* __restrict__ accs, float eps2,
-                                                 int enabled, DevCounters* __restrict__ ctr)
+// Persistent: each warp takes the next PP work item until none is left.
+__global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pp,
+                                                 const unsigned int* __restrict__ base_pp,
+                                                 const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
+                                                 const int* __restrict__ ccount, const int* __restrict__ cnact,
+                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                                 const int* __restrict__ bucket_cell, const float4* __restrict__ off,
+                                                 float4* __restrict__ part_pp, float eps2, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 tile[IW][PP_TILE];
     __shared__ PPChunk chunk[IW];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     float4* T = tile[wl];
+    const unsigned long long n_items = *(volatile unsigned int*)&ctr->n_item_pp;
     unsigned long long pairs = 0;
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(&ctr->pp_work, 1ull);
         i = __shfl_sync(FMM_FULL_MASK, i, 0);
-        if ((long long)i >= n_groups) break;
-        const Group G = groups[order[i]];
+        if (i >= n_items) break;
+        const unsigned int gi = item_pp[i];
+        const Group G = groups[gi];
+        const int k = (int)(i - base_pp[gi]);
         const Com4 ck = com[G.cell];
         const int n = G.count;
+        float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
-#define PP_CALL(R, Q) pp_group<R, Q>(G, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, accs, T, chunk[wl], eps2, enabled, lane)
+#define PP_CALL(R, Q) pp_item<R, Q>(G, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane)
         if (n <= 8) nsrc = PP_CALL(1, 4);
         else if (n <= 16) nsrc = PP_CALL(1, 2);
         else if (n <= 24) nsrc = PP_CALL(3, 4);
@@ -232,11 +245,12 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
 // are taken one after another against each staged chunk of cell records, so a single copy of
 // the (large) particle-cell body serves every layout.
 #define PC_RMAX 3
-__device__ __forceinline__ void pc_group(const Group& G, int R, int Q, const Com4& ck, const unsigned int* __restrict__ pc,
-                                         const Com4* __restrict__ com, const int* __restrict__ bucket_of,
-                                         const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                         const float4* __restrict__ rec4, float4* __restrict__ accs, float4* R4,
-                                         float4* Z, int* ids, float eps2, int lane)
+__device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q, const Com4& ck,
+                                        const unsigned int* __restrict__ pc, const Com4* __restrict__ com,
+                                        const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
+                                        const float4* __restrict__ off, const float4* __restrict__ rec4,
+                                        float4* __restrict__ part, float4* R4, float4* Z, int* ids, float eps2,
+                                        int lane)
 {
     const int S = 32 / Q, split = lane / S, slot = lane % S;
     float ux[PC_RMAX], uy[PC_RMAX], uz[PC_RMAX];
@@ -251,8 +265,9 @@ __device__ __forceinline__ void pc_group(const Group& G, int R, int Q, const Com
             load_sink(G.first + i, ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
         }
     }
-    for (int base = 0; base < G.pc_len; base += PC_CHUNK) {
-        const int ne = min(PC_CHUNK, G.pc_len - base);
+    const int e0 = chunk * FMM_PC_CHUNK, e1 = min(e0 + FMM_PC_CHUNK, G.pc_len);
+    for (int base = e0; base < e1; base += PC_CHUNK) {
+        const int ne = min(PC_CHUNK, e1 - base);
         if (lane < ne) {
             const unsigned int c = pc[G.pc_off + base + lane];
             const Com4 cs = com[c];
@@ -295,34 +310,33 @@ __device__ __forceinline__ void pc_group(const Group& G, int R, int Q, const Com
             ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
         }
         const int i = slot + r * S;
-        if (split == 0 && i < G.count) {
-            const int s = G.first + i;
-            const float4 a = accs[s];
-            accs[s] = make_float4(a.x + ax[r], a.y + ay[r], a.z + az[r], a.w + ph[r]);
-        }
+        if (split == 0 && i < G.count) part[i] = make_float4(ax[r], ay[r], az[r], ph[r]);
     }
 }
 
-__global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ order,
-                                                 long long n_groups, const unsigned int* __restrict__ pc,
-                                                 const int* __restrict__ cnact, const Com4* __restrict__ com,
-                                                 const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
-                                                 const float4* __restrict__ off, const float* __restrict__ rec,
-                                                 float4* __restrict__ accs, float eps2, DevCounters* __restrict__ ctr)
+__global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pc,
+                                                 const unsigned int* __restrict__ base_pc,
+                                                 const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
+                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                                 const int* __restrict__ bucket_cell, const float4* __restrict__ off,
+                                                 const float* __restrict__ rec, float4* __restrict__ part_pc,
+                                                 float eps2, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
     __shared__ int idss[IW][PC_CHUNK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
+    const unsigned long long n_items = *(volatile unsigned int*)&ctr->n_item_pc;
     unsigned long long pairs = 0;
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(&ctr->pc_work, 1ull);
         i = __shfl_sync(FMM_FULL_MASK, i, 0);
-        if ((long long)i >= n_groups) break;
-        const Group G = groups[order[i]];
-        if (G.pc_len == 0) continue;
+        if (i >= n_items) break;
+        const unsigned int gi = item_pc[i];
+        const Group G = groups[gi];
+        const int k = (int)(i - base_pc[gi]);
         const Com4 ck = com[G.cell];
         const int n = G.count;
         int R, Q;
@@ -332,21 +346,32 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         else if (n <= 32) { R = 1; Q = 1; }
         else if (n <= 48) { R = 3; Q = 2; }
         else { R = 2; Q = 1; }
-        pc_group(G, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, accs, R4s[wl], Zs[wl], idss[wl], eps2, lane);
-        if (lane == 0) pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)G.pc_len;
+        pc_item(G, k, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
+                idss[wl], eps2, lane);
+        if (lane == 0) {
+            const int nc = min(FMM_PC_CHUNK, G.pc_len - k * FMM_PC_CHUNK);
+            pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nc;
+        }
     }
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pc_pairs, pairs);
 }
 
+// Per group: each sink adds its PP partials and PC partials in item order, then the group's
+// local expansion, and the result goes to the caller's order (active particles only).
 __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ groups, long long n_groups,
                                                       const Com4* __restrict__ com,
                                                       const int* __restrict__ bucket_of,
                                                       const int* __restrict__ bucket_cell,
                                                       const float4* __restrict__ off, const float* __restrict__ Lg,
-                                                      const float4* __restrict__ accs,
+                                                      const unsigned int* __restrict__ cnt_pp,
+                                                      const unsigned int* __restrict__ base_pp,
+                                                      const float4* __restrict__ part_pp,
+                                                      const unsigned int* __restrict__ cnt_pc,
+                                                      const unsigned int* __restrict__ base_pc,
+                                                      const float4* __restrict__ part_pc,
                                                       const unsigned char* __restrict__ sact,
                                                       const unsigned int* __restrict__ perm, long long n,
-                                                      float* __restrict__ acc, float* __restrict__ pot, int use_local)
+                                                      float* __restrict__ acc, float* __restrict__ pot, int terms)
 {
     __shared__ float Ls[IW][FMM_NL];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -357,12 +382,30 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
         const Com4 ck = com[G.cell];
         for (int i = lane; i < FMM_NL; i += 32) Ls[wl][i] = Lg[gi * FMM_NL + i];
         __syncwarp();
+        const unsigned int npp = (terms & 1) ? cnt_pp[gi] : 0u, bpp = base_pp[gi];
+        const unsigned int npc = (terms & 2) ? cnt_pc[gi] : 0u, bpc = base_pc[gi];
         for (int i = lane; i < G.count; i += 32) {
             const int s = G.first + i;
-            float ux, uy, uz, m;
-            load_sink(s, ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
-            float4 a = accs[s];
-            if (use_local) fmm_l2p_acc(Ls[wl], ux, uy, uz, a.x, a.y, a.z, a.w);
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (unsigned int k = 0; k < npp; k++) {
+                const float4 p = part_pp[(unsigned long long)(bpp + k) * FMM_GMAX + i];
+                a.x += p.x;
+                a.y += p.y;
+                a.z += p.z;
+                a.w += p.w;
+            }
+            for (unsigned int k = 0; k < npc; k++) {
+                const float4 p = part_pc[(unsigned long long)(bpc + k) * FMM_GMAX + i];
+                a.x += p.x;
+                a.y += p.y;
+                a.z += p.z;
+                a.w += p.w;
+            }
+            if (terms & 4) {
+                float ux, uy, uz, m;
+                load_sink(s, ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
+                fmm_l2p_acc(Ls[wl], ux, uy, uz, a.x, a.y, a.z, a.w);
+            }
             if (sact[s]) {
                 const unsigned int p = perm[s];
                 acc[p] = a.x;
@@ -400,35 +443,49 @@ static int persistent_blocks(K kernel)
     return (per_sm < 1 ? 1 : per_sm) * sms;
 }
 
-// One order for both interaction kernels, most expensive group first (longest-processing-time
-// first for the persistent grids): the key is 16 bits of log2 of the group's FP32 flops
-// (19 per PP pair, FMM_FLOPS_PC per PC pair), descending; two 8-bit radix passes.
-__global__ void k_group_costs(const Group* __restrict__ groups, long long ng, unsigned long long* __restrict__ key,
-                              unsigned int* __restrict__ val)
+// Work items: per group ceil(pp_len / FMM_PP_CHUNK) PP items and ceil(pc_len / FMM_PC_CHUNK)
+// PC items; exclusive scans give each group's first item, and every item learns its group.
+__global__ void k_item_counts(const Group* __restrict__ groups, long long ng, unsigned int* __restrict__ cnt_pp,
+                              unsigned int* __restrict__ cnt_pc)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ng) return;
     const Group G = groups[i];
-    const float flops = (float)G.count * (19.0f * (float)G.pp_src + (float)FMM_FLOPS_PC * (float)G.pc_len) + 1.0f;
-    const float q = fminf(__log2f(flops) * 1024.0f, 65535.0f);  // log2(flops) < 64
-    key[i] = 65535ull - (unsigned long long)q;
-    val[i] = (unsigned int)i;
+    cnt_pp[i] = (unsigned int)fmm_ceil_div(G.pp_len, FMM_PP_CHUNK);
+    cnt_pc[i] = (unsigned int)fmm_ceil_div(G.pc_len, FMM_PC_CHUNK);
 }
 
-cudaError_t fmm_launch_group_order(DevTree& t, DevWalk& w, cudaStream_t s)
+__global__ void k_item_expand(long long ng, const unsigned int* __restrict__ cnt_pp,
+                              const unsigned int* __restrict__ base_pp, const unsigned int* __restrict__ cnt_pc,
+                              const unsigned int* __restrict__ base_pc, unsigned int* __restrict__ item_pp,
+                              unsigned int* __restrict__ item_pc)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ng) return;
+    for (unsigned int k = 0; k < cnt_pp[i]; k++) item_pp[base_pp[i] + k] = (unsigned int)i;
+    for (unsigned int k = 0; k < cnt_pc[i]; k++) item_pc[base_pc[i] + k] = (unsigned int)i;
+}
+
+cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s)
 {
     const long long ng = w.n_groups;
-    k_group_costs<<<(unsigned)fmm_ceil_div(ng, 256), 256, 0, s>>>(w.groups, ng, w.gkey, w.order_pp);
-    return fmm_radix_sort_kv(w.gkey, w.gkey_alt, w.order_pp, w.gval_alt, ng, 2, t, s);
+    const unsigned blocks = (unsigned)fmm_ceil_div(ng, 256);
+    k_item_counts<<<blocks, 256, 0, s>>>(w.groups, ng, w.cnt_pp, w.cnt_pc);
+    cudaError_t e = fmm_scan_exclusive(w.cnt_pp, w.base_pp, ng, &ctr->n_item_pp, t, s);
+    if (e == cudaSuccess) e = fmm_scan_exclusive(w.cnt_pc, w.base_pc, ng, &ctr->n_item_pc, t, s);
+    if (e != cudaSuccess) return e;
+    k_item_expand<<<blocks, 256, 0, s>>>(ng, w.cnt_pp, w.base_pp, w.cnt_pc, w.base_pc, w.item_pp, w.item_pc);
+    return cudaGetLastError();
 }
 
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s)
 {
+    if (!(a.terms & 1)) return cudaSuccess;
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_pp);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
-    k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.order_pp, w.n_groups, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
-                                     t.bucket_of, t.bucket_cell, t.off, t.accs, a.eps2, a.terms & 1, ctr);
+    k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
+                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, a.eps2, ctr);
     return cudaGetLastError();
 }
 
@@ -438,8 +495,8 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_pc);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
-    k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.order_pp, w.n_groups, w.pc, t.cnact, t.com, t.bucket_of,
-                                     t.bucket_cell, t.off, t.rec, t.accs, a.eps2, ctr);
+    k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.com, t.bucket_of,
+                                     t.bucket_cell, t.off, t.rec, w.part_pc, a.eps2, ctr);
     return cudaGetLastError();
 }
 
@@ -448,7 +505,7 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
 {
     (void)ctr;
     k_l2p_out<<<grid_for(w.n_groups), ITHREADS, 0, s>>>(w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell,
-                                                        t.off, w.Lg, t.accs, t.sact, t.idx, n, acc, pot,
-                                                        (a.terms & 4) ? 1 : 0);
+                                                        t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc,
+                                                        w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
     return cudaGetLastError();
 }

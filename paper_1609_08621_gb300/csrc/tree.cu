@@ -326,7 +326,6 @@ __global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ 
         float Mq[FMM_NMOM];
 #pragma unroll
         for (int i = 0; i < FMM_NMOM; i++) Mq[i] = 0.0f;
-        double bound = 0.0;
         for (int h = 0; h < 2; h++) {
             int ch = h ? c1 : c0;
             Com4 ac = h ? a1 : a0;
@@ -336,14 +335,12 @@ __global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ 
             for (int i = 0; i < FMM_NMOM; i++) Mc[i] = __ldcg(src + i);
             double tx = ac.x - px, ty = ac.y - py, tz = ac.z - pz;
             fmm_m2m_acc(Mc, __double2float_rn(tx), __double2float_rn(ty), __double2float_rn(tz), Mq);
-            bound = fmax(bound, sqrt(tx * tx + ty * ty + tz * tz) + __ldcg(&bmax[ch]));
         }
         com[p] = make_com4(px, py, pz, Mp);
         for (int a = 0; a < 3; a++) {
             clo[3 * p + a] = fmin(__ldcg(&clo[3 * c0 + a]), __ldcg(&clo[3 * c1 + a]));
             chi[3 * p + a] = fmax(__ldcg(&chi[3 * c0 + a]), __ldcg(&chi[3 * c1 + a]));
         }
-        bmax[p] = bound;  // upper bound; replaced by the exact value in k_bmax_exact
         cnact[p] = __ldcg(&cnact[c0]) + __ldcg(&cnact[c1]);
         write_record(rec + (long long)p * FMM_NREC, Mq);
         p = cparent[p];
@@ -353,47 +350,75 @@ __global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ 
 // Exact b_max of every internal cell: the distance from its centre of mass p to the farthest
 // of its particles, in FP64 (the same operations as a brute-force scan, so the value is the
 // exact one).  One thread per cell runs a branch-and-bound descent of the cell's subtree:
-//   lb = a lower bound of the answer: 0.999998 x any FP32 distance from p to a sub-cell's
-//        centre of mass (inside the hull of the particles) or to a particle;
-//   a sub-cell is skipped when (FP32 distance to its centre + its b_max bound) x 1.000002 < lb;
+//   lb = a lower bound of the answer: 0.999998 x the largest distance from p to a face of
+//        the cell's bounding box along an axis (a particle lies on that face), raised by the
+//        FP32 distances of the particles visited;
+//   ub(node) = the distance from p to the farthest corner of the node's bounding box, an
+//        upper bound of any of its particles' distances; a node is skipped when
+//        ub x 1.000002 < lb, and the child with the larger ub is visited first;
 //   a particle of a visited bucket gets its FP64 distance only if its FP32 distance could
 //   reach lb.
-// FP32 distances are formed from fl(com_node - p) (FP64 difference, rounded) plus the
-// particle's stored offset from its bucket centre, so their relative error is below 1e-6 of
-// the cell's b_max; the 2e-6 margins therefore never discard the farthest particle.  Only a
-// handful of buckets per cell reach the FP64 stage (FP64 issue is 1/64 of FP32 here).
-// bmax[] holds exact values for buckets and the upward pass's upper bounds for internal cells;
-// threads may read either a bound or an exact value of another cell, both valid bounds.
+// FP32 distances are formed from fl(com_bucket - p) (FP64 difference, rounded) plus the
+// particle's stored offset from its bucket centre, and bounding-box offsets from fl(lo - p),
+// fl(hi - p); their relative errors are below 1e-6, so the 2e-6 margins never discard the
+// farthest particle.  The bounds do not depend on other cells' b_max, so every cell is
+// independent.
 #define BMAX_STACK 128
+
+__device__ __forceinline__ float box_far(const double* __restrict__ clo, const double* __restrict__ chi, int nd,
+                                         const Com4& p)
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double pa = a == 0 ? p.x : (a == 1 ? p.y : p.z);
+        const float e = fmaxf(fabsf(__double2float_rn(clo[3 * nd + a] - pa)), fabsf(__double2float_rn(chi[3 * nd + a] - pa)));
+        s = fmaf(e, e, s);
+    }
+    return sqrtf(s) * (1.0f + 2e-6f);
+}
 
 __global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __restrict__ cfirst,
                                                     const int* __restrict__ ccount, const int* __restrict__ cchild,
-                                                    const Com4* __restrict__ com, const float4* __restrict__ off,
+                                                    const Com4* __restrict__ com, const double* __restrict__ clo,
+                                                    const double* __restrict__ chi, const float4* __restrict__ off,
                                                     const double* __restrict__ sx, const double* __restrict__ sy,
-                                                    const double* __restrict__ sz, double* bmax,
+                                                    const double* __restrict__ sz, double* __restrict__ bmax,
                                                     unsigned int* __restrict__ status)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     if (cchild[2 * c] < 0) return;  // buckets are exact already
     const Com4 p = com[c];
-    int stack[BMAX_STACK];
-    int sp = 0;
-    stack[sp++] = cchild[2 * c];
-    stack[sp++] = cchild[2 * c + 1];
     float lb = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double pa = a == 0 ? p.x : (a == 1 ? p.y : p.z);
+        lb = fmaxf(lb, fmaxf(fabsf(__double2float_rn(clo[3 * c + a] - pa)), fabsf(__double2float_rn(chi[3 * c + a] - pa))));
+    }
+    lb *= (1.0f - 2e-6f);
+    int stk[BMAX_STACK];
+    float sub[BMAX_STACK];
+    int sp = 0;
+    {
+        const int c0 = cchild[2 * c], c1 = cchild[2 * c + 1];
+        const float u0 = box_far(clo, chi, c0, p), u1 = box_far(clo, chi, c1, p);
+        const bool first0 = u0 >= u1;  // the larger bound is popped first
+        stk[sp] = first0 ? c1 : c0;
+        sub[sp++] = first0 ? u1 : u0;
+        stk[sp] = first0 ? c0 : c1;
+        sub[sp++] = first0 ? u0 : u1;
+    }
     double best2 = 0.0;
     while (sp > 0) {
-        const int nd = stack[--sp];
-        const Com4 cm = com[nd];
-        const float dx = __double2float_rn(cm.x - p.x), dy = __double2float_rn(cm.y - p.y),
-                    dz = __double2float_rn(cm.z - p.z);
-        const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-        lb = fmaxf(lb, d * (1.0f - 2e-6f));
-        const float ub = d + __double2float_ru(bmax[nd]);
-        if (ub * (1.0f + 2e-6f) < lb) continue;
+        --sp;
+        const int nd = stk[sp];
+        if (sub[sp] < lb) continue;
         const int c0 = cchild[2 * nd];
         if (c0 < 0) {
+            const Com4 cm = com[nd];
+            const float dx = __double2float_rn(cm.x - p.x), dy = __double2float_rn(cm.y - p.y),
+                        dz = __double2float_rn(cm.z - p.z);
             const int f = cfirst[nd], cnt = ccount[nd];
             for (int j = f; j < f + cnt; j++) {
                 const float4 o = off[j];
@@ -409,8 +434,13 @@ __global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __rest
                 atomicOr(status, FMM_DEV_ERR_NUMERIC);
                 return;
             }
-            stack[sp++] = c0;
-            stack[sp++] = cchild[2 * nd + 1];
+            const int c1 = cchild[2 * nd + 1];
+            const float u0 = box_far(clo, chi, c0, p), u1 = box_far(clo, chi, c1, p);
+            const bool first0 = u0 >= u1;
+            stk[sp] = first0 ? c1 : c0;
+            sub[sp++] = first0 ? u1 : u0;
+            stk[sp] = first0 ? c0 : c1;
+            sub[sp++] = first0 ? u0 : u1;
         }
     }
     bmax[c] = __dsqrt_rn(best2);
@@ -434,8 +464,9 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
     k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
                                                               t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact, t.com, t.clo,
                                                               t.chi, t.bmax, t.cnact, t.rec, t.off, t.arrive);
-    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.com, t.off, t.sx,
-                                                                  t.sy, t.sz, t.bmax, &ctr->status);
+    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.com, t.clo,
+                                                                  t.chi, t.off, t.sx, t.sy, t.sz, t.bmax,
+                                                                  &ctr->status);
     return cudaGetLastError();
 }
 

@@ -174,6 +174,10 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
         }
+        if (lane == 0) {
+            atomicAdd(&ctr->lv_entries[level], (unsigned long long)(ncl + nq));
+            atomicMax(&ctr->lv_max_entries[level], (unsigned long long)(ncl + nq));
+        }
         __syncwarp();
         // local-expansion entries of this sink
         unsigned long long off = 0;
