@@ -150,6 +150,16 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const double *pos, const float *mass, co
 fmm_status fmm_compute_forces(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,
                               long long n, double eps, double theta, float *acc, float *pot);
 
+/* Force solve of several independent isolated boxes in one pass (one tree build, one walk and
+ * one launch of every interaction kernel for all boxes).  Box b holds the particles
+ * [box_offsets[b], box_offsets[b+1]) of the concatenated SoA arrays; each box is its own unit
+ * box [0,1)^3 and its particles feel only each other.  box_offsets: HOST array of nbox + 1
+ * non-decreasing values from 0 to n; 1 <= nbox <= 256.  Other arguments, outputs and
+ * semantics as for fmm_compute_forces; every box's results equal those of solving it alone. */
+fmm_status fmm_compute_forces_batch(fmm_ctx *ctx, const double *pos, const float *mass,
+                                    const unsigned char *active, long long n, const long long *box_offsets,
+                                    int nbox, double eps, double theta, float *acc, float *pot);
+
 /* Same as fmm_compute_forces with HOST buffers: pos (3N doubles), mass (N floats),
  * active (N bytes or NULL) are copied to device memory owned by the context, and
  * acc (3N floats) / pot (N floats or NULL) are copied back before returning. */

@@ -75,6 +75,7 @@ def load(build_if_missing: bool = True):
         "fmm_build_tree": (i, [vp, vp, vp, vp, ll, C.POINTER(fmm_params)]),
         "fmm_compute_forces": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
         "fmm_compute_forces_host": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
+        "fmm_compute_forces_batch": (i, [vp, vp, vp, vp, ll, vp, i, d, d, vp, vp]),
         "fmm_kick_drift": (i, [vp, vp, vp, vp, vp, vp, ll, d, d, i, i, i]),
         "fmm_assign_rungs": (i, [vp, vp, vp, ll, d, d, i]),
         "fmm_get_stats": (i, [vp, C.POINTER(fmm_stats)]),
@@ -208,6 +209,19 @@ class Context:
                                          _ptr(active, torch.uint8, n, "active", True), n, float(eps), float(theta),
                                          _ptr(acc, torch.float32, 3 * n, "acc"),
                                          _ptr(pot, torch.float32, n, "pot", True)))
+
+    def compute_forces_batch(self, pos, mass, box_offsets, eps, theta, acc, pot=None, active=None):
+        """Several isolated boxes in one solve; box_offsets: int64 numpy array of nbox + 1 offsets."""
+        import torch
+
+        n = mass.numel()
+        off = np.ascontiguousarray(box_offsets, dtype=np.int64)
+        _check(load().fmm_compute_forces_batch(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                               _ptr(mass, torch.float32, n, "mass"),
+                                               _ptr(active, torch.uint8, n, "active", True), n, off.ctypes.data,
+                                               off.size - 1, float(eps), float(theta),
+                                               _ptr(acc, torch.float32, 3 * n, "acc"),
+                                               _ptr(pot, torch.float32, n, "pot", True)))
 
     def compute_forces_host(self, pos, mass, eps, theta, acc, pot=None, active=None):
         """Host (numpy) buffers; copies happen inside the library call."""

@@ -121,7 +121,7 @@ static void free_all(fmm_ctx* c)
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
                   t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.L, t.scan_part, t.hist};
+                  t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
@@ -133,6 +133,7 @@ static void free_all(fmm_ctx* c)
     if (c->totals) cudaFree(c->totals);
     if (c->seed) cudaFree(c->seed);
     if (c->ctr_h) cudaFreeHost(c->ctr_h);
+    if (t.box_off_h) cudaFreeHost(t.box_off_h);
     if (c->totals_h) cudaFreeHost(c->totals_h);
     void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact};
     for (void* p : hs)
@@ -198,7 +199,7 @@ extern "C" fmm_status fmm_get_params(const fmm_ctx* c, fmm_params* p)
     return FMM_OK;
 }
 
-static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket)
+static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
 {
     DevTree& t = c->t;
     if (n > t.cap_n) {
@@ -225,7 +226,9 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket)
         CK(alloc(&t.keep, 2 * cap));
         t.cap_n = cap;
     }
-    long long need_cells = 6 * n / (bucket + 1) + 8;
+    // nodes holding > b particles form a binary tree with at most n / (b + 1) leaves, each with at
+    // most two bucket children; several boxes add their top levels (< 2 nbox nodes)
+    long long need_cells = 6 * n / (bucket + 1) + 8 + 2LL * nbox;
     if (need_cells > 2 * n + 1) need_cells = 2 * n + 1;
     if (need_cells > t.cap_cells) {
         long long cap = need_cells;
@@ -259,17 +262,58 @@ static fmm_status read_status(fmm_ctx* c, const char* where)
     return FMM_OK;
 }
 
+static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int nbox)
+{
+    DevTree& t = c->t;
+    if (nbox < 1 || nbox > 256) return fail(FMM_ERR_ARG, "nbox must be in [1, 256], got %d", nbox);
+    if (off) {
+        if (off[0] != 0 || off[nbox] != n) return fail(FMM_ERR_ARG, "box offsets must start at 0 and end at n");
+        for (int b = 0; b < nbox; b++)
+            if (off[b + 1] < off[b]) return fail(FMM_ERR_ARG, "box offsets must not decrease");
+    } else if (nbox != 1) {
+        return fail(FMM_ERR_ARG, "box offsets are required for several boxes");
+    }
+    t.nbox = nbox;
+    if (nbox == 1) return FMM_OK;
+    if (nbox + 1 > t.cap_box) {
+        CK(alloc(&t.box_off, nbox + 1));
+        CK(alloc(&t.box_root, nbox + 1));
+        if (t.box_off_h) cudaFreeHost(t.box_off_h);
+        t.box_off_h = nullptr;
+        CK(cudaMallocHost(&t.box_off_h, sizeof(long long) * (size_t)(nbox + 1)));
+        t.cap_box = nbox + 1;
+    }
+    if (n > t.cap_box_n) {
+        CK(alloc(&t.sbox, n));
+        CK(alloc(&t.key_orig, n));
+        t.cap_box_n = n;
+    }
+    memcpy(t.box_off_h, off, sizeof(long long) * (size_t)(nbox + 1));
+    CK(cudaMemcpyAsync(t.box_off, t.box_off_h, sizeof(long long) * (size_t)(nbox + 1), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemsetAsync(t.box_root, 0xff, sizeof(int) * (size_t)nbox, c->stream));
+    return FMM_OK;
+}
+
 static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
-                             long long n, int bucket)
+                             long long n, int bucket, const long long* box_off = nullptr, int nbox = 1)
 {
     DevTree& t = c->t;
     cudaStream_t s = c->stream;
-    fmm_status st = ensure_tree(c, n, bucket);
+    fmm_status st = ensure_tree(c, n, bucket, nbox);
+    if (st != FMM_OK) return st;
+    st = set_boxes(c, n, box_off, nbox);
     if (st != FMM_OK) return st;
     c->have_tree = false;
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
     CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
-    CK(fmm_radix_sort(t, n, s));
+    if (nbox > 1) {
+        CK(fmm_launch_box_sort(t, n, s));
+        c->launches += 8 * 5 + 1 + 2 * 5 + 1;
+    } else {
+        CK(fmm_radix_sort(t, n, s));
+        c->launches += 8 * 5;
+    }
     CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s));
     CK(fmm_launch_radix_tree(t, n, bucket, s));
     CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
@@ -289,9 +333,13 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     t.n_buckets = c->totals_h[1];
     if (t.n_cells > t.cap_cells) return fail(FMM_ERR_CUDA, "internal: %lld cells exceed capacity", t.n_cells);
     CK(fmm_launch_upward(t, n, bucket, c->ctr, s));
-    // keys, 8 x (histogram, 3-kernel scan, scatter), gather, radix tree + keep, scan, cells, scan,
-    // bucket index, bucket cells, upward, exact b_max
-    c->launches += 1 + 8 * 5 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
+    if (nbox > 1) {
+        CK(fmm_launch_box_roots(t, s));
+        c->launches += 1;
+    }
+    // keys, gather, radix tree + keep, scan, cells, scan, bucket index, depth, bucket cells,
+    // upward, exact b_max
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
     t.depth = (int)c->ctr_h->depth;
     c->have_tree = true;
     c->theta_nodes = -1.0f;
@@ -392,6 +440,8 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
         fmm_status st = ensure_walk(c, n, scale);
         if (st != FMM_OK) return st;
         CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
+        // cells above a box's root are never walked: their local lists must read as empty
+        CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.n_cells, s));
         CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
         CK(fmm_launch_walk_seed(t, w, c->ctr, s));
         c->launches += 1;
@@ -423,7 +473,8 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
 }
 
 static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
-                        double eps, double theta, float* acc, float* pot)
+                        double eps, double theta, float* acc, float* pot, const long long* box_off = nullptr,
+                        int nbox = 1)
 {
     fmm_params q = c->params;
     q.eps = eps;
@@ -436,7 +487,7 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     memset(&c->stats, 0, sizeof c->stats);
     c->launches = 0;
     CK(cudaEventRecord(c->ev[0], s));
-    st = build_tree(c, pos, mass, active, n, q.bucket);
+    st = build_tree(c, pos, mass, active, n, q.bucket, box_off, nbox);
     if (st != FMM_OK) return st;
     c->stats.n_active = (long long)c->ctr_h->n_active;
     CK(fmm_launch_nodes(c->t, theta, s));
@@ -521,6 +572,16 @@ extern "C" fmm_status fmm_compute_forces(fmm_ctx* c, const double* pos, const fl
     fmm_status st = check_common(c, pos, mass, n);
     if (st != FMM_OK) return st;
     return solve(c, pos, mass, active, n, eps, theta, acc, pot);
+}
+
+extern "C" fmm_status fmm_compute_forces_batch(fmm_ctx* c, const double* pos, const float* mass,
+                                               const unsigned char* active, long long n, const long long* box_offsets,
+                                               int nbox, double eps, double theta, float* acc, float* pot)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!box_offsets) return fail(FMM_ERR_ARG, "box_offsets must not be NULL");
+    return solve(c, pos, mass, active, n, eps, theta, acc, pot, box_offsets, nbox);
 }
 
 extern "C" fmm_status fmm_compute_forces_host(fmm_ctx* c, const double* pos, const float* mass,

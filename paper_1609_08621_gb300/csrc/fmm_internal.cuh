@@ -106,6 +106,15 @@ struct DevTree {
     float *rec = nullptr;        // FMM_NREC per cell
     WalkNode *node = nullptr;
     float *L = nullptr;          // FMM_NL per cell: own local expansion of walked cells
+    // several independent boxes: box b holds sorted particles [box_off[b], box_off[b+1])
+    int nbox = 1;
+    long long *box_off = nullptr;            // device, nbox + 1
+    long long *box_off_h = nullptr;          // pinned copy
+    int *box_root = nullptr;                 // device, nbox: the cell spanning the box
+    long long cap_box = 0;
+    unsigned long long *sbox = nullptr;      // sorted box id per particle (several boxes only)
+    unsigned long long *key_orig = nullptr;  // Morton keys in input order (several boxes only)
+    long long cap_box_n = 0;
     // scan scratch
     unsigned int *scan_part = nullptr;
     long long cap_scan_part = 0;
@@ -161,6 +170,8 @@ cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s);
 cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_box_sort(DevTree& t, long long n, cudaStream_t s);
+cudaError_t fmm_launch_box_roots(DevTree& t, cudaStream_t s);
 
 // walk.cu
 struct WalkArgs {

@@ -101,34 +101,44 @@ cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, 
 
 // ---------------------------------------------------------------- radix tree
 
-// length of the common prefix of the augmented keys (key, position); -1 outside [0, n)
-__device__ __forceinline__ int delta(const unsigned long long* __restrict__ k, int n, int i, long long j)
+// length of the common prefix of the augmented keys (box, key, position); -1 outside [0, n).
+// With several boxes the 8-bit box id is the most significant part, so every box is one
+// subtree of the radix tree; with one box (box == NULL) it is absent.
+__device__ __forceinline__ int delta(const unsigned long long* __restrict__ k, const unsigned long long* __restrict__ box,
+                                     int n, int i, long long j)
 {
     if (j < 0 || j >= n) return -1;
+    int base = 0;
+    if (box) {
+        unsigned long long ba = box[i], bb = box[j];
+        if (ba != bb) return __clzll(ba ^ bb) - 56;
+        base = 8;
+    }
     unsigned long long a = k[i], b = k[j];
-    if (a != b) return __clzll(a ^ b);
-    return 64 + __clz((unsigned int)(i ^ (int)j));
+    if (a != b) return base + __clzll(a ^ b);
+    return base + 64 + __clz((unsigned int)(i ^ (int)j));
 }
 
-__global__ void k_radix_tree(const unsigned long long* __restrict__ key, int n, int* __restrict__ ifirst,
+__global__ void k_radix_tree(const unsigned long long* __restrict__ key, const unsigned long long* __restrict__ box,
+                             int n, int* __restrict__ ifirst,
                              int* __restrict__ ilast, int* __restrict__ ileft, int* __restrict__ iright,
                              int* __restrict__ nparent)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    int d = (delta(key, n, i, i + 1) - delta(key, n, i, i - 1)) > 0 ? 1 : -1;
-    int dmin = delta(key, n, i, i - d);
+    int d = (delta(key, box, n, i, i + 1) - delta(key, box, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = delta(key, box, n, i, i - d);
     long long lmax = 2;
-    while (delta(key, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    while (delta(key, box, n, i, i + lmax * d) > dmin) lmax <<= 1;
     long long l = 0;
     for (long long t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(key, n, i, i + (l + t) * d) > dmin) l += t;
+        if (delta(key, box, n, i, i + (l + t) * d) > dmin) l += t;
     int j = (int)(i + l * d);
-    int dnode = delta(key, n, i, j);
+    int dnode = delta(key, box, n, i, j);
     long long s = 0;
     for (long long div = 2;; div <<= 1) {
         long long t = (l + div - 1) / div;
-        if (delta(key, n, i, i + (s + t) * d) > dnode) s += t;
+        if (delta(key, box, n, i, i + (s + t) * d) > dnode) s += t;
         if (t <= 1) break;
     }
     int gamma = (int)(i + s * d + (d < 0 ? -1 : 0));
@@ -227,7 +237,8 @@ cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStrea
 {
     int ni = (int)n;
     if (ni > 1)
-        k_radix_tree<<<(unsigned)fmm_ceil_div(ni - 1, TB), TB, 0, s>>>(t.key, ni, t.ifirst, t.ilast, t.ileft,
+        k_radix_tree<<<(unsigned)fmm_ceil_div(ni - 1, TB), TB, 0, s>>>(t.key, t.nbox > 1 ? t.sbox : nullptr, ni,
+                                                                       t.ifirst, t.ilast, t.ileft,
                                                                        t.iright, t.nparent);
     k_keep<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.nparent, ni, bucket, t.keep);
     return cudaGetLastError();
@@ -515,5 +526,70 @@ __global__ void k_depth(const unsigned int* __restrict__ ncell, const int* __res
 cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s)
 {
     k_depth<<<(unsigned)fmm_ceil_div(t.cap_cells, TB), TB, 0, s>>>(ncell_dev, t.cparent, ctr);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- several boxes
+
+__device__ __forceinline__ int box_of(const long long* __restrict__ off, int nbox, long long i)
+{
+    int lo = 0, hi = nbox - 1;  // largest b with off[b] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// after the Morton sort: box id of every sorted particle, as the key of a second stable sort
+__global__ void k_box_keys(const long long* __restrict__ off, int nbox, const unsigned int* __restrict__ idx,
+                           long long n, unsigned long long* __restrict__ bkey)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bkey[i] = (unsigned long long)box_of(off, nbox, idx[i]);
+}
+
+// final order is (box, key, input index): Morton keys follow the permutation
+__global__ void k_regather_keys(const unsigned long long* __restrict__ korig, const unsigned int* __restrict__ idx,
+                                long long n, unsigned long long* __restrict__ key)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = korig[idx[i]];
+}
+
+// the cell spanning exactly each box's particles (the box's own root)
+__global__ void k_box_roots(int ncell, const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                            const long long* __restrict__ off, int nbox, int* __restrict__ box_root)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const long long f = cfirst[c];
+    const int b = box_of(off, nbox, f);
+    if (off[b] == f && off[b + 1] - f == ccount[c]) box_root[b] = c;
+}
+
+// Stable sort of all boxes' particles by (box, Morton key): Morton keys first (8 passes), then
+// the box ids (2 passes); t.key_orig keeps the keys in input order.
+cudaError_t fmm_launch_box_sort(DevTree& t, long long n, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(t.key_orig, t.key, sizeof(unsigned long long) * (size_t)n,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = fmm_radix_sort(t, n, s);
+    if (e != cudaSuccess) return e;
+    k_box_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(t.box_off, t.nbox, t.idx, n, t.sbox);
+    e = fmm_radix_sort_kv(t.sbox, t.key_alt, t.idx, t.idx_alt, n, 2, t, s);
+    if (e != cudaSuccess) return e;
+    k_regather_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(t.key_orig, t.idx, n, t.key);
+    return cudaGetLastError();
+}
+
+cudaError_t fmm_launch_box_roots(DevTree& t, cudaStream_t s)
+{
+    int nc = (int)t.n_cells;
+    k_box_roots<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(nc, t.cfirst, t.ccount, t.box_off, t.nbox, t.box_root);
     return cudaGetLastError();
 }

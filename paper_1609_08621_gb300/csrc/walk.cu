@@ -389,21 +389,29 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
     }
 }
 
-// level 0 of the walk: the root as the only sink, with the root on its checklist (no sink
-// at all when no particle is active)
+// level 0 of the walk: every box's root cell as a sink, with that root alone on its checklist
+// (isolated boxes: sources of other boxes are never seen); boxes without an active particle
+// are not walked
 __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl,
-                            const int* __restrict__ cnact, DevCounters* ctr)
+                            const int* __restrict__ cnact, const int* __restrict__ box_root, int nbox,
+                            DevCounters* ctr)
 {
-    f_cell[0] = 0;
-    f_cloff[0] = 0;
-    f_cllen[0] = 1;
-    cl[0] = 0u;
-    ctr->lv_front[0] = cnact[0] > 0 ? 1ull : 0ull;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const int r = box_root ? box_root[b] : 0;
+    if (r < 0 || cnact[r] <= 0) return;  // an empty box has no root cell
+    const unsigned long long k = atomicAdd(&ctr->lv_front[0], 1ull);
+    f_cell[k] = r;
+    f_cloff[k] = k;
+    f_cllen[k] = 1;
+    cl[k] = (unsigned int)r;
 }
 
 cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s)
 {
-    k_walk_seed<<<1, 1, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0], t.cnact, ctr);
+    k_walk_seed<<<(unsigned)fmm_ceil_div(t.nbox, 128), 128, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0],
+                                                                     t.cnact, t.nbox > 1 ? t.box_root : nullptr,
+                                                                     t.nbox, ctr);
     return cudaGetLastError();
 }
 
