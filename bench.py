@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="nfw2m", choices=["nfw2m", "plummer4096", "rungs16m"])
+    ap.add_argument("--workload", default="nfw2m", choices=["nfw2m", "plummer4096", "batch64", "rungs16m"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
@@ -148,25 +148,187 @@ def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
 
 
 def run_reference(args, rank, world):
+    """The CPU oracle as it stands, timed on the host cores on bounded samples of the workload."""
     if rank != 0:
         return
-    pos, mass, eps, theta = workload(args.workload, 0, args.n)
+    if args.workload == "batch64":
+        from paper_1609_08621_gb300 import synth
+
+        w = synth.WORKLOADS["batch64"]
+        boxes, off = synth.batch_boxes(w["boxes"], w["seed"])
+        b = int(np.argmax(np.diff(off)))
+        pos, mass = boxes[b]
+        eps, theta = w["eps"], w["theta"]
+        frac = args.cpu_sample or min(1.0, 1024.0 / mass.size)
+        cfg = {"workload": "batch64", "sample_box": b, "n": int(mass.size), "eps": eps, "theta": theta}
+    else:
+        pos, mass, eps, theta = workload(args.workload, 0, args.n)
+        frac = args.cpu_sample or min(1.0, 1024.0 / mass.size)
+        cfg = {"workload": args.workload, "n": int(mass.size), "eps": eps, "theta": theta}
     steps = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(pos, mass, eps, theta, frac=args.cpu_sample or min(1.0, 1024.0 / mass.size))
+        r = cpu_baseline(pos, mass, eps, theta, frac=frac)
         if k >= args.warmup:
             steps.append(r)
     v = float(np.mean([s["value"] for s in steps]))
     sec = float(np.mean([s["seconds"] for s in steps]))
     line = {"impl": "reference", "metric": "interactions/s (PP + PC) per force solve", "value": v,
-            "unit": "interactions/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "unit": "interactions/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(mass.size), "eps": eps, "theta": theta},
+            "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {k: steps[-1][k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     line["cpu_baseline"]["value"] = v
     print(json.dumps(line), flush=True)
+
+
+class Box:
+    """One box (nfw2m, plummer4096): a step is one force solve plus one rung-0 kick-drift."""
+
+    def __init__(self, args, rank, dev, ctx):
+        import torch
+
+        self.pos, self.mass, self.eps, self.theta = workload(args.workload, rank, args.n)
+        n = self.n = self.mass.size
+        self.ctx, self.dev = ctx, dev
+        self.tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(dev)
+        self.tmass = torch.from_numpy(self.mass).to(dev)
+        self.vel = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+        self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.rung = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.act = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.dt0 = 1e-5  # tiny base step: the box barely changes, so every step solves the same workload
+        self.config = {"workload": args.workload, "n": int(n), "eps": self.eps, "theta": self.theta, "bucket": 16,
+                       "group": 64, "l2": "inputs and tree larger than L2 are rebuilt every step"}
+
+    def step(self, k):
+        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+        self.ctx.kick_drift(self.tpos, self.vel, self.acc, self.rung, self.act, self.eps, self.dt0, 0, 0,
+                            1 if k > 0 else 0)
+
+    def e2e(self, steps):
+        """Through fmm_compute_forces_host: host inputs in, host results out, copies timed."""
+        import torch
+
+        hpos = torch.from_numpy(self.pos.reshape(-1).copy()).pin_memory().numpy()
+        hmass = torch.from_numpy(self.mass.copy()).pin_memory().numpy()
+        hacc = torch.zeros(3 * self.n, dtype=torch.float32).pin_memory().numpy()
+        hpot = torch.zeros(self.n, dtype=torch.float32).pin_memory().numpy()
+        for _ in range(2):
+            self.ctx.compute_forces_host(hpos, hmass, self.eps, self.theta, hacc, hpot)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            self.ctx.compute_forces_host(hpos, hmass, self.eps, self.theta, hacc, hpot)
+        dt = (time.perf_counter() - t0) / steps
+        return dt, int(hpos.nbytes + hmass.nbytes), int(hacc.nbytes + hpot.nbytes)
+
+    def cpu_sample(self, frac):
+        return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac)
+
+
+class Batch:
+    """64 independent boxes of N ~ U[32^3, 96^3] (Plummer-clustered): one batched solve per step."""
+
+    def __init__(self, args, rank, dev, ctx):
+        import torch
+
+        from paper_1609_08621_gb300 import synth
+
+        w = synth.WORKLOADS["batch64"]
+        boxes, self.off = synth.batch_boxes(w["boxes"], w["seed"] + 1000 * rank)
+        self.boxes = boxes
+        self.pos = np.concatenate([b[0] for b in boxes], axis=1)
+        self.mass = np.concatenate([b[1] for b in boxes])
+        self.eps, self.theta = w["eps"], w["theta"]
+        n = self.n = self.mass.size
+        self.ctx, self.dev = ctx, dev
+        self.tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(dev)
+        self.tmass = torch.from_numpy(self.mass).to(dev)
+        self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.config = {"workload": "batch64", "boxes": int(w["boxes"]), "n": int(n), "eps": self.eps,
+                       "theta": self.theta, "bucket": 16, "group": 64,
+                       "l2": "inputs and trees larger than L2 are rebuilt every step"}
+
+    def step(self, k):
+        self.ctx.compute_forces_batch(self.tpos, self.tmass, self.off, self.eps, self.theta, self.acc, self.pot)
+
+    def e2e(self, steps):
+        """Pinned host inputs copied in and results copied out around the batched call, every step."""
+        import torch
+
+        hpos = torch.from_numpy(self.pos.reshape(-1).copy()).pin_memory()
+        hmass = torch.from_numpy(self.mass.copy()).pin_memory()
+        hacc = torch.zeros(3 * self.n, dtype=torch.float32).pin_memory()
+        hpot = torch.zeros(self.n, dtype=torch.float32).pin_memory()
+
+        def one():
+            self.tpos.copy_(hpos, non_blocking=True)
+            self.tmass.copy_(hmass, non_blocking=True)
+            self.step(0)
+            hacc.copy_(self.acc, non_blocking=True)
+            hpot.copy_(self.pot, non_blocking=True)
+            torch.cuda.current_stream(self.dev).synchronize()
+
+        one()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        dt = (time.perf_counter() - t0) / steps
+        return dt, int(hpos.numel() * 8 + hmass.numel() * 4), int(hacc.numel() * 4 + hpot.numel() * 4)
+
+    def cpu_sample(self, frac):
+        # one box of the batch (the largest), a random subset of its particles as sinks
+        b = int(np.argmax(np.diff(self.off)))
+        p, m = self.boxes[b]
+        return cpu_baseline(p, m, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / m.size))
+
+
+class Rungs:
+    """256^3 Plummer-clustered box on rungs 0-5 (Sec. 3.2): a step is one substep of the KDK
+    hierarchy -- kick-drift of the active particles and drift of all, then the force solve of the
+    particles active at the next substep (about 10% on average)."""
+
+    R = 5
+
+    def __init__(self, args, rank, dev, ctx):
+        import torch
+
+        self.pos, self.mass, self.eps, self.theta = workload("rungs16m", rank, args.n)
+        n = self.n = self.mass.size
+        self.ctx, self.dev = ctx, dev
+        self.tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(dev)
+        self.tmass = torch.from_numpy(self.mass).to(dev)
+        self.vel = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+        self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.rung = torch.zeros(n, dtype=torch.uint8, device=dev)
+        self.act = torch.ones(n, dtype=torch.uint8, device=dev)
+        ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+        a = self.acc.cpu().numpy().reshape(3, n).astype(np.float64)
+        dtp = 0.2 * np.sqrt(self.eps / np.maximum(np.linalg.norm(a, axis=0), 1e-30))
+        # base step such that about 10% of the particles sit on the finest rung: rung R holds the
+        # particles with Delta T < dt0 / 2^(R-1)
+        self.dt0 = float(np.ldexp(np.quantile(dtp, 0.10), self.R - 1))
+        ctx.assign_rungs(self.acc, self.rung, self.eps, self.dt0, self.R)
+        hist = np.bincount(self.rung.cpu().numpy(), minlength=self.R + 1)
+        self.config = {"workload": "rungs16m", "n": int(n), "eps": self.eps, "theta": self.theta,
+                       "max_rung": self.R, "dt0": self.dt0, "rung_hist": hist.tolist(), "bucket": 16, "group": 64,
+                       "l2": "inputs and tree larger than L2 are rebuilt every substep"}
+        self.active_frac = []
+
+    def step(self, k):
+        s = k % (1 << self.R)
+        self.ctx.kick_drift(self.tpos, self.vel, self.acc, self.rung, self.act, self.eps, self.dt0, self.R, s,
+                            1 if k > 0 else 0)
+        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
+
+    def e2e(self, steps):
+        return None
+
+    def cpu_sample(self, frac):
+        return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / self.n))
 
 
 def main():
@@ -188,23 +350,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    pos, mass, eps, theta = workload(args.workload, rank, args.n)
-    n = mass.size
-    tpos0 = torch.from_numpy(pos.reshape(-1).copy()).to(dev)
-    tpos = tpos0.clone()
-    tmass = torch.from_numpy(mass).to(dev)
-    vel = torch.zeros(3 * n, dtype=torch.float64, device=dev)
-    acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
-    pot = torch.zeros(n, dtype=torch.float32, device=dev)
-    rung = torch.zeros(n, dtype=torch.uint8, device=dev)
-    act_next = torch.zeros(n, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     ctx = binding.Context(local, stream)
-    dt0 = 1e-5  # tiny base step: the box barely changes, so every step solves the same workload
-
-    def step(k):
-        ctx.compute_forces(tpos, tmass, eps, theta, acc, pot)
-        ctx.kick_drift(tpos, vel, acc, rung, act_next, eps, dt0, 0, 0, 1 if k > 0 else 0)
+    kind = {"batch64": Batch, "rungs16m": Rungs}.get(args.workload, Box)
+    wl = kind(args, rank, dev, ctx)
 
     def barrier():
         if world > 1:
@@ -213,7 +362,7 @@ def main():
             dist.barrier()
 
     for k in range(args.warmup):
-        step(k)
+        wl.step(k)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -222,82 +371,72 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     kt = {"pp": 0.0, "pc": 0.0, "tree": 0.0, "walk": 0.0, "l2p": 0.0}
+    flops = {"pp": 0.0, "pc": 0.0}
     inter = []
     launches = 0
+    active = []
     e0.record(stream)
     for k in range(args.steps):
-        step(args.warmup + k)
+        wl.step(args.warmup + k)
         st = ctx.stats()
         for key in kt:
             kt[key] += st["ms_" + key]
+        flops["pp"] += st["kernel_flops_pp"]
+        flops["pc"] += st["kernel_flops_pc"]
         inter.append(st["n_pp_pairs"] + st["n_pc_pairs"])
-        launches += st["n_launches"] + 1
+        active.append(st["n_active"])
+        launches += st["n_launches"] + (1 if args.workload != "batch64" else 0)
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    inter_mean = float(np.mean(inter))
     if world > 1:
         import torch.distributed as dist
 
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-        tot = torch.tensor([float(np.mean(inter))], device=dev, dtype=torch.float64)
+        tot = torch.tensor([inter_mean], device=dev, dtype=torch.float64)
         dist.all_reduce(tot)
         inter_job = float(tot.item())
     else:
-        inter_job = float(np.mean(inter))
+        inter_job = inter_mean
     value = inter_job / (ms * 1e-3)
     st = ctx.stats()
-    # roofline of the dominant kernel (FP32 ALU bound)
+    # roofline of the dominant interaction kernel (FP32 ALU bound), CUDA events on the context's stream
     pp_ms, pc_ms = kt["pp"] / args.steps, kt["pc"] / args.steps
-    flops_pc = st["kernel_flops_pc"]
-    flops_pp = st["kernel_flops_pp"]
+    fpp, fpc = flops["pp"] / args.steps, flops["pc"] / args.steps
     dom = "k_pc" if pc_ms >= pp_ms else "k_pp"
-    dom_ms = pc_ms if dom == "k_pc" else pp_ms
-    dom_flops = flops_pc if dom == "k_pc" else flops_pp
+    dom_ms, dom_flops = (pc_ms, fpc) if dom == "k_pc" else (pp_ms, fpp)
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(dom),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-            "pp_pc_frac": ((flops_pp + flops_pc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
+            "pp_pc_frac": ((fpp + fpc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
             if pp_ms + pc_ms > 0 else 0.0}
     line = {"metric": "interactions/s (PP + PC) per force solve", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(n), "eps": eps, "theta": theta, "bucket": 16,
-                       "group": 64, "l2": "inputs and tree larger than L2 are rebuilt every step"},
-            "phase_ms": {k: v / args.steps for k, v in kt.items()},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": wl.config, "phase_ms": {k: v / args.steps for k, v in kt.items()},
             "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
             "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
-            "roofline": roof, "clocks": ck, "gpu_launches": launches}
-    # end to end through the host-buffer entry point
+            "active_per_step": float(np.mean(active)), "roofline": roof, "clocks": ck, "gpu_launches": launches}
     if not args.no_e2e:
-        hpos = torch.from_numpy(pos.reshape(-1).copy()).pin_memory().numpy()
-        hmass = torch.from_numpy(mass.copy()).pin_memory().numpy()
-        hacc = torch.zeros(3 * n, dtype=torch.float32).pin_memory().numpy()
-        hpot = torch.zeros(n, dtype=torch.float32).pin_memory().numpy()
-        for _ in range(2):
-            ctx.compute_forces_host(hpos, hmass, eps, theta, hacc, hpot)
         barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ctx.compute_forces_host(hpos, hmass, eps, theta, hacc, hpot)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            import torch.distributed as dist
+        r = wl.e2e(args.steps)
+        if r is not None:
+            dt, hb, db = r
+            if world > 1:
+                import torch.distributed as dist
 
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": inter_job / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
-                       "h2d_bytes_per_step": int(hpos.nbytes + hmass.nbytes),
-                       "d2h_bytes_per_step": int(hacc.nbytes + hpot.nbytes)}
+                t = torch.tensor([dt], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                dt = float(t.item())
+            line["e2e"] = {"value": inter_job / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
+                           "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(pos, mass, eps, theta, args.cpu_sample).items()
-                                if k != "seconds"}
+        line["cpu_baseline"] = {k: v for k, v in wl.cpu_sample(args.cpu_sample).items() if k != "seconds"}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
