@@ -40,10 +40,10 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul, 3 fma, 1 add)
 
-# DRAM traffic per launch of the dominant kernel from an ncu capture (bytes), or None.
-# Filled from the committed profile summary of the current kernel; reset to None whenever the
-# kernel changes.
-NCU_TRAFFIC = {"k_pc": None, "k_pp": None}
+# DRAM bytes (read + write) per launch of the interaction kernels on the 128^3 NFW box, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_pc_k_pp_nfw2m.md).
+# Set back to None whenever a kernel changes after that capture.
+NCU_TRAFFIC = {"k_pc": 300888832, "k_pp": 135446016}
 
 
 def parse():
