@@ -78,6 +78,15 @@ typedef struct fmm_params {
     int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion; default 7 */
     int reserved;          /* must be 0 */
     long long spin_limit;  /* iteration cap of any device-side wait (default 1<<26) */
+    /* learned criterion (criterion = 1), not in the paper: for a source cell with
+     * theta_eff = (1.5 b_max(sink) + b_max(source)) / d, the pair is accepted as a cell-cell
+     * interaction when theta_eff < band_lo, rejected when theta_eff >= band_hi, and in between
+     * accepted when the network's predicted log10 relative force error is < mlp_tau.  A guard
+     * (d > 1.1 (b_max(sink) + b_max(source)), bounding boxes >= 2 eps apart) always applies.
+     * Defaults: band 0.35 .. 1.0, mlp_tau = -3.5. */
+    double mlp_tau;
+    double band_lo;
+    double band_hi;
 } fmm_params;
 
 /* Per-solve statistics of the last fmm_compute_forces on a context. */
@@ -105,6 +114,7 @@ typedef struct fmm_stats {
     double kernel_flops_pc; /* FP32 flops performed by the PC kernel (per pair count, see fmm_flops_per_pc) */
     int retries;            /* walk restarts after a capacity grow */
     int n_launches;         /* kernels launched by the solve */
+    long long n_learned;    /* decisions taken by the learned criterion's network */
 } fmm_stats;
 
 /* Fill *p with the defaults: theta 0.55, eps 1e-3, bucket 16, group 64, criterion 0,
@@ -198,6 +208,52 @@ fmm_status fmm_kick_drift(fmm_ctx *ctx, double *pos, double *vel, const float *a
  * Asynchronous. */
 fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung, long long n, double eps,
                             double dt0, int max_rung);
+
+/* ---------------- learned opening criterion (not in the paper; criterion = 1) ----------------
+ * The network x (8) -> 64 -> 64 -> 64 -> 1 (ReLU) predicts log10 of the relative force error of
+ * accepting a (sink cell, source cell) pair as a cell-cell interaction, from the features
+ *   b_max(s)/d, b_max(k)/d, eps/d, gap/d, log2 N_s, log2 N_k, |M2|_F/(M b_s^2), |M4|_F/(M b_s^4)
+ * (d distance of the centres of mass, gap that of the bounding boxes).  Parameters: FMM_MLP_NP
+ * floats, W1 [64x8], b1 [64], W2 [64x64], b2 [64], W3 [64x64], b3 [64], w4 [64], b4 [1] (row-
+ * major), then the feature normalisation mean [8] and inv_std [8].  Inference runs on the tensor
+ * cores with BF16 weights and FP32 accumulation; training in FP32 with Adam. */
+#define FMM_MLP_NP 8977
+#define FMM_MLP_NW 8961
+
+/* Load (host, FMM_MLP_NP floats) or read back the context's network parameters. */
+fmm_status fmm_mlp_load(fmm_ctx *ctx, const float *params, long long n);
+fmm_status fmm_mlp_get(const fmm_ctx *ctx, float *params, long long n);
+
+/* Predictions for n feature rows: feats device n x 8 floats (raw features), out device n floats. */
+fmm_status fmm_mlp_predict(fmm_ctx *ctx, const float *feats, long long n, float *out);
+
+/* Loss 0.5 mean((y - label)^2) and its gradient with respect to the FMM_MLP_NW weights over
+ * the n rows (feats device n x 8, labels device n); grad and loss are HOST outputs. */
+fmm_status fmm_mlp_gradient(fmm_ctx *ctx, const float *feats, const float *labels, long long n, float *grad,
+                            float *loss);
+
+/* Train the network on n labelled rows (device): feature normalisation from the data, weights
+ * initialised from seed (He-uniform, output bias = mean label), then epochs of Adam on shuffled
+ * minibatches of `batch` rows with learning rate lr.  *final_loss (host, may be NULL) gets the
+ * last epoch's mean training loss. */
+fmm_status fmm_mlp_train(fmm_ctx *ctx, const float *feats, const float *labels, long long n, int epochs, int batch,
+                         float lr, unsigned int seed, float *final_loss);
+
+/* Audit: build the tree of N particles, walk it with the fixed criterion at theta, record every
+ * (sink cell, source cell) pair with band_lo <= theta_eff < band_hi that passes the guard (at
+ * most max_pairs), and write for each its 8 features (feats, device max_pairs x 8) and label
+ * (labels, device max_pairs): log10 of the largest relative force error, over up to 32
+ * particles of the sink, of the cell-cell expansion of the source against the direct sum of its
+ * particles, relative to the particle's total acceleration acc_ref (device, 3N SoA, input order).
+ * *n_pairs (host) = pairs written. */
+fmm_status fmm_mlp_audit(fmm_ctx *ctx, const double *pos, const float *mass, long long n, double eps,
+                         double theta, double band_lo, double band_hi, const float *acc_ref, long long max_pairs,
+                         float *feats, float *labels, long long *n_pairs);
+
+/* The (sink cell, source cell) pairs of the last audit as particle ranges in the sorted order
+ * (HOST outputs of n entries, n <= the audit's *n_pairs; any pointer may be NULL). */
+fmm_status fmm_mlp_audit_pairs(const fmm_ctx *ctx, int *sink_first, int *sink_count, int *src_first, int *src_count,
+                               long long n);
 
 /* Statistics of the last solve.  Synchronises the context's stream. */
 fmm_status fmm_get_stats(const fmm_ctx *ctx, fmm_stats *out);

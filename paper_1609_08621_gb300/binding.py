@@ -32,7 +32,8 @@ class FmmError(RuntimeError):
 class fmm_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("bucket", C.c_int), ("group", C.c_int),
                 ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("reserved", C.c_int),
-                ("spin_limit", C.c_longlong)]
+                ("spin_limit", C.c_longlong), ("mlp_tau", C.c_double), ("band_lo", C.c_double),
+                ("band_hi", C.c_double)]
 
 
 class fmm_stats(C.Structure):
@@ -41,7 +42,7 @@ class fmm_stats(C.Structure):
                                              "n_pc_entries")] + \
                [(k, C.c_double) for k in ("ms_tree", "ms_walk", "ms_pp", "ms_pc", "ms_l2p", "ms_total",
                                           "paper_flops", "kernel_flops_pp", "kernel_flops_pc")] + \
-               [("retries", C.c_int), ("n_launches", C.c_int)]
+               [("retries", C.c_int), ("n_launches", C.c_int), ("n_learned", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -88,6 +89,13 @@ def load(build_if_missing: bool = True):
         "fmm_export_locals": (i, [vp, vp, vp, ll]),
         "fmm_multi_index": (i, [vp, vp]),
         "fmm_export_walk_levels": (i, [vp, vp, i, C.POINTER(i)]),
+        "fmm_mlp_load": (i, [vp, vp, ll]),
+        "fmm_mlp_get": (i, [vp, vp, ll]),
+        "fmm_mlp_predict": (i, [vp, vp, ll, vp]),
+        "fmm_mlp_gradient": (i, [vp, vp, vp, ll, vp, vp]),
+        "fmm_mlp_train": (i, [vp, vp, vp, ll, i, i, C.c_float, C.c_uint, vp]),
+        "fmm_mlp_audit": (i, [vp, vp, vp, ll, d, d, d, d, vp, ll, vp, vp, C.POINTER(ll)]),
+        "fmm_mlp_audit_pairs": (i, [vp, vp, vp, vp, vp, ll]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -254,6 +262,67 @@ class Context:
         s = fmm_stats()
         _check(load().fmm_get_stats(self.h, C.byref(s)))
         return s.as_dict()
+
+    # -- learned criterion
+    MLP_NP = 8977
+    MLP_NW = 8961
+
+    def mlp_load(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().fmm_mlp_load(self.h, p.ctypes.data, p.size))
+
+    def mlp_get(self):
+        p = np.zeros(self.MLP_NP, np.float32)
+        _check(load().fmm_mlp_get(self.h, p.ctypes.data, p.size))
+        return p
+
+    def mlp_predict(self, feats):
+        import torch
+
+        n = feats.shape[0]
+        out = torch.zeros(n, dtype=torch.float32, device=feats.device)
+        _check(load().fmm_mlp_predict(self.h, _ptr(feats, torch.float32, 8 * n, "feats"), n, out.data_ptr()))
+        return out
+
+    def mlp_gradient(self, feats, labels):
+        import torch
+
+        n = labels.numel()
+        g = np.zeros(self.MLP_NW, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(load().fmm_mlp_gradient(self.h, _ptr(feats, torch.float32, 8 * n, "feats"),
+                                       _ptr(labels, torch.float32, n, "labels"), n, g.ctypes.data, loss.ctypes.data))
+        return g, float(loss[0])
+
+    def mlp_train(self, feats, labels, epochs=30, batch=256, lr=1e-3, seed=1):
+        import torch
+
+        n = labels.numel()
+        loss = np.zeros(1, np.float32)
+        _check(load().fmm_mlp_train(self.h, _ptr(feats, torch.float32, 8 * n, "feats"),
+                                    _ptr(labels, torch.float32, n, "labels"), n, int(epochs), int(batch), float(lr),
+                                    int(seed), loss.ctypes.data))
+        return float(loss[0])
+
+    def mlp_audit(self, pos, mass, eps, theta, band_lo, band_hi, acc_ref, max_pairs):
+        """Audit walk: (features (n, 8), labels (n,)) as CUDA tensors."""
+        import torch
+
+        n = mass.numel()
+        feats = torch.zeros(max_pairs * 8, dtype=torch.float32, device=pos.device)
+        labels = torch.zeros(max_pairs, dtype=torch.float32, device=pos.device)
+        got = C.c_longlong()
+        _check(load().fmm_mlp_audit(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                    _ptr(mass, torch.float32, n, "mass"), n, float(eps), float(theta), float(band_lo),
+                                    float(band_hi), _ptr(acc_ref, torch.float32, 3 * n, "acc_ref"), int(max_pairs),
+                                    feats.data_ptr(), labels.data_ptr(), C.byref(got)))
+        m = got.value
+        return feats[:8 * m].reshape(m, 8), labels[:m]
+
+    def mlp_audit_pairs(self, n):
+        arrs = [np.zeros(max(n, 1), np.int32) for _ in range(4)]
+        _check(load().fmm_mlp_audit_pairs(self.h, *[a.ctypes.data for a in arrs], n))
+        return [a[:n] for a in arrs]
 
     # -- introspection (host numpy outputs)
     def tree_info(self):

@@ -7,8 +7,19 @@
 #include <string>
 #include <vector>
 
+#include <math.h>
+
 #include "expansions.cuh"
 #include "fmm_internal.cuh"
+#include "mlp.cuh"
+
+cudaError_t fmm_mlp_pack(const float* params, unsigned char* packed, cudaStream_t s);
+cudaError_t fmm_mlp_grad(const float* params, const float* feats, const float* labels, const unsigned int* idx,
+                         long long nrows, float inv_b, float loss_scale, float* grad, float* loss, cudaStream_t s);
+cudaError_t fmm_mlp_adam(float* p, const float* g, float* m, float* v, float lr, int step, cudaStream_t s);
+cudaError_t fmm_mlp_predict(const unsigned char* packed, const float* feats, long long n, float* out, cudaStream_t s);
+cudaError_t fmm_launch_audit_labels(DevTree& t, const int2* pairs, long long npairs, const float* acc_ref,
+                                    long long n, float eps, float* feats, float* labels, cudaStream_t s);
 
 namespace {
 
@@ -73,6 +84,14 @@ struct fmm_ctx {
     bool have_tree = false, have_solve = false;
     int launches = 0;  // kernels launched by the current solve
     float theta_nodes = -1.0f;
+    // learned criterion: FP32 master parameters, Adam state, packed BF16 copy
+    float *mlp_p = nullptr, *mlp_g = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_loss = nullptr;
+    unsigned char* mlp_packed = nullptr;
+    bool mlp_ready = false;
+    int2* audit_pairs = nullptr;
+    long long audit_cap = 0;
+    unsigned int* mlp_idx = nullptr;
+    long long mlp_idx_cap = 0;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
     float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
@@ -88,7 +107,10 @@ static fmm_status check_params(const fmm_params* p)
     if (p->bucket < 1 || p->bucket > 16) return fail(FMM_ERR_ARG, "bucket must be in [1, 16], got %d", p->bucket);
     if (p->group < p->bucket || p->group > 64)
         return fail(FMM_ERR_ARG, "group must be in [bucket, 64], got %d", p->group);
-    if (p->criterion != 0) return fail(FMM_ERR_ARG, "criterion %d is not available", p->criterion);
+    if (p->criterion != 0 && p->criterion != 1) return fail(FMM_ERR_ARG, "criterion must be 0 or 1, got %d", p->criterion);
+    if (!(p->band_lo > 0.0 && p->band_lo <= p->band_hi && p->band_hi <= 2.0))
+        return fail(FMM_ERR_ARG, "band must satisfy 0 < band_lo <= band_hi <= 2");
+    if (!isfinite(p->mlp_tau)) return fail(FMM_ERR_ARG, "mlp_tau must be finite");
     if (p->accumulate != 0) return fail(FMM_ERR_ARG, "accumulate %d is not available", p->accumulate);
     if (p->terms < 0 || p->terms > 7) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4, got %d", p->terms);
     if (p->reserved != 0) return fail(FMM_ERR_ARG, "reserved must be 0");
@@ -108,6 +130,9 @@ extern "C" fmm_status fmm_default_params(fmm_params* p)
     p->accumulate = 0;
     p->terms = 7;
     p->spin_limit = 1LL << 26;
+    p->mlp_tau = -3.5;
+    p->band_lo = 0.35;
+    p->band_hi = 1.0;
     return FMM_OK;
 }
 
@@ -121,7 +146,7 @@ static void free_all(fmm_ctx* c)
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
                   t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
+                  t.mnorm, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
@@ -135,7 +160,8 @@ static void free_all(fmm_ctx* c)
     if (c->ctr_h) cudaFreeHost(c->ctr_h);
     if (t.box_off_h) cudaFreeHost(t.box_off_h);
     if (c->totals_h) cudaFreeHost(c->totals_h);
-    void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact};
+    void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact, c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v, c->mlp_loss,
+                  c->mlp_packed, c->audit_pairs, c->mlp_idx};
     for (void* p : hs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -245,6 +271,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.bmax, cap));
         CK(alloc(&t.rec, (long long)FMM_NREC * cap));
         CK(alloc(&t.node, cap));
+        CK(alloc(&t.mnorm, cap));
         CK(alloc(&t.L, (long long)FMM_NL * cap));
         t.cap_cells = cap;
     }
@@ -421,7 +448,7 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
     return FMM_OK;
 }
 
-static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int group)
+static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int group, int mode = 0)
 {
     DevTree& t = c->t;
     DevWalk& w = c->w;
@@ -432,6 +459,14 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     a.eps2 = (float)(eps * eps);
     a.bucket = bucket;
     a.group = group;
+    a.eps = (float)eps;
+    a.mode = mode;
+    a.band_lo = (float)c->params.band_lo;
+    a.band_hi = (float)c->params.band_hi;
+    a.tau = (float)c->params.mlp_tau;
+    a.mlp_packed = c->mlp_packed;
+    a.audit_pairs = c->audit_pairs;
+    a.audit_cap = c->audit_cap;
     // groups sit at most at the deepest cell level: depth + 1 levels, no host round trip between them
     const int levels = t.depth + 1;
     if (levels + 1 > FMM_MAX_LEVELS) return fail(FMM_ERR_STATE, "tree depth %d exceeds the walk's levels", t.depth);
@@ -493,7 +528,8 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     CK(fmm_launch_nodes(c->t, theta, s));
     c->launches += 1;
     CK(cudaEventRecord(c->ev[1], s));
-    st = run_walk(c, n, eps, q.bucket, q.group);
+    if (q.criterion == 1 && !c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
+    st = run_walk(c, n, eps, q.bucket, q.group, q.criterion);
     if (st != FMM_OK) return st;
     CK(cudaEventRecord(c->ev[2], s));
     InteractArgs ia;
@@ -561,6 +597,7 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     S.kernel_flops_pp = 19.0 * S.n_pp_pairs;
     S.kernel_flops_pc = (double)FMM_FLOPS_PC * S.n_pc_pairs;
     S.n_launches = c->launches;
+    S.n_learned = (long long)c->ctr_h->n_mlp;
     c->have_solve = true;
     return FMM_OK;
 }
@@ -817,5 +854,225 @@ extern "C" fmm_status fmm_multi_index(int* local_idx, int* moment_idx)
 {
     if (local_idx) memcpy(local_idx, fmm_multi_index_table, sizeof(fmm_multi_index_table));
     if (moment_idx) memcpy(moment_idx, fmm_moment_index_table, sizeof(fmm_moment_index_table));
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------- learned criterion
+
+static_assert(FMM_MLP_NP == MLP_NP && FMM_MLP_NW == MLP_NW, "network sizes in fmm.h and mlp.cuh differ");
+
+static fmm_status mlp_alloc(fmm_ctx* c)
+{
+    if (c->mlp_p) return FMM_OK;
+    CK(alloc(&c->mlp_p, MLP_NP));
+    CK(alloc(&c->mlp_g, MLP_NW));
+    CK(alloc(&c->mlp_m, MLP_NW));
+    CK(alloc(&c->mlp_v, MLP_NW));
+    CK(alloc(&c->mlp_loss, 1));
+    CK(alloc(&c->mlp_packed, MLPP_SIZE));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_load(fmm_ctx* c, const float* params, long long n)
+{
+    if (!c || !params) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n != MLP_NP) return fail(FMM_ERR_ARG, "expected %d parameters, got %lld", MLP_NP, n);
+    for (long long i = 0; i < n; i++)
+        if (!isfinite(params[i])) return fail(FMM_ERR_NUMERIC, "parameter %lld is not finite", i);
+    CK(cudaSetDevice(c->device));
+    fmm_status st = mlp_alloc(c);
+    if (st != FMM_OK) return st;
+    CK(cudaMemcpyAsync(c->mlp_p, params, sizeof(float) * MLP_NP, cudaMemcpyHostToDevice, c->stream));
+    CK(fmm_mlp_pack(c->mlp_p, c->mlp_packed, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->mlp_ready = true;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_get(const fmm_ctx* c, float* params, long long n)
+{
+    if (!c || !params) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < MLP_NP) return fail(FMM_ERR_ARG, "need room for %d parameters", MLP_NP);
+    if (!c->mlp_ready) return fail(FMM_ERR_STATE, "no network parameters");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(params, c->mlp_p, sizeof(float) * MLP_NP, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_predict(fmm_ctx* c, const float* feats, long long n, float* out)
+{
+    if (!c || !feats || !out) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 0) return fail(FMM_ERR_ARG, "n must be >= 0");
+    if (!c->mlp_ready) return fail(FMM_ERR_STATE, "no network parameters");
+    if (n == 0) return FMM_OK;
+    CK(cudaSetDevice(c->device));
+    CK(fmm_mlp_predict(c->mlp_packed, feats, n, out, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_gradient(fmm_ctx* c, const float* feats, const float* labels, long long n, float* grad,
+                                       float* loss)
+{
+    if (!c || !feats || !labels || !grad) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 1) return fail(FMM_ERR_ARG, "n must be >= 1");
+    if (!c->mlp_ready) return fail(FMM_ERR_STATE, "no network parameters");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(c->mlp_g, 0, sizeof(float) * MLP_NW, c->stream));
+    CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), c->stream));
+    CK(fmm_mlp_grad(c->mlp_p, feats, labels, nullptr, n, 1.0f / (float)n, 1.0f / (float)n, c->mlp_g, c->mlp_loss,
+                    c->stream));
+    CK(cudaMemcpyAsync(grad, c->mlp_g, sizeof(float) * MLP_NW, cudaMemcpyDeviceToHost, c->stream));
+    if (loss) CK(cudaMemcpyAsync(loss, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return FMM_OK;
+}
+
+namespace {
+// splitmix64: the seed of the weight initialisation and of the minibatch shuffles
+unsigned long long splitmix(unsigned long long& s)
+{
+    unsigned long long z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+double uniform01(unsigned long long& s) { return (double)(splitmix(s) >> 11) * (1.0 / 9007199254740992.0); }
+}  // namespace
+
+extern "C" fmm_status fmm_mlp_train(fmm_ctx* c, const float* feats, const float* labels, long long n, int epochs,
+                                    int batch, float lr, unsigned int seed, float* final_loss)
+{
+    if (!c || !feats || !labels) return fail(FMM_ERR_ARG, "NULL argument");
+    if (n < 2 || epochs < 1 || batch < 1 || !(lr > 0.0f)) return fail(FMM_ERR_ARG, "invalid training arguments");
+    if (n >= (1LL << 32)) return fail(FMM_ERR_ARG, "too many rows");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    fmm_status st = mlp_alloc(c);
+    if (st != FMM_OK) return st;
+    // normalisation from the data, weights from the seed
+    std::vector<float> hf((size_t)n * MLP_F), hl((size_t)n);
+    CK(cudaMemcpyAsync(hf.data(), feats, sizeof(float) * hf.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hl.data(), labels, sizeof(float) * hl.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<float> p(MLP_NP, 0.0f);
+    double lmean = 0.0;
+    for (long long i = 0; i < n; i++) lmean += hl[i];
+    lmean /= (double)n;
+    for (int k = 0; k < MLP_F; k++) {
+        double m = 0.0, v = 0.0;
+        for (long long i = 0; i < n; i++) m += hf[i * MLP_F + k];
+        m /= (double)n;
+        for (long long i = 0; i < n; i++) v += (hf[i * MLP_F + k] - m) * (hf[i * MLP_F + k] - m);
+        v /= (double)n;
+        p[MLP_MEAN + k] = (float)m;
+        p[MLP_ISTD + k] = (float)(v > 1e-20 ? 1.0 / sqrt(v) : 1.0);
+    }
+    unsigned long long rs = 0x5eedull ^ ((unsigned long long)seed << 17);
+    auto init = [&](int off, int rows, int cols) {
+        const double a = sqrt(6.0 / cols);
+        for (int i = 0; i < rows * cols; i++) p[off + i] = (float)(a * (2.0 * uniform01(rs) - 1.0));
+    };
+    init(MLP_W1, MLP_H, MLP_F);
+    init(MLP_W2, MLP_H, MLP_H);
+    init(MLP_W3, MLP_H, MLP_H);
+    init(MLP_W4, 1, MLP_H);
+    for (int i = 0; i < MLP_H; i++) p[MLP_W4 + i] *= 0.1f;
+    p[MLP_B4] = (float)lmean;
+    CK(cudaMemcpyAsync(c->mlp_p, p.data(), sizeof(float) * MLP_NP, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(c->mlp_m, 0, sizeof(float) * MLP_NW, s));
+    CK(cudaMemsetAsync(c->mlp_v, 0, sizeof(float) * MLP_NW, s));
+    if (n > c->mlp_idx_cap) {
+        CK(alloc(&c->mlp_idx, n));
+        c->mlp_idx_cap = n;
+    }
+    std::vector<unsigned int> perm((size_t)n);
+    for (long long i = 0; i < n; i++) perm[i] = (unsigned int)i;
+    int step = 0;
+    float last = 0.0f;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (long long i = n - 1; i > 0; i--) {  // Fisher-Yates
+            long long j = (long long)(splitmix(rs) % (unsigned long long)(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        CK(cudaMemcpyAsync(c->mlp_idx, perm.data(), sizeof(unsigned int) * (size_t)n, cudaMemcpyHostToDevice, s));
+        CK(cudaMemsetAsync(c->mlp_loss, 0, sizeof(float), s));
+        for (long long b = 0; b < n; b += batch) {
+            const long long nr = std::min<long long>(batch, n - b);
+            CK(cudaMemsetAsync(c->mlp_g, 0, sizeof(float) * MLP_NW, s));
+            // minibatch-mean gradient; the loss is accumulated as the epoch mean
+            CK(fmm_mlp_grad(c->mlp_p, feats, labels, c->mlp_idx + b, nr, 1.0f / (float)nr, 1.0f / (float)n, c->mlp_g,
+                            c->mlp_loss, s));
+            CK(fmm_mlp_adam(c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v, lr, ++step, s));
+        }
+        CK(cudaMemcpyAsync(&last, c->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!isfinite(last)) return fail(FMM_ERR_NUMERIC, "training diverged at epoch %d", ep);
+    }
+    CK(fmm_mlp_pack(c->mlp_p, c->mlp_packed, s));
+    CK(cudaStreamSynchronize(s));
+    c->mlp_ready = true;
+    if (final_loss) *final_loss = last;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_audit(fmm_ctx* c, const double* pos, const float* mass, long long n, double eps,
+                                    double theta, double band_lo, double band_hi, const float* acc_ref,
+                                    long long max_pairs, float* feats, float* labels, long long* n_pairs)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!acc_ref || !feats || !labels || !n_pairs || max_pairs < 1) return fail(FMM_ERR_ARG, "invalid audit buffers");
+    fmm_params q = c->params;
+    q.eps = eps;
+    q.theta = theta;
+    q.band_lo = band_lo;
+    q.band_hi = band_hi;
+    q.criterion = 0;
+    st = check_params(&q);
+    if (st != FMM_OK) return st;
+    const fmm_params saved = c->params;
+    c->params = q;
+    cudaStream_t s = c->stream;
+    if (max_pairs > c->audit_cap) {
+        CK(alloc(&c->audit_pairs, max_pairs));
+        c->audit_cap = max_pairs;
+    }
+    c->launches = 0;
+    st = build_tree(c, pos, mass, nullptr, n, q.bucket);
+    if (st == FMM_OK) {
+        cudaError_t e = fmm_launch_nodes(c->t, theta, s);
+        if (e != cudaSuccess) st = fail(FMM_ERR_CUDA, "nodes: %s", cudaGetErrorString(e));
+    }
+    if (st == FMM_OK) st = run_walk(c, n, eps, q.bucket, q.group, 2);
+    c->params = saved;
+    if (st != FMM_OK) return st;
+    const long long np = std::min<long long>((long long)c->ctr_h->n_audit, max_pairs);
+    if (np > 0) CK(fmm_launch_audit_labels(c->t, c->audit_pairs, np, acc_ref, n, (float)eps, feats, labels, s));
+    CK(cudaStreamSynchronize(s));
+    *n_pairs = np;
+    c->have_solve = false;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_mlp_audit_pairs(const fmm_ctx* c, int* sink_first, int* sink_count, int* src_first,
+                                          int* src_count, long long n)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (n < 0 || n > c->audit_cap || n > (long long)c->ctr_h->n_audit) return fail(FMM_ERR_ARG, "bad pair count");
+    CK(cudaSetDevice(c->device));
+    std::vector<int2> pr((size_t)n);
+    std::vector<int> cf((size_t)c->t.n_cells), cn((size_t)c->t.n_cells);
+    CK(d2h(pr.data(), c->audit_pairs, n, c->stream));
+    CK(d2h(cf.data(), c->t.cfirst, c->t.n_cells, c->stream));
+    CK(d2h(cn.data(), c->t.ccount, c->t.n_cells, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (long long i = 0; i < n; i++) {
+        if (sink_first) sink_first[i] = cf[pr[i].x];
+        if (sink_count) sink_count[i] = cn[pr[i].x];
+        if (src_first) src_first[i] = cf[pr[i].y];
+        if (src_count) src_count[i] = cn[pr[i].y];
+    }
     return FMM_OK;
 }

@@ -291,6 +291,36 @@ __device__ __forceinline__ void fmm_moment_traces(float* __restrict__ R)
     R[43] = 0.0f;
 }
 
+/* squared Frobenius norms of the order-2 and order-4 moment tensors of a record, each
+   component scaled (by s2, s4) before it is squared so that small cells do not underflow */
+__device__ __forceinline__ void fmm_moment_norms2(const float* __restrict__ R, float s2, float s4, float& n2,
+                                                  float& n4)
+{
+    const float t1 = R[1] * s2;
+    const float t2 = R[2] * s2;
+    const float t3 = R[3] * s2;
+    const float t4 = R[4] * s2;
+    const float t5 = R[5] * s2;
+    const float t6 = R[6] * s2;
+    n2 = t1 * t1 + 2.0f * t2 * t2 + 2.0f * t3 * t3 + t4 * t4 + 2.0f * t5 * t5 + t6 * t6;
+    const float t17 = R[17] * s4;
+    const float t18 = R[18] * s4;
+    const float t19 = R[19] * s4;
+    const float t20 = R[20] * s4;
+    const float t21 = R[21] * s4;
+    const float t22 = R[22] * s4;
+    const float t23 = R[23] * s4;
+    const float t24 = R[24] * s4;
+    const float t25 = R[25] * s4;
+    const float t26 = R[26] * s4;
+    const float t27 = R[27] * s4;
+    const float t28 = R[28] * s4;
+    const float t29 = R[29] * s4;
+    const float t30 = R[30] * s4;
+    const float t31 = R[31] * s4;
+    n4 = t17 * t17 + 4.0f * t18 * t18 + 4.0f * t19 * t19 + 6.0f * t20 * t20 + 12.0f * t21 * t21 + 6.0f * t22 * t22 + 4.0f * t23 * t23 + 12.0f * t24 * t24 + 12.0f * t25 * t25 + 4.0f * t26 * t26 + t27 * t27 + 4.0f * t28 * t28 + 6.0f * t29 * t29 + 4.0f * t30 * t30 + t31 * t31;
+}
+
 /* multipole (moment record M about z) -> local coefficients about c; r = c - z */
 __device__ __forceinline__ void fmm_m2l_acc(const float* __restrict__ M, float rx, float ry, float rz,
                                             float eps2, float* __restrict__ Lc)
@@ -710,5 +740,5 @@ __device__ __forceinline__ void fmm_pc_acc(const float* __restrict__ R, float rx
     az = fmaf(ir2, fmaf(S, qz, ir2 * vz), az);
 }
 
-/* FP32 flops of the generated bodies (fmaf = 2): green 300, p2m 94, m2m 344, traces 22, m2l 810, p2l 119, l2l 1095, l2p 499, pc 293 */
+/* FP32 flops of the generated bodies (fmaf = 2): green 300, p2m 94, m2m 344, traces 22, norms 76, m2l 810, p2l 119, l2l 1095, l2p 499, pc 293 */
 #define FMM_FLOPS_PC 293

@@ -66,6 +66,8 @@ struct DevCounters {
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
+    unsigned long long n_audit;           // (sink, source) pairs recorded by an audit walk
+    unsigned long long n_mlp;             // learned decisions taken
     // per walk level: frontier size, work counters of the walk and local kernels, and the
     // number of checklist entries handed to that level
     unsigned long long lv_front[FMM_MAX_LEVELS];
@@ -105,6 +107,7 @@ struct DevTree {
     double *bmax = nullptr;
     float *rec = nullptr;        // FMM_NREC per cell
     WalkNode *node = nullptr;
+    float2 *mnorm = nullptr;     // per cell: multipole norms |M2|/(M b^2), |M4|/(M b^4)
     float *L = nullptr;          // FMM_NL per cell: own local expansion of walked cells
     // several independent boxes: box b holds sorted particles [box_off[b], box_off[b+1])
     int nbox = 1;
@@ -180,6 +183,13 @@ struct WalkArgs {
     int bucket, group;
     float four_eps2;
     float eps2;
+    float eps;
+    // learned criterion (mode 1) and audit (mode 2); mode 0 is the fixed-theta criterion
+    int mode;
+    float band_lo, band_hi, tau;
+    const unsigned char* mlp_packed;
+    int2* audit_pairs;
+    long long audit_cap;
 };
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s);

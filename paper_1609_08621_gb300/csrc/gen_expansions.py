@@ -204,6 +204,27 @@ def gen_traces():
     return L
 
 
+def gen_norms():
+    """Frobenius norms of the symmetric moment tensors of orders 2 and 4: sum over tensor
+    components = sum over multi-indices of (|n|! / n!) M_n^2."""
+    L = ["/* squared Frobenius norms of the order-2 and order-4 moment tensors of a record, each",
+         "   component scaled (by s2, s4) before it is squared so that small cells do not underflow */",
+         "__device__ __forceinline__ void fmm_moment_norms2(const float* __restrict__ R, float s2, float s4, float& n2,",
+         "                                                  float& n4)", "{"]
+    for o, var, sv in ((2, "n2", "s2"), (4, "n4", "s4")):
+        terms = []
+        for n in MOM:
+            if sum(n) != o:
+                continue
+            w = math.factorial(o) // nfact(n)
+            L.append(f"    const float t{MSLOT[n]} = R[{MSLOT[n]}] * {sv};")
+            t = f"t{MSLOT[n]} * t{MSLOT[n]}"
+            terms.append(t if w == 1 else f"{lit(w)} * {t}")
+        L.append(f"    {var} = " + " + ".join(terms) + ";")
+    L.append("}")
+    return L
+
+
 def gen_m2l():
     """L_k += R^-(|k|+1) sum_{|n|+|k|<=5} (-1)^|n|/n! (M_n R^-|n|) Dhat^(n+k)(q), r = c_sink - z_source."""
     L = ["/* multipole (moment record M about z) -> local coefficients about c; r = c - z */",
@@ -400,6 +421,7 @@ def main():
     here = os.path.dirname(os.path.abspath(__file__))
     parts = {
         "green": gen_green_scaled(), "p2m": gen_p2m(), "m2m": gen_m2m(), "traces": gen_traces(),
+        "norms": gen_norms(),
         "m2l": gen_m2l(), "p2l": gen_p2l(), "l2l": gen_l2l(), "l2p": gen_l2p(), "pc": gen_pc(),
     }
     out = ["// GENERATED by gen_expansions.py -- do not edit by hand.",

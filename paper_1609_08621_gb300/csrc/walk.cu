@@ -23,6 +23,7 @@
 // (CP) terms, computed by a second kernel per level after the walk kernel of that level.
 #include "expansions.cuh"
 #include "fmm_internal.cuh"
+#include "mlp.cuh"
 
 #define WALK_WPB 4
 #define WALK_THREADS (WALK_WPB * 32)
@@ -41,7 +42,11 @@ __device__ __forceinline__ float gap_axis(float lo_s, float hi_s, float lo_k, fl
     return g > 0.0f ? g : 0.0f;
 }
 
-__global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
+// MODE 0: fixed-theta criterion.  MODE 1: learned criterion for source cells (the network
+// decides inside the band, see mlp.cuh).  MODE 2: fixed criterion, and every (sink, source cell)
+// pair of the band is recorded for labelling (audit).
+template <int MODE>
+__global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
     const WalkNode* __restrict__ node, const float4* __restrict__ posf, const int* __restrict__ cnact,
     const int* __restrict__ f_cell, const unsigned long long* __restrict__ f_cloff, const int* __restrict__ f_cllen,
     int level, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
@@ -51,8 +56,17 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
     unsigned int* __restrict__ pc,
     long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
     Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
-    DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2)
+    DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float2* __restrict__ mnorm,
+    float eps, float band_lo, float band_hi, float tau, const unsigned char* __restrict__ mlp_packed,
+    int2* __restrict__ audit_pairs, long long audit_cap)
 {
+    extern __shared__ __align__(16) unsigned char walk_smem[];
+    if (MODE == 1) {
+        mlp_load_smem(mlp_packed, walk_smem);
+        __syncthreads();
+    }
+    unsigned char* mlp_scratch = walk_smem + MLPP_SIZE + (threadIdx.x >> 5) * MLP_WARP_SCRATCH;
+    unsigned long long n_mlp = 0;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned int* Q = scratch + gw * 5 * cap_scr;
@@ -88,10 +102,11 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             unsigned int e = 0;
             if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
             int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1, nsrc_cell = 0;
-            bool sleaf = false;
+            bool sleaf = false, pointlike = false, acc = false, need = false;
+            float d2 = 0.0f, ro = 0.0f;
+            WalkNode S;
             if (valid) {
-                float cx, cy, cz, ro, lox, loy, loz, hix, hiy, hiz;
-                bool pointlike;
+                float cx, cy, cz, lox, loy, loz, hix, hiy, hiz;
                 if (e & FMM_PARTICLE_BIT) {
                     float4 p = posf[e & ~FMM_PARTICLE_BIT];
                     cx = lox = hix = p.x;
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
                     ro = 0.0f;
                     pointlike = true;
                 } else {
-                    const WalkNode S = node[e];
+                    S = node[e];
                     cx = S.a.x; cy = S.a.y; cz = S.a.z; ro = S.a.w;
                     lox = S.b.x; loy = S.b.y; loz = S.b.z;
                     hix = S.c.x; hiy = S.c.y; hiz = S.c.z;
@@ -112,13 +127,38 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
                     nsrc_cell = S.d.w;
                     nadd = sleaf ? S.d.w : 2;
                 }
-                const float d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
+                d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
                 const float thr = __fadd_rn(__fmul_rn(1.5f, rk), ro);
                 const float gx = gap_axis(lox, hix, K.b.x, K.c.x);
                 const float gy = gap_axis(loy, hiy, K.b.y, K.c.y);
                 const float gz = gap_axis(loz, hiz, K.b.z, K.c.z);
                 const float gap2 = d2_ordered(gx, gy, gz);
-                if (d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2) {
+                acc = d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2;
+                if (MODE != 0 && !pointlike) {
+                    const int band = mlp_band(K, S, d2, gap2, four_eps2, band_lo, band_hi);
+                    if (MODE == 1) {
+                        acc = band == 1;
+                        need = band == 3;
+                    } else if (band == 3) {
+                        const unsigned long long q = atomicAdd(&ctr->n_audit, 1ull);
+                        if ((long long)q < audit_cap) audit_pairs[q] = make_int2(k, (int)e);
+                    }
+                }
+            }
+            if (MODE == 1) {
+                const unsigned int nm = __ballot_sync(FMM_FULL_MASK, need);
+                if (nm) {
+                    float f[MLP_F];
+#pragma unroll
+                    for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
+                    if (need) mlp_pair_features(K, S, mnorm[e], eps, f);
+                    const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane);
+                    if (need) acc = pred < tau;
+                    n_mlp += __popc(nm);
+                }
+            }
+            if (valid) {
+                if (acc) {
                     out = OUT_ACCEPT;
                 } else if (!kg) {
                     out = (pointlike || ro <= rk) ? OUT_DEFER : OUT_OPEN;
@@ -250,6 +290,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk_level(
             }
         }
     }
+    if (MODE == 1 && lane == 0 && n_mlp) atomicAdd(&ctr->n_mlp, n_mlp);
 }
 
 #define LOCAL_WPB 2
@@ -427,11 +468,27 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     const int cur = a.level_parity, nxt = cur ^ 1;
     // persistent grid: every warp owns a scratch slot; idle warps exit after one atomic
     const int blocks = w.n_warps / WALK_WPB;
-    k_walk_level<<<blocks, WALK_THREADS, 0, s>>>(
-        t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],
-        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,
-        w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr,
-        a.bucket, a.group, a.four_eps2);
+#define WALK_ARGS                                                                                                   \
+    t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],      \
+        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
+        w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
+        a.bucket, a.group, a.four_eps2, t.mnorm, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
+        a.audit_cap
+    if (a.mode == 1) {
+        const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_walk_level<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        k_walk_level<1><<<blocks, WALK_THREADS, smem, s>>>(WALK_ARGS);
+    } else if (a.mode == 2) {
+        k_walk_level<2><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
+    } else {
+        k_walk_level<0><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
+    }
+#undef WALK_ARGS
     return cudaGetLastError();
 }
 

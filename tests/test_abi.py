@@ -47,3 +47,31 @@ def test_library_loads_and_host_only_calls_work():
     # invalid arguments are rejected before any device work
     assert L.fmm_set_params(None, C.byref(p)) == -1
     assert L.fmm_compute_forces(None, None, None, None, 0, 0.1, 0.5, None, None) == -1
+
+
+def declared_arities():
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(fmm_\w+)\s*\(([^)]*)\)", src):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes prototype of the binding takes as many arguments as the header declares."""
+    lib = binding.load()
+    for name, k in declared_arities().items():
+        f = getattr(lib, name)
+        if f.argtypes is not None:
+            assert len(f.argtypes) == k, (name, len(f.argtypes), k)
+
+
+def test_network_sizes_agree():
+    from oracle import mlp as omlp
+
+    src = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    np_ = int(re.search(r"#define FMM_MLP_NP (\d+)", src).group(1))
+    nw = int(re.search(r"#define FMM_MLP_NW (\d+)", src).group(1))
+    assert (np_, nw) == (omlp.N_PARAMS, omlp.N_WEIGHTS) == (binding.Context.MLP_NP, binding.Context.MLP_NW)
