@@ -304,6 +304,34 @@ fmm_status fmm_export_walk_levels(const fmm_ctx *ctx, long long *counts, int cap
  * and the 32 multi-indices of the moment slots (96 ints).  Either may be NULL. */
 fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
 
+/* ---------------------------------------------------------------- allocation-free Morton order
+ *
+ * The paper has no counterpart to this call: it exists for callers that cannot let a library
+ * allocate device memory while they run, such as an application that has already given the
+ * device's free memory to its own pool (cudaMalloc would fail there), or one whose loop cannot
+ * take the device-wide synchronisation that cudaFree implies.  It computes the key and sort stage
+ * of fmm_build_tree (Sec. 3.1, hierarchically sorted order) with no context, no cudaMalloc or
+ * cudaFree and no other allocating routine: its scratch is a fixed ~13.6 MB array in the
+ * library's device image, which bounds n by FMM_STATIC_ORDER_MAX_N.
+ *
+ *   pos   device, FP64, SoA [3][n] (x then y then z), read only; every coordinate in [0, 1)
+ *   n     1 <= n <= FMM_STATIC_ORDER_MAX_N; larger n is rejected with FMM_ERR_ARG before any work
+ *   keys  device, n values, written: the 63-bit Morton keys in ascending order
+ *   order device, n values, written: order[i] = input index of the i-th particle in that order
+ *         (ties in input order); keys and order equal fmm_export_order after fmm_build_tree
+ *   cuda_stream  the cudaStream_t to run on (NULL: the legacy default stream), on the calling
+ *         thread's current device; the call returns after that stream has finished the work.
+ *
+ * The first call on each device looks up the scratch array's device address (and sets a kernel
+ * attribute) with that device current; make that first call before any stream capture begins.
+ * One scratch array serves all calls on a device: calls that overlap in time (from several
+ * threads, or on several streams) race on it and must be serialised by the caller.
+ * Errors: FMM_ERR_ARG for NULL pointers, n out of range or a position outside [0, 1) (keys and
+ * order are then not valid), FMM_ERR_CUDA when a CUDA call fails. */
+#define FMM_STATIC_ORDER_MAX_N 1048576
+fmm_status fmm_morton_order_static(const double *pos, long long n, unsigned long long *keys, unsigned int *order,
+                                   void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ def load(build_if_missing: bool = True):
         "fmm_mlp_train": (i, [vp, vp, vp, ll, i, i, C.c_float, C.c_uint, vp]),
         "fmm_mlp_audit": (i, [vp, vp, vp, ll, d, d, d, d, vp, ll, vp, vp, C.POINTER(ll)]),
         "fmm_mlp_audit_pairs": (i, [vp, vp, vp, vp, vp, ll]),
+        "fmm_morton_order_static": (i, [vp, ll, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -156,6 +157,24 @@ def fmm_multi_index():
     mom = np.zeros(32 * 3, np.int32)
     _check(load().fmm_multi_index(loc.ctypes.data, mom.ctypes.data))
     return loc.reshape(56, 3), mom.reshape(32, 3)
+
+
+STATIC_ORDER_MAX_N = 1048576
+
+
+def morton_order_static(pos, keys, order, stream=None):
+    """Allocation-free Morton order (fmm_morton_order_static): pos is a (3, n) or 3n float64
+    CUDA tensor; the sorted keys (int64 holding the uint64 keys) and the order (int32 holding
+    the uint32 indices) are written into the caller's n-element CUDA tensors.  Nothing is
+    allocated on this path; the call returns once the stream has finished."""
+    import torch
+
+    n = keys.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream(keys.device)
+    _check(load().fmm_morton_order_static(_ptr(pos, torch.float64, 3 * n, "pos"), n,
+                                          _ptr(keys, torch.int64, n, "keys"), _ptr(order, torch.int32, n, "order"),
+                                          C.c_void_p(stream.cuda_stream)))
 
 
 class Context:

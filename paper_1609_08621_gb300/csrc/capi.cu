@@ -68,6 +68,13 @@ cudaError_t alloc(T** p, long long need)
 
 }  // namespace
 
+// records the message returned by fmm_last_error for entry points of other translation units
+fmm_status fmm_report_error(fmm_status st, const char* msg)
+{
+    g_err = msg;
+    return st;
+}
+
 struct fmm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -161,6 +161,12 @@ cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s);
 cudaError_t fmm_radix_sort_kv(unsigned long long* ka, unsigned long long* kb, unsigned int* va, unsigned int* vb,
                               long long n, int passes, DevTree& t, cudaStream_t s);
 cudaError_t fmm_sort_ensure(DevTree& t, long long n);
+long long fmm_sort_hist_entries(long long n);
+long long fmm_sort_part_entries(long long n);
+cudaError_t fmm_sort_prepare();
+cudaError_t fmm_radix_sort_kv_scratch(unsigned long long* ka, unsigned long long* kb, unsigned int* va,
+                                      unsigned int* vb, long long n, int passes, unsigned int* hist,
+                                      unsigned int* part, cudaStream_t s);
 
 // tree.cu
 cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,

@@ -272,3 +272,40 @@ cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s)
 {
     return fmm_radix_sort_kv(t.key, t.key_alt, t.idx, t.idx_alt, n, 8, t, s);
 }
+
+// ---------------------------------------------------------------- sort on caller scratch
+
+// Scratch entries the sort below needs for n keys: digit counts (256 per tile) and the partial
+// sums of their scan.
+long long fmm_sort_hist_entries(long long n) { return 256LL * fmm_ceil_div(n, RS_TILE); }
+long long fmm_sort_part_entries(long long n) { return fmm_ceil_div(fmm_sort_hist_entries(n), SCAN_TILE); }
+
+// Lets the scatter kernel use its shared-memory tile on the current device.
+cudaError_t fmm_sort_prepare() { return cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem_bytes()); }
+
+// The same stable LSD sort as fmm_radix_sort_kv, with every scratch buffer supplied by the
+// caller (hist, part of the sizes above; kb, vb of n entries) and nothing allocated here.
+// fmm_sort_prepare must have run on the current device.
+cudaError_t fmm_radix_sort_kv_scratch(unsigned long long* ka, unsigned long long* kb, unsigned int* va,
+                                      unsigned int* vb, long long n, int passes, unsigned int* hist,
+                                      unsigned int* part, cudaStream_t s)
+{
+    if (n <= 1) return cudaSuccess;
+    const int nblk = (int)fmm_ceil_div(n, RS_TILE);
+    const long long nh = 256LL * nblk, nb = fmm_ceil_div(nh, SCAN_TILE);
+    for (int pass = 0; pass < passes; pass++) {
+        const int shift = 8 * pass;
+        k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(ka, n, shift, hist, nblk);
+        k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(hist, nh, part);
+        k_scan_parts<<<1, SCAN_THREADS, 0, s>>>(part, nb, nullptr);
+        k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(hist, hist, nh, part);
+        k_rs_scatter<<<nblk, RS_THREADS, rs_smem_bytes(), s>>>(ka, va, kb, vb, n, shift, hist, nblk);
+        unsigned long long* tk = ka;
+        ka = kb;
+        kb = tk;
+        unsigned int* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    return cudaGetLastError();
+}

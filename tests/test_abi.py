@@ -75,3 +75,8 @@ def test_network_sizes_agree():
     np_ = int(re.search(r"#define FMM_MLP_NP (\d+)", src).group(1))
     nw = int(re.search(r"#define FMM_MLP_NW (\d+)", src).group(1))
     assert (np_, nw) == (omlp.N_PARAMS, omlp.N_WEIGHTS) == (binding.Context.MLP_NP, binding.Context.MLP_NW)
+
+
+def test_static_order_limit_agrees():
+    src = open(os.path.join(ROOT, "include", "fmm.h")).read()
+    assert int(re.search(r"#define FMM_STATIC_ORDER_MAX_N (\d+)", src).group(1)) == binding.STATIC_ORDER_MAX_N
