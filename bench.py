@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="nfw2m", choices=["nfw2m", "plummer4096", "batch64", "rungs16m"])
+    ap.add_argument("--workload", default="nfw2m",
+                    choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
@@ -331,6 +332,153 @@ class Rungs:
         return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / self.n))
 
 
+class Learned(Box):
+    """512^3 Plummer-clustered box solved with the learned opening criterion, compared with the
+    fixed criterion (theta = 0.55) at equal rms force error.
+
+    Set-up, outside the timed region: the network is trained on the GPU from audit walks of
+    the 4096-particle box, the 128^3 NFW box and two boxes of the 64-box batch (labels are the
+    method's own cell-cell errors, normalised by each particle's acceleration from a theta = 0.3
+    solve).  The judge of force error is an FMM solve at theta = 0.25 with the FP64 combine,
+    restricted to 65,536 random sinks (an active subset, so it costs little); the tests pin that
+    judge against the FP64 direct sum.  The budget tau of the network is searched until its rms
+    error matches the fixed criterion's, then both are timed.  A step is one learned solve."""
+
+    N_SINKS = 65536
+
+    def __init__(self, args, rank, dev, ctx):
+        import torch
+
+        from paper_1609_08621_gb300 import synth
+
+        args.workload = "learned134m"
+        super().__init__(args, rank, dev, ctx)
+        n = self.n
+        self._train(args, rank, dev, ctx, synth)
+        rng = np.random.default_rng(12345 + rank)
+        self.sinks = torch.from_numpy(np.sort(rng.choice(n, min(self.N_SINKS, n), replace=False))).to(dev)
+        act = torch.zeros(n, dtype=torch.uint8, device=dev)
+        act[self.sinks] = 1
+        ctx.set_params(criterion=0, accumulate=1)
+        ctx.compute_forces(self.tpos, self.tmass, self.eps, 0.25, self.acc, self.pot, act)
+        ctx.set_params(accumulate=0)
+        self.ref = self._at_sinks()
+        e_fixed = self._err(0, None)
+        t_fixed = self._time(0, None)
+        st_fixed = ctx.stats()
+        # tau search: coarse grid, then bisection on the bracket around the fixed criterion's error
+        grid = [-7.0, -6.5, -6.0, -5.5, -5.0, -4.5, -4.0, -3.5, -3.0]
+        errs = [self._err(1, t) for t in grid]
+        lo, hi = grid[0], grid[-1]
+        for t, e in zip(grid, errs):
+            if e <= e_fixed:
+                lo = t
+        for t, e in zip(grid, errs):
+            if t > lo and e > e_fixed:
+                hi = t
+                break
+        e_lo = self._err(1, lo)
+        for _ in range(5):
+            mid = 0.5 * (lo + hi)
+            e = self._err(1, mid)
+            if e <= e_fixed:
+                lo, e_lo = mid, e
+            else:
+                hi = mid
+        self.tau = lo
+        t_learned = self._time(1, lo)
+        st_learned = ctx.stats()
+        ctx.set_params(criterion=1, mlp_tau=self.tau)
+        self.config = dict(self.config, criterion="learned", tau=self.tau)
+        self.learned = {
+            "judge": "FMM at theta=0.25 with FP64 combine on 65,536 random sinks (pinned against the FP64 "
+                     "direct sum in the tests)",
+            "train_pairs": self.train_pairs, "train_loss": self.train_loss,
+            "fixed": {"theta": self.theta, "rms_err": e_fixed, "ms_per_solve": t_fixed,
+                      "interactions": st_fixed["n_pp_pairs"] + st_fixed["n_pc_pairs"],
+                      "n_cc": st_fixed["n_cc"], "ms_walk": st_fixed["ms_walk"]},
+            "learned": {"tau": self.tau, "rms_err": e_lo, "ms_per_solve": t_learned,
+                        "interactions": st_learned["n_pp_pairs"] + st_learned["n_pc_pairs"],
+                        "n_cc": st_learned["n_cc"], "ms_walk": st_learned["ms_walk"],
+                        "network_calls": st_learned["n_learned"]},
+            "speedup_at_equal_error": t_fixed / t_learned if t_learned > 0 else None,
+            "tau_grid": [[t, e] for t, e in zip(grid, errs)],
+        }
+
+    def _train(self, args, rank, dev, ctx, synth):
+        import torch
+
+        sets = []
+        w1 = synth.WORKLOADS["plummer4096"]
+        sets.append(synth.make("plummer", w1["n"], w1["seed"]) + (w1["eps"], w1["theta"]))
+        w2 = synth.WORKLOADS["nfw2m"]
+        sets.append(synth.make("nfw", w2["n"], w2["seed"]) + (w2["eps"], w2["theta"]))
+        w3 = synth.WORKLOADS["batch64"]
+        boxes, _ = synth.batch_boxes(w3["boxes"], w3["seed"])
+        for b in boxes[:2]:
+            sets.append(tuple(b) + (w3["eps"], w3["theta"]))
+        fs, ls = [], []
+        for p, m, eps, theta in sets:
+            n = m.size
+            tp = torch.from_numpy(np.ascontiguousarray(p).reshape(-1)).to(dev)
+            tm = torch.from_numpy(m).to(dev)
+            ref = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+            ctx.set_params(criterion=0)
+            ctx.compute_forces(tp, tm, eps, 0.3, ref)
+            f, l = ctx.mlp_audit(tp, tm, eps, theta, 0.35, 1.0, ref, 4 * n + 4096)
+            fs.append(f.clone())
+            ls.append(l.clone())
+        feats, labels = torch.cat(fs).contiguous(), torch.cat(ls).contiguous()
+        self.train_pairs = int(labels.numel())
+        self.train_loss = ctx.mlp_train(feats, labels, epochs=20, batch=256, lr=2e-3, seed=1)
+
+    def _at_sinks(self):
+        a = self.acc.view(3, self.n)
+        return a.index_select(1, self.sinks).double()
+
+    def _solve(self, criterion, tau):
+        if criterion == 1:
+            self.ctx.set_params(criterion=1, mlp_tau=tau)
+        else:
+            self.ctx.set_params(criterion=0)
+        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+
+    def _err(self, criterion, tau):
+        import torch
+
+        self._solve(criterion, tau)
+        a = self._at_sinks()
+        e = torch.linalg.norm(a - self.ref, dim=0) / torch.linalg.norm(self.ref, dim=0)
+        return float(torch.sqrt(torch.mean(e * e)).item())
+
+    def _time(self, criterion, tau, reps=3):
+        import torch
+
+        self._solve(criterion, tau)
+        s = torch.cuda.current_stream(self.dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            self._solve(criterion, tau)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def step(self, k):
+        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+
+    def cpu_sample(self, frac):
+        # the oracle (fixed theta) on a random 2^21-particle subset of the box, masses rescaled to
+        # a total of 1: the full 512^3 tree alone would take the host minutes
+        k = min(self.n, 1 << 21)
+        idx = np.sort(np.random.default_rng(7).choice(self.n, k, replace=False))
+        m = (self.mass[idx].astype(np.float64) * (self.n / k)).astype(np.float32)
+        r = cpu_baseline(np.ascontiguousarray(self.pos[:, idx]), m, self.eps, self.theta,
+                         frac if frac else min(1.0, 4096.0 / k))
+        r["sample"] = f"random {k}-particle subset of the box; " + r["sample"]
+        return r
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -352,7 +500,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = binding.Context(local, stream)
-    kind = {"batch64": Batch, "rungs16m": Rungs}.get(args.workload, Box)
+    kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned}.get(args.workload, Box)
     wl = kind(args, rank, dev, ctx)
 
     def barrier():
@@ -422,6 +570,8 @@ def main():
             "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
             "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
             "active_per_step": float(np.mean(active)), "roofline": roof, "clocks": ck, "gpu_launches": launches}
+    if hasattr(wl, "learned"):
+        line["learned"] = wl.learned
     if not args.no_e2e:
         barrier()
         r = wl.e2e(args.steps)

@@ -74,7 +74,8 @@ typedef struct fmm_params {
     int bucket;            /* b: maximum particles per leaf, 1..16 (Sec. 3.1: ~16; default 16) */
     int group;             /* g: sink group size, bucket..64 (Sec. 3.1: 64 = 4 b; default 64) */
     int criterion;         /* 0: fixed theta (Sec. 3.1); 1: learned (MLP, requires fmm_mlp_load) */
-    int accumulate;        /* 0: FP32 partial sums; 1: compensated (double-float) accumulation */
+    int accumulate;        /* 0: a particle's partial sums (one per list chunk of <= 64 entries, and the
+                              local expansion) are added in FP32; 1: they are added in FP64 */
     int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion; default 7 */
     int reserved;          /* must be 0 */
     long long spin_limit;  /* iteration cap of any device-side wait (default 1<<26) */
@@ -154,7 +155,10 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const double *pos, const float *mass, co
  *   eps, theta             softening (> 0) and opening angle (0 < theta <= 1);
  *                          they override the context's parameters for this call
  *   acc    device, 3N floats SoA out (ax|ay|az); entries of inactive particles
- *          are left unchanged
+ *          are left unchanged.  With criterion 1 it is also read on entry: an estimate of
+ *          every particle's acceleration (e.g. the previous step's) that scales the learned
+ *          criterion's error budget; a zero estimate makes that criterion reject every pair
+ *          it decides
  *   pot    device, N floats out, or NULL
  * Returns after completion (see Streams).  Statistics via fmm_get_stats. */
 fmm_status fmm_compute_forces(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,
@@ -172,7 +176,8 @@ fmm_status fmm_compute_forces_batch(fmm_ctx *ctx, const double *pos, const float
 
 /* Same as fmm_compute_forces with HOST buffers: pos (3N doubles), mass (N floats),
  * active (N bytes or NULL) are copied to device memory owned by the context, and
- * acc (3N floats) / pot (N floats or NULL) are copied back before returning. */
+ * acc (3N floats) / pot (N floats or NULL) are copied back before returning (acc is also
+ * copied in first when active is given or the criterion is 1). */
 fmm_status fmm_compute_forces_host(fmm_ctx *ctx, const double *pos, const float *mass,
                                    const unsigned char *active, long long n, double eps, double theta, float *acc,
                                    float *pot);
@@ -212,8 +217,10 @@ fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung,
 /* ---------------- learned opening criterion (not in the paper; criterion = 1) ----------------
  * The network x (8) -> 64 -> 64 -> 64 -> 1 (ReLU) predicts log10 of the relative force error of
  * accepting a (sink cell, source cell) pair as a cell-cell interaction, from the features
- *   b_max(s)/d, b_max(k)/d, eps/d, gap/d, log2 N_s, log2 N_k, |M2|_F/(M b_s^2), |M4|_F/(M b_s^4)
- * (d distance of the centres of mass, gap that of the bounding boxes).  Parameters: FMM_MLP_NP
+ *   b_max(s)/d, b_max(k)/d, eps/d, log10(M_s / (d^2 a_k)), log2 N_s, log2 N_k,
+ *   |M2|_F/(M_s b_s^2), |M4|_F/(M_s b_s^4)
+ * (d distance of the centres of mass, M_s the source's mass, a_k the smallest acceleration
+ * estimate of the sink's particles).  Parameters: FMM_MLP_NP
  * floats, W1 [64x8], b1 [64], W2 [64x64], b2 [64], W3 [64x64], b3 [64], w4 [64], b4 [1] (row-
  * major), then the feature normalisation mean [8] and inv_std [8].  Inference runs on the tensor
  * cores with BF16 weights and FP32 accumulation; training in FP32 with Adam. */
@@ -244,7 +251,8 @@ fmm_status fmm_mlp_train(fmm_ctx *ctx, const float *feats, const float *labels, 
  * most max_pairs), and write for each its 8 features (feats, device max_pairs x 8) and label
  * (labels, device max_pairs): log10 of the largest relative force error, over up to 32
  * particles of the sink, of the cell-cell expansion of the source against the direct sum of its
- * particles, relative to the particle's total acceleration acc_ref (device, 3N SoA, input order).
+ * particles, relative to the particle's total acceleration acc_ref (device, 3N SoA, input order),
+ * which also serves as the acceleration estimate of the features.
  * *n_pairs (host) = pairs written. */
 fmm_status fmm_mlp_audit(fmm_ctx *ctx, const double *pos, const float *mass, long long n, double eps,
                          double theta, double band_lo, double band_hi, const float *acc_ref, long long max_pairs,

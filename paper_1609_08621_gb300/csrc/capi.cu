@@ -20,6 +20,7 @@ cudaError_t fmm_mlp_adam(float* p, const float* g, float* m, float* v, float lr,
 cudaError_t fmm_mlp_predict(const unsigned char* packed, const float* feats, long long n, float* out, cudaStream_t s);
 cudaError_t fmm_launch_audit_labels(DevTree& t, const int2* pairs, long long npairs, const float* acc_ref,
                                     long long n, float eps, float* feats, float* labels, cudaStream_t s);
+cudaError_t fmm_launch_cell_amin(DevTree& t, const float* acc, long long n, cudaStream_t s);
 
 namespace {
 
@@ -118,7 +119,7 @@ static fmm_status check_params(const fmm_params* p)
     if (!(p->band_lo > 0.0 && p->band_lo <= p->band_hi && p->band_hi <= 2.0))
         return fail(FMM_ERR_ARG, "band must satisfy 0 < band_lo <= band_hi <= 2");
     if (!isfinite(p->mlp_tau)) return fail(FMM_ERR_ARG, "mlp_tau must be finite");
-    if (p->accumulate != 0) return fail(FMM_ERR_ARG, "accumulate %d is not available", p->accumulate);
+    if (p->accumulate != 0 && p->accumulate != 1) return fail(FMM_ERR_ARG, "accumulate must be 0 or 1, got %d", p->accumulate);
     if (p->terms < 0 || p->terms > 7) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4, got %d", p->terms);
     if (p->reserved != 0) return fail(FMM_ERR_ARG, "reserved must be 0");
     if (p->spin_limit < 1) return fail(FMM_ERR_ARG, "spin_limit must be >= 1");
@@ -153,7 +154,7 @@ static void free_all(fmm_ctx* c)
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
                   t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.mnorm, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
+                  t.mnorm, t.amin, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
@@ -279,6 +280,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.rec, (long long)FMM_NREC * cap));
         CK(alloc(&t.node, cap));
         CK(alloc(&t.mnorm, cap));
+        CK(alloc(&t.amin, cap));
         CK(alloc(&t.L, (long long)FMM_NL * cap));
         t.cap_cells = cap;
     }
@@ -535,7 +537,12 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     CK(fmm_launch_nodes(c->t, theta, s));
     c->launches += 1;
     CK(cudaEventRecord(c->ev[1], s));
-    if (q.criterion == 1 && !c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
+    if (q.criterion == 1) {
+        if (!c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
+        // the acceleration estimate held by acc on entry sets each sink cell's error scale
+        CK(fmm_launch_cell_amin(c->t, acc, n, s));
+        c->launches += 1;
+    }
     st = run_walk(c, n, eps, q.bucket, q.group, q.criterion);
     if (st != FMM_OK) return st;
     CK(cudaEventRecord(c->ev[2], s));
@@ -647,8 +654,9 @@ extern "C" fmm_status fmm_compute_forces_host(fmm_ctx* c, const double* pos, con
     CK(cudaMemcpyAsync(c->hpos, pos, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c->hmass, mass, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s));
     if (active) CK(cudaMemcpyAsync(c->hact, active, (size_t)n, cudaMemcpyHostToDevice, s));
-    if (active) {
-        // entries of inactive particles keep the caller's values
+    if (active || c->params.criterion == 1) {
+        // entries of inactive particles keep the caller's values; the learned criterion reads acc
+        // on entry as its acceleration estimate
         CK(cudaMemcpyAsync(c->hacc, acc, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, s));
         if (pot) CK(cudaMemcpyAsync(c->hpot, pot, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice, s));
     }
@@ -1051,6 +1059,10 @@ extern "C" fmm_status fmm_mlp_audit(fmm_ctx* c, const double* pos, const float* 
     if (st == FMM_OK) {
         cudaError_t e = fmm_launch_nodes(c->t, theta, s);
         if (e != cudaSuccess) st = fail(FMM_ERR_CUDA, "nodes: %s", cudaGetErrorString(e));
+    }
+    if (st == FMM_OK) {
+        cudaError_t e = fmm_launch_cell_amin(c->t, acc_ref, n, s);
+        if (e != cudaSuccess) st = fail(FMM_ERR_CUDA, "cell amin: %s", cudaGetErrorString(e));
     }
     if (st == FMM_OK) st = run_walk(c, n, eps, q.bucket, q.group, 2);
     c->params = saved;

@@ -107,7 +107,8 @@ struct DevTree {
     double *bmax = nullptr;
     float *rec = nullptr;        // FMM_NREC per cell
     WalkNode *node = nullptr;
-    float2 *mnorm = nullptr;     // per cell: multipole norms |M2|/(M b^2), |M4|/(M b^4)
+    float4 *mnorm = nullptr;     // per cell: |M2|/(M b^2), |M4|/(M b^4), M (float), 0
+    float *amin = nullptr;       // per cell: smallest |a| estimate of its particles (learned criterion)
     float *L = nullptr;          // FMM_NL per cell: own local expansion of walked cells
     // several independent boxes: box b holds sorted particles [box_off[b], box_off[b+1])
     int nbox = 1;

@@ -358,6 +358,8 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
 
 // Per group: each sink adds its PP partials and PC partials in item order, then the group's
 // local expansion, and the result goes to the caller's order (active particles only).
+// T = float: partial sums added in FP32; T = double: added in FP64 (accumulate = 1)
+template <typename T>
 __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ groups, long long n_groups,
                                                       const Com4* __restrict__ com,
                                                       const int* __restrict__ bucket_of,
@@ -386,32 +388,37 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
         const unsigned int npc = (terms & 2) ? cnt_pc[gi] : 0u, bpc = base_pc[gi];
         for (int i = lane; i < G.count; i += 32) {
             const int s = G.first + i;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            T ax = 0, ay = 0, az = 0, aw = 0;
             for (unsigned int k = 0; k < npp; k++) {
                 const float4 p = part_pp[(unsigned long long)(bpp + k) * FMM_GMAX + i];
-                a.x += p.x;
-                a.y += p.y;
-                a.z += p.z;
-                a.w += p.w;
+                ax += p.x;
+                ay += p.y;
+                az += p.z;
+                aw += p.w;
             }
             for (unsigned int k = 0; k < npc; k++) {
                 const float4 p = part_pc[(unsigned long long)(bpc + k) * FMM_GMAX + i];
-                a.x += p.x;
-                a.y += p.y;
-                a.z += p.z;
-                a.w += p.w;
+                ax += p.x;
+                ay += p.y;
+                az += p.z;
+                aw += p.w;
             }
             if (terms & 4) {
                 float ux, uy, uz, m;
                 load_sink(s, ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
-                fmm_l2p_acc(Ls[wl], ux, uy, uz, a.x, a.y, a.z, a.w);
+                float lx = 0.f, ly = 0.f, lz = 0.f, lw = 0.f;
+                fmm_l2p_acc(Ls[wl], ux, uy, uz, lx, ly, lz, lw);
+                ax += lx;
+                ay += ly;
+                az += lz;
+                aw += lw;
             }
             if (sact[s]) {
                 const unsigned int p = perm[s];
-                acc[p] = a.x;
-                acc[n + p] = a.y;
-                acc[2 * n + p] = a.z;
-                if (pot) pot[p] = a.w;
+                acc[p] = (float)ax;
+                acc[n + p] = (float)ay;
+                acc[2 * n + p] = (float)az;
+                if (pot) pot[p] = (float)aw;
             }
         }
         __syncwarp();
@@ -504,8 +511,13 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
                                float* pot, long long n, cudaStream_t s)
 {
     (void)ctr;
-    k_l2p_out<<<grid_for(w.n_groups), ITHREADS, 0, s>>>(w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell,
-                                                        t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc,
-                                                        w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
+    if (a.accumulate == 1)
+        k_l2p_out<double><<<grid_for(w.n_groups), ITHREADS, 0, s>>>(
+            w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell, t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp,
+            w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
+    else
+        k_l2p_out<float><<<grid_for(w.n_groups), ITHREADS, 0, s>>>(
+            w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell, t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp,
+            w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
     return cudaGetLastError();
 }

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_mlp_predict(const unsigned char* __rest
         float f[MLP_F];
 #pragma unroll
         for (int k = 0; k < MLP_F; k++) f[k] = r < n ? feats[r * MLP_F + k] : 0.0f;
-        const float y = mlp_predict_warp(W, scratch, f, lane);
+        const float y = mlp_predict_warp(W, scratch, f, lane, __ballot_sync(FMM_FULL_MASK, r < n));
         if (r < n) out[r] = y;
     }
 }
@@ -256,7 +256,8 @@ cudaError_t fmm_mlp_predict(const unsigned char* packed, const float* feats, lon
 // reference solve.  One warp per pair, one sampled sink particle per lane.
 __global__ void __launch_bounds__(128) k_audit_labels(
     const int2* __restrict__ pairs, long long npairs, const int* __restrict__ cfirst, const int* __restrict__ ccount,
-    const Com4* __restrict__ com, const float* __restrict__ rec, const float2* __restrict__ mnorm,
+    const Com4* __restrict__ com, const float* __restrict__ rec, const float4* __restrict__ mnorm,
+    const float* __restrict__ amin,
     const WalkNode* __restrict__ node, const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
     const float4* __restrict__ off, const unsigned int* __restrict__ perm, const float* __restrict__ acc_ref,
     long long n, float eps, float* __restrict__ feats, float* __restrict__ labels)
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(128) k_audit_labels(
         for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(FMM_FULL_MASK, err, o));
         if (lane == 0) {
             labels[q] = log10f(err + 1e-12f);
-            mlp_pair_features(node[k], node[s], mnorm[s], eps, feats + q * MLP_F);
+            mlp_pair_features(node[k], node[s], mnorm[s], amin[k], eps, feats + q * MLP_F);
         }
     }
 }
@@ -338,8 +339,50 @@ cudaError_t fmm_launch_audit_labels(DevTree& t, const int2* pairs, long long npa
     long long blocks = fmm_ceil_div(npairs, 4);
     if (blocks > 152LL * 32) blocks = 152LL * 32;
     if (blocks < 1) blocks = 1;
-    k_audit_labels<<<(unsigned)blocks, 128, 0, s>>>(pairs, npairs, t.cfirst, t.ccount, t.com, t.rec, t.mnorm, t.node,
+    k_audit_labels<<<(unsigned)blocks, 128, 0, s>>>(pairs, npairs, t.cfirst, t.ccount, t.com, t.rec, t.mnorm, t.amin, t.node,
                                                      t.bucket_of, t.bucket_cell, t.off, t.idx, acc_ref, n, eps, feats,
                                                      labels);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- sink acceleration scale
+
+// Per cell, the smallest |a| of its particles from an acceleration estimate acc (3 x n SoA in
+// input order, e.g. the previous step's forces): bucket cells scan their particles, and the
+// second child to arrive at a parent takes the smaller of the two (arrive[] zeroed first).
+__global__ void __launch_bounds__(128) k_cell_amin(int nb, const int* __restrict__ bucket_cell,
+                                                   const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                                                   const int* __restrict__ cparent, const int* __restrict__ cchild,
+                                                   const unsigned int* __restrict__ perm,
+                                                   const float* __restrict__ acc, long long n, float* amin,
+                                                   unsigned int* arrive)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int c = bucket_cell[b];
+    float a = INFINITY;
+    for (int j = cfirst[c], e = cfirst[c] + ccount[c]; j < e; j++) {
+        const unsigned int p = perm[j];
+        const float x = acc[p], y = acc[n + p], z = acc[2 * n + p];
+        a = fminf(a, sqrtf(x * x + y * y + z * z));
+    }
+    amin[c] = a;
+    int p = cparent[c];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&arrive[p], 1u) == 0u) return;
+        __threadfence();
+        amin[p] = fminf(__ldcg(&amin[cchild[2 * p]]), __ldcg(&amin[cchild[2 * p + 1]]));
+        p = cparent[p];
+    }
+}
+
+cudaError_t fmm_launch_cell_amin(DevTree& t, const float* acc, long long n, cudaStream_t s)
+{
+    const int nb = (int)t.n_buckets;
+    cudaError_t e = cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)t.n_cells, s);
+    if (e != cudaSuccess) return e;
+    k_cell_amin<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
+                                                                 t.cchild, t.idx, acc, n, t.amin, t.arrive);
     return cudaGetLastError();
 }

@@ -98,24 +98,30 @@ __device__ __forceinline__ void mlp_hidden(const unsigned char* W, int wbyte, in
     }
 }
 
-// Forward pass of the 32 samples held by the lanes of a warp (lane i: raw features f[8]).
-// W: packed weights in shared memory; scratch: this warp's MLP_WARP_SCRATCH bytes.  All 32
-// lanes must call it (mma.sync is warp-wide); returns this lane's prediction.
+// Forward pass of the samples held by the lanes in mask (lane i: raw features f[8]).  The samples
+// are packed into the first popc(mask) rows, so a warp with at most 16 of them runs one m-tile
+// instead of two.  W: packed weights in shared memory; scratch: this warp's MLP_WARP_SCRATCH
+// bytes.  All 32 lanes must call it (mma.sync is warp-wide); returns this lane's prediction
+// (meaningful for lanes in mask).
 __device__ __forceinline__ float mlp_predict_warp(const unsigned char* W, unsigned char* scratch, const float* f,
-                                                  int lane)
+                                                  int lane, unsigned int mask)
 {
     __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(scratch);
     float* ps = reinterpret_cast<float*>(scratch + 32 * 24 * 2);
     const float* mean = reinterpret_cast<const float*>(W + MLPP_MEAN);
     const float* istd = reinterpret_cast<const float*>(W + MLPP_ISTD);
+    const unsigned int lt = (1u << lane) - 1u;
+    const int cnt = __popc(mask);
+    const int row = ((mask >> lane) & 1u) ? __popc(mask & lt) : cnt + __popc(~mask & lt);
 #pragma unroll
-    for (int k = 0; k < MLP_F; k++) xs[lane * 24 + k] = __float2bfloat16_rn((f[k] - mean[k]) * istd[k]);
+    for (int k = 0; k < MLP_F; k++) xs[row * 24 + k] = __float2bfloat16_rn((f[k] - mean[k]) * istd[k]);
 #pragma unroll
-    for (int k = MLP_F; k < 16; k++) xs[lane * 24 + k] = __float2bfloat16_rn(0.0f);
+    for (int k = MLP_F; k < 16; k++) xs[row * 24 + k] = __float2bfloat16_rn(0.0f);
     __syncwarp();
     const int g = lane >> 2, t = lane & 3;
     const float b4 = *reinterpret_cast<const float*>(W + MLPP_B4);
-    for (int mt = 0; mt < 2; mt++) {
+    const int mtiles = (cnt + 15) >> 4;
+    for (int mt = 0; mt < mtiles; mt++) {
         const int r0 = mt * 16 + g, r1 = r0 + 8;
         unsigned int a1[4][4], a2[4][4];
         a1[0][0] = *reinterpret_cast<const unsigned int*>(xs + r0 * 24 + 2 * t);
@@ -139,7 +145,7 @@ __device__ __forceinline__ float mlp_predict_warp(const unsigned char* W, unsign
         }
     }
     __syncwarp();
-    const float p = ps[lane];
+    const float p = ps[row];
     __syncwarp();
     return p;
 }
@@ -160,24 +166,21 @@ __device__ __forceinline__ int mlp_band(const WalkNode& K, const WalkNode& S, fl
     return 3;
 }
 
-// the 8 features of a (sink k, source s) pair: b_max(s)/d, b_max(k)/d, eps/d, gap/d,
-// log2 N_s, log2 N_k, |M2|_F/(M b^2), |M4|_F/(M b^4) of the source
-__device__ __forceinline__ void mlp_pair_features(const WalkNode& K, const WalkNode& S, float2 mn, float eps, float* f)
+// the 8 features of a (sink k, source s) pair: b_max(s)/d, b_max(k)/d, eps/d,
+// log10(M_s / (d^2 a_k)) (the source's monopole field at the sink relative to the sink's smallest
+// particle acceleration a_k), log2 N_s, log2 N_k, |M2|_F/(M b^2), |M4|_F/(M b^4) of the source.
+// mn = (|M2| norm, |M4| norm, M_s, -) of the source; ak = a_k (clamped below at 1e-30).
+__device__ __forceinline__ void mlp_pair_features(const WalkNode& K, const WalkNode& S, float4 mn, float ak, float eps,
+                                                  float* f)
 {
     const float dx = K.a.x - S.a.x, dy = K.a.y - S.a.y, dz = K.a.z - S.a.z;
-    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
-    float g2 = 0.0f;
-    {
-        const float gx = fmaxf(0.0f, fmaxf(S.b.x - K.c.x, K.b.x - S.c.x));
-        const float gy = fmaxf(0.0f, fmaxf(S.b.y - K.c.y, K.b.y - S.c.y));
-        const float gz = fmaxf(0.0f, fmaxf(S.b.z - K.c.z, K.b.z - S.c.z));
-        g2 = gx * gx + gy * gy + gz * gz;
-    }
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float d = sqrtf(d2);
     const float id = 1.0f / d;
     f[0] = S.b.w * id;
     f[1] = K.b.w * id;
     f[2] = eps * id;
-    f[3] = sqrtf(g2) * id;
+    f[3] = log10f(mn.z) - log10f(d2) - log10f(fmaxf(ak, 1e-30f));
     f[4] = log2f((float)S.d.w);
     f[5] = log2f((float)K.d.w);
     f[6] = mn.x;

@@ -467,7 +467,7 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
 __global__ void k_nodes(int ncell, float theta, const int* __restrict__ cfirst, const int* __restrict__ ccount,
                         const int* __restrict__ cchild, const Com4* __restrict__ com, const double* __restrict__ clo,
                         const double* __restrict__ chi, const double* __restrict__ bmax, const float* __restrict__ rec,
-                        WalkNode* __restrict__ node, float2* __restrict__ mnorm)
+                        WalkNode* __restrict__ node, float4* __restrict__ mnorm)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -485,12 +485,13 @@ __global__ void k_nodes(int ncell, float theta, const int* __restrict__ cfirst, 
     node[c] = w;
     // multipole norms for the learned criterion: |M2|_F / (M b^2), |M4|_F / (M b^4), both in [0, 1];
     // cells smaller than 1e-7 of the box (coincident particles) report 0
-    float2 mn = make_float2(0.0f, 0.0f);
+    float4 mn = make_float4(0.0f, 0.0f, (float)cm.w, 0.0f);
     if (bm > 1e-7f && cnt > 1) {
         const float b2 = bm * bm, s2 = 1.0f / ((float)cm.w * b2), s4 = s2 / b2;
         float n2, n4;
         fmm_moment_norms2(rec + (long long)c * FMM_NREC, s2, s4, n2, n4);
-        mn = make_float2(fminf(sqrtf(n2), 1.0f), fminf(sqrtf(n4), 1.0f));
+        mn.x = fminf(sqrtf(n2), 1.0f);
+        mn.y = fminf(sqrtf(n4), 1.0f);
     }
     mnorm[c] = mn;
 }

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
     unsigned int* __restrict__ pc,
     long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
     Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
-    DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float2* __restrict__ mnorm,
+    DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float4* __restrict__ mnorm,
+    const float* __restrict__ amin,
     float eps, float band_lo, float band_hi, float tau, const unsigned char* __restrict__ mlp_packed,
     int2* __restrict__ audit_pairs, long long audit_cap)
 {
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
         const WalkNode K = node[k];
         const bool kg = K.d.w <= group;
         const float rk = K.a.w, bk = K.b.w;
+        const float ak = MODE == 1 ? amin[k] : 0.0f;
         const unsigned long long cl0 = f_cloff[fi];
         const long long ncl = f_cllen[fi];
         long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
@@ -151,8 +153,8 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
                     float f[MLP_F];
 #pragma unroll
                     for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
-                    if (need) mlp_pair_features(K, S, mnorm[e], eps, f);
-                    const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane);
+                    if (need) mlp_pair_features(K, S, mnorm[e], ak, eps, f);
+                    const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane, nm);
                     if (need) acc = pred < tau;
                     n_mlp += __popc(nm);
                 }
@@ -472,7 +474,7 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],      \
         w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
         w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
-        a.bucket, a.group, a.four_eps2, t.mnorm, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
+        a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
         a.audit_cap
     if (a.mode == 1) {
         const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;

@@ -113,10 +113,19 @@ def test_audit_labels_and_features_match_oracle(ctx):
     assert np.allclose(feats[:, 4], np.log2(sn), rtol=5e-7, atol=5e-7)
     assert np.allclose(feats[:, 5], np.log2(kn), rtol=5e-7, atol=5e-7)
     assert np.all((feats[:, 6:] >= 0) & (feats[:, 6:] <= 1)) and np.all(np.isfinite(feats))
-    # labels of a sample of pairs recomputed by the oracle (FP64 expansion and direct sum)
     f = oracle.FMM(pos, mass, eps, theta)
     perm = f.perm()
     ps, msr, rs = pos[:, perm], mass[perm].astype(np.float64), ref[:, perm]
+    # the relative monopole feature log10(M_s / (d^2 a_k)), a_k the smallest |a| (of the FP32
+    # reference handed to the audit) among the sink's particles
+    r32 = np.linalg.norm(ref.astype(np.float32).astype(np.float64)[:, perm], axis=0)
+    for q in np.random.default_rng(1).choice(m, 200, replace=False):
+        xs, ms_ = ps[:, sf[q]:sf[q] + sn[q]], msr[sf[q]:sf[q] + sn[q]]
+        xk, mk = ps[:, kf[q]:kf[q] + kn[q]], msr[kf[q]:kf[q] + kn[q]]
+        d2 = np.sum(((xs * ms_).sum(1) / ms_.sum() - (xk * mk).sum(1) / mk.sum()) ** 2)
+        want = np.log10(ms_.sum() / (d2 * r32[kf[q]:kf[q] + kn[q]].min()))
+        assert abs(feats[q, 3] - want) <= 2e-3 * max(1.0, abs(want)), (q, feats[q, 3], want)
+    # labels of a sample of pairs recomputed by the oracle (FP64 expansion and direct sum)
     rng = np.random.default_rng(0)
     checked = 0
     for q in rng.choice(m, 60, replace=False):
@@ -132,10 +141,13 @@ def _rms_p99(a, ref):
     return float(np.sqrt(np.mean(e ** 2))), float(np.quantile(e, 0.99))
 
 
-def _solve(ctx, pos, mass, eps, theta, criterion=0, tau=-3.5):
+def _solve(ctx, pos, mass, eps, theta, criterion=0, tau=-3.5, estimate=None):
+    """One solve; with the learned criterion, acc starts as the acceleration estimate."""
     n = mass.size
     ctx.set_params(criterion=criterion, mlp_tau=tau)
     acc = torch.zeros(3 * n, dtype=torch.float32, device="cuda:0")
+    if estimate is not None:
+        acc.copy_(t(estimate, torch.float32))
     ctx.compute_forces(t(pos, torch.float64), t(mass, torch.float32), eps, theta, acc)
     torch.cuda.synchronize()
     st = ctx.stats()
@@ -182,9 +194,11 @@ def test_learned_criterion_gain_at_equal_error(ctx):
     for th in (0.4, 0.5, 0.55, 0.6, 0.7, 0.8):
         a, fl, _ = _solve(ctx, pos, mass, eps, th)
         fixed.append((_rms_p99(a, ref)[0], fl))
+        if th == 0.55:
+            estimate = a  # the estimate a time step would carry over: a fixed-theta solve
     learned = []
-    for tau in (-5.0, -4.5, -4.0, -3.5, -3.0, -2.5):
-        a, fl, st = _solve(ctx, pos, mass, eps, 0.55, criterion=1, tau=tau)
+    for tau in (-6.5, -6.0, -5.5, -5.0, -4.5, -4.0, -3.5):
+        a, fl, st = _solve(ctx, pos, mass, eps, 0.55, criterion=1, tau=tau, estimate=estimate)
         rms, p99 = _rms_p99(a, ref)
         learned.append((rms, fl))
         assert st["n_learned"] > 0
