@@ -222,9 +222,13 @@ fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung,
  * (d distance of the centres of mass, M_s the source's mass, a_k the smallest acceleration
  * estimate of the sink's particles).  Parameters: FMM_MLP_NP
  * floats, W1 [64x8], b1 [64], W2 [64x64], b2 [64], W3 [64x64], b3 [64], w4 [64], b4 [1] (row-
- * major), then the feature normalisation mean [8] and inv_std [8].  Inference runs on the tensor
- * cores with BF16 weights and FP32 accumulation; training in FP32 with Adam. */
-#define FMM_MLP_NP 8977
+ * major), then the feature normalisation mean [8] and inv_std [8], then a surrogate bound
+ * [alpha, beta, r_lo, r_hi, gamma[8]]: pairs whose y_lin = f_3 + alpha log10(theta_eff) + beta +
+ * sum_i gamma_i f_i (f the raw features) satisfies y_lin + r_hi < mlp_tau are accepted and those
+ * with y_lin + r_lo >= mlp_tau are rejected without evaluating the network (training sets it from
+ * the labels and the network's residuals; r_hi <= r_lo turns it off).  Inference runs on the tensor cores with BF16 weights and
+ * FP32 accumulation; training in FP32 with Adam. */
+#define FMM_MLP_NP 8989
 #define FMM_MLP_NW 8961
 
 /* Load (host, FMM_MLP_NP floats) or read back the context's network parameters. */
@@ -241,8 +245,8 @@ fmm_status fmm_mlp_gradient(fmm_ctx *ctx, const float *feats, const float *label
 
 /* Train the network on n labelled rows (device): feature normalisation from the data, weights
  * initialised from seed (He-uniform, output bias = mean label), then epochs of Adam on shuffled
- * minibatches of `batch` rows with learning rate lr.  *final_loss (host, may be NULL) gets the
- * last epoch's mean training loss. */
+ * minibatches of `batch` rows with learning rate lr; last, the surrogate bound is fitted to the
+ * same rows.  *final_loss (host, may be NULL) gets the last epoch's mean training loss. */
 fmm_status fmm_mlp_train(fmm_ctx *ctx, const float *feats, const float *labels, long long n, int epochs, int batch,
                          float lr, unsigned int seed, float *final_loss);
 

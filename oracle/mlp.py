@@ -10,7 +10,8 @@ Loss: mean squared error 0.5 * mean((y - label)^2).
 
 Flat parameter layout (shared with the C ABI, float32 there):
     W1 [64 x 8] row-major, b1 [64], W2 [64 x 64], b2 [64], W3 [64 x 64], b3 [64], w4 [64], b4 [1]
-    followed by the feature normalisation: mean [8], inv_std [8]  (x = (f - mean) * inv_std).
+    followed by the feature normalisation: mean [8], inv_std [8]  (x = (f - mean) * inv_std),
+    and N_SUR floats of a surrogate bound that only the walk uses (zero here).
 """
 from __future__ import annotations
 
@@ -21,7 +22,8 @@ F = 8
 SIZES = [("W1", (H, F)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, H)), ("b3", (H,)),
          ("w4", (H,)), ("b4", (1,))]
 N_WEIGHTS = sum(int(np.prod(s)) for _, s in SIZES)  # 8961
-N_PARAMS = N_WEIGHTS + 2 * F
+N_SUR = 12  # the surrogate bound (alpha, beta, r_lo, r_hi, gamma[8]), which only the walk uses
+N_PARAMS = N_WEIGHTS + 2 * F + N_SUR
 
 
 def unpack(flat):
@@ -33,12 +35,14 @@ def unpack(flat):
         o += k
     out["mean"] = flat[o:o + F]
     out["inv_std"] = flat[o + F:o + 2 * F]
+    out["surrogate"] = flat[o + 2 * F:o + 2 * F + N_SUR]
     return out
 
 
 def pack(p):
+    sur = np.asarray(p.get("surrogate", np.zeros(N_SUR)), dtype=np.float64)
     return np.concatenate([np.asarray(p[name], dtype=np.float64).reshape(-1) for name, _ in SIZES] +
-                          [np.asarray(p["mean"], dtype=np.float64), np.asarray(p["inv_std"], dtype=np.float64)])
+                          [np.asarray(p["mean"], dtype=np.float64), np.asarray(p["inv_std"], dtype=np.float64), sur])
 
 
 def forward(flat, feats):

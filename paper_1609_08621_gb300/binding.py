@@ -283,7 +283,7 @@ class Context:
         return s.as_dict()
 
     # -- learned criterion
-    MLP_NP = 8977
+    MLP_NP = 8989
     MLP_NW = 8961
 
     def mlp_load(self, params):

@@ -100,6 +100,8 @@ struct fmm_ctx {
     long long audit_cap = 0;
     unsigned int* mlp_idx = nullptr;
     long long mlp_idx_cap = 0;
+    float* mlp_pred = nullptr;  // predictions over the training rows (surrogate fit)
+    long long mlp_pred_cap = 0;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
     float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
@@ -169,7 +171,7 @@ static void free_all(fmm_ctx* c)
     if (t.box_off_h) cudaFreeHost(t.box_off_h);
     if (c->totals_h) cudaFreeHost(c->totals_h);
     void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact, c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v, c->mlp_loss,
-                  c->mlp_packed, c->audit_pairs, c->mlp_idx};
+                  c->mlp_packed, c->audit_pairs, c->mlp_idx, c->mlp_pred};
     for (void* p : hs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -1025,6 +1027,102 @@ extern "C" fmm_status fmm_mlp_train(fmm_ctx* c, const float* feats, const float*
         CK(cudaStreamSynchronize(s));
         if (!isfinite(last)) return fail(FMM_ERR_NUMERIC, "training diverged at epoch %d", ep);
     }
+    CK(fmm_mlp_pack(c->mlp_p, c->mlp_packed, s));
+    // surrogate bound: y_lin = f3 + alpha log10(theta_eff) + beta + sum_i gamma_i f_i fitted to the
+    // labels by least squares (normal equations in FP64, columns scaled to unit RMS), then the
+    // 0.05% and 99.95% quantiles of the network's residual y_net - y_lin
+    if (n > c->mlp_pred_cap) {
+        CK(alloc(&c->mlp_pred, n));
+        c->mlp_pred_cap = n;
+    }
+    CK(fmm_mlp_predict(c->mlp_packed, feats, n, c->mlp_pred, s));
+    std::vector<float> pred((size_t)n);
+    CK(cudaMemcpyAsync(pred.data(), c->mlp_pred, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int NC = 2 + MLP_F;  // columns: log10(theta_eff), 1, f_0..f_7
+    auto columns = [&](long long i, double* x) -> bool {
+        const double te = 1.5 * hf[i * MLP_F + 1] + hf[i * MLP_F + 0];
+        if (!(te > 0)) return false;
+        x[0] = log10(te);
+        x[1] = 1.0;
+        for (int k = 0; k < MLP_F; k++) x[2 + k] = hf[i * MLP_F + k];
+        for (int k = 0; k < NC; k++)
+            if (!isfinite(x[k])) return false;
+        return isfinite((double)hl[i]) && isfinite((double)pred[i]);
+    };
+    std::vector<double> scale(NC, 0.0);
+    double cnt = 0;
+    {
+        double x[2 + MLP_F];
+        for (long long i = 0; i < n; i++) {
+            if (!columns(i, x)) continue;
+            for (int k = 0; k < NC; k++) scale[k] += x[k] * x[k];
+            cnt += 1;
+        }
+    }
+    float sur[MLP_NSUR] = {};  // off unless the fit is well posed
+    if (cnt > 100) {
+        for (int k = 0; k < NC; k++) scale[k] = scale[k] > 0 ? 1.0 / sqrt(scale[k] / cnt) : 1.0;
+        std::vector<double> G((size_t)NC * NC, 0.0), rhs(NC, 0.0);
+        double x[2 + MLP_F];
+        for (long long i = 0; i < n; i++) {
+            if (!columns(i, x)) continue;
+            const double z = hl[i] - hf[i * MLP_F + 3];
+            for (int a = 0; a < NC; a++) {
+                const double xa = x[a] * scale[a];
+                rhs[a] += xa * z;
+                for (int b = 0; b <= a; b++) G[a * NC + b] += xa * x[b] * scale[b];
+            }
+        }
+        for (int a = 0; a < NC; a++) {
+            G[a * NC + a] += 1e-9 * cnt;  // ridge: keeps collinear columns solvable
+            for (int b = a + 1; b < NC; b++) G[a * NC + b] = G[b * NC + a];
+        }
+        // Gauss-Jordan elimination with partial pivoting
+        std::vector<double> coef(rhs);
+        bool ok = true;
+        for (int col = 0; col < NC && ok; col++) {
+            int piv = col;
+            for (int r = col + 1; r < NC; r++)
+                if (fabs(G[r * NC + col]) > fabs(G[piv * NC + col])) piv = r;
+            if (!(fabs(G[piv * NC + col]) > 0)) {
+                ok = false;
+                break;
+            }
+            if (piv != col) {
+                for (int k = 0; k < NC; k++) std::swap(G[col * NC + k], G[piv * NC + k]);
+                std::swap(coef[col], coef[piv]);
+            }
+            for (int r = 0; r < NC; r++) {
+                if (r == col) continue;
+                const double m = G[r * NC + col] / G[col * NC + col];
+                for (int k = col; k < NC; k++) G[r * NC + k] -= m * G[col * NC + k];
+                coef[r] -= m * coef[col];
+            }
+        }
+        if (ok) {
+            for (int a = 0; a < NC; a++) coef[a] = coef[a] / G[a * NC + a] * scale[a];
+            std::vector<float> r;
+            r.reserve((size_t)cnt);
+            for (long long i = 0; i < n; i++) {
+                if (!columns(i, x)) continue;
+                double y = hf[i * MLP_F + 3];
+                for (int a = 0; a < NC; a++) y += coef[a] * x[a];
+                r.push_back((float)(pred[i] - y));
+            }
+            const size_t klo = r.size() / 2000, khi = r.size() - 1 - r.size() / 2000;
+            std::nth_element(r.begin(), r.begin() + klo, r.end());
+            const float rlo = r[klo];
+            std::nth_element(r.begin(), r.begin() + khi, r.end());
+            const float rhi = r[khi];
+            sur[0] = (float)coef[0];
+            sur[1] = (float)coef[1];
+            sur[2] = rlo;
+            sur[3] = rhi;
+            for (int k = 0; k < MLP_F; k++) sur[4 + k] = (float)coef[2 + k];
+        }
+    }
+    CK(cudaMemcpyAsync(c->mlp_p + MLP_SUR, sur, sizeof sur, cudaMemcpyHostToDevice, s));
     CK(fmm_mlp_pack(c->mlp_p, c->mlp_packed, s));
     CK(cudaStreamSynchronize(s));
     c->mlp_ready = true;

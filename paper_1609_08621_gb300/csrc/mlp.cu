@@ -39,6 +39,7 @@ __global__ void k_mlp_pack(const float* __restrict__ p, unsigned char* __restric
         reinterpret_cast<float*>(out + MLPP_MEAN)[i] = p[MLP_MEAN + i];
         reinterpret_cast<float*>(out + MLPP_ISTD)[i] = p[MLP_ISTD + i];
     }
+    if (i < MLP_NSUR) reinterpret_cast<float*>(out + MLPP_SUR)[i] = p[MLP_SUR + i];
 }
 
 cudaError_t fmm_mlp_pack(const float* params, unsigned char* packed, cudaStream_t s)

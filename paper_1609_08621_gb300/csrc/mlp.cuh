@@ -27,7 +27,11 @@
 #define MLP_NW (MLP_B4 + 1)          // 8961 trainable weights
 #define MLP_MEAN MLP_NW
 #define MLP_ISTD (MLP_MEAN + MLP_F)
-#define MLP_NP (MLP_ISTD + MLP_F)    // 8977 parameters in all
+// surrogate bound of the network's output, set by training: alpha, beta, r_lo, r_hi, then the
+// coefficients gamma[8] of the raw features (see mlp_surrogate); r_hi <= r_lo switches it off
+#define MLP_NSUR 12
+#define MLP_SUR (MLP_ISTD + MLP_F)
+#define MLP_NP (MLP_SUR + MLP_NSUR)  // 8989 parameters in all
 
 // packed inference layout (bytes), identical in global and shared memory; matrix rows are
 // padded (24 / 72 BF16) so the fragment loads of the 8 row groups hit distinct banks
@@ -41,7 +45,8 @@
 #define MLPP_B4 23424    // f32 (16 bytes reserved)
 #define MLPP_MEAN 23440  // [8] f32
 #define MLPP_ISTD 23472  // [8] f32
-#define MLPP_SIZE 23504
+#define MLPP_SUR 23504   // [12] f32
+#define MLPP_SIZE 23552
 // per-warp scratch of the forward pass: inputs [32][24] bf16 and predictions [32] f32
 #define MLP_WARP_SCRATCH (32 * 24 * 2 + 32 * 4)
 
@@ -154,13 +159,15 @@ __device__ __forceinline__ float mlp_predict_warp(const unsigned char* W, unsign
 // opening angle at which the fixed criterion would accept the pair.  A hard guard applies first:
 // never accept unless d > 1.1 (b_max(k) + b_max(s)) (the expansion converges) and the bounding
 // boxes are >= 2 eps apart.  Returns 0 = guard fails (not accepted), 1 = accept without the
-// network (theta_eff < band_lo), 2 = reject (theta_eff >= band_hi), 3 = the network decides.
+// network (theta_eff < band_lo), 2 = reject (theta_eff >= band_hi), 3 = the network decides;
+// te = theta_eff.
 __device__ __forceinline__ int mlp_band(const WalkNode& K, const WalkNode& S, float d2, float gap2, float four_eps2,
-                                        float band_lo, float band_hi)
+                                        float band_lo, float band_hi, float& te)
 {
     const float d = sqrtf(d2), bk = K.b.w, bs = S.b.w;
+    te = 0.0f;
     if (!(d > 1.1f * (bk + bs)) || !(gap2 >= four_eps2)) return 0;
-    const float te = (1.5f * bk + bs) / d;
+    te = (1.5f * bk + bs) / d;
     if (te < band_lo) return 1;
     if (te >= band_hi) return 2;
     return 3;
@@ -185,4 +192,25 @@ __device__ __forceinline__ void mlp_pair_features(const WalkNode& K, const WalkN
     f[5] = log2f((float)K.d.w);
     f[6] = mn.x;
     f[7] = mn.y;
+}
+
+// Surrogate of the network's output, linear in the raw features f[8] around the physical scaling of
+// a truncated expansion's error (the source's monopole field relative to the sink's acceleration,
+// f[3], times a power of the opening angle):
+//   y_lin = f[3] + alpha log10(theta_eff) + beta + sum_i gamma_i f[i].
+// Training fits it to the labels by least squares and records the range [r_lo, r_hi] of the
+// network's residual y_net - y_lin over its training rows (0.05% quantiles).  A pair with
+// y_lin + r_hi < tau is accepted and one with y_lin + r_lo >= tau rejected without running the
+// network; the network decides the rest.  sur: the MLP_NSUR floats.  Returns 1 accept, 2 reject,
+// 3 ask the network.
+__device__ __forceinline__ int mlp_surrogate(const float* sur, const float* f, float te, float tau)
+{
+    const float r_lo = sur[2], r_hi = sur[3];
+    if (!(r_hi > r_lo)) return 3;
+    float y = f[3] + sur[0] * log10f(te) + sur[1];
+#pragma unroll
+    for (int i = 0; i < MLP_F; i++) y = fmaf(sur[4 + i], f[i], y);
+    if (y + r_hi < tau) return 1;
+    if (y + r_lo >= tau) return 2;
+    return 3;
 }

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
             unsigned int e = 0;
             if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
             int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1, nsrc_cell = 0;
+            float f[MLP_F];  // learned criterion: the pair's features (set for band pairs)
             bool sleaf = false, pointlike = false, acc = false, need = false;
             float d2 = 0.0f, ro = 0.0f;
             WalkNode S;
@@ -137,8 +138,13 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
                 const float gap2 = d2_ordered(gx, gy, gz);
                 acc = d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2;
                 if (MODE != 0 && !pointlike) {
-                    const int band = mlp_band(K, S, d2, gap2, four_eps2, band_lo, band_hi);
+                    float te;
+                    int band = mlp_band(K, S, d2, gap2, four_eps2, band_lo, band_hi, te);
                     if (MODE == 1) {
+                        if (band == 3) {
+                            mlp_pair_features(K, S, mnorm[e], ak, eps, f);
+                            band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau);
+                        }
                         acc = band == 1;
                         need = band == 3;
                     } else if (band == 3) {
@@ -150,10 +156,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
             if (MODE == 1) {
                 const unsigned int nm = __ballot_sync(FMM_FULL_MASK, need);
                 if (nm) {
-                    float f[MLP_F];
+                    if (!need) {
 #pragma unroll
-                    for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
-                    if (need) mlp_pair_features(K, S, mnorm[e], ak, eps, f);
+                        for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
+                    }
                     const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane, nm);
                     if (need) acc = pred < tau;
                     n_mlp += __popc(nm);

@@ -178,6 +178,20 @@ def test_training_fits_held_out_labels(ctx):
     y = lte.cpu().numpy()
     r2 = 1.0 - np.mean((pred - y) ** 2) / np.var(y)
     assert np.isfinite(loss) and r2 > 0.8, (loss, r2)
+    # the surrogate bound decides only where it agrees with the network (FP64 reference network,
+    # held-out rows): at most 0.5% of its accepts or rejects go the other way
+    params = ctx.mlp_get().astype(np.float64)
+    sur = omlp.unpack(params)["surrogate"]
+    alpha, beta, r_lo, r_hi, gamma = sur[0], sur[1], sur[2], sur[3], sur[4:]
+    assert r_hi > r_lo
+    f = fte.cpu().numpy().astype(np.float64)
+    y_net, _ = omlp.forward(params, f)
+    y_lin = f[:, 3] + alpha * np.log10(1.5 * f[:, 1] + f[:, 0]) + beta + f @ gamma
+    for tau in (-6.0, -5.0, -4.0, -3.0):
+        acc, rej = y_lin + r_hi < tau, y_lin + r_lo >= tau
+        assert np.mean(y_net[acc] >= tau) <= 5e-3 if acc.any() else True
+        assert np.mean(y_net[rej] < tau) <= 5e-3 if rej.any() else True
+        print(f"tau {tau}: surrogate decides {np.mean(acc | rej):.3f} of the rows")
 
 
 def test_learned_criterion_gain_at_equal_error(ctx):
