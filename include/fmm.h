@@ -157,8 +157,8 @@ fmm_status fmm_build_tree(fmm_ctx *ctx, const double *pos, const float *mass, co
  *   acc    device, 3N floats SoA out (ax|ay|az); entries of inactive particles
  *          are left unchanged.  With criterion 1 it is also read on entry: an estimate of
  *          every particle's acceleration (e.g. the previous step's) that scales the learned
- *          criterion's error budget; a zero estimate makes that criterion reject every pair
- *          it decides
+ *          criterion's error budget; sink cells whose smallest estimate is zero fall back to
+ *          the fixed criterion
  *   pot    device, N floats out, or NULL
  * Returns after completion (see Streams).  Statistics via fmm_get_stats. */
 fmm_status fmm_compute_forces(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,

@@ -141,7 +141,9 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
                     float te;
                     int band = mlp_band(K, S, d2, gap2, four_eps2, band_lo, band_hi, te);
                     if (MODE == 1) {
-                        if (band == 3) {
+                        if (band == 3 && !(ak > 0.0f)) {
+                            band = acc ? 1 : 2;  // no acceleration estimate: the fixed criterion decides
+                        } else if (band == 3) {
                             mlp_pair_features(K, S, mnorm[e], ak, eps, f);
                             band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau);
                         }
