@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--workload", default="nfw2m",
                     choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (buckets 16, groups 64)")
+    ap.add_argument("--no-graphs", action="store_true", help="solve eagerly instead of replaying a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
     ap.add_argument("--n", type=int, default=None,
@@ -183,6 +185,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def tune(args, ctx, tpos, tmass, eps, theta, acc, box_offsets=None, buckets=(16,)):
+    """Autotune group size and work-item size (and the bucket sizes given) before the timed region;
+    returns the chosen settings for the config.  --no-tune keeps buckets of 16, groups of 64."""
+    if args.no_tune:
+        ctx.set_params(bucket=16, group=64, list_chunk=0)
+        return {"bucket": 16, "group": 64, "list_chunk": 64, "tuned": False}
+    cands = [(b, g, ch) for b in buckets for g in (32, 48, 64) for ch in (32, 64, 128) if g >= b]
+    best, ms = ctx.autotune(tpos, tmass, eps, theta, acc, candidates=cands, reps=2, box_offsets=box_offsets)
+    return {"bucket": best.bucket, "group": best.group, "list_chunk": best.list_chunk, "tuned": True,
+            "tuned_over": "bucket %s x group {32,48,64} x list_chunk {32,64,128}" % (list(buckets),)}
+
+
 class Box:
     """One box (nfw2m, plummer4096): a step is one force solve plus one rung-0 kick-drift."""
 
@@ -200,8 +214,10 @@ class Box:
         self.rung = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.act = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.dt0 = 1e-5  # tiny base step: the box barely changes, so every step solves the same workload
-        self.config = {"workload": args.workload, "n": int(n), "eps": self.eps, "theta": self.theta, "bucket": 16,
-                       "group": 64, "l2": "inputs and tree larger than L2 are rebuilt every step"}
+        self.config = {"workload": args.workload, "n": int(n), "eps": self.eps, "theta": self.theta,
+                       "l2": "inputs and tree larger than L2 are rebuilt every step"}
+        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc))
+        self.small = n * 64 < (128 << 20)  # inputs plus tree well inside the 129 MB L2
 
     def step(self, k):
         self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
@@ -251,8 +267,9 @@ class Batch:
         self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
         self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
         self.config = {"workload": "batch64", "boxes": int(w["boxes"]), "n": int(n), "eps": self.eps,
-                       "theta": self.theta, "bucket": 16, "group": 64,
-                       "l2": "inputs and trees larger than L2 are rebuilt every step"}
+                       "theta": self.theta, "l2": "inputs and trees larger than L2 are rebuilt every step"}
+        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc,
+                                box_offsets=self.off, buckets=(8, 12, 16)))
 
     def step(self, k):
         self.ctx.compute_forces_batch(self.tpos, self.tmass, self.off, self.eps, self.theta, self.acc, self.pot)
@@ -317,8 +334,10 @@ class Rungs:
         ctx.assign_rungs(self.acc, self.rung, self.eps, self.dt0, self.R)
         hist = np.bincount(self.rung.cpu().numpy(), minlength=self.R + 1)
         self.config = {"workload": "rungs16m", "n": int(n), "eps": self.eps, "theta": self.theta,
-                       "max_rung": self.R, "dt0": self.dt0, "rung_hist": hist.tolist(), "bucket": 16, "group": 64,
+                       "max_rung": self.R, "dt0": self.dt0, "rung_hist": hist.tolist(),
                        "l2": "inputs and tree larger than L2 are rebuilt every substep"}
+        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc))
+        ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
         self.active_frac = []
 
     def step(self, k):
@@ -504,6 +523,8 @@ def main():
     ctx = binding.Context(local, stream)
     kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned}.get(args.workload, Box)
     wl = kind(args, rank, dev, ctx)
+    ctx.set_graphs(not args.no_graphs)
+    wl.config["cuda_graph"] = not args.no_graphs
 
     def barrier():
         if world > 1:
@@ -525,9 +546,21 @@ def main():
     inter = []
     launches = 0
     active = []
+    # workloads smaller than L2 get L2 flushed (a 256 MB write, outside the step's events) before
+    # every step; larger ones rebuild a tree bigger than L2 each step
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if getattr(wl, "small", False) else None
+    if flush is not None:
+        wl.config["l2"] = "flushed before every step (256 MB write, not timed)"
+    step_ms = []
     e0.record(stream)
     for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
         wl.step(args.warmup + k)
+        s1.record(stream)
+        step_ms.append((s0, s1))
         st = ctx.stats()
         for key in kt:
             kt[key] += st["ms_" + key]
@@ -540,6 +573,8 @@ def main():
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    if flush is not None:
+        ms = float(np.mean([a.elapsed_time(b) for a, b in step_ms]))
     inter_mean = float(np.mean(inter))
     if world > 1:
         import torch.distributed as dist

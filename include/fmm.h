@@ -77,7 +77,8 @@ typedef struct fmm_params {
     int accumulate;        /* 0: a particle's partial sums (one per list chunk of <= 64 entries, and the
                               local expansion) are added in FP32; 1: they are added in FP64 */
     int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion; default 7 */
-    int reserved;          /* must be 0 */
+    int list_chunk;        /* list entries per PP / PC work item: 0 (default, 64) or a multiple of
+                              32 in [32, 1024] */
     long long spin_limit;  /* iteration cap of any device-side wait (default 1<<26) */
     /* learned criterion (criterion = 1), not in the paper: for a source cell with
      * theta_eff = (1.5 b_max(sink) + b_max(source)) / d, the pair is accepted as a cell-cell
@@ -173,6 +174,38 @@ fmm_status fmm_compute_forces(fmm_ctx *ctx, const double *pos, const float *mass
 fmm_status fmm_compute_forces_batch(fmm_ctx *ctx, const double *pos, const float *mass,
                                     const unsigned char *active, long long n, const long long *box_offsets,
                                     int nbox, double eps, double theta, float *acc, float *pot);
+
+/* CUDA graphs (not in the paper).  With enable = 1, a force solve (fmm_compute_forces, _batch,
+ * _host, and the autotuner's solves) that repeats the previous call's buffers (pos, mass,
+ * active, acc, pot pointers), n, box offsets, eps, theta and parameters replays a CUDA graph of
+ * the whole solve: one launch, no host synchronisation inside, one at the end.  The first call of
+ * a new combination runs eagerly and captures the graph (on the context's stream, in thread-local
+ * capture mode) for the next.  A replay that finds a buffer or the walk's level count too small
+ * repeats the solve eagerly, which grows what it must, and recaptures.  Results are identical to
+ * eager solves.  enable = 0 (the default) drops the graph.  The contents of the buffers may change
+ * between calls; their addresses may not (a new address means a new capture). */
+fmm_status fmm_set_graphs(fmm_ctx *ctx, int enable);
+
+/* Whether a graph is currently captured (*captured 0/1) and how many solves replayed one so far
+ * (*replays); either pointer may be NULL. */
+fmm_status fmm_graph_info(const fmm_ctx *ctx, int *captured, long long *replays);
+
+/* Autotuner (not in the paper): times force solves of the given particles (device buffers, as
+ * for fmm_compute_forces; box_offsets/nbox as for fmm_compute_forces_batch, or NULL/1 for one box)
+ * for each candidate setting and leaves the fastest in the context's parameters.
+ *   candidates   host array of n_candidates fmm_params of which bucket, group and list_chunk are
+ *                tried (the other fields stay the context's), or NULL for the built-in grid:
+ *                bucket {8, 12, 16} x group {32, 48, 64} x list_chunk {32, 64, 128}
+ *   reps         timed solves per candidate after one untimed solve, 1..100
+ *   acc          device scratch of 3N floats (overwritten)
+ *   best, best_ms  HOST outputs (may be NULL): the chosen parameters and their mean time per
+ *                solve in ms (CUDA events on the context's stream)
+ * Every candidate is a valid FMM at the same theta; they differ in how work is cut (leaf and group
+ * sizes, work-item size), so the force errors differ only slightly.  A failing candidate stops
+ * the tuner with its error and restores the previous parameters. */
+fmm_status fmm_autotune(fmm_ctx *ctx, const double *pos, const float *mass, long long n, const long long *box_offsets,
+                        int nbox, double eps, double theta, const fmm_params *candidates, int n_candidates, int reps,
+                        float *acc, fmm_params *best, float *best_ms);
 
 /* Same as fmm_compute_forces with HOST buffers: pos (3N doubles), mass (N floats),
  * active (N bytes or NULL) are copied to device memory owned by the context, and

@@ -31,7 +31,7 @@ class FmmError(RuntimeError):
 
 class fmm_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("bucket", C.c_int), ("group", C.c_int),
-                ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("reserved", C.c_int),
+                ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("list_chunk", C.c_int),
                 ("spin_limit", C.c_longlong), ("mlp_tau", C.c_double), ("band_lo", C.c_double),
                 ("band_hi", C.c_double)]
 
@@ -97,6 +97,9 @@ def load(build_if_missing: bool = True):
         "fmm_mlp_audit": (i, [vp, vp, vp, ll, d, d, d, d, vp, ll, vp, vp, C.POINTER(ll)]),
         "fmm_mlp_audit_pairs": (i, [vp, vp, vp, vp, vp, ll]),
         "fmm_morton_order_static": (i, [vp, ll, vp, vp, vp]),
+        "fmm_set_graphs": (i, [vp, i]),
+        "fmm_graph_info": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
+        "fmm_autotune": (i, [vp, vp, vp, ll, vp, i, d, d, vp, i, i, vp, C.POINTER(fmm_params), C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -249,6 +252,38 @@ class Context:
                                                off.size - 1, float(eps), float(theta),
                                                _ptr(acc, torch.float32, 3 * n, "acc"),
                                                _ptr(pot, torch.float32, n, "pot", True)))
+
+    def set_graphs(self, enable=True):
+        _check(load().fmm_set_graphs(self.h, 1 if enable else 0))
+
+    def graph_info(self):
+        cap, rep = C.c_int(), C.c_longlong()
+        _check(load().fmm_graph_info(self.h, C.byref(cap), C.byref(rep)))
+        return {"captured": bool(cap.value), "replays": rep.value}
+
+    def autotune(self, pos, mass, eps, theta, acc, candidates=None, reps=2, box_offsets=None):
+        """Time each candidate (list of (bucket, group, list_chunk)) or the built-in grid; the
+        fastest stays in the context.  Returns (best fmm_params, ms per solve)."""
+        import torch
+
+        n = mass.numel()
+        arr, nc = None, 0
+        if candidates is not None:
+            arr = (fmm_params * len(candidates))()
+            for k, (b, g, ch) in enumerate(candidates):
+                arr[k].bucket, arr[k].group, arr[k].list_chunk = b, g, ch
+            nc = len(candidates)
+        off, nbox = None, 1
+        if box_offsets is not None:
+            off = np.ascontiguousarray(box_offsets, dtype=np.int64)
+            nbox = off.size - 1
+        best = fmm_params()
+        ms = C.c_float()
+        _check(load().fmm_autotune(self.h, _ptr(pos, torch.float64, 3 * n, "pos"), _ptr(mass, torch.float32, n, "mass"),
+                                   n, None if off is None else off.ctypes.data, nbox, float(eps), float(theta),
+                                   None if arr is None else C.cast(arr, C.c_void_p), nc, int(reps),
+                                   _ptr(acc, torch.float32, 3 * n, "acc"), C.byref(best), C.byref(ms)))
+        return best, float(ms.value)
 
     def compute_forces_host(self, pos, mass, eps, theta, acc, pot=None, active=None):
         """Host (numpy) buffers; copies happen inside the library call."""

@@ -102,6 +102,21 @@ struct fmm_ctx {
     long long mlp_idx_cap = 0;
     float* mlp_pred = nullptr;  // predictions over the training rows (surrogate fit)
     long long mlp_pred_cap = 0;
+    // CUDA graph of the whole solve (fmm_set_graphs): captured after an eager solve and replayed
+    // while the call's inputs, buffers and parameters stay the same
+    bool graphs = false;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;  // capture needs a stream of its own (the caller's may be the legacy one)
+    struct GraphKey {
+        const void *pos, *mass, *active, *acc, *pot;
+        long long n;
+        int nbox;
+        std::vector<long long> off;
+        fmm_params p;
+        double eps, theta;
+    } gkey;
+    int graph_levels = 0, graph_launches = 0;
+    long long graph_replays = 0;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
     float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
@@ -123,7 +138,8 @@ static fmm_status check_params(const fmm_params* p)
     if (!isfinite(p->mlp_tau)) return fail(FMM_ERR_ARG, "mlp_tau must be finite");
     if (p->accumulate != 0 && p->accumulate != 1) return fail(FMM_ERR_ARG, "accumulate must be 0 or 1, got %d", p->accumulate);
     if (p->terms < 0 || p->terms > 7) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4, got %d", p->terms);
-    if (p->reserved != 0) return fail(FMM_ERR_ARG, "reserved must be 0");
+    if (p->list_chunk != 0 && (p->list_chunk < 32 || p->list_chunk > 1024 || p->list_chunk % 32 != 0))
+        return fail(FMM_ERR_ARG, "list_chunk must be 0 or a multiple of 32 in [32, 1024], got %d", p->list_chunk);
     if (p->spin_limit < 1) return fail(FMM_ERR_ARG, "spin_limit must be >= 1");
     return FMM_OK;
 }
@@ -176,6 +192,10 @@ static void free_all(fmm_ctx* c)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->cap_stream = nullptr;
 }
 
 extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
@@ -206,6 +226,7 @@ extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
                     cudaGetErrorString(e));
     }
     c->w.n_warps = fmm_walk_warps(device);
+    c->t.dcount = c->totals;
     *out = c;
     return FMM_OK;
 }
@@ -300,9 +321,8 @@ static fmm_status read_status(fmm_ctx* c, const char* where)
     return FMM_OK;
 }
 
-static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int nbox)
+static fmm_status set_boxes_check(long long n, const long long* off, int nbox)
 {
-    DevTree& t = c->t;
     if (nbox < 1 || nbox > 256) return fail(FMM_ERR_ARG, "nbox must be in [1, 256], got %d", nbox);
     if (off) {
         if (off[0] != 0 || off[nbox] != n) return fail(FMM_ERR_ARG, "box offsets must start at 0 and end at n");
@@ -311,6 +331,14 @@ static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int n
     } else if (nbox != 1) {
         return fail(FMM_ERR_ARG, "box offsets are required for several boxes");
     }
+    return FMM_OK;
+}
+
+static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int nbox)
+{
+    DevTree& t = c->t;
+    fmm_status st = set_boxes_check(n, off, nbox);
+    if (st != FMM_OK) return st;
     t.nbox = nbox;
     if (nbox == 1) return FMM_OK;
     if (nbox + 1 > t.cap_box) {
@@ -518,7 +546,9 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     }
 }
 
-static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
+static fmm_status finish_stats(fmm_ctx* c, long long n);
+
+static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
                         double eps, double theta, float* acc, float* pot, const long long* box_off = nullptr,
                         int nbox = 1)
 {
@@ -552,11 +582,12 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     ia.eps2 = (float)(eps * eps);
     ia.terms = q.terms;
     ia.accumulate = q.accumulate;
+    ia.chunk = q.list_chunk ? q.list_chunk : FMM_LIST_CHUNK;
     if (c->w.n_groups > 0) {
         // work items: at most one partial chunk per group beyond the full chunks
         DevWalk& w = c->w;
-        long long need_pp = w.pp_len / FMM_PP_CHUNK + w.n_groups + 1;
-        long long need_pc = w.pc_len / FMM_PC_CHUNK + w.n_groups + 1;
+        long long need_pp = w.pp_len / ia.chunk + w.n_groups + 1;
+        long long need_pc = w.pc_len / ia.chunk + w.n_groups + 1;
         if (need_pp > w.cap_item_pp) {
             CK(alloc(&w.item_pp, need_pp));
             CK(alloc(&w.part_pp, need_pp * FMM_GMAX));
@@ -567,7 +598,7 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
             CK(alloc(&w.part_pc, need_pc * FMM_GMAX));
             w.cap_item_pc = need_pc;
         }
-        CK(fmm_launch_items(c->t, w, c->ctr, s));
+        CK(fmm_launch_items(c->t, w, c->ctr, ia.chunk, s));
         c->launches += 2 + 2 * 3;
         CK(fmm_launch_pp(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[3], s));
@@ -584,6 +615,11 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     CK(cudaStreamSynchronize(s));
     st = read_status(c, "fmm_compute_forces");
     if (st != FMM_OK) return st;
+    return finish_stats(c, n);
+}
+
+static fmm_status finish_stats(fmm_ctx* c, long long n)
+{
     fmm_stats& S = c->stats;
     S.n = n;
     S.n_cells = c->t.n_cells;
@@ -596,25 +632,296 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     S.n_cp = (long long)c->ctr_h->n_cp;
     S.n_pp_entries = c->w.pp_len;
     S.n_pc_entries = c->w.pc_len;
-    float ms;
-    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
-    S.ms_tree = ms;
-    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
-    S.ms_walk = ms;
-    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
-    S.ms_pp = ms;
-    cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]);
-    S.ms_pc = ms;
-    cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
-    S.ms_l2p = ms;
-    cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]);
-    S.ms_total = ms;
+    float ms[6] = {};
+    const int from[6] = {0, 1, 2, 3, 4, 0}, to[6] = {1, 2, 3, 4, 5, 5};
+    for (int i = 0; i < 6; i++) CK(cudaEventElapsedTime(&ms[i], c->ev[from[i]], c->ev[to[i]]));
+    S.ms_tree = ms[0];
+    S.ms_walk = ms[1];
+    S.ms_pp = ms[2];
+    S.ms_pc = ms[3];
+    S.ms_l2p = ms[4];
+    S.ms_total = ms[5];
     S.paper_flops = 53.0 * S.n_pp_pairs + 215.0 * S.n_pc_pairs + 479.0 * S.n_cc + 213.0 * S.n_cp;
     S.kernel_flops_pp = 19.0 * S.n_pp_pairs;
     S.kernel_flops_pc = (double)FMM_FLOPS_PC * S.n_pc_pairs;
     S.n_launches = c->launches;
     S.n_learned = (long long)c->ctr_h->n_mlp;
     c->have_solve = true;
+    return FMM_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graph of a solve
+
+// Enqueue the whole solve without a host synchronisation: the same launches as solve_eager, with
+// every launch over cells, buckets or groups covering the capacity (kernels read the counts on the
+// device) and the walk run for graph_levels levels (levels past the deepest cell find an empty
+// front).  Used only inside stream capture, after an eager solve has sized every buffer.
+static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
+                                     long long n, const fmm_params& q, float* acc, float* pot,
+                                     const long long* box_off, int nbox)
+{
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    cudaStream_t s = c->stream;
+    c->launches = 0;
+    t.cap_grid = true;
+    struct Reset {
+        DevTree& t;
+        ~Reset() { t.cap_grid = false; }
+    } reset{t};
+    CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
+    fmm_status st = set_boxes(c, n, box_off, nbox);
+    if (st != FMM_OK) return st;
+    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
+    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
+    if (nbox > 1) {
+        CK(fmm_launch_box_sort(t, n, s));
+        c->launches += 8 * 5 + 1 + 2 * 5 + 1;
+    } else {
+        CK(fmm_radix_sort(t, n, s));
+        c->launches += 8 * 5;
+    }
+    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s));
+    CK(fmm_launch_radix_tree(t, n, q.bucket, s));
+    CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
+    CK(cudaMemsetAsync(t.bflag, 0, sizeof(unsigned int) * (size_t)n, s));
+    CK(fmm_launch_cells(t, n, q.bucket, s));
+    CK(fmm_scan_exclusive(t.bflag, t.keep, n, c->totals + 1, t, s));
+    CK(fmm_launch_bucket_index(t, n, s));
+    CK(fmm_launch_depth(t, c->totals, c->ctr, s));
+    CK(fmm_launch_upward(t, n, q.bucket, c->ctr, s));
+    if (nbox > 1) {
+        CK(fmm_launch_box_roots(t, s));
+        c->launches += 1;
+    }
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
+    CK(fmm_launch_nodes(t, q.theta, s));
+    c->launches += 1;
+    CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
+    if (q.criterion == 1) {
+        CK(fmm_launch_cell_amin(t, acc, n, s));
+        c->launches += 1;
+    }
+    WalkArgs a;
+    const float e2 = (float)(2.0 * q.eps);
+    a.four_eps2 = e2 * e2;
+    a.eps2 = (float)(q.eps * q.eps);
+    a.bucket = q.bucket;
+    a.group = q.group;
+    a.eps = (float)q.eps;
+    a.mode = q.criterion;
+    a.band_lo = (float)q.band_lo;
+    a.band_hi = (float)q.band_hi;
+    a.tau = (float)q.mlp_tau;
+    a.mlp_packed = c->mlp_packed;
+    a.audit_pairs = c->audit_pairs;
+    a.audit_cap = c->audit_cap;
+    CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
+    CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.cap_cells, s));
+    CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
+    CK(fmm_launch_walk_seed(t, w, c->ctr, s));
+    c->launches += 1;
+    for (int L = 0; L < c->graph_levels; L++) {
+        a.level = L;
+        a.level_parity = L & 1;
+        CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
+        c->launches += 1;
+    }
+    CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
+    c->launches += 2;
+    CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
+    InteractArgs ia;
+    ia.eps2 = (float)(q.eps * q.eps);
+    ia.terms = q.terms;
+    ia.accumulate = q.accumulate;
+    ia.chunk = q.list_chunk ? q.list_chunk : FMM_LIST_CHUNK;
+    CK(fmm_launch_items(t, w, c->ctr, ia.chunk, s));
+    c->launches += 2 + 2 * 3;
+    CK(fmm_launch_pp(t, w, c->ctr, ia, s));
+    CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
+    CK(fmm_launch_pc(t, w, c->ctr, ia, s));
+    CK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
+    CK(fmm_launch_l2p_out(t, w, c->ctr, ia, acc, pot, n, s));
+    c->launches += ((q.terms & 1) ? 1 : 0) + ((q.terms & 2) ? 1 : 0) + 1;
+    CK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
+    CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    return FMM_OK;
+}
+
+static bool same_params(const fmm_params& a, const fmm_params& b)
+{
+    return a.theta == b.theta && a.eps == b.eps && a.bucket == b.bucket && a.group == b.group &&
+           a.criterion == b.criterion && a.accumulate == b.accumulate && a.terms == b.terms &&
+           a.list_chunk == b.list_chunk && a.spin_limit == b.spin_limit && a.mlp_tau == b.mlp_tau &&
+           a.band_lo == b.band_lo && a.band_hi == b.band_hi;
+}
+
+static fmm_ctx::GraphKey make_key(const double* pos, const float* mass, const unsigned char* active, float* acc,
+                                  float* pot, long long n, const long long* box_off, int nbox, const fmm_params& q,
+                                  double eps, double theta)
+{
+    fmm_ctx::GraphKey k;
+    k.pos = pos;
+    k.mass = mass;
+    k.active = active;
+    k.acc = acc;
+    k.pot = pot;
+    k.n = n;
+    k.nbox = nbox;
+    if (box_off) k.off.assign(box_off, box_off + nbox + 1);
+    k.p = q;
+    k.eps = eps;
+    k.theta = theta;
+    return k;
+}
+
+static bool same_key(const fmm_ctx::GraphKey& a, const fmm_ctx::GraphKey& b)
+{
+    return a.pos == b.pos && a.mass == b.mass && a.active == b.active && a.acc == b.acc && a.pot == b.pot &&
+           a.n == b.n && a.nbox == b.nbox && a.off == b.off && same_params(a.p, b.p) && a.eps == b.eps &&
+           a.theta == b.theta;
+}
+
+static void drop_graph(fmm_ctx* c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
+// Capture the solve just done eagerly (same arguments) into a graph; on any failure the context
+// simply keeps solving eagerly.
+static void capture_graph(fmm_ctx* c, const fmm_ctx::GraphKey& key, const double* pos, const float* mass,
+                          const unsigned char* active, long long n, const fmm_params& q, float* acc, float* pot,
+                          const long long* box_off, int nbox)
+{
+    drop_graph(c);
+    if (c->w.n_groups < 1) return;
+    // buffers the capacity-sized launches need, reserved now (no allocation may happen inside capture)
+    if (fmm_scan_reserve(c->t, std::max(2 * n, c->w.cap_groups)) != cudaSuccess) return;
+    c->graph_levels = c->t.depth + 1 + 4;  // a few levels of slack for a slightly deeper tree
+    if (c->graph_levels + 1 > FMM_MAX_LEVELS) return;
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        cudaGetLastError();
+        return;
+    }
+    // the work is recorded on the context's capture stream; replays launch on the caller's stream
+    const cudaStream_t user = c->stream;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    c->stream = c->cap_stream;
+    const int saved_launches = c->launches;
+    fmm_status st = enqueue_graph_body(c, pos, mass, active, n, q, acc, pot, box_off, nbox);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->stream = user;
+    c->graph_launches = c->launches;
+    c->launches = saved_launches;
+    if (st != FMM_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return;
+    }
+    cudaGraphExec_t ge = nullptr;
+    if (cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+        c->gexec = ge;
+        c->gkey = key;
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+}
+
+enum { GRAPH_DONE = 0, GRAPH_RETRY = 1 };
+
+// Replay the captured solve; GRAPH_RETRY when a capacity or the level count was not enough (the
+// eager path then repeats the solve, growing what it must).
+static fmm_status replay_graph(fmm_ctx* c, long long n, int* outcome)
+{
+    *outcome = GRAPH_RETRY;
+    cudaStream_t s = c->stream;
+    CK(cudaGraphLaunch(c->gexec, s));
+    CK(cudaStreamSynchronize(s));
+    fmm_status st = read_status(c, "fmm_compute_forces");
+    if (st != FMM_OK) return st;
+    const DevCounters& h = *c->ctr_h;
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    if (h.overflow || h.lv_front[c->graph_levels] != 0 || (long long)h.n_groups > w.cap_groups) return FMM_OK;
+    t.n = n;
+    t.n_cells = c->totals_h[0];
+    t.n_buckets = c->totals_h[1];
+    t.depth = (int)h.depth;
+    long long used = 0;
+    while (used < c->graph_levels && h.lv_front[used] > 0) used++;
+    w.n_levels = used;
+    w.n_groups = (long long)h.n_groups;
+    w.pp_len = (long long)h.pp_len;
+    w.pc_len = (long long)h.pc_len;
+    w.cc_len = (long long)h.cc_len;
+    c->have_tree = true;
+    c->theta_nodes = -1.0f;
+    memset(&c->stats, 0, sizeof c->stats);
+    c->stats.n_active = (long long)h.n_active;
+    c->launches = c->graph_launches;
+    st = finish_stats(c, n);
+    if (st != FMM_OK) return st;
+    c->graph_replays++;
+    *outcome = GRAPH_DONE;
+    return FMM_OK;
+}
+
+static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
+                        double eps, double theta, float* acc, float* pot, const long long* box_off = nullptr,
+                        int nbox = 1)
+{
+    if (!c->graphs) return solve_eager(c, pos, mass, active, n, eps, theta, acc, pot, box_off, nbox);
+    fmm_params q = c->params;
+    q.eps = eps;
+    q.theta = theta;
+    fmm_status st = check_params(&q);
+    if (st != FMM_OK) return st;
+    if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
+    if (q.criterion == 1 && !c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
+    st = set_boxes_check(n, box_off, nbox);
+    if (st != FMM_OK) return st;
+    const fmm_ctx::GraphKey key = make_key(pos, mass, active, acc, pot, n, box_off, nbox, q, eps, theta);
+    if (c->gexec && same_key(c->gkey, key)) {
+        c->have_solve = false;
+        int outcome = GRAPH_RETRY;
+        st = replay_graph(c, n, &outcome);
+        if (st != FMM_OK) {
+            drop_graph(c);
+            return st;
+        }
+        if (outcome == GRAPH_DONE) return FMM_OK;
+        drop_graph(c);
+    }
+    st = solve_eager(c, pos, mass, active, n, eps, theta, acc, pot, box_off, nbox);
+    if (st != FMM_OK) return st;
+    const fmm_stats saved = c->stats;
+    capture_graph(c, key, pos, mass, active, n, q, acc, pot, box_off, nbox);
+    c->stats = saved;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_set_graphs(fmm_ctx* c, int enable)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (enable != 0 && enable != 1) return fail(FMM_ERR_ARG, "enable must be 0 or 1");
+    CK(cudaSetDevice(c->device));
+    c->graphs = enable == 1;
+    if (!c->graphs) drop_graph(c);
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_graph_info(const fmm_ctx* c, int* captured, long long* replays)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (captured) *captured = c->gexec ? 1 : 0;
+    if (replays) *replays = c->graph_replays;
     return FMM_OK;
 }
 
@@ -625,6 +932,74 @@ extern "C" fmm_status fmm_compute_forces(fmm_ctx* c, const double* pos, const fl
     fmm_status st = check_common(c, pos, mass, n);
     if (st != FMM_OK) return st;
     return solve(c, pos, mass, active, n, eps, theta, acc, pot);
+}
+
+extern "C" fmm_status fmm_autotune(fmm_ctx* c, const double* pos, const float* mass, long long n,
+                                   const long long* box_offsets, int nbox, double eps, double theta,
+                                   const fmm_params* candidates, int n_candidates, int reps, float* acc,
+                                   fmm_params* best, float* best_ms)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
+    if (reps < 1 || reps > 100) return fail(FMM_ERR_ARG, "reps must be in [1, 100]");
+    if (candidates && (n_candidates < 1 || n_candidates > 4096)) return fail(FMM_ERR_ARG, "bad candidate count");
+    // the built-in grid: bucket x group x list_chunk, group >= bucket
+    std::vector<fmm_params> cand;
+    const fmm_params base = c->params;
+    if (candidates) {
+        for (int i = 0; i < n_candidates; i++) {
+            fmm_params p = base;
+            p.bucket = candidates[i].bucket;
+            p.group = candidates[i].group;
+            p.list_chunk = candidates[i].list_chunk;
+            st = check_params(&p);
+            if (st != FMM_OK) return st;
+            cand.push_back(p);
+        }
+    } else {
+        for (int b : {8, 12, 16})
+            for (int g : {32, 48, 64})
+                for (int ch : {32, 64, 128}) {
+                    fmm_params p = base;
+                    p.bucket = b;
+                    p.group = g;
+                    p.list_chunk = ch;
+                    cand.push_back(p);
+                }
+    }
+    cudaStream_t s = c->stream;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_t = INFINITY;
+    fmm_params best_p = base;
+    for (const fmm_params& p : cand) {
+        c->params = p;
+        st = solve(c, pos, mass, nullptr, n, eps, theta, acc, nullptr, box_offsets, nbox);  // untimed
+        float t = 0.0f;
+        if (st == FMM_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == FMM_OK; r++)
+                st = solve(c, pos, mass, nullptr, n, eps, theta, acc, nullptr, box_offsets, nbox);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t, e0, e1);
+            t /= (float)reps;
+        }
+        if (st != FMM_OK) break;
+        if (t < best_t) {
+            best_t = t;
+            best_p = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->params = st == FMM_OK ? best_p : base;
+    if (st != FMM_OK) return st;
+    if (best) *best = best_p;
+    if (best_ms) *best_ms = best_t;
+    return FMM_OK;
 }
 
 extern "C" fmm_status fmm_compute_forces_batch(fmm_ctx* c, const double* pos, const float* mass,

@@ -48,8 +48,7 @@ struct __align__(16) Group {
     int pp_len, pc_len;
 };
 
-#define FMM_PP_CHUNK 64   // PP list entries per work item
-#define FMM_PC_CHUNK 64   // PC list entries per work item
+#define FMM_LIST_CHUNK 64  // default list entries per PP / PC work item
 #define FMM_GMAX 64       // sink slots per group
 #define FMM_MAX_LEVELS 192  // walk levels: tree depth + 1 (63 key bits + 31 position bits at most)
 
@@ -82,6 +81,11 @@ struct DevTree {
     long long n = 0, cap_n = 0;
     long long n_cells = 0, cap_cells = 0, n_buckets = 0;
     int depth = 0;
+    // device copies of the cell and bucket counts [n_cells, n_buckets]; kernels over cells or
+    // buckets read their bound there, so a launch may cover the capacity (graph capture, where
+    // the host does not know the counts) instead of the count
+    const unsigned int* dcount = nullptr;
+    bool cap_grid = false;
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;
     unsigned int *idx = nullptr, *idx_alt = nullptr;
@@ -137,8 +141,8 @@ struct DevWalk {
     int *lcc_len = nullptr;
     int *lcells = nullptr;                  // cells with a non-empty local list
     float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
-    // work items of the interaction kernels: group g's PP list is cut into chunks of
-    // FMM_PP_CHUNK entries (items base_pp[g] ..), its PC list into chunks of FMM_PC_CHUNK cells;
+    // work items of the interaction kernels: group g's PP list is cut into chunks of list_chunk
+    // entries (items base_pp[g] ..), its PC list into chunks of list_chunk cells;
     // every item writes one partial result per sink slot, summed per sink in item order
     unsigned int *cnt_pp = nullptr, *cnt_pc = nullptr, *base_pp = nullptr, *base_pc = nullptr;
     unsigned int *item_pp = nullptr, *item_pc = nullptr;
@@ -162,6 +166,7 @@ cudaError_t fmm_radix_sort(DevTree& t, long long n, cudaStream_t s);
 cudaError_t fmm_radix_sort_kv(unsigned long long* ka, unsigned long long* kb, unsigned int* va, unsigned int* vb,
                               long long n, int passes, DevTree& t, cudaStream_t s);
 cudaError_t fmm_sort_ensure(DevTree& t, long long n);
+cudaError_t fmm_scan_reserve(DevTree& t, long long n);
 long long fmm_sort_hist_entries(long long n);
 long long fmm_sort_part_entries(long long n);
 cudaError_t fmm_sort_prepare();
@@ -208,8 +213,9 @@ struct InteractArgs {
     float eps2;
     int terms;
     int accumulate;
+    int chunk;  // list entries per PP / PC work item (multiple of 32)
 };
-cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk, cudaStream_t s);
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,

@@ -11,8 +11,8 @@
 // per bucket or cell (never per interaction: FP64 issue is 1/64 of FP32 on this GPU),
 // and fl(x - com_bucket) is stored per particle by the upward pass.
 //
-// Work items: each group's PP list is cut into chunks of FMM_PP_CHUNK entries and its PC list
-// into chunks of FMM_PC_CHUNK cells; a persistent grid of warps takes items from an atomic
+// Work items: each group's PP list is cut into chunks of `chunk` entries and its PC list into
+// chunks of `chunk` cells (list_chunk, default 64); a persistent grid of warps takes items from an atomic
 // counter, so a group with a very long list no longer sets the kernel's duration.  Each item
 // writes one partial (ax, ay, az, phi) per sink slot; the output kernel adds a sink's
 // partials in item order (deterministic), then the local expansion.
@@ -122,12 +122,12 @@ __device__ __forceinline__ long long pp_item(const Group& G, int chunk, const Co
                                              const int* __restrict__ ccount, const Com4* __restrict__ com,
                                              const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                              const float4* __restrict__ off, float4* __restrict__ part, float4* T,
-                                             PPChunk& E, float eps2, int lane)
+                                             PPChunk& E, float eps2, int lane, int csize)
 {
     Sinks<R, Q> K;
     K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
     long long nsrc = 0;
-    const int e0 = chunk * FMM_PP_CHUNK, e1 = min(e0 + FMM_PP_CHUNK, G.pp_len);
+    const int e0 = chunk * csize, e1 = min(e0 + csize, G.pp_len);
     {
         for (int base = e0; base < e1; base += 32) {
             const int ne = min(32, e1 - base);
@@ -208,13 +208,15 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
                                                  const int* __restrict__ ccount, const int* __restrict__ cnact,
                                                  const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                                 float4* __restrict__ part_pp, float eps2, DevCounters* __restrict__ ctr)
+                                                 float4* __restrict__ part_pp, float eps2, int csize,
+                                                 long long cap_items, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 tile[IW][PP_TILE];
     __shared__ PPChunk chunk[IW];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     float4* T = tile[wl];
-    const unsigned long long n_items = *(volatile unsigned int*)&ctr->n_item_pp;
+    const unsigned long long n_items =
+        min((unsigned long long)*(volatile unsigned int*)&ctr->n_item_pp, (unsigned long long)cap_items);
     unsigned long long pairs = 0;
     for (;;) {
         unsigned long long i = 0;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
         const int n = G.count;
         float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
-#define PP_CALL(R, Q) pp_item<R, Q>(G, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane)
+#define PP_CALL(R, Q) pp_item<R, Q>(G, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
         if (n <= 8) nsrc = PP_CALL(1, 4);
         else if (n <= 16) nsrc = PP_CALL(1, 2);
         else if (n <= 24) nsrc = PP_CALL(3, 4);
@@ -250,7 +252,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q,
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
                                         float4* __restrict__ part, float4* R4, float4* Z, int* ids, float eps2,
-                                        int lane)
+                                        int lane, int csize)
 {
     const int S = 32 / Q, split = lane / S, slot = lane % S;
     float ux[PC_RMAX], uy[PC_RMAX], uz[PC_RMAX];
@@ -265,7 +267,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q,
             load_sink(G.first + i, ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
         }
     }
-    const int e0 = chunk * FMM_PC_CHUNK, e1 = min(e0 + FMM_PC_CHUNK, G.pc_len);
+    const int e0 = chunk * csize, e1 = min(e0 + csize, G.pc_len);
     for (int base = e0; base < e1; base += PC_CHUNK) {
         const int ne = min(PC_CHUNK, e1 - base);
         if (lane < ne) {
@@ -320,14 +322,16 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
                                                  const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  const float* __restrict__ rec, float4* __restrict__ part_pc,
-                                                 float eps2, DevCounters* __restrict__ ctr)
+                                                 float eps2, int csize, long long cap_items,
+                                                 DevCounters* __restrict__ ctr)
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
     __shared__ int idss[IW][PC_CHUNK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
-    const unsigned long long n_items = *(volatile unsigned int*)&ctr->n_item_pc;
+    const unsigned long long n_items =
+        min((unsigned long long)*(volatile unsigned int*)&ctr->n_item_pc, (unsigned long long)cap_items);
     unsigned long long pairs = 0;
     for (;;) {
         unsigned long long i = 0;
@@ -347,9 +351,9 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         else if (n <= 48) { R = 3; Q = 2; }
         else { R = 2; Q = 1; }
         pc_item(G, k, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
-                idss[wl], eps2, lane);
+                idss[wl], eps2, lane, csize);
         if (lane == 0) {
-            const int nc = min(FMM_PC_CHUNK, G.pc_len - k * FMM_PC_CHUNK);
+            const int nc = min(csize, G.pc_len - k * csize);
             pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nc;
         }
     }
@@ -360,7 +364,9 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
 // local expansion, and the result goes to the caller's order (active particles only).
 // T = float: partial sums added in FP32; T = double: added in FP64 (accumulate = 1)
 template <typename T>
-__global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ groups, long long n_groups,
+__global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ groups,
+                                                      const unsigned long long* __restrict__ ngroups_dev, long long cap_groups,
+                                                      long long cap_item_pp, long long cap_item_pc,
                                                       const Com4* __restrict__ com,
                                                       const int* __restrict__ bucket_of,
                                                       const int* __restrict__ bucket_cell,
@@ -379,13 +385,17 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long n_groups = (long long)min(*ngroups_dev, (unsigned long long)cap_groups);
     for (long long gi = gw; gi < n_groups; gi += nw) {
         const Group G = groups[gi];
         const Com4 ck = com[G.cell];
         for (int i = lane; i < FMM_NL; i += 32) Ls[wl][i] = Lg[gi * FMM_NL + i];
         __syncwarp();
-        const unsigned int npp = (terms & 1) ? cnt_pp[gi] : 0u, bpp = base_pp[gi];
-        const unsigned int npc = (terms & 2) ? cnt_pc[gi] : 0u, bpc = base_pc[gi];
+        // items beyond the buffers (an overflow the host then repairs) are skipped
+        unsigned int npp = (terms & 1) ? cnt_pp[gi] : 0u, bpp = base_pp[gi];
+        unsigned int npc = (terms & 2) ? cnt_pc[gi] : 0u, bpc = base_pc[gi];
+        if ((long long)bpp + npp > cap_item_pp) npp = 0;
+        if ((long long)bpc + npc > cap_item_pc) npc = 0;
         for (int i = lane; i < G.count; i += 32) {
             const int s = G.first + i;
             T ax = 0, ay = 0, az = 0, aw = 0;
@@ -450,38 +460,50 @@ static int persistent_blocks(K kernel)
     return (per_sm < 1 ? 1 : per_sm) * sms;
 }
 
-// Work items: per group ceil(pp_len / FMM_PP_CHUNK) PP items and ceil(pc_len / FMM_PC_CHUNK)
-// PC items; exclusive scans give each group's first item, and every item learns its group.
-__global__ void k_item_counts(const Group* __restrict__ groups, long long ng, unsigned int* __restrict__ cnt_pp,
-                              unsigned int* __restrict__ cnt_pc)
+// Work items: per group ceil(pp_len / chunk) PP items and ceil(pc_len / chunk) PC items; exclusive scans give each group's first item, and every item learns its group.
+__global__ void k_item_counts(const Group* __restrict__ groups, long long grid, const unsigned long long* __restrict__ ng,
+                              unsigned int* __restrict__ cnt_pp, unsigned int* __restrict__ cnt_pc, int csize)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ng) return;
+    if (i >= grid) return;
+    if (i >= (long long)*ng) {  // slots past the group count (capacity-sized launches) add nothing
+        cnt_pp[i] = 0u;
+        cnt_pc[i] = 0u;
+        return;
+    }
     const Group G = groups[i];
-    cnt_pp[i] = (unsigned int)fmm_ceil_div(G.pp_len, FMM_PP_CHUNK);
-    cnt_pc[i] = (unsigned int)fmm_ceil_div(G.pc_len, FMM_PC_CHUNK);
+    cnt_pp[i] = (unsigned int)fmm_ceil_div(G.pp_len, csize);
+    cnt_pc[i] = (unsigned int)fmm_ceil_div(G.pc_len, csize);
 }
 
-__global__ void k_item_expand(long long ng, const unsigned int* __restrict__ cnt_pp,
+__global__ void k_item_expand(long long grid, const unsigned int* __restrict__ cnt_pp,
                               const unsigned int* __restrict__ base_pp, const unsigned int* __restrict__ cnt_pc,
                               const unsigned int* __restrict__ base_pc, unsigned int* __restrict__ item_pp,
-                              unsigned int* __restrict__ item_pc)
+                              unsigned int* __restrict__ item_pc, long long cap_pp, long long cap_pc,
+                              unsigned int* __restrict__ overflow)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ng) return;
-    for (unsigned int k = 0; k < cnt_pp[i]; k++) item_pp[base_pp[i] + k] = (unsigned int)i;
-    for (unsigned int k = 0; k < cnt_pc[i]; k++) item_pc[base_pc[i] + k] = (unsigned int)i;
+    if (i >= grid) return;
+    const long long bp = base_pp[i], np = cnt_pp[i], bc = base_pc[i], nc = cnt_pc[i];
+    if (bp + np > cap_pp || bc + nc > cap_pc) {
+        atomicOr(overflow, 1u);
+        return;
+    }
+    for (long long k = 0; k < np; k++) item_pp[bp + k] = (unsigned int)i;
+    for (long long k = 0; k < nc; k++) item_pc[bc + k] = (unsigned int)i;
 }
 
-cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s)
+cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk, cudaStream_t s)
 {
-    const long long ng = w.n_groups;
+    // under graph capture the group count is known only on the device: cover the capacity
+    const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     const unsigned blocks = (unsigned)fmm_ceil_div(ng, 256);
-    k_item_counts<<<blocks, 256, 0, s>>>(w.groups, ng, w.cnt_pp, w.cnt_pc);
+    k_item_counts<<<blocks, 256, 0, s>>>(w.groups, ng, &ctr->n_groups, w.cnt_pp, w.cnt_pc, chunk);
     cudaError_t e = fmm_scan_exclusive(w.cnt_pp, w.base_pp, ng, &ctr->n_item_pp, t, s);
     if (e == cudaSuccess) e = fmm_scan_exclusive(w.cnt_pc, w.base_pc, ng, &ctr->n_item_pc, t, s);
     if (e != cudaSuccess) return e;
-    k_item_expand<<<blocks, 256, 0, s>>>(ng, w.cnt_pp, w.base_pp, w.cnt_pc, w.base_pc, w.item_pp, w.item_pc);
+    k_item_expand<<<blocks, 256, 0, s>>>(ng, w.cnt_pp, w.base_pp, w.cnt_pc, w.base_pc, w.item_pp, w.item_pc,
+                                         w.cap_item_pp, w.cap_item_pc, &ctr->overflow);
     return cudaGetLastError();
 }
 
@@ -492,7 +514,7 @@ cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pp);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
     k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
-                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, a.eps2, ctr);
+                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, a.eps2, a.chunk, w.cap_item_pp, ctr);
     return cudaGetLastError();
 }
 
@@ -503,21 +525,23 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pc);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
     k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.com, t.bucket_of,
-                                     t.bucket_cell, t.off, t.rec, w.part_pc, a.eps2, ctr);
+                                     t.bucket_cell, t.off, t.rec, w.part_pc, a.eps2, a.chunk, w.cap_item_pc, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,
                                float* pot, long long n, cudaStream_t s)
 {
-    (void)ctr;
+    const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     if (a.accumulate == 1)
-        k_l2p_out<double><<<grid_for(w.n_groups), ITHREADS, 0, s>>>(
-            w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell, t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp,
-            w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
+        k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
+            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot,
+            a.terms);
     else
-        k_l2p_out<float><<<grid_for(w.n_groups), ITHREADS, 0, s>>>(
-            w.groups, w.n_groups, t.com, t.bucket_of, t.bucket_cell, t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp,
-            w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot, a.terms);
+        k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
+            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot,
+            a.terms);
     return cudaGetLastError();
 }

@@ -351,7 +351,8 @@ cudaError_t fmm_launch_audit_labels(DevTree& t, const int2* pairs, long long npa
 // Per cell, the smallest |a| of its particles from an acceleration estimate acc (3 x n SoA in
 // input order, e.g. the previous step's forces): bucket cells scan their particles, and the
 // second child to arrive at a parent takes the smaller of the two (arrive[] zeroed first).
-__global__ void __launch_bounds__(128) k_cell_amin(int nb, const int* __restrict__ bucket_cell,
+__global__ void __launch_bounds__(128) k_cell_amin(const unsigned int* __restrict__ nbucket,
+                                                   const int* __restrict__ bucket_cell,
                                                    const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                                    const int* __restrict__ cparent, const int* __restrict__ cchild,
                                                    const unsigned int* __restrict__ perm,
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(128) k_cell_amin(int nb, const int* __restrict
                                                    unsigned int* arrive)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    if (b >= (int)*nbucket) return;
     const int c = bucket_cell[b];
     float a = INFINITY;
     for (int j = cfirst[c], e = cfirst[c] + ccount[c]; j < e; j++) {
@@ -380,10 +381,10 @@ __global__ void __launch_bounds__(128) k_cell_amin(int nb, const int* __restrict
 
 cudaError_t fmm_launch_cell_amin(DevTree& t, const float* acc, long long n, cudaStream_t s)
 {
-    const int nb = (int)t.n_buckets;
-    cudaError_t e = cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)t.n_cells, s);
+    const long long nb = t.cap_grid ? t.cap_cells : t.n_buckets, nc = t.cap_grid ? t.cap_cells : t.n_cells;
+    cudaError_t e = cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)nc, s);
     if (e != cudaSuccess) return e;
-    k_cell_amin<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
-                                                                 t.cchild, t.idx, acc, n, t.amin, t.arrive);
+    k_cell_amin<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(t.dcount + 1, t.bucket_cell, t.cfirst, t.ccount,
+                                                                 t.cparent, t.cchild, t.idx, acc, n, t.amin, t.arrive);
     return cudaGetLastError();
 }

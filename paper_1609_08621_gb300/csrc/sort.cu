@@ -113,6 +113,12 @@ static cudaError_t ensure_u32(unsigned int** p, long long* cap, long long need)
     return e;
 }
 
+// scratch of fmm_scan_exclusive for scans of up to n values, allocated ahead (graph capture)
+cudaError_t fmm_scan_reserve(DevTree& t, long long n)
+{
+    return ensure_u32(&t.scan_part, &t.cap_scan_part, fmm_ceil_div(n, SCAN_TILE));
+}
+
 cudaError_t fmm_scan_exclusive(const unsigned int* in, unsigned int* out, long long n, unsigned int* total_dev,
                                DevTree& t, cudaStream_t s)
 {

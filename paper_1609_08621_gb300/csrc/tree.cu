@@ -200,11 +200,12 @@ __global__ void k_bucket_index(const unsigned int* __restrict__ bscan, const uns
     bucket_of[i] = (int)(bscan[i] + bflag_raw[i]) - 1;
 }
 
-__global__ void k_bucket_cells(const int* __restrict__ cfirst, const int* __restrict__ cchild, int ncell,
-                               const int* __restrict__ bucket_of, int* __restrict__ bucket_cell)
+__global__ void k_bucket_cells(const int* __restrict__ cfirst, const int* __restrict__ cchild,
+                               const unsigned int* __restrict__ ncell, const int* __restrict__ bucket_of,
+                               int* __restrict__ bucket_cell)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+    if (c >= (int)*ncell) return;
     if (cchild[2 * c] < 0) bucket_cell[bucket_of[cfirst[c]]] = c;
 }
 
@@ -251,7 +252,7 @@ __device__ __forceinline__ double dist2_ordered(double dx, double dy, double dz)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-__global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ bucket_cell,
+__global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__ nbucket, const int* __restrict__ bucket_cell,
                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                                 const int* __restrict__ cparent, const int* __restrict__ cchild,
                                                 const double* __restrict__ sx, const double* __restrict__ sy,
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(128) k_upward(int nb, const int* __restrict__ 
                                                 float4* __restrict__ off, unsigned int* arrive)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    if (b >= (int)*nbucket) return;
     int c = bucket_cell[b];
     int f = cfirst[c], cnt = ccount[c];
     double M = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
@@ -370,7 +371,7 @@ __device__ __forceinline__ float box_far(const double* __restrict__ clo, const d
     return sqrtf(s) * (1.0f + 2e-6f);
 }
 
-__global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __restrict__ cfirst,
+__global__ void __launch_bounds__(128) k_bmax_exact(const unsigned int* __restrict__ ncell, const int* __restrict__ cfirst,
                                                     const int* __restrict__ ccount, const int* __restrict__ cchild,
                                                     const Com4* __restrict__ com, const double* __restrict__ clo,
                                                     const double* __restrict__ chi, const float4* __restrict__ off,
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(128) k_bmax_exact(int ncell, const int* __rest
                                                     unsigned int* __restrict__ status)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+    if (c >= (int)*ncell) return;
     if (cchild[2 * c] < 0) return;  // buckets are exact already
     const Com4 p = com[c];
     float lb = 0.0f;
@@ -447,30 +448,38 @@ cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s
     return cudaGetLastError();
 }
 
+// cells and buckets covered by a launch: the counts, or the capacity under graph capture
+static long long grid_cells(const DevTree& t) { return t.cap_grid ? t.cap_cells : t.n_cells; }
+static long long grid_buckets(const DevTree& t) { return t.cap_grid ? t.cap_cells : t.n_buckets; }
+
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s)
 {
     (void)bucket;
-    int nc = (int)t.n_cells, nb = (int)t.n_buckets;
-    k_bucket_cells<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.cfirst, t.cchild, nc, t.bucket_of, t.bucket_cell);
+    (void)n;
+    const long long nc = grid_cells(t), nb = grid_buckets(t);
+    k_bucket_cells<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.cfirst, t.cchild, t.dcount, t.bucket_of,
+                                                                 t.bucket_cell);
     cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)nc, s);
-    k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(nb, t.bucket_cell, t.cfirst, t.ccount, t.cparent,
-                                                              t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact, t.com, t.clo,
-                                                              t.chi, t.bmax, t.cnact, t.rec, t.off, t.arrive);
-    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(nc, t.cfirst, t.ccount, t.cchild, t.com, t.clo,
-                                                                  t.chi, t.off, t.sx, t.sy, t.sz, t.bmax,
+    k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(t.dcount + 1, t.bucket_cell, t.cfirst, t.ccount,
+                                                              t.cparent, t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact,
+                                                              t.com, t.clo, t.chi, t.bmax, t.cnact, t.rec, t.off,
+                                                              t.arrive);
+    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(t.dcount, t.cfirst, t.ccount, t.cchild, t.com,
+                                                                  t.clo, t.chi, t.off, t.sx, t.sy, t.sz, t.bmax,
                                                                   &ctr->status);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- walk nodes (depend on theta)
 
-__global__ void k_nodes(int ncell, float theta, const int* __restrict__ cfirst, const int* __restrict__ ccount,
+__global__ void k_nodes(const unsigned int* __restrict__ ncell, float theta, const int* __restrict__ cfirst,
+                        const int* __restrict__ ccount,
                         const int* __restrict__ cchild, const Com4* __restrict__ com, const double* __restrict__ clo,
                         const double* __restrict__ chi, const double* __restrict__ bmax, const float* __restrict__ rec,
                         WalkNode* __restrict__ node, float4* __restrict__ mnorm)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+    if (c >= (int)*ncell) return;
     Com4 cm = com[c];
     float bm = __double2float_rn(bmax[c]);
     int cnt = ccount[c];
@@ -498,9 +507,9 @@ __global__ void k_nodes(int ncell, float theta, const int* __restrict__ cfirst, 
 
 cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s)
 {
-    int nc = (int)t.n_cells;
-    k_nodes<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(nc, (float)theta, t.cfirst, t.ccount, t.cchild, t.com,
-                                                          t.clo, t.chi, t.bmax, t.rec, t.node, t.mnorm);
+    const long long nc = grid_cells(t);
+    k_nodes<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.dcount, (float)theta, t.cfirst, t.ccount, t.cchild,
+                                                          t.com, t.clo, t.chi, t.bmax, t.rec, t.node, t.mnorm);
     return cudaGetLastError();
 }
 
@@ -554,11 +563,12 @@ __global__ void k_regather_keys(const unsigned long long* __restrict__ korig, co
 }
 
 // the cell spanning exactly each box's particles (the box's own root)
-__global__ void k_box_roots(int ncell, const int* __restrict__ cfirst, const int* __restrict__ ccount,
-                            const long long* __restrict__ off, int nbox, int* __restrict__ box_root)
+__global__ void k_box_roots(const unsigned int* __restrict__ ncell, const int* __restrict__ cfirst,
+                            const int* __restrict__ ccount, const long long* __restrict__ off, int nbox,
+                            int* __restrict__ box_root)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
+    if (c >= (int)*ncell) return;
     const long long f = cfirst[c];
     const int b = box_of(off, nbox, f);
     if (off[b] == f && off[b + 1] - f == ccount[c]) box_root[b] = c;
@@ -582,7 +592,8 @@ cudaError_t fmm_launch_box_sort(DevTree& t, long long n, cudaStream_t s)
 
 cudaError_t fmm_launch_box_roots(DevTree& t, cudaStream_t s)
 {
-    int nc = (int)t.n_cells;
-    k_box_roots<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(nc, t.cfirst, t.ccount, t.box_off, t.nbox, t.box_root);
+    const long long nc = grid_cells(t);
+    k_box_roots<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.dcount, t.cfirst, t.ccount, t.box_off, t.nbox,
+                                                              t.box_root);
     return cudaGetLastError();
 }

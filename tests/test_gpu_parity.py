@@ -308,3 +308,50 @@ def test_tight_theta_judge_against_direct_sum(ctx):
     print(f"\njudge theta=0.25: rms {rms(e):.3e} max {e.max():.3e}")
     # measured: rms 9.7e-7, max 7.0e-6
     assert rms(e) <= 3e-6 and e.max() <= 3e-5, (rms(e), e.max())
+
+
+def test_list_chunk_sizes(ctx):
+    """The work-item size only regroups each sink's partial sums: same interaction counts, forces
+    equal to FP32 rounding, for chunks of 32, 64 (default) and 128 entries."""
+    n, eps, theta = 20000, 1e-3, 0.55
+    pos, mass = synth.clustered_plummer(n, 31)
+    res = {}
+    for ch in (32, 64, 128):
+        ctx.set_params(list_chunk=ch)
+        try:
+            a, _ = gpu_solve(ctx, pos, mass, eps, theta)
+        finally:
+            ctx.set_params(list_chunk=0)
+        st = ctx.stats()
+        res[ch] = (a, st["n_pp_pairs"], st["n_pc_pairs"])
+    a64 = res[64][0]
+    for ch in (32, 128):
+        assert res[ch][1:] == res[64][1:]
+        assert rms(np.linalg.norm(res[ch][0] - a64, axis=0) / np.linalg.norm(a64, axis=0)) <= 1e-6
+    for bad in (16, 48, 2048):
+        with pytest.raises(binding.FmmError):
+            ctx.set_params(list_chunk=bad)
+
+
+def test_autotune_picks_a_candidate(ctx):
+    n, eps, theta = 60000, 1e-3, 0.55
+    pos, mass = synth.clustered_plummer(n, 32)
+    tp, tm = dev(pos, torch.float64), dev(mass, torch.float32)
+    acc = torch.zeros(3 * n, dtype=torch.float32, device="cuda:0")
+    cands = [(16, 64, 64), (8, 32, 32), (12, 48, 128)]
+    best, ms = ctx.autotune(tp, tm, eps, theta, acc, candidates=cands, reps=1)
+    assert (best.bucket, best.group, best.list_chunk) in cands and ms > 0
+    p = ctx.get_params()
+    assert (p.bucket, p.group, p.list_chunk) == (best.bucket, best.group, best.list_chunk)
+    # the tuned context still solves correctly
+    a, _ = gpu_solve(ctx, pos, mass, eps, theta, bucket=best.bucket, group=best.group)
+    ref, _ = oracle.direct(pos, mass, eps, np.arange(0, n, 97))
+    e = rel_err(a[:, ::97], ref)
+    assert rms(e) <= 1e-3 and np.quantile(e, 0.99) <= 1e-2
+    # an invalid candidate is an error and leaves the parameters as they were
+    p = ctx.get_params()
+    with pytest.raises(binding.FmmError):
+        ctx.autotune(tp, tm, eps, theta, acc, candidates=[(16, 64, 48)], reps=1)
+    p2 = ctx.get_params()
+    assert (p2.bucket, p2.group, p2.list_chunk) == (p.bucket, p.group, p.list_chunk)
+    ctx.set_params(bucket=16, group=64, list_chunk=0)
