@@ -172,7 +172,7 @@ static void free_all(fmm_ctx* c)
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
                   t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.mnorm, t.amin, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
+                  t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
@@ -304,6 +304,10 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.node, cap));
         CK(alloc(&t.mnorm, cap));
         CK(alloc(&t.amin, cap));
+        CK(alloc(&t.bm_cnt, cap));
+        CK(alloc(&t.bm_base, cap));
+        CK(alloc(&t.bm32, cap));
+        CK(alloc(&t.bm64, cap));
         CK(alloc(&t.L, (long long)FMM_NL * cap));
         t.cap_cells = cap;
     }
@@ -398,14 +402,21 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     t.n_cells = c->totals_h[0];
     t.n_buckets = c->totals_h[1];
     if (t.n_cells > t.cap_cells) return fail(FMM_ERR_CUDA, "internal: %lld cells exceed capacity", t.n_cells);
+    {
+        const long long need = fmm_bmax_items_bound(n, (int)c->ctr_h->depth, t.n_cells);
+        if (need > t.cap_bm_items) {
+            CK(alloc(&t.bm_item, need));
+            t.cap_bm_items = need;
+        }
+    }
     CK(fmm_launch_upward(t, n, bucket, c->ctr, s));
     if (nbox > 1) {
         CK(fmm_launch_box_roots(t, s));
         c->launches += 1;
     }
     // keys, gather, radix tree + keep, scan, cells, scan, bucket index, depth, bucket cells,
-    // upward, exact b_max
-    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
+    // upward, exact b_max (count, scan, expand, two passes, final)
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
     t.depth = (int)c->ctr_h->depth;
     c->have_tree = true;
     c->theta_nodes = -1.0f;
@@ -694,7 +705,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
         CK(fmm_launch_box_roots(t, s));
         c->launches += 1;
     }
-    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 3;
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
     CK(fmm_launch_nodes(t, q.theta, s));
     c->launches += 1;
     CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
@@ -798,7 +809,7 @@ static void capture_graph(fmm_ctx* c, const fmm_ctx::GraphKey& key, const double
     drop_graph(c);
     if (c->w.n_groups < 1) return;
     // buffers the capacity-sized launches need, reserved now (no allocation may happen inside capture)
-    if (fmm_scan_reserve(c->t, std::max(2 * n, c->w.cap_groups)) != cudaSuccess) return;
+    if (fmm_scan_reserve(c->t, std::max(2 * n + 2, std::max(c->w.cap_groups, c->t.cap_cells))) != cudaSuccess) return;
     c->graph_levels = c->t.depth + 1 + 4;  // a few levels of slack for a slightly deeper tree
     if (c->graph_levels + 1 > FMM_MAX_LEVELS) return;
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -65,6 +65,7 @@ struct DevCounters {
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
+    unsigned int n_bm_items, pad1;        // (cell, particle chunk) items of the exact b_max
     unsigned long long n_audit;           // (sink, source) pairs recorded by an audit walk
     unsigned long long n_mlp;             // learned decisions taken
     // per walk level: frontier size, work counters of the walk and local kernels, and the
@@ -86,6 +87,12 @@ struct DevTree {
     // the host does not know the counts) instead of the count
     const unsigned int* dcount = nullptr;
     bool cap_grid = false;
+    // exact b_max of internal cells: per cell a count and first index of (cell, chunk) items, the
+    // FP32 and FP64 running maxima (as ordered bit patterns), and the items' cells
+    unsigned int *bm_cnt = nullptr, *bm_base = nullptr, *bm32 = nullptr;
+    unsigned long long* bm64 = nullptr;
+    int* bm_item = nullptr;
+    long long cap_bm_items = 0;
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;
     unsigned int *idx = nullptr, *idx_alt = nullptr;
@@ -183,6 +190,7 @@ cudaError_t fmm_launch_bucket_index(DevTree& t, long long n, cudaStream_t s);
 cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s);
+long long fmm_bmax_items_bound(long long n, int depth, long long n_cells);
 cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s);
 cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_box_sort(DevTree& t, long long n, cudaStream_t s);

@@ -18,6 +18,8 @@
 // counter per cell; the second child to arrive computes the parent.
 #include <math.h>
 
+#include <algorithm>
+
 #include "expansions.cuh"
 #include "fmm_internal.cuh"
 #include "morton.cuh"
@@ -340,103 +342,112 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
     }
 }
 
-// Exact b_max of every internal cell: the distance from its centre of mass p to the farthest
-// of its particles, in FP64 (the same operations as a brute-force scan, so the value is the
-// exact one).  One thread per cell runs a branch-and-bound descent of the cell's subtree:
-//   lb = a lower bound of the answer: 0.999998 x the largest distance from p to a face of
-//        the cell's bounding box along an axis (a particle lies on that face), raised by the
-//        FP32 distances of the particles visited;
-//   ub(node) = the distance from p to the farthest corner of the node's bounding box, an
-//        upper bound of any of its particles' distances; a node is skipped when
-//        ub x 1.000002 < lb, and the child with the larger ub is visited first;
-//   a particle of a visited bucket gets its FP64 distance only if its FP32 distance could
-//   reach lb.
-// FP32 distances are formed from fl(com_bucket - p) (FP64 difference, rounded) plus the
-// particle's stored offset from its bucket centre, and bounding-box offsets from fl(lo - p),
-// fl(hi - p); their relative errors are below 1e-6, so the 2e-6 margins never discard the
-// farthest particle.  The bounds do not depend on other cells' b_max, so every cell is
-// independent.
-#define BMAX_STACK 128
+// Exact b_max of every internal cell: the distance from its centre of mass p to the farthest of
+// its particles, in FP64 with the same operations as a brute-force scan (so the value is the exact
+// one).  Every (cell, chunk of BM_CHUNK of its particles) pair is a work item of one warp, so big
+// cells are spread over many warps and every lane does the same work.  Two passes over the items:
+//   1. the largest FP32 distance d32 = |fl(x) - fl(p)| of each cell (atomic max of its bits);
+//   2. the FP64 squared distance, for the particles whose d32 is within the FP32 error margin
+//      4e-7 + 6e-7 d of that maximum (atomic max of the bits of the non-negative double).
+// The FP32 distance of a particle differs from the exact one by less than about 1.1e-7 + 1.3e-7 d
+// (positions in [0, 1) and the centre rounded to FP32, one subtraction and the norm), so the
+// margin, twice the sum of two such errors, keeps the farthest particle among the candidates.
+#define BM_CHUNK 2048
 
-__device__ __forceinline__ float box_far(const double* __restrict__ clo, const double* __restrict__ chi, int nd,
-                                         const Com4& p)
+// items of the b_max passes: at most one partial chunk per internal cell beyond the full chunks,
+// and every particle is in at most depth + 1 cells
+long long fmm_bmax_items_bound(long long n, int depth, long long n_cells)
 {
-    float s = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const double pa = a == 0 ? p.x : (a == 1 ? p.y : p.z);
-        const float e = fmaxf(fabsf(__double2float_rn(clo[3 * nd + a] - pa)), fabsf(__double2float_rn(chi[3 * nd + a] - pa)));
-        s = fmaf(e, e, s);
-    }
-    return sqrtf(s) * (1.0f + 2e-6f);
+    return fmm_ceil_div(n * (long long)(depth + 1), BM_CHUNK) + n_cells + 1;
 }
 
-__global__ void __launch_bounds__(128) k_bmax_exact(const unsigned int* __restrict__ ncell, const int* __restrict__ cfirst,
-                                                    const int* __restrict__ ccount, const int* __restrict__ cchild,
-                                                    const Com4* __restrict__ com, const double* __restrict__ clo,
-                                                    const double* __restrict__ chi, const float4* __restrict__ off,
-                                                    const double* __restrict__ sx, const double* __restrict__ sy,
-                                                    const double* __restrict__ sz, double* __restrict__ bmax,
-                                                    unsigned int* __restrict__ status)
+__global__ void k_bm_count(const unsigned int* __restrict__ ncell, long long grid, const int* __restrict__ ccount,
+                           const int* __restrict__ cchild, unsigned int* __restrict__ cnt, unsigned int* __restrict__ bm32,
+                           unsigned long long* __restrict__ bm64)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= (int)*ncell) return;
-    if (cchild[2 * c] < 0) return;  // buckets are exact already
-    const Com4 p = com[c];
-    float lb = 0.0f;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= grid) return;
+    unsigned int k = 0;
+    if (c < (long long)*ncell && cchild[2 * c] >= 0) k = (unsigned int)fmm_ceil_div(ccount[c], BM_CHUNK);
+    cnt[c] = k;
+    bm32[c] = 0u;
+    bm64[c] = 0ull;
+}
+
+__global__ void k_bm_expand(long long grid, const unsigned int* __restrict__ cnt, const unsigned int* __restrict__ base,
+                            int* __restrict__ item, long long cap, unsigned int* __restrict__ overflow)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= grid) return;
+    const long long b = base[c], k = cnt[c];
+    if (b + k > cap) {
+        if (k) atomicOr(overflow, 1u);
+        return;
+    }
+    for (long long i = 0; i < k; i++) item[b + i] = (int)c;
+}
+
+__device__ __forceinline__ float bm_d32(const float4 v, float px, float py, float pz)
+{
+    const float dx = v.x - px, dy = v.y - py, dz = v.z - pz;
+    return sqrtf(dx * dx + dy * dy + dz * dz);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, const unsigned int* __restrict__ n_items,
+                                                 long long cap, const unsigned int* __restrict__ ncell,
+                                                 const unsigned int* __restrict__ cnt, const unsigned int* __restrict__ base,
+                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
+                                                 const Com4* __restrict__ com, const float4* __restrict__ posf,
+                                                 const double* __restrict__ sx, const double* __restrict__ sy,
+                                                 const double* __restrict__ sz, unsigned int* __restrict__ bm32,
+                                                 unsigned long long* __restrict__ bm64)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long ni = min((long long)*n_items, cap);
+    for (long long i = gw; i < ni; i += nw) {
+        // an item the expansion could not write (capacity overflow, reported to the host) is skipped
+        const int c = item[i];
+        if (c < 0 || c >= (int)*ncell) continue;
+        const long long k = i - (long long)base[c];
+        if (k < 0 || k >= (long long)cnt[c]) continue;
+        const long long f = cfirst[c], e = f + ccount[c];
+        const long long j0 = f + k * BM_CHUNK, j1 = min(j0 + BM_CHUNK, e);
+        const Com4 p = com[c];
+        const float px = __double2float_rn(p.x), py = __double2float_rn(p.y), pz = __double2float_rn(p.z);
+        if (PASS == 1) {
+            float m = 0.0f;
+            for (long long j = j0 + lane; j < j1; j += 32) m = fmaxf(m, bm_d32(posf[j], px, py, pz));
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const double pa = a == 0 ? p.x : (a == 1 ? p.y : p.z);
-        lb = fmaxf(lb, fmaxf(fabsf(__double2float_rn(clo[3 * c + a] - pa)), fabsf(__double2float_rn(chi[3 * c + a] - pa))));
-    }
-    lb *= (1.0f - 2e-6f);
-    int stk[BMAX_STACK];
-    float sub[BMAX_STACK];
-    int sp = 0;
-    {
-        const int c0 = cchild[2 * c], c1 = cchild[2 * c + 1];
-        const float u0 = box_far(clo, chi, c0, p), u1 = box_far(clo, chi, c1, p);
-        const bool first0 = u0 >= u1;  // the larger bound is popped first
-        stk[sp] = first0 ? c1 : c0;
-        sub[sp++] = first0 ? u1 : u0;
-        stk[sp] = first0 ? c0 : c1;
-        sub[sp++] = first0 ? u0 : u1;
-    }
-    double best2 = 0.0;
-    while (sp > 0) {
-        --sp;
-        const int nd = stk[sp];
-        if (sub[sp] < lb) continue;
-        const int c0 = cchild[2 * nd];
-        if (c0 < 0) {
-            const Com4 cm = com[nd];
-            const float dx = __double2float_rn(cm.x - p.x), dy = __double2float_rn(cm.y - p.y),
-                        dz = __double2float_rn(cm.z - p.z);
-            const int f = cfirst[nd], cnt = ccount[nd];
-            for (int j = f; j < f + cnt; j++) {
-                const float4 o = off[j];
-                const float vx = dx + o.x, vy = dy + o.y, vz = dz + o.z;
-                const float dj = sqrtf(vx * vx + vy * vy + vz * vz);
-                if (dj * (1.0f + 2e-6f) >= lb) {
-                    best2 = fmax(best2, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
-                    lb = fmaxf(lb, dj * (1.0f - 2e-6f));
-                }
-            }
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FMM_FULL_MASK, m, o));
+            if (lane == 0) atomicMax(bm32 + c, __float_as_uint(m));
         } else {
-            if (sp + 2 > BMAX_STACK) {  // deeper than any 63-bit radix tree with 31-bit positions
-                atomicOr(status, FMM_DEV_ERR_NUMERIC);
-                return;
+            const float top = __uint_as_float(bm32[c]);
+            const float thr = top - (4e-7f + 6e-7f * top);
+            // FP64 runs at a small fraction of the FP32 rate: only warp steps that hold a candidate
+            // enter the FP64 branch
+            double best = 0.0;
+            for (long long jb = j0; jb < j1; jb += 32) {
+                const long long j = jb + lane;
+                const bool cand = j < j1 && bm_d32(posf[j], px, py, pz) >= thr;
+                if (__any_sync(FMM_FULL_MASK, cand) && cand)
+                    best = fmax(best, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
             }
-            const int c1 = cchild[2 * nd + 1];
-            const float u0 = box_far(clo, chi, c0, p), u1 = box_far(clo, chi, c1, p);
-            const bool first0 = u0 >= u1;
-            stk[sp] = first0 ? c1 : c0;
-            sub[sp++] = first0 ? u1 : u0;
-            stk[sp] = first0 ? c0 : c1;
-            sub[sp++] = first0 ? u0 : u1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
+            if (lane == 0 && best > 0.0) atomicMax(bm64 + c, (unsigned long long)__double_as_longlong(best));
         }
     }
-    bmax[c] = __dsqrt_rn(best2);
+}
+
+__global__ void k_bm_final(const unsigned int* __restrict__ ncell, const int* __restrict__ cchild,
+                           const unsigned long long* __restrict__ bm64, double* __restrict__ bmax)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (int)*ncell || cchild[2 * c] < 0) return;  // buckets are exact already
+    bmax[c] = __dsqrt_rn(__longlong_as_double((long long)bm64[c]));
 }
 
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s)
@@ -464,9 +475,24 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
                                                               t.cparent, t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact,
                                                               t.com, t.clo, t.chi, t.bmax, t.cnact, t.rec, t.off,
                                                               t.arrive);
-    k_bmax_exact<<<(unsigned)fmm_ceil_div(nc, 128), 128, 0, s>>>(t.dcount, t.cfirst, t.ccount, t.cchild, t.com,
-                                                                  t.clo, t.chi, t.off, t.sx, t.sy, t.sz, t.bmax,
-                                                                  &ctr->status);
+    // exact b_max of the internal cells: items, then the two passes
+    const unsigned gb = (unsigned)fmm_ceil_div(nc, TB);
+    k_bm_count<<<gb, TB, 0, s>>>(t.dcount, nc, t.ccount, t.cchild, t.bm_cnt, t.bm32, t.bm64);
+    cudaError_t e = fmm_scan_exclusive(t.bm_cnt, t.bm_base, nc, &ctr->n_bm_items, t, s);
+    if (e != cudaSuccess) return e;
+    k_bm_expand<<<gb, TB, 0, s>>>(nc, t.bm_cnt, t.bm_base, t.bm_item, t.cap_bm_items, &ctr->overflow);
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = fmm_ceil_div(t.cap_bm_items, 8);
+    const unsigned pb = (unsigned)std::max(1LL, std::min(want, (long long)sms * 8));
+    k_bm_pass<1><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
+                                    t.cfirst, t.ccount,
+                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64);
+    k_bm_pass<2><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
+                                    t.cfirst, t.ccount,
+                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64);
+    k_bm_final<<<gb, TB, 0, s>>>(t.dcount, t.cchild, t.bm64, t.bmax);
     return cudaGetLastError();
 }
 
