@@ -40,10 +40,12 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul, 3 fma, 1 add)
 
-# DRAM bytes (read + write) per launch of the interaction kernels on the 128^3 NFW box, from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_pc_k_pp_nfw2m.md).
-# Set back to None whenever a kernel changes after that capture.
-NCU_TRAFFIC = {"k_pc": 300888832, "k_pp": 135446016}
+# DRAM bytes (read + write) per launch of the interaction kernels on the 128^3 NFW box with
+# buckets of 16, groups of 64 and work items of 128 list entries, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_pc_k_pp_nfw2m.md).  Reported only for
+# runs with those settings; set back to None whenever a kernel changes after that capture.
+NCU_TRAFFIC = {"k_pc": 244846336, "k_pp": 109093632}
+NCU_TRAFFIC_PARAMS = (16, 64, 128)
 
 
 def parse():
@@ -57,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (buckets 16, groups 64)")
     ap.add_argument("--no-graphs", action="store_true", help="solve eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--params", default=None, help="bucket,group,list_chunk instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
     ap.add_argument("--n", type=int, default=None,
@@ -188,6 +191,10 @@ def run_reference(args, rank, world):
 def tune(args, ctx, tpos, tmass, eps, theta, acc, box_offsets=None, buckets=(16,)):
     """Autotune group size and work-item size (and the bucket sizes given) before the timed region;
     returns the chosen settings for the config.  --no-tune keeps buckets of 16, groups of 64."""
+    if args.params:
+        b, g, ch = (int(x) for x in args.params.split(","))
+        ctx.set_params(bucket=b, group=g, list_chunk=ch)
+        return {"bucket": b, "group": g, "list_chunk": ch, "tuned": False}
     if args.no_tune:
         ctx.set_params(bucket=16, group=64, list_chunk=0)
         return {"bucket": 16, "group": 64, "list_chunk": 64, "tuned": False}
@@ -597,7 +604,9 @@ def main():
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": NCU_TRAFFIC.get(dom) if args.workload == "nfw2m" and args.n is None else None,
+            "traffic": NCU_TRAFFIC.get(dom) if NCU_TRAFFIC and args.workload == "nfw2m" and args.n is None and
+            (wl.config.get("bucket"), wl.config.get("group"), wl.config.get("list_chunk")) == NCU_TRAFFIC_PARAMS
+            else None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "pp_pc_frac": ((fpp + fpc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
             if pp_ms + pc_ms > 0 else 0.0}
