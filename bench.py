@@ -131,6 +131,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_totals(ms, interactions, world, device):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's time per step (max) and the
+    interactions of all ranks (sum), through torch.distributed when world > 1."""
+    if world <= 1:
+        return ms, interactions
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([interactions], device=device, dtype=torch.float64)
+    dist.all_reduce(tot)
+    return float(t.item()), float(tot.item())
+
+
 def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
     """The oracle's plain FP64 FMM on a bounded sample: the full tree, forces for a random
     subset of active sinks.  Returns interactions/s over the sample."""
@@ -583,17 +598,7 @@ def main():
     if flush is not None:
         ms = float(np.mean([a.elapsed_time(b) for a, b in step_ms]))
     inter_mean = float(np.mean(inter))
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([inter_mean], device=dev, dtype=torch.float64)
-        dist.all_reduce(tot)
-        inter_job = float(tot.item())
-    else:
-        inter_job = inter_mean
+    ms, inter_job = job_totals(ms, inter_mean, world, dev)
     value = inter_job / (ms * 1e-3)
     st = ctx.stats()
     # roofline of the dominant interaction kernel (FP32 ALU bound), CUDA events on the context's stream
@@ -624,12 +629,7 @@ def main():
         r = wl.e2e(args.steps)
         if r is not None:
             dt, hb, db = r
-            if world > 1:
-                import torch.distributed as dist
-
-                t = torch.tensor([dt], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                dt = float(t.item())
+            dt, _ = job_totals(dt, 0.0, world, dev)
             line["e2e"] = {"value": inter_job / dt, "unit": "interactions/s", "ms_per_step": dt * 1e3,
                            "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
