@@ -49,6 +49,7 @@ struct __align__(16) Group {
 };
 
 #define FMM_LIST_CHUNK 64  // default list entries per PP / PC work item
+#define FMM_LOCAL_RANGE 512  // local entries per warp range of the own-expansion kernel
 #define FMM_GMAX 64       // sink slots per group
 #define FMM_MAX_LEVELS 192  // walk levels: tree depth + 1 (63 key bits + 31 position bits at most)
 
@@ -157,7 +158,7 @@ struct DevWalk {
     long long cap_item_pp = 0, cap_item_pc = 0;
     unsigned int *cl[2] = {nullptr, nullptr};
     unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
-    int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry, for export
+    int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry
     Group *groups = nullptr;
     unsigned int *scratch = nullptr;
     // levels kept for export of the local lists

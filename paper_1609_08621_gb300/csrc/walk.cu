@@ -306,71 +306,122 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
 #define LOCAL_WPB 2
 #define LOCAL_THREADS (LOCAL_WPB * 32)
 
-// Own local expansion of every walked cell with a non-empty local list: the sum of the M2L
-// (CC) and P2L (CP) terms of that cell's list, about its centre of mass.  One warp per cell,
-// lanes take list entries, partial sums are reduced in shared memory.  All cells are done in
-// one launch after the walk.
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local_own(
-    const int* __restrict__ lcells, const unsigned long long* __restrict__ lcc_off, const int* __restrict__ lcc_len,
-    const unsigned int* __restrict__ cc, const int* __restrict__ ccount, const Com4* __restrict__ com,
+// Own local expansions over the flat list of all local entries (every walked sink's CC and CP
+// entries, contiguous per sink).  A warp takes a range of about LF_ENTRIES entries, moved to the
+// next sink boundaries so that no sink is split between warps, and walks it in chunks of 32, one
+// entry per lane, so lanes stay busy whatever the list lengths.  Each sink's 56 coefficients are
+// added strictly in list order (runs of equal sink along the lanes, a run that continues into
+// the next chunk carried on): the result depends only on the sink's own list, not on where the
+// list lies in the flat array or which warp took it.
+#define LF_ENTRIES FMM_LOCAL_RANGE
+
+__device__ __forceinline__ void local_entry(unsigned int e, const Com4& ck, const int* __restrict__ ccount,
+                                            const Com4* __restrict__ com, const double* __restrict__ sx,
+                                            const double* __restrict__ sy, const double* __restrict__ sz,
+                                            const float* __restrict__ sm, const float* __restrict__ rec, float eps2,
+                                            float* acc, int& ncc, int& ncp)
+{
+    if (e & FMM_PARTICLE_BIT) {
+        const unsigned int j = e & ~FMM_PARTICLE_BIT;
+        fmm_p2l_acc(sm[j], __double2float_rn(ck.x - sx[j]), __double2float_rn(ck.y - sy[j]),
+                    __double2float_rn(ck.z - sz[j]), eps2, acc);
+        ncp++;
+    } else if (ccount[e] == 1) {  // a one-particle cell: its particle -> local expansion
+        const Com4 cs = com[e];
+        fmm_p2l_acc((float)cs.w, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
+                    __double2float_rn(ck.z - cs.z), eps2, acc);
+        ncp++;
+    } else {
+        const Com4 cs = com[e];
+        float M[FMM_NMOM];
+        const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)e * FMM_NREC);
+#pragma unroll
+        for (int q = 0; q < FMM_NMOM / 4; q++) {
+            const float4 v = r4[q];
+            M[4 * q] = v.x;
+            M[4 * q + 1] = v.y;
+            M[4 * q + 2] = v.z;
+            M[4 * q + 3] = v.w;
+        }
+        fmm_m2l_acc(M, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y), __double2float_rn(ck.z - cs.z),
+                    eps2, acc);
+        ncc++;
+    }
+}
+
+// first entry of the first sink that starts at or after position p of the flat list
+__device__ __forceinline__ long long local_boundary(long long p, long long total, const int* __restrict__ cc_sink,
+                                                    const unsigned long long* __restrict__ lcc_off,
+                                                    const int* __restrict__ lcc_len)
+{
+    if (p >= total) return total;
+    const int k = cc_sink[p];
+    const long long f = (long long)lcc_off[k];
+    return f == p ? p : f + lcc_len[k];
+}
+
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
+    const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
+    const int* __restrict__ lcc_len, const int* __restrict__ ccount, const Com4* __restrict__ com,
     const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
-    const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ Lown, float eps2,
-    DevCounters* __restrict__ ctr)
+    const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
+    float eps2, DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long ncells = (long long)*(volatile unsigned long long*)&ctr->n_lcells;
+    const long long total = min((long long)*(volatile unsigned long long*)&ctr->cc_len, cap_cc);
+    const long long nranges = fmm_ceil_div(total, LF_ENTRIES);
+    const int c0 = lane, c1 = lane + 32;  // this lane's coefficients in the reduction
     int ncc = 0, ncp = 0;
-    for (long long li = gw; li < ncells; li += nw) {
-        const int k = lcells[li];
-        const unsigned long long off = lcc_off[k];
-        const int len = lcc_len[k];
-        const Com4 ck = com[k];
-        float acc[FMM_NL];
+    for (long long r = gw; r < nranges; r += nw) {
+        const long long r0 = local_boundary(r * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
+        const long long r1 = local_boundary((r + 1) * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
+        float carry0 = 0.0f, carry1 = 0.0f;
+        int carry_sink = -1;
+        for (long long base = r0; base < r1; base += 32) {
+            const long long idx = base + lane;
+            const bool valid = idx < r1;
+            int sink = -1;
+            float acc[FMM_NL];
 #pragma unroll
-        for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
-        for (int i = lane; i < len; i += 32) {
-            unsigned int e = cc[off + i];
-            if (e & FMM_PARTICLE_BIT) {
-                unsigned int j = e & ~FMM_PARTICLE_BIT;
-                fmm_p2l_acc(sm[j], __double2float_rn(ck.x - sx[j]), __double2float_rn(ck.y - sy[j]),
-                            __double2float_rn(ck.z - sz[j]), eps2, acc);
-                ncp++;
-            } else if (ccount[e] == 1) {
-                // a one-particle cell: its particle -> local expansion
-                const Com4 cs = com[e];
-                fmm_p2l_acc((float)cs.w, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
-                            __double2float_rn(ck.z - cs.z), eps2, acc);
-                ncp++;
-            } else {
-                const Com4 cs = com[e];
-                float M[FMM_NMOM];
-                const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)e * FMM_NREC);
-#pragma unroll
-                for (int q = 0; q < FMM_NMOM / 4; q++) {
-                    float4 v = r4[q];
-                    M[4 * q] = v.x;
-                    M[4 * q + 1] = v.y;
-                    M[4 * q + 2] = v.z;
-                    M[4 * q + 3] = v.w;
-                }
-                fmm_m2l_acc(M, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
-                            __double2float_rn(ck.z - cs.z), eps2, acc);
-                ncc++;
+            for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
+            if (valid) {
+                sink = cc_sink[idx];
+                local_entry(cc[idx], com[sink], ccount, com, sx, sy, sz, sm, rec, eps2, acc, ncc, ncp);
             }
-        }
 #pragma unroll
-        for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
-        __syncwarp();
-        float* Lk = Lown + (long long)k * FMM_NL;
-        for (int c = lane; c < FMM_NL; c += 32) {
-            float sum = 0.0f;
-            for (int r = 0; r < 32; r++) sum += red[wl][r][c];
-            Lk[c] = sum;
+            for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
+            const int prev = __shfl_up_sync(FMM_FULL_MASK, sink, 1);
+            unsigned int heads = __ballot_sync(FMM_FULL_MASK, valid && (lane == 0 || sink != prev));
+            __syncwarp();
+            const int nvalid = (int)min(32LL, r1 - base);
+            while (heads) {
+                const int st = __ffs(heads) - 1;
+                heads &= heads - 1;
+                const int en = heads ? __ffs(heads) - 1 : nvalid;  // exclusive
+                const int s_sink = __shfl_sync(FMM_FULL_MASK, sink, st);
+                const bool cont = st == 0 && carry_sink == s_sink;
+                float sum0 = cont ? carry0 : 0.0f, sum1 = cont ? carry1 : 0.0f;
+                for (int row = st; row < en; row++) {
+                    sum0 += red[wl][row][c0];
+                    if (c1 < FMM_NL) sum1 += red[wl][row][c1];
+                }
+                carry_sink = -1;
+                const long long se = (long long)lcc_off[s_sink] + lcc_len[s_sink];
+                if (base + en < se) {  // the sink's list goes on in the next chunk
+                    carry0 = sum0;
+                    carry1 = sum1;
+                    carry_sink = s_sink;
+                    continue;
+                }
+                float* dst = Lown + (long long)s_sink * FMM_NL;
+                dst[c0] = sum0;
+                if (c1 < FMM_NL) dst[c1] = sum1;
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -505,8 +556,8 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s)
 {
     const int blocks = w.n_warps / LOCAL_WPB;
-    k_local_own<<<blocks, LOCAL_THREADS, 0, s>>>(w.lcells, w.lcc_off, w.lcc_len, w.cc, t.ccount, t.com, t.sx, t.sy,
-                                                  t.sz, t.sm, t.rec, t.L, eps2, ctr);
+    k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.com, t.sx, t.sy,
+                                                   t.sz, t.sm, t.rec, t.L, w.cap_cc, eps2, ctr);
     k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, ctr);
     return cudaGetLastError();
 }
