@@ -284,7 +284,8 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
         hi[2] = fmax(hi[2], z);
         na += sact[j] ? 1 : 0;
     }
-    double cx = mx / M, cy = my / M, cz = mz / M;
+    const double iM = 1.0 / M;  // one FP64 division (a software sequence on this part) instead of three
+    double cx = mx * iM, cy = my * iM, cz = mz * iM;
     double b2 = 0.0;
     float Mo[FMM_NMOM];
 #pragma unroll
@@ -315,9 +316,10 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
         int c0 = cchild[2 * p], c1 = cchild[2 * p + 1];
         Com4 a0 = ldcg_d4(&com[c0]), a1 = ldcg_d4(&com[c1]);
         double Mp = a0.w + a1.w;
-        double px = (a0.w * a0.x + a1.w * a1.x) / Mp;
-        double py = (a0.w * a0.y + a1.w * a1.y) / Mp;
-        double pz = (a0.w * a0.z + a1.w * a1.z) / Mp;
+        const double iMp = 1.0 / Mp;
+        double px = (a0.w * a0.x + a1.w * a1.x) * iMp;
+        double py = (a0.w * a0.y + a1.w * a1.y) * iMp;
+        double pz = (a0.w * a0.z + a1.w * a1.z) * iMp;
         float Mq[FMM_NMOM];
 #pragma unroll
         for (int i = 0; i < FMM_NMOM; i++) Mq[i] = 0.0f;
