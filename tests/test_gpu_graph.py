@@ -121,3 +121,59 @@ def test_batch_solves_replay(dev):
         assert np.array_equal(acc.cpu().numpy(), first)
     finally:
         c.close()
+
+
+def test_learned_criterion_replays(dev):
+    """A graph captured with the learned criterion (its walk mode and the per-cell acceleration
+    scale) replays to the eager result."""
+    from oracle import mlp as omlp
+
+    n, eps, theta = 20000, 1e-3, 0.55
+    pos, mass = synth.clustered_plummer(n, 71)
+    rng = np.random.default_rng(5)
+    flat = np.zeros(omlp.N_PARAMS)
+    flat[:omlp.N_WEIGHTS] = 0.1 * rng.standard_normal(omlp.N_WEIGHTS)
+    p = omlp.unpack(flat)
+    p["b4"][:] = -4.0
+    p["inv_std"][:] = 1.0
+    params = omlp.pack(p).astype(np.float32)
+    tp, tm = t(pos, torch.float64), t(mass, torch.float32)
+    est = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+    c0 = binding.Context(0)
+    try:  # the acceleration estimate: a fixed-theta solve
+        c0.compute_forces(tp, tm, eps, theta, est)
+    finally:
+        c0.close()
+    outs = []
+    for graphs in (False, True):
+        c = binding.Context(0)
+        try:
+            c.mlp_load(params)
+            c.set_params(criterion=1, mlp_tau=-3.5)
+            c.set_graphs(graphs)
+            acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+            for _ in range(3):
+                acc.copy_(est)
+                c.compute_forces(tp, tm, eps, theta, acc)
+            if graphs:
+                assert c.graph_info()["replays"] == 2
+            assert c.stats()["n_learned"] > 0
+            outs.append(acc.cpu().numpy())
+        finally:
+            c.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_autotune_over_a_batch(dev):
+    boxes, off = synth.batch_boxes(5, 72)
+    pos = np.concatenate([b[0] for b in boxes], axis=1)
+    mass = np.concatenate([b[1] for b in boxes])
+    n = mass.size
+    c = binding.Context(0)
+    try:
+        acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        best, ms = c.autotune(t(pos, torch.float64), t(mass, torch.float32), 1e-3, 0.7, acc,
+                              candidates=[(16, 64, 64), (8, 32, 128)], reps=1, box_offsets=off)
+        assert (best.bucket, best.group, best.list_chunk) in [(16, 64, 64), (8, 32, 128)] and ms > 0
+    finally:
+        c.close()
