@@ -172,7 +172,7 @@ static void free_all(fmm_ctx* c)
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
                   t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
+                  t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
         if (p) cudaFree(p);
     DevWalk& w = c->w;
@@ -406,6 +406,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
         const long long need = fmm_bmax_items_bound(n, (int)c->ctr_h->depth, t.n_cells);
         if (need > t.cap_bm_items) {
             CK(alloc(&t.bm_item, need));
+            CK(alloc(&t.bm_imax, need));
             t.cap_bm_items = need;
         }
     }

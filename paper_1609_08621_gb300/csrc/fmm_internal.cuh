@@ -93,6 +93,7 @@ struct DevTree {
     unsigned int *bm_cnt = nullptr, *bm_base = nullptr, *bm32 = nullptr;
     unsigned long long* bm64 = nullptr;
     int* bm_item = nullptr;
+    float* bm_imax = nullptr;  // FP32 maximum of each item
     long long cap_bm_items = 0;
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;

@@ -348,7 +348,8 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
 // its particles, in FP64 with the same operations as a brute-force scan (so the value is the exact
 // one).  Every (cell, chunk of BM_CHUNK of its particles) pair is a work item of one warp, so big
 // cells are spread over many warps and every lane does the same work.  Two passes over the items:
-//   1. the largest FP32 distance d32 = |fl(x) - fl(p)| of each cell (atomic max of its bits);
+//   1. the largest FP32 distance d32 = |fl(x) - fl(p)| of each cell (atomic max of its bits; a cell
+//      of a single item finishes step 2 at once);
 //   2. the FP64 squared distance, for the particles whose d32 is within the FP32 error margin
 //      4e-7 + 6e-7 d of that maximum (atomic max of the bits of the non-negative double).
 // The FP32 distance of a particle differs from the exact one by less than about 1.1e-7 + 1.3e-7 d
@@ -395,6 +396,30 @@ __device__ __forceinline__ float bm_d32(const float4 v, float px, float py, floa
     return sqrtf(dx * dx + dy * dy + dz * dz);
 }
 
+// the largest FP64 squared distance from p among the particles [j0, j1) whose FP32 distance
+// reaches thr (warp-wide; FP64 runs at a small fraction of the FP32 rate, so only warp steps that
+// hold a candidate enter the FP64 branch)
+__device__ __forceinline__ double bm_candidates(long long j0, long long j1, const Com4& p, float px, float py,
+                                                float pz, float thr, const float4* __restrict__ posf,
+                                                const double* __restrict__ sx, const double* __restrict__ sy,
+                                                const double* __restrict__ sz, int lane)
+{
+    double best = 0.0;
+    for (long long jb = j0; jb < j1; jb += 32) {
+        const long long j = jb + lane;
+        const bool cand = j < j1 && bm_d32(posf[j], px, py, pz) >= thr;
+        if (__any_sync(FMM_FULL_MASK, cand) && cand) best = fmax(best, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
+    return best;
+}
+
+__device__ __forceinline__ float bm_threshold(float top) { return top - (4e-7f + 6e-7f * top); }
+
+// PASS 1: per item the FP32 maximum; a cell of one item finishes at once (its FP64 candidates),
+// a cell of several items records the item's maximum and raises the cell's.  PASS 2: the items of
+// multi-item cells whose maximum reaches the cell's threshold look for FP64 candidates.
 template <int PASS>
 __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, const unsigned int* __restrict__ n_items,
                                                  long long cap, const unsigned int* __restrict__ ncell,
@@ -403,7 +428,7 @@ __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, c
                                                  const Com4* __restrict__ com, const float4* __restrict__ posf,
                                                  const double* __restrict__ sx, const double* __restrict__ sy,
                                                  const double* __restrict__ sz, unsigned int* __restrict__ bm32,
-                                                 unsigned long long* __restrict__ bm64)
+                                                 unsigned long long* __restrict__ bm64, float* __restrict__ imax)
 {
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -414,7 +439,9 @@ __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, c
         const int c = item[i];
         if (c < 0 || c >= (int)*ncell) continue;
         const long long k = i - (long long)base[c];
-        if (k < 0 || k >= (long long)cnt[c]) continue;
+        const long long nk = cnt[c];
+        if (k < 0 || k >= nk) continue;
+        if (PASS == 2 && nk == 1) continue;
         const long long f = cfirst[c], e = f + ccount[c];
         const long long j0 = f + k * BM_CHUNK, j1 = min(j0 + BM_CHUNK, e);
         const Com4 p = com[c];
@@ -424,21 +451,17 @@ __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, c
             for (long long j = j0 + lane; j < j1; j += 32) m = fmaxf(m, bm_d32(posf[j], px, py, pz));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FMM_FULL_MASK, m, o));
-            if (lane == 0) atomicMax(bm32 + c, __float_as_uint(m));
-        } else {
-            const float top = __uint_as_float(bm32[c]);
-            const float thr = top - (4e-7f + 6e-7f * top);
-            // FP64 runs at a small fraction of the FP32 rate: only warp steps that hold a candidate
-            // enter the FP64 branch
-            double best = 0.0;
-            for (long long jb = j0; jb < j1; jb += 32) {
-                const long long j = jb + lane;
-                const bool cand = j < j1 && bm_d32(posf[j], px, py, pz) >= thr;
-                if (__any_sync(FMM_FULL_MASK, cand) && cand)
-                    best = fmax(best, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
+            if (nk == 1) {
+                const double best = bm_candidates(j0, j1, p, px, py, pz, bm_threshold(m), posf, sx, sy, sz, lane);
+                if (lane == 0) bm64[c] = (unsigned long long)__double_as_longlong(best);
+            } else if (lane == 0) {
+                imax[i] = m;
+                atomicMax(bm32 + c, __float_as_uint(m));
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
+        } else {
+            const float thr = bm_threshold(__uint_as_float(bm32[c]));
+            if (imax[i] < thr) continue;  // no particle of this item can be the farthest
+            const double best = bm_candidates(j0, j1, p, px, py, pz, thr, posf, sx, sy, sz, lane);
             if (lane == 0 && best > 0.0) atomicMax(bm64 + c, (unsigned long long)__double_as_longlong(best));
         }
     }
@@ -490,10 +513,10 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
     const unsigned pb = (unsigned)std::max(1LL, std::min(want, (long long)sms * 8));
     k_bm_pass<1><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
                                     t.cfirst, t.ccount,
-                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64);
+                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64, t.bm_imax);
     k_bm_pass<2><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
                                     t.cfirst, t.ccount,
-                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64);
+                                    t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64, t.bm_imax);
     k_bm_final<<<gb, TB, 0, s>>>(t.dcount, t.cchild, t.bm64, t.bmax);
     return cudaGetLastError();
 }
