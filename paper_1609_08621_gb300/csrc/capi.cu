@@ -170,7 +170,7 @@ static void free_all(fmm_ctx* c)
 {
     DevTree& t = c->t;
     void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
-                  t.accs, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
+                  t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
                   t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
     for (void* p : ps)
@@ -273,6 +273,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.posf, cap));
         CK(alloc(&t.off, cap));
         CK(alloc(&t.accs, cap));
+        CK(alloc(&t.act, cap));
         CK(alloc(&t.bucket_of, cap));
         CK(alloc(&t.bflag, cap));
         CK(alloc(&t.ifirst, cap));
@@ -611,7 +612,7 @@ static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, 
             w.cap_item_pc = need_pc;
         }
         CK(fmm_launch_items(c->t, w, c->ctr, ia.chunk, s));
-        c->launches += 2 + 2 * 3;
+        c->launches += 3 + 2 * 3;
         CK(fmm_launch_pp(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[3], s));
         CK(fmm_launch_pc(c->t, c->w, c->ctr, ia, s));
@@ -748,7 +749,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     ia.accumulate = q.accumulate;
     ia.chunk = q.list_chunk ? q.list_chunk : FMM_LIST_CHUNK;
     CK(fmm_launch_items(t, w, c->ctr, ia.chunk, s));
-    c->launches += 2 + 2 * 3;
+    c->launches += 3 + 2 * 3;
     CK(fmm_launch_pp(t, w, c->ctr, ia, s));
     CK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     CK(fmm_launch_pc(t, w, c->ctr, ia, s));

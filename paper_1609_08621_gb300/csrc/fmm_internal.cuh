@@ -106,6 +106,7 @@ struct DevTree {
     float4 *off = nullptr;   // (x - com_bucket) in single precision, mass
     int *bucket_of = nullptr;
     float4 *accs = nullptr;  // accumulator in sorted order (ax, ay, az, pot)
+    int *act = nullptr;      // per group, its active particles compacted (see k_group_active)
     // radix tree (nodes 0..n-2 internal, leaf p is node n-1+p)
     int *ifirst = nullptr, *ilast = nullptr, *ileft = nullptr, *iright = nullptr;  // child node ids
     int *nparent = nullptr;  // parent internal node of every node (2n-1)

@@ -31,6 +31,8 @@
 // PC: the order-4 moment record of each source cell evaluated at u_i - z_s
 // (fmm_pc_acc, trace form).  Records of 32 cells are staged per warp in shared memory.
 // L2P: the group's order-5 local coefficients evaluated at u_i.
+#include <algorithm>
+
 #include "expansions.cuh"
 #include "fmm_internal.cuh"
 
@@ -71,24 +73,23 @@ struct Sinks {
     static constexpr int S = 32 / Q;
     float ux[R], uy[R], uz[R], m[R];
     float ax[R], ay[R], az[R], ph[R];
-    int idx[R];
     bool v[R];
-    int split;
+    int split, slot;
 
-    __device__ __forceinline__ void load(const Group& G, const Com4& ck, const int* __restrict__ bucket_of,
-                                         const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
-                                         const float4* __restrict__ off, int lane)
+    // sink slot i of the group is its i-th active particle act[G.first + i], i < nact
+    __device__ __forceinline__ void load(const Group& G, int nact, const int* __restrict__ act, const Com4& ck,
+                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
+                                         const Com4* __restrict__ com, const float4* __restrict__ off, int lane)
     {
         split = lane / S;
-        const int slot = lane % S;
+        slot = lane % S;
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const int i = slot + r * S;
-            v[r] = i < G.count;
-            idx[r] = G.first + i;
+            v[r] = i < nact;
             ux[r] = uy[r] = uz[r] = m[r] = 0.0f;
             ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
-            if (v[r]) load_sink(idx[r], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m[r]);
+            if (v[r]) load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m[r]);
         }
     }
 
@@ -117,7 +118,8 @@ struct PPChunk {
 };
 
 template <int R, int Q>
-__device__ __forceinline__ long long pp_item(const Group& G, int chunk, const Com4& ck,
+__device__ __forceinline__ long long pp_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
+                                             const Com4& ck,
                                              const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
                                              const int* __restrict__ ccount, const Com4* __restrict__ com,
                                              const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
@@ -125,7 +127,7 @@ __device__ __forceinline__ long long pp_item(const Group& G, int chunk, const Co
                                              PPChunk& E, float eps2, int lane, int csize)
 {
     Sinks<R, Q> K;
-    K.load(G, ck, bucket_of, bucket_cell, com, off, lane);
+    K.load(G, nact, act, ck, bucket_of, bucket_cell, com, off, lane);
     long long nsrc = 0;
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pp_len);
     {
@@ -196,7 +198,7 @@ __device__ __forceinline__ long long pp_item(const Group& G, int chunk, const Co
     if (K.split == 0) {
 #pragma unroll
         for (int r = 0; r < R; r++)
-            if (K.v[r]) part[K.idx[r] - G.first] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+            if (K.v[r]) part[K.slot + r * K.S] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
     }
     return nsrc;
 }
@@ -208,8 +210,9 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
                                                  const int* __restrict__ ccount, const int* __restrict__ cnact,
                                                  const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
-                                                 float4* __restrict__ part_pp, float eps2, int csize,
-                                                 long long cap_items, DevCounters* __restrict__ ctr)
+                                                 float4* __restrict__ part_pp, const int* __restrict__ act,
+                                                 float eps2, int csize, long long cap_items,
+                                                 DevCounters* __restrict__ ctr)
 {
     __shared__ float4 tile[IW][PP_TILE];
     __shared__ PPChunk chunk[IW];
@@ -227,10 +230,10 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
         const Group G = groups[gi];
         const int k = (int)(i - base_pp[gi]);
         const Com4 ck = com[G.cell];
-        const int n = G.count;
+        const int n = cnact[G.cell];  // active sinks of the group
         float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
-#define PP_CALL(R, Q) pp_item<R, Q>(G, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
+#define PP_CALL(R, Q) pp_item<R, Q>(G, n, act, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
         if (n <= 8) nsrc = PP_CALL(1, 4);
         else if (n <= 16) nsrc = PP_CALL(1, 2);
         else if (n <= 24) nsrc = PP_CALL(3, 4);
@@ -247,7 +250,8 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
 // are taken one after another against each staged chunk of cell records, so a single copy of
 // the (large) particle-cell body serves every layout.
 #define PC_RMAX 3
-__device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q, const Com4& ck,
+__device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __restrict__ act, int chunk, int R,
+                                        int Q, const Com4& ck,
                                         const unsigned int* __restrict__ pc, const Com4* __restrict__ com,
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
@@ -262,9 +266,9 @@ __device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q,
         ux[r] = uy[r] = uz[r] = 0.0f;
         ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
         const int i = slot + r * S;
-        if (r < R && i < G.count) {
+        if (r < R && i < nact) {
             float m;
-            load_sink(G.first + i, ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
+            load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
         }
     }
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pc_len);
@@ -312,7 +316,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int chunk, int R, int Q,
             ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
         }
         const int i = slot + r * S;
-        if (split == 0 && i < G.count) part[i] = make_float4(ax[r], ay[r], az[r], ph[r]);
+        if (split == 0 && i < nact) part[i] = make_float4(ax[r], ay[r], az[r], ph[r]);
     }
 }
 
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
                                                  const Com4* __restrict__ com, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  const float* __restrict__ rec, float4* __restrict__ part_pc,
-                                                 float eps2, int csize, long long cap_items,
+                                                 const int* __restrict__ act, float eps2, int csize, long long cap_items,
                                                  DevCounters* __restrict__ ctr)
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         const Group G = groups[gi];
         const int k = (int)(i - base_pc[gi]);
         const Com4 ck = com[G.cell];
-        const int n = G.count;
+        const int n = cnact[G.cell];  // active sinks of the group
         int R, Q;
         if (n <= 8) { R = 1; Q = 4; }
         else if (n <= 16) { R = 1; Q = 2; }
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         else if (n <= 32) { R = 1; Q = 1; }
         else if (n <= 48) { R = 3; Q = 2; }
         else { R = 2; Q = 1; }
-        pc_item(G, k, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
+        pc_item(G, n, act, k, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
                 idss[wl], eps2, lane, csize);
         if (lane == 0) {
             const int nc = min(csize, G.pc_len - k * csize);
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
                                                       const unsigned int* __restrict__ cnt_pc,
                                                       const unsigned int* __restrict__ base_pc,
                                                       const float4* __restrict__ part_pc,
-                                                      const unsigned char* __restrict__ sact,
+                                                      const int* __restrict__ act, const int* __restrict__ cnact,
                                                       const unsigned int* __restrict__ perm, long long n,
                                                       float* __restrict__ acc, float* __restrict__ pot, int terms)
 {
@@ -396,8 +400,9 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
         unsigned int npc = (terms & 2) ? cnt_pc[gi] : 0u, bpc = base_pc[gi];
         if ((long long)bpp + npp > cap_item_pp) npp = 0;
         if ((long long)bpc + npc > cap_item_pc) npc = 0;
-        for (int i = lane; i < G.count; i += 32) {
-            const int s = G.first + i;
+        const int nact = cnact[G.cell];
+        for (int i = lane; i < nact; i += 32) {
+            const int s = act[G.first + i];
             T ax = 0, ay = 0, az = 0, aw = 0;
             for (unsigned int k = 0; k < npp; k++) {
                 const float4 p = part_pp[(unsigned long long)(bpp + k) * FMM_GMAX + i];
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
                 az += lz;
                 aw += lw;
             }
-            if (sact[s]) {
+            {
                 const unsigned int p = perm[s];
                 acc[p] = (float)ax;
                 acc[n + p] = (float)ay;
@@ -458,6 +463,29 @@ static int persistent_blocks(K kernel)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ITHREADS, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     return (per_sm < 1 ? 1 : per_sm) * sms;
+}
+
+// Active sinks of every group, compacted in particle order: act[G.first + i] = the group's i-th
+// active particle (with no inactive particles, the identity).  One warp per group.
+__global__ void k_group_active(const Group* __restrict__ groups, const unsigned long long* __restrict__ ngroups_dev,
+                               long long cap_groups, const unsigned char* __restrict__ sact, int* __restrict__ act)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long ng = (long long)min(*ngroups_dev, (unsigned long long)cap_groups);
+    const unsigned int lt = fmm_lanemask_lt();
+    for (long long gi = gw; gi < ng; gi += nw) {
+        const Group G = groups[gi];
+        int done = 0;
+        for (int b = 0; b < G.count; b += 32) {
+            const int i = b + lane;
+            const bool a = i < G.count && sact[G.first + i] != 0;
+            const unsigned int m = __ballot_sync(FMM_FULL_MASK, a);
+            if (a) act[G.first + done + __popc(m & lt)] = G.first + i;
+            done += __popc(m);
+        }
+    }
 }
 
 // Work items: per group ceil(pp_len / chunk) PP items and ceil(pc_len / chunk) PC items; exclusive scans give each group's first item, and every item learns its group.
@@ -504,6 +532,8 @@ cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk
     if (e != cudaSuccess) return e;
     k_item_expand<<<blocks, 256, 0, s>>>(ng, w.cnt_pp, w.base_pp, w.cnt_pc, w.base_pc, w.item_pp, w.item_pc,
                                          w.cap_item_pp, w.cap_item_pc, &ctr->overflow);
+    k_group_active<<<(unsigned)std::max(1LL, std::min(fmm_ceil_div(ng, ITHREADS / 32), 152LL * 16)), ITHREADS, 0, s>>>(
+        w.groups, &ctr->n_groups, w.cap_groups, t.sact, t.act);
     return cudaGetLastError();
 }
 
@@ -514,7 +544,7 @@ cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pp);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
     k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
-                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, a.eps2, a.chunk, w.cap_item_pp, ctr);
+                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, t.act, a.eps2, a.chunk, w.cap_item_pp, ctr);
     return cudaGetLastError();
 }
 
@@ -525,7 +555,7 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pc);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
     k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.com, t.bucket_of,
-                                     t.bucket_cell, t.off, t.rec, w.part_pc, a.eps2, a.chunk, w.cap_item_pc, ctr);
+                                     t.bucket_cell, t.off, t.rec, w.part_pc, t.act, a.eps2, a.chunk, w.cap_item_pc, ctr);
     return cudaGetLastError();
 }
 
@@ -536,12 +566,12 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
     if (a.accumulate == 1)
         k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
-            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
             a.terms);
     else
         k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
-            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.sact, t.idx, n, acc, pot,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
             a.terms);
     return cudaGetLastError();
 }

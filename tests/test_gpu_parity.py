@@ -215,7 +215,11 @@ def test_active_subset_matches_full_solve(ctx):
     full, fp = gpu_solve(ctx, pos, mass, 1e-3, 0.7)
     part, pp = gpu_solve(ctx, pos, mass, 1e-3, 0.7, active=act)
     sel = act.astype(bool)
-    assert np.array_equal(part[:, sel], full[:, sel]) and np.array_equal(pp[sel], fp[sel])
+    # the same interaction lists; only the split of each sink's sums across lanes follows the
+    # group's active count, so the results agree to FP32 summation order
+    na = np.linalg.norm(full[:, sel], axis=0)
+    assert np.all(np.linalg.norm(part[:, sel] - full[:, sel], axis=0) <= 2e-6 * na)
+    assert np.all(np.abs(pp[sel] - fp[sel]) <= 2e-6 * np.abs(fp[sel]))
     assert np.all(np.isnan(part[:, ~sel]))
     assert ctx.stats()["n_active"] == int(sel.sum())
     none, _ = gpu_solve(ctx, pos, mass, 1e-3, 0.7, active=np.zeros(n, np.uint8))
