@@ -249,9 +249,4 @@ __device__ __forceinline__ unsigned int fmm_lanemask_lt()
     return m;
 }
 
-__device__ __forceinline__ int fmm_lane() { return threadIdx.x & 31; }
-
-template <typename T>
-__device__ __forceinline__ T fmm_ldcg(const T* p) { return __ldcg(p); }
-
 __host__ __device__ __forceinline__ long long fmm_ceil_div(long long a, long long b) { return (a + b - 1) / b; }
