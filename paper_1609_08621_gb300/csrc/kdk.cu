@@ -19,6 +19,7 @@
 
 __device__ __forceinline__ int target_rung(float ax, float ay, float az, double eps, double dt0, int R)
 {
+    if (R == 0) return 0;  // a single rung: nothing to decide (and FP64 sqrt and division are slow here)
     double x = ax, y = ay, z = az;
     double a2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
     double am = __dsqrt_rn(a2);
