@@ -293,7 +293,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
             if (r >= R) break;
             float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
             const float sx = ux[r], sy = uy[r], sz = uz[r];
-#pragma unroll 1
+#pragma unroll 2
             for (int j = split; j < ne; j += Q) {
                 const float4 z = Z[j];
                 fmm_pc_acc(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]), sx - z.x, sy - z.y, sz - z.z,
