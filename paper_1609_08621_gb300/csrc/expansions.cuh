@@ -7,6 +7,16 @@
 #define FMM_NMOM 32    /* moment slots: M, M2, M3, M4 */
 #define FMM_NREC 44    /* moment record incl. traces */
 
+/* 1/sqrt(x) for x >= eps^2 > 0, which is never subnormal: the approximate reciprocal square
+   root instruction in its subnormal-flushing form, which needs no scaling of subnormal inputs
+   around the special-function unit (PTX ISA, rsqrt.approx.ftz.f32) */
+__device__ __forceinline__ float fmm_rsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 /* multi-index table (a, b, c) of the local coefficients, in storage order */
 static const int fmm_multi_index_table[FMM_NL * 3] = {
     0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 1, 2, 0, 0, 1, 1, 0, 1, 0, 1, 0, 2, 0, 0, 1, 1, 0, 0, 2, 3, 0, 0, 2, 1, 0, 2, 0, 1, 1, 2, 0, 1, 1, 1, 1, 0, 2, 0, 3, 0, 0, 2, 1, 0, 1, 2, 0, 0, 3, 4, 0, 0, 3, 1, 0, 3, 0, 1, 2, 2, 0, 2, 1, 1, 2, 0, 2, 1, 3, 0, 1, 2, 1, 1, 1, 2, 1, 0, 3, 0, 4, 0, 0, 3, 1, 0, 2, 2, 0, 1, 3, 0, 0, 4, 5, 0, 0, 4, 1, 0, 4, 0, 1, 3, 2, 0, 3, 1, 1, 3, 0, 2, 2, 3, 0, 2, 2, 1, 2, 1, 2, 2, 0, 3, 1, 4, 0, 1, 3, 1, 1, 2, 2, 1, 1, 3, 1, 0, 4, 0, 5, 0, 0, 4, 1, 0, 3, 2, 0, 2, 3, 0, 1, 4, 0, 0, 5
@@ -325,7 +335,7 @@ __device__ __forceinline__ void fmm_moment_norms2(const float* __restrict__ R, f
 __device__ __forceinline__ void fmm_m2l_acc(const float* __restrict__ M, float rx, float ry, float rz,
                                             float eps2, float* __restrict__ Lc)
 {
-    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
+    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
     float D[56];
     fmm_green_scaled(rx * ir, ry * ir, rz * ir, D);
     const float ir2 = ir * ir, ir3 = ir2 * ir, ir4 = ir2 * ir2;
@@ -429,7 +439,7 @@ __device__ __forceinline__ void fmm_m2l_acc(const float* __restrict__ M, float r
 __device__ __forceinline__ void fmm_p2l_acc(float m, float rx, float ry, float rz, float eps2,
                                             float* __restrict__ Lc)
 {
-    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
+    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
     float D[56];
     fmm_green_scaled(rx * ir, ry * ir, rz * ir, D);
     float p = m * ir;
@@ -682,7 +692,7 @@ __device__ __forceinline__ void fmm_l2p_acc(const float* __restrict__ Lc, float 
 __device__ __forceinline__ void fmm_pc_acc(const float* __restrict__ R, float rx, float ry, float rz,
                                            float eps2, float& ax, float& ay, float& az, float& phi)
 {
-    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
+    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));
     const float qx = rx * ir, qy = ry * ir, qz = rz * ir;
     const float ir2 = ir * ir;
     const float A3_300 = R[17] * qx + R[18] * qy + R[19] * qz;

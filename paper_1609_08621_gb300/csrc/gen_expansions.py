@@ -230,7 +230,7 @@ def gen_m2l():
     L = ["/* multipole (moment record M about z) -> local coefficients about c; r = c - z */",
          "__device__ __forceinline__ void fmm_m2l_acc(const float* __restrict__ M, float rx, float ry, float rz,",
          "                                            float eps2, float* __restrict__ Lc)", "{",
-         "    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
+         "    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
          "    float D[56];",
          "    fmm_green_scaled(rx * ir, ry * ir, rz * ir, D);",
          "    const float ir2 = ir * ir, ir3 = ir2 * ir, ir4 = ir2 * ir2;"]
@@ -262,7 +262,7 @@ def gen_p2l():
     L = ["/* particle of mass m at z -> local coefficients about c; r = c - z */",
          "__device__ __forceinline__ void fmm_p2l_acc(float m, float rx, float ry, float rz, float eps2,",
          "                                            float* __restrict__ Lc)", "{",
-         "    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
+         "    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
          "    float D[56];",
          "    fmm_green_scaled(rx * ir, ry * ir, rz * ir, D);",
          "    float p = m * ir;"]
@@ -344,7 +344,7 @@ def gen_pc():
     L = ["/* particle-cell: acceleration and potential at r = x - z of the record R (44 floats, smem) */",
          "__device__ __forceinline__ void fmm_pc_acc(const float* __restrict__ R, float rx, float ry, float rz,",
          "                                           float eps2, float& ax, float& ay, float& az, float& phi)", "{",
-         "    const float ir = rsqrtf(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
+         "    const float ir = fmm_rsqrt(fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, eps2))));",
          "    const float qx = rx * ir, qy = ry * ir, qz = rz * ir;",
          "    const float ir2 = ir * ir;"]
     q = ["qx", "qy", "qz"]
@@ -402,7 +402,7 @@ def gen_pc():
 
 def count_flops(lines):
     """FP32 flops of generated straight-line code: each binary '*', '+', '-' is 1 flop, fmaf is 2,
-    an update 'x += e' / 'x -= e' adds 1; rsqrtf is not counted (special-function unit)."""
+    an update 'x += e' / 'x -= e' adds 1; fmm_rsqrt is not counted (special-function unit)."""
     n = 0
     for ln in lines:
         st = ln.strip()
@@ -431,6 +431,15 @@ def main():
            f"#define FMM_NL {NL}      /* local coefficients, |k| <= 5 */",
            f"#define FMM_NMOM {NMOM}    /* moment slots: M, M2, M3, M4 */",
            f"#define FMM_NREC {NREC}    /* moment record incl. traces */", "",
+           "/* 1/sqrt(x) for x >= eps^2 > 0, which is never subnormal: the approximate reciprocal square",
+           "   root instruction in its subnormal-flushing form, which needs no scaling of subnormal inputs",
+           "   around the special-function unit (PTX ISA, rsqrt.approx.ftz.f32) */",
+           "__device__ __forceinline__ float fmm_rsqrt(float x)",
+           "{",
+           "    float y;",
+           '    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));',
+           "    return y;",
+           "}", "",
            "/* multi-index table (a, b, c) of the local coefficients, in storage order */",
            "static const int fmm_multi_index_table[FMM_NL * 3] = {"]
     out.append("    " + ", ".join(f"{a}, {b}, {c}" for a, b, c in MI))

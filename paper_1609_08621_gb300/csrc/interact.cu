@@ -17,11 +17,13 @@
 // writes one partial (ax, ay, az, phi) per sink slot; the output kernel adds a sink's
 // partials in item order (deterministic), then the local expansion.
 //
-// One warp per item.  The warp's 32 lanes are laid out as Q list splits of 32/Q lanes,
-// each lane holding R sinks (slots lane%S, +S, ...): a group of n <= R*32/Q sinks uses
-// the (R, Q) of the smallest such slot count, so few lanes idle whatever the group size
-// (groups hold <= g particles, typically 30-64).  Each split takes every Q-th source; the
-// splits' partial sums are added with warp shuffles.
+// One warp per item.  The warp's 32 lanes are laid out as Q list splits of S = 32/Q lanes,
+// each lane holding R sinks (slots lane%S, +S, ...); each split takes every Q-th source and the
+// splits' partial sums are added with warp shuffles.  Groups hold <= g particles (typically
+// 30-64), and a layout with more slots than active sinks idles lanes, so the slot count follows
+// the active count closely: PP uses one or two compile-time layouts in steps of 8 slots up to 48
+// (e.g. 32 + 8 for 40 sinks), each lane holding its sinks in pairs that share FP32x2
+// instructions; PC a runtime sequence of passes of 32, 16, 8 or 4 slots (at most 3 idle).
 //
 // PP: a_i += m_j (s_j - u_i) / (|s_j - u_i|^2 + eps^2)^(3/2), phi_i -= m_j / (...)^(1/2)
 // over every particle of every PP source, the sink itself included: its force term is
@@ -59,7 +61,7 @@ __device__ __forceinline__ void pp_pair(float ux, float uy, float uz, float4 s, 
 {
     const float dx = s.x - ux, dy = s.y - uy, dz = s.z - uz;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    const float ir = rsqrtf(r2);
+    const float ir = fmm_rsqrt(r2);
     const float mir = s.w * ir;
     const float mir3 = mir * ir * ir;
     ax = fmaf(mir3, dx, ax);
@@ -68,28 +70,66 @@ __device__ __forceinline__ void pp_pair(float ux, float uy, float uz, float4 s, 
     ph -= mir;
 }
 
+// Two (sink, source) pairs in one set of FP32x2 instructions: the same operations, in the same
+// order and rounding, as pp_pair for each component (fmaf / fadd / fmul round to nearest per
+// component), so the sums are bit-identical, but half the FP32 instructions are issued.  The
+// sink offsets come negated (s - u = s + (-u) exactly) and the potential is summed positively and
+// negated at the end (rounding to nearest is symmetric), so no negation is issued per pair.
+__device__ __forceinline__ void pp_pair2(float2 nux, float2 nuy, float2 nuz, float4 s, float2 eps2, float2& ax,
+                                         float2& ay, float2& az, float2& pw)
+{
+    const float2 dx = __fadd2_rn(make_float2(s.x, s.x), nux);
+    const float2 dy = __fadd2_rn(make_float2(s.y, s.y), nuy);
+    const float2 dz = __fadd2_rn(make_float2(s.z, s.z), nuz);
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 ir = make_float2(fmm_rsqrt(r2.x), fmm_rsqrt(r2.y));
+    const float2 mir = __fmul2_rn(make_float2(s.w, s.w), ir);
+    const float2 mir3 = __fmul2_rn(__fmul2_rn(mir, ir), ir);
+    ax = __ffma2_rn(mir3, dx, ax);
+    ay = __ffma2_rn(mir3, dy, ay);
+    az = __ffma2_rn(mir3, dz, az);
+    pw = __fadd2_rn(pw, mir);
+}
+
+// R (even) sinks per lane as R/2 pairs: slots base + slot + r*S, pair p holding r = 2p and 2p+1.
 template <int R, int Q>
 struct Sinks {
-    static constexpr int S = 32 / Q;
-    float ux[R], uy[R], uz[R], m[R];
-    float ax[R], ay[R], az[R], ph[R];
-    bool v[R];
+    static_assert(R % 2 == 0, "sinks are taken in pairs");
+    static constexpr int S = 32 / Q, P = R / 2;
+    float2 nux[P], nuy[P], nuz[P];
+    float2 ax[P], ay[P], az[P], pw[P];
     int split, slot;
 
-    // sink slot i of the group is its i-th active particle act[G.first + i], i < nact
-    __device__ __forceinline__ void load(const Group& G, int nact, const int* __restrict__ act, const Com4& ck,
-                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
-                                         const Com4* __restrict__ com, const float4* __restrict__ off, int lane)
+    // sink slot base + slot + r*S of the group is its active particle act[G.first + i], i < nact
+    __device__ __forceinline__ void load(const Group& G, int nact, int base, const int* __restrict__ act,
+                                         const Com4& ck, const int* __restrict__ bucket_of,
+                                         const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                         const float4* __restrict__ off, int lane)
     {
         split = lane / S;
         slot = lane % S;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int i = slot + r * S;
-            v[r] = i < nact;
-            ux[r] = uy[r] = uz[r] = m[r] = 0.0f;
-            ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
-            if (v[r]) load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m[r]);
+        for (int p = 0; p < P; p++) {
+            float ux0 = 0.f, uy0 = 0.f, uz0 = 0.f, ux1 = 0.f, uy1 = 0.f, uz1 = 0.f, m;
+            const int i0 = base + slot + 2 * p * S, i1 = i0 + S;
+            if (i0 < nact) load_sink(act[G.first + i0], ck, bucket_of, bucket_cell, com, off, ux0, uy0, uz0, m);
+            if (i1 < nact) load_sink(act[G.first + i1], ck, bucket_of, bucket_cell, com, off, ux1, uy1, uz1, m);
+            nux[p] = make_float2(-ux0, -ux1);
+            nuy[p] = make_float2(-uy0, -uy1);
+            nuz[p] = make_float2(-uz0, -uz1);
+            ax[p] = ay[p] = az[p] = pw[p] = make_float2(0.f, 0.f);
+        }
+    }
+
+    // every Q-th staged source from this lane's split, against the lane's R sinks
+    __device__ __forceinline__ void sweep(const float4* T, int total, float eps2)
+    {
+        const float2 e2 = make_float2(eps2, eps2);
+#pragma unroll 4
+        for (int t = split; t < total; t += Q) {
+            const float4 s = T[t];
+#pragma unroll
+            for (int p = 0; p < P; p++) pp_pair2(nux[p], nuy[p], nuz[p], s, e2, ax[p], ay[p], az[p], pw[p]);
         }
     }
 
@@ -99,11 +139,36 @@ struct Sinks {
 #pragma unroll
         for (int o = S; o < 32; o <<= 1)
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                ax[r] += __shfl_xor_sync(FMM_FULL_MASK, ax[r], o);
-                ay[r] += __shfl_xor_sync(FMM_FULL_MASK, ay[r], o);
-                az[r] += __shfl_xor_sync(FMM_FULL_MASK, az[r], o);
-                ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
+            for (int p = 0; p < P; p++) {
+                ax[p].x += __shfl_xor_sync(FMM_FULL_MASK, ax[p].x, o);
+                ax[p].y += __shfl_xor_sync(FMM_FULL_MASK, ax[p].y, o);
+                ay[p].x += __shfl_xor_sync(FMM_FULL_MASK, ay[p].x, o);
+                ay[p].y += __shfl_xor_sync(FMM_FULL_MASK, ay[p].y, o);
+                az[p].x += __shfl_xor_sync(FMM_FULL_MASK, az[p].x, o);
+                az[p].y += __shfl_xor_sync(FMM_FULL_MASK, az[p].y, o);
+                pw[p].x += __shfl_xor_sync(FMM_FULL_MASK, pw[p].x, o);
+                pw[p].y += __shfl_xor_sync(FMM_FULL_MASK, pw[p].y, o);
+            }
+    }
+
+    // split 0 writes the sums; with self_term the sink's own potential term m_i / eps, which the
+    // sweep included through the identical pair computation, is added back first
+    __device__ __forceinline__ void store(const Group& G, int nact, int base, const int* __restrict__ act,
+                                          const float4* __restrict__ off, float4* __restrict__ part, bool self_term,
+                                          float eps2)
+    {
+        if (split != 0) return;
+        const float ie = fmm_rsqrt(eps2);
+#pragma unroll
+        for (int p = 0; p < P; p++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int i = base + slot + (2 * p + h) * S;
+                if (i < nact) {
+                    float ph = -(h ? pw[p].y : pw[p].x);
+                    if (self_term) ph += off[act[G.first + i]].w * ie;
+                    part[i] = make_float4(h ? ax[p].y : ax[p].x, h ? ay[p].y : ay[p].x, h ? az[p].y : az[p].x, ph);
+                }
             }
     }
 };
@@ -117,7 +182,10 @@ struct PPChunk {
     float dx[32], dy[32], dz[32];
 };
 
-template <int R, int Q>
+// One PP work item with the sink layout (R1, Q1) for slots [0, R1*32/Q1) and, when R2 > 0, a
+// second layout (R2, Q2) for the slots from there on, both swept over each staged tile: a group of
+// 24 or 40 sinks takes 16 + 8 or 32 + 8 slots instead of 32 or 48.
+template <int R1, int Q1, int R2, int Q2>
 __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
                                              const Com4& ck,
                                              const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
@@ -126,79 +194,71 @@ __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int
                                              const float4* __restrict__ off, float4* __restrict__ part, float4* T,
                                              PPChunk& E, float eps2, int lane, int csize)
 {
-    Sinks<R, Q> K;
-    K.load(G, nact, act, ck, bucket_of, bucket_cell, com, off, lane);
+    constexpr int B2 = R1 * (32 / Q1);
+    Sinks<R1, Q1> K;
+    Sinks<(R2 > 0 ? R2 : 2), (R2 > 0 ? Q2 : 1)> K2;
+    K.load(G, nact, 0, act, ck, bucket_of, bucket_cell, com, off, lane);
+    if (R2 > 0) K2.load(G, nact, B2, act, ck, bucket_of, bucket_cell, com, off, lane);
     long long nsrc = 0;
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pp_len);
-    {
-        for (int base = e0; base < e1; base += 32) {
-            const int ne = min(32, e1 - base);
-            int first = 0, cnt = 0;
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-            if (lane < ne) {
-                const unsigned int e = pp[G.pp_off + base + lane];
-                int bc;
-                if (e & FMM_PARTICLE_BIT) {
-                    first = (int)(e & ~FMM_PARTICLE_BIT);
-                    cnt = 1;
-                    bc = bucket_cell[bucket_of[first]];
-                } else {
-                    first = cfirst[e];
-                    cnt = ccount[e];
-                    bc = (int)e;
-                }
-                const Com4 cb = com[bc];
-                dx = __double2float_rn(cb.x - ck.x);
-                dy = __double2float_rn(cb.y - ck.y);
-                dz = __double2float_rn(cb.z - ck.z);
+    for (int base = e0; base < e1; base += 32) {
+        const int ne = min(32, e1 - base);
+        int first = 0, cnt = 0;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        if (lane < ne) {
+            const unsigned int e = pp[G.pp_off + base + lane];
+            int bc;
+            if (e & FMM_PARTICLE_BIT) {
+                first = (int)(e & ~FMM_PARTICLE_BIT);
+                cnt = 1;
+                bc = bucket_cell[bucket_of[first]];
+            } else {
+                first = cfirst[e];
+                cnt = ccount[e];
+                bc = (int)e;
             }
-            int incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int total = __shfl_sync(FMM_FULL_MASK, incl, 31);
-            E.first[lane] = first;
-            E.excl[lane] = incl - cnt;
-            E.dx[lane] = dx;
-            E.dy[lane] = dy;
-            E.dz[lane] = dz;
-            if (lane == 31) E.excl[32] = total;
-            __syncwarp();
-            for (int t = lane; t < total; t += 32) {
-                // largest j with excl[j] <= t (entries with cnt 0 never occur)
-                int lo = 0, hi = ne - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (E.excl[mid] <= t) lo = mid;
-                    else hi = mid - 1;
-                }
-                const float4 o = off[E.first[lo] + (t - E.excl[lo])];
-                T[t] = make_float4(E.dx[lo] + o.x, E.dy[lo] + o.y, E.dz[lo] + o.z, o.w);
-            }
-            __syncwarp();
-#pragma unroll 4
-            for (int t = K.split; t < total; t += Q) {
-                const float4 s = T[t];
-#pragma unroll
-                for (int r = 0; r < R; r++) pp_pair(K.ux[r], K.uy[r], K.uz[r], s, eps2, K.ax[r], K.ay[r], K.az[r], K.ph[r]);
-            }
-            nsrc += total;
-            __syncwarp();
+            const Com4 cb = com[bc];
+            dx = __double2float_rn(cb.x - ck.x);
+            dy = __double2float_rn(cb.y - ck.y);
+            dz = __double2float_rn(cb.z - ck.z);
         }
-        K.reduce();
-        // remove the self term of the potential (the force term is exactly zero), once per sink
-        if (chunk == 0) {
-            const float ie = rsqrtf(eps2);
+        int incl = cnt;
 #pragma unroll
-            for (int r = 0; r < R; r++) K.ph[r] += K.m[r] * ie;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
         }
+        const int total = __shfl_sync(FMM_FULL_MASK, incl, 31);
+        E.first[lane] = first;
+        E.excl[lane] = incl - cnt;
+        E.dx[lane] = dx;
+        E.dy[lane] = dy;
+        E.dz[lane] = dz;
+        if (lane == 31) E.excl[32] = total;
+        __syncwarp();
+        for (int t = lane; t < total; t += 32) {
+            // largest j with excl[j] <= t (entries with cnt 0 never occur)
+            int lo = 0, hi = ne - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (E.excl[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            const float4 o = off[E.first[lo] + (t - E.excl[lo])];
+            T[t] = make_float4(E.dx[lo] + o.x, E.dy[lo] + o.y, E.dz[lo] + o.z, o.w);
+        }
+        __syncwarp();
+        K.sweep(T, total, eps2);
+        if (R2 > 0) K2.sweep(T, total, eps2);
+        nsrc += total;
+        __syncwarp();
     }
-    if (K.split == 0) {
-#pragma unroll
-        for (int r = 0; r < R; r++)
-            if (K.v[r]) part[K.slot + r * K.S] = make_float4(K.ax[r], K.ay[r], K.az[r], K.ph[r]);
+    // the self term of the potential is removed once per sink, by the group's first item
+    K.reduce();
+    K.store(G, nact, 0, act, off, part, chunk == 0, eps2);
+    if (R2 > 0) {
+        K2.reduce();
+        K2.store(G, nact, B2, act, off, part, chunk == 0, eps2);
     }
     return nsrc;
 }
@@ -233,49 +293,58 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
         const int n = cnact[G.cell];  // active sinks of the group
         float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
-#define PP_CALL(R, Q) pp_item<R, Q>(G, n, act, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
-        if (n <= 8) nsrc = PP_CALL(1, 4);
-        else if (n <= 16) nsrc = PP_CALL(1, 2);
-        else if (n <= 24) nsrc = PP_CALL(3, 4);
-        else if (n <= 32) nsrc = PP_CALL(1, 1);
-        else if (n <= 48) nsrc = PP_CALL(3, 2);
-        else nsrc = PP_CALL(2, 1);
+#define PP_CALL(R1, Q1, R2, Q2) \
+    pp_item<R1, Q1, R2, Q2>(G, n, act, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
+        // sink slots in steps of 8 up to 48 sinks, in pairs per lane
+        if (n <= 8) nsrc = PP_CALL(2, 8, 0, 0);
+        else if (n <= 16) nsrc = PP_CALL(2, 4, 0, 0);
+        else if (n <= 24) nsrc = PP_CALL(2, 4, 2, 8);
+        else if (n <= 32) nsrc = PP_CALL(2, 2, 0, 0);
+        else if (n <= 40) nsrc = PP_CALL(2, 2, 2, 8);
+        else if (n <= 48) nsrc = PP_CALL(2, 2, 2, 4);
+        else nsrc = PP_CALL(4, 2, 0, 0);
 #undef PP_CALL
         if (lane == 0) pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nsrc;
     }
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pp_pairs, pairs);
 }
 
-// PC for one group with a runtime sink layout (R sinks per lane, Q list splits): the sinks
-// are taken one after another against each staged chunk of cell records, so a single copy of
-// the (large) particle-cell body serves every layout.
-#define PC_RMAX 3
-__device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __restrict__ act, int chunk, int R,
-                                        int Q, const Com4& ck,
+// PC sink passes: the group's active sinks [0, n) are covered by passes of S = 32, 16, 8 or 4
+// slots; in a pass lane l holds sink base + l % S and takes every Q-th staged cell (Q = 32 / S,
+// split l / S).  Full passes of 32 first, then the remainder r in passes of 16 (r > 12), 8 (r > 4)
+// or 4, so a group wastes at most 3 slots.
+#define PC_PMAX 4  // passes for n <= 64: 32 + 16 + 8 + 4 at most
+__device__ __forceinline__ int pc_pass_slots(int rem)
+{
+    return rem >= 32 ? 32 : rem > 12 ? 16 : rem > 4 ? 8 : 4;
+}
+
+// PC for one work item: each pass sweeps every staged chunk of cell records; a lane's sink offset
+// and running sum per pass stay in shared memory (U, A: PC_PMAX x 32 per warp) between chunks, so
+// one copy of the particle-cell body serves every pass.
+__device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
+                                        const Com4& ck,
                                         const unsigned int* __restrict__ pc, const Com4* __restrict__ com,
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
-                                        float4* __restrict__ part, float4* R4, float4* Z, int* ids, float eps2,
-                                        int lane, int csize)
+                                        float4* __restrict__ part, float4* R4, float4* Z, int* ids, float4* U,
+                                        float4* A, float eps2, int lane, int csize)
 {
-    const int S = 32 / Q, split = lane / S, slot = lane % S;
-    float ux[PC_RMAX], uy[PC_RMAX], uz[PC_RMAX];
-    float ax[PC_RMAX], ay[PC_RMAX], az[PC_RMAX], ph[PC_RMAX];
-#pragma unroll
-    for (int r = 0; r < PC_RMAX; r++) {
-        ux[r] = uy[r] = uz[r] = 0.0f;
-        ax[r] = ay[r] = az[r] = ph[r] = 0.0f;
-        const int i = slot + r * S;
-        if (r < R && i < nact) {
-            float m;
-            load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux[r], uy[r], uz[r], m);
-        }
+    int npass = 0;
+    for (int base = 0; base < nact; npass++) {
+        const int S = pc_pass_slots(nact - base);
+        const int i = base + lane % S;
+        float ux = 0.f, uy = 0.f, uz = 0.f, m;
+        if (i < nact) load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
+        U[npass * 32 + lane] = make_float4(ux, uy, uz, 0.0f);
+        A[npass * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        base += S;
     }
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pc_len);
-    for (int base = e0; base < e1; base += PC_CHUNK) {
-        const int ne = min(PC_CHUNK, e1 - base);
+    for (int cbase = e0; cbase < e1; cbase += PC_CHUNK) {
+        const int ne = min(PC_CHUNK, e1 - cbase);
         if (lane < ne) {
-            const unsigned int c = pc[G.pc_off + base + lane];
+            const unsigned int c = pc[G.pc_off + cbase + lane];
             const Com4 cs = com[c];
             ids[lane] = (int)c;
             Z[lane] = make_float4(__double2float_rn(cs.x - ck.x), __double2float_rn(cs.y - ck.y),
@@ -283,43 +352,49 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
         }
         __syncwarp();
         const int nv = ne * (FMM_NREC / 4);
-        for (int i = lane; i < nv; i += 32) {
-            const int cl = i / (FMM_NREC / 4), part = i - cl * (FMM_NREC / 4);
-            R4[i] = rec4[(long long)ids[cl] * (FMM_NREC / 4) + part];
+        for (int v = lane; v < nv; v += 32) {
+            const int cl = v / (FMM_NREC / 4), q = v - cl * (FMM_NREC / 4);
+            R4[v] = rec4[(long long)ids[cl] * (FMM_NREC / 4) + q];
         }
         __syncwarp();
-#pragma unroll
-        for (int r = 0; r < PC_RMAX; r++) {
-            if (r >= R) break;
+        for (int p = 0, base = 0; p < npass; p++) {
+            const int S = pc_pass_slots(nact - base), Q = 32 / S, split = lane / S;
+            const float4 u = U[p * 32 + lane];
             float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
-            const float sx = ux[r], sy = uy[r], sz = uz[r];
 #pragma unroll 2
             for (int j = split; j < ne; j += Q) {
                 const float4 z = Z[j];
-                fmm_pc_acc(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]), sx - z.x, sy - z.y, sz - z.z,
+                fmm_pc_acc(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]), u.x - z.x, u.y - z.y, u.z - z.z,
                            eps2, bx, by, bz, bp);
             }
-            ax[r] += bx;
-            ay[r] += by;
-            az[r] += bz;
-            ph[r] += bp;
+            float4 a = A[p * 32 + lane];
+            a.x += bx;
+            a.y += by;
+            a.z += bz;
+            a.w += bp;
+            A[p * 32 + lane] = a;
+            base += S;
         }
         __syncwarp();
     }
-#pragma unroll
-    for (int r = 0; r < PC_RMAX; r++) {
-        if (r >= R) break;
+    // add each pass's Q split sums (lanes l, l ^ S, l ^ 2S, ...) and write the sinks' partials
+    for (int p = 0, base = 0; p < npass; p++) {
+        const int S = pc_pass_slots(nact - base);
+        float4 a = A[p * 32 + lane];
         for (int o = S; o < 32; o <<= 1) {
-            ax[r] += __shfl_xor_sync(FMM_FULL_MASK, ax[r], o);
-            ay[r] += __shfl_xor_sync(FMM_FULL_MASK, ay[r], o);
-            az[r] += __shfl_xor_sync(FMM_FULL_MASK, az[r], o);
-            ph[r] += __shfl_xor_sync(FMM_FULL_MASK, ph[r], o);
+            a.x += __shfl_xor_sync(FMM_FULL_MASK, a.x, o);
+            a.y += __shfl_xor_sync(FMM_FULL_MASK, a.y, o);
+            a.z += __shfl_xor_sync(FMM_FULL_MASK, a.z, o);
+            a.w += __shfl_xor_sync(FMM_FULL_MASK, a.w, o);
         }
-        const int i = slot + r * S;
-        if (split == 0 && i < nact) part[i] = make_float4(ax[r], ay[r], az[r], ph[r]);
+        const int i = base + lane % S;
+        if (lane < S && i < nact) part[i] = a;
+        base += S;
     }
+    __syncwarp();
 }
 
+// Persistent: each warp takes the next PC work item until none is left.
 __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pc,
                                                  const unsigned int* __restrict__ base_pc,
                                                  const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
@@ -332,6 +407,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
     __shared__ int idss[IW][PC_CHUNK];
+    __shared__ float4 Us[IW][PC_PMAX * 32], As[IW][PC_PMAX * 32];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
     const unsigned long long n_items =
@@ -347,15 +423,8 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         const int k = (int)(i - base_pc[gi]);
         const Com4 ck = com[G.cell];
         const int n = cnact[G.cell];  // active sinks of the group
-        int R, Q;
-        if (n <= 8) { R = 1; Q = 4; }
-        else if (n <= 16) { R = 1; Q = 2; }
-        else if (n <= 24) { R = 3; Q = 4; }
-        else if (n <= 32) { R = 1; Q = 1; }
-        else if (n <= 48) { R = 3; Q = 2; }
-        else { R = 2; Q = 1; }
-        pc_item(G, n, act, k, R, Q, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
-                idss[wl], eps2, lane, csize);
+        pc_item(G, n, act, k, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
+                idss[wl], Us[wl], As[wl], eps2, lane, csize);
         if (lane == 0) {
             const int nc = min(csize, G.pc_len - k * csize);
             pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nc;
