@@ -750,5 +750,71 @@ __device__ __forceinline__ void fmm_pc_acc(const float* __restrict__ R, float rx
     az = fmaf(ir2, fmaf(S, qz, ir2 * vz), az);
 }
 
+/* particle-cell for two sinks (FP32x2 lanes): field of the record R at r0 and r1; phip sums -phi */
+__device__ __forceinline__ void fmm_pc_acc2(const float* __restrict__ R, float2 rx, float2 ry, float2 rz,
+                                            float2 eps2, float2& ax, float2& ay, float2& az, float2& phip)
+{
+    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __ffma2_rn(rz, rz, eps2)));
+    const float2 ir = make_float2(fmm_rsqrt(r2.x), fmm_rsqrt(r2.y));
+    const float2 qx = __fmul2_rn(rx, ir), qy = __fmul2_rn(ry, ir), qz = __fmul2_rn(rz, ir);
+    const float2 ir2 = __fmul2_rn(ir, ir);
+    const float2 A3_300 = __ffma2_rn(make_float2(R[19], R[19]), qz, __ffma2_rn(make_float2(R[18], R[18]), qy, __fmul2_rn(make_float2(R[17], R[17]), qx)));
+    const float2 A3_210 = __ffma2_rn(make_float2(R[21], R[21]), qz, __ffma2_rn(make_float2(R[20], R[20]), qy, __fmul2_rn(make_float2(R[18], R[18]), qx)));
+    const float2 A3_201 = __ffma2_rn(make_float2(R[22], R[22]), qz, __ffma2_rn(make_float2(R[21], R[21]), qy, __fmul2_rn(make_float2(R[19], R[19]), qx)));
+    const float2 A3_120 = __ffma2_rn(make_float2(R[24], R[24]), qz, __ffma2_rn(make_float2(R[23], R[23]), qy, __fmul2_rn(make_float2(R[20], R[20]), qx)));
+    const float2 A3_111 = __ffma2_rn(make_float2(R[25], R[25]), qz, __ffma2_rn(make_float2(R[24], R[24]), qy, __fmul2_rn(make_float2(R[21], R[21]), qx)));
+    const float2 A3_102 = __ffma2_rn(make_float2(R[26], R[26]), qz, __ffma2_rn(make_float2(R[25], R[25]), qy, __fmul2_rn(make_float2(R[22], R[22]), qx)));
+    const float2 A3_030 = __ffma2_rn(make_float2(R[28], R[28]), qz, __ffma2_rn(make_float2(R[27], R[27]), qy, __fmul2_rn(make_float2(R[23], R[23]), qx)));
+    const float2 A3_021 = __ffma2_rn(make_float2(R[29], R[29]), qz, __ffma2_rn(make_float2(R[28], R[28]), qy, __fmul2_rn(make_float2(R[24], R[24]), qx)));
+    const float2 A3_012 = __ffma2_rn(make_float2(R[30], R[30]), qz, __ffma2_rn(make_float2(R[29], R[29]), qy, __fmul2_rn(make_float2(R[25], R[25]), qx)));
+    const float2 A3_003 = __ffma2_rn(make_float2(R[31], R[31]), qz, __ffma2_rn(make_float2(R[30], R[30]), qy, __fmul2_rn(make_float2(R[26], R[26]), qx)));
+    const float2 A2_200 = __ffma2_rn(A3_201, qz, __ffma2_rn(A3_210, qy, __fmul2_rn(A3_300, qx)));
+    const float2 A2_110 = __ffma2_rn(A3_111, qz, __ffma2_rn(A3_120, qy, __fmul2_rn(A3_210, qx)));
+    const float2 A2_101 = __ffma2_rn(A3_102, qz, __ffma2_rn(A3_111, qy, __fmul2_rn(A3_201, qx)));
+    const float2 A2_020 = __ffma2_rn(A3_021, qz, __ffma2_rn(A3_030, qy, __fmul2_rn(A3_120, qx)));
+    const float2 A2_011 = __ffma2_rn(A3_012, qz, __ffma2_rn(A3_021, qy, __fmul2_rn(A3_111, qx)));
+    const float2 A2_002 = __ffma2_rn(A3_003, qz, __ffma2_rn(A3_012, qy, __fmul2_rn(A3_102, qx)));
+    const float2 A1_100 = __ffma2_rn(A2_101, qz, __ffma2_rn(A2_110, qy, __fmul2_rn(A2_200, qx)));
+    const float2 A1_010 = __ffma2_rn(A2_011, qz, __ffma2_rn(A2_020, qy, __fmul2_rn(A2_110, qx)));
+    const float2 A1_001 = __ffma2_rn(A2_002, qz, __ffma2_rn(A2_011, qy, __fmul2_rn(A2_101, qx)));
+    const float2 A0_000 = __ffma2_rn(A1_001, qz, __ffma2_rn(A1_010, qy, __fmul2_rn(A1_100, qx)));
+    const float2 B2_200 = __ffma2_rn(make_float2(R[9], R[9]), qz, __ffma2_rn(make_float2(R[8], R[8]), qy, __fmul2_rn(make_float2(R[7], R[7]), qx)));
+    const float2 B2_110 = __ffma2_rn(make_float2(R[11], R[11]), qz, __ffma2_rn(make_float2(R[10], R[10]), qy, __fmul2_rn(make_float2(R[8], R[8]), qx)));
+    const float2 B2_101 = __ffma2_rn(make_float2(R[12], R[12]), qz, __ffma2_rn(make_float2(R[11], R[11]), qy, __fmul2_rn(make_float2(R[9], R[9]), qx)));
+    const float2 B2_020 = __ffma2_rn(make_float2(R[14], R[14]), qz, __ffma2_rn(make_float2(R[13], R[13]), qy, __fmul2_rn(make_float2(R[10], R[10]), qx)));
+    const float2 B2_011 = __ffma2_rn(make_float2(R[15], R[15]), qz, __ffma2_rn(make_float2(R[14], R[14]), qy, __fmul2_rn(make_float2(R[11], R[11]), qx)));
+    const float2 B2_002 = __ffma2_rn(make_float2(R[16], R[16]), qz, __ffma2_rn(make_float2(R[15], R[15]), qy, __fmul2_rn(make_float2(R[12], R[12]), qx)));
+    const float2 B1_100 = __ffma2_rn(B2_101, qz, __ffma2_rn(B2_110, qy, __fmul2_rn(B2_200, qx)));
+    const float2 B1_010 = __ffma2_rn(B2_011, qz, __ffma2_rn(B2_020, qy, __fmul2_rn(B2_110, qx)));
+    const float2 B1_001 = __ffma2_rn(B2_002, qz, __ffma2_rn(B2_011, qy, __fmul2_rn(B2_101, qx)));
+    const float2 B0_000 = __ffma2_rn(B1_001, qz, __ffma2_rn(B1_010, qy, __fmul2_rn(B1_100, qx)));
+    const float2 C1_100 = __ffma2_rn(make_float2(R[3], R[3]), qz, __ffma2_rn(make_float2(R[2], R[2]), qy, __fmul2_rn(make_float2(R[1], R[1]), qx)));
+    const float2 C1_010 = __ffma2_rn(make_float2(R[5], R[5]), qz, __ffma2_rn(make_float2(R[4], R[4]), qy, __fmul2_rn(make_float2(R[2], R[2]), qx)));
+    const float2 C1_001 = __ffma2_rn(make_float2(R[6], R[6]), qz, __ffma2_rn(make_float2(R[5], R[5]), qy, __fmul2_rn(make_float2(R[3], R[3]), qx)));
+    const float2 C0_000 = __ffma2_rn(C1_001, qz, __ffma2_rn(C1_010, qy, __fmul2_rn(C1_100, qx)));
+    const float2 T1_100 = __ffma2_rn(make_float2(R[38], R[38]), qz, __ffma2_rn(make_float2(R[37], R[37]), qy, __fmul2_rn(make_float2(R[36], R[36]), qx)));
+    const float2 T1_010 = __ffma2_rn(make_float2(R[40], R[40]), qz, __ffma2_rn(make_float2(R[39], R[39]), qy, __fmul2_rn(make_float2(R[37], R[37]), qx)));
+    const float2 T1_001 = __ffma2_rn(make_float2(R[41], R[41]), qz, __ffma2_rn(make_float2(R[40], R[40]), qy, __fmul2_rn(make_float2(R[38], R[38]), qx)));
+    const float2 T0_000 = __ffma2_rn(T1_001, qz, __ffma2_rn(T1_010, qy, __fmul2_rn(T1_100, qx)));
+    const float2 U0_000 = __ffma2_rn(make_float2(R[35], R[35]), qz, __ffma2_rn(make_float2(R[34], R[34]), qy, __fmul2_rn(make_float2(R[33], R[33]), qx)));
+    const float2 p2 = __ffma2_rn(make_float2(1.5f, 1.5f), C0_000, make_float2(-0.5f * R[32], -0.5f * R[32]));
+    const float2 p3 = __ffma2_rn(make_float2(2.5f, 2.5f), B0_000, __fmul2_rn(make_float2(-1.5f, -1.5f), U0_000));
+    const float2 p4 = __ffma2_rn(make_float2(4.375f, 4.375f), A0_000, __ffma2_rn(make_float2(-3.75f, -3.75f), T0_000, make_float2(0.375f * R[42], 0.375f * R[42])));
+    const float2 s2 = __ffma2_rn(make_float2(-7.5f, -7.5f), C0_000, make_float2(1.5f * R[32], 1.5f * R[32]));
+    const float2 s3 = __ffma2_rn(make_float2(-17.5f, -17.5f), B0_000, __fmul2_rn(make_float2(7.5f, 7.5f), U0_000));
+    const float2 s4 = __ffma2_rn(make_float2(-39.375f, -39.375f), A0_000, __ffma2_rn(make_float2(26.25f, 26.25f), T0_000, make_float2(-1.875f * R[42], -1.875f * R[42])));
+    const float2 S = __ffma2_rn(ir2, __ffma2_rn(ir, __ffma2_rn(ir, s4, s3), s2), make_float2(-R[0], -R[0]));
+    phip = __ffma2_rn(ir, __ffma2_rn(ir2, __ffma2_rn(ir, __ffma2_rn(ir, p4, p3), p2), make_float2(R[0], R[0])), phip);
+    const float2 wx = __ffma2_rn(make_float2(17.5f, 17.5f), A1_100, __fmul2_rn(make_float2(-7.5f, -7.5f), T1_100));
+    const float2 vx = __ffma2_rn(make_float2(3.0f, 3.0f), C1_100, __fmul2_rn(ir, __ffma2_rn(ir, wx, __ffma2_rn(make_float2(7.5f, 7.5f), B1_100, make_float2(-1.5f * R[33], -1.5f * R[33])))));
+    ax = __ffma2_rn(ir2, __ffma2_rn(S, qx, __fmul2_rn(ir2, vx)), ax);
+    const float2 wy = __ffma2_rn(make_float2(17.5f, 17.5f), A1_010, __fmul2_rn(make_float2(-7.5f, -7.5f), T1_010));
+    const float2 vy = __ffma2_rn(make_float2(3.0f, 3.0f), C1_010, __fmul2_rn(ir, __ffma2_rn(ir, wy, __ffma2_rn(make_float2(7.5f, 7.5f), B1_010, make_float2(-1.5f * R[34], -1.5f * R[34])))));
+    ay = __ffma2_rn(ir2, __ffma2_rn(S, qy, __fmul2_rn(ir2, vy)), ay);
+    const float2 wz = __ffma2_rn(make_float2(17.5f, 17.5f), A1_001, __fmul2_rn(make_float2(-7.5f, -7.5f), T1_001));
+    const float2 vz = __ffma2_rn(make_float2(3.0f, 3.0f), C1_001, __fmul2_rn(ir, __ffma2_rn(ir, wz, __ffma2_rn(make_float2(7.5f, 7.5f), B1_001, make_float2(-1.5f * R[35], -1.5f * R[35])))));
+    az = __ffma2_rn(ir2, __ffma2_rn(S, qz, __fmul2_rn(ir2, vz)), az);
+}
+
 /* FP32 flops of the generated bodies (fmaf = 2): green 300, p2m 94, m2m 344, traces 22, norms 76, m2l 810, p2l 119, l2l 1095, l2p 499, pc 293 */
 #define FMM_FLOPS_PC 293

@@ -400,6 +400,72 @@ def gen_pc():
     return L
 
 
+def gen_pc2():
+    """gen_pc for two sinks at once (FP32x2): the same field of one record at r0 and r1, as
+    float2 lanes.  Record values and constants are shared by both sinks; each multiply-add of the
+    scalar body becomes one __ffma2_rn, so a pair of sinks costs the FP32 instructions of one.
+    The potential is summed with the opposite sign (phip += ..., phi = -phip), so no negation is
+    issued per pair."""
+    f2 = lambda x: f"make_float2({x}, {x})"
+    L = ["/* particle-cell for two sinks (FP32x2 lanes): field of the record R at r0 and r1; phip sums -phi */",
+         "__device__ __forceinline__ void fmm_pc_acc2(const float* __restrict__ R, float2 rx, float2 ry, float2 rz,",
+         "                                            float2 eps2, float2& ax, float2& ay, float2& az, float2& phip)",
+         "{",
+         "    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __ffma2_rn(rz, rz, eps2)));",
+         "    const float2 ir = make_float2(fmm_rsqrt(r2.x), fmm_rsqrt(r2.y));",
+         "    const float2 qx = __fmul2_rn(rx, ir), qy = __fmul2_rn(ry, ir), qz = __fmul2_rn(rz, ir);",
+         "    const float2 ir2 = __fmul2_rn(ir, ir);"]
+    q = ["qx", "qy", "qz"]
+
+    def contract(rank, name, load, scalar):
+        lines, out = [], {}
+        for m in mindices(rank - 1):
+            if sum(m) != rank - 1:
+                continue
+            ops = [load(add(m, E[a])) for a in range(3)]
+            if scalar:
+                ops = [f2(o) for o in ops]
+            v = f"{name}{m[0]}{m[1]}{m[2]}"
+            lines.append(f"    const float2 {v} = __ffma2_rn({ops[2]}, {q[2]}, __ffma2_rn({ops[1]}, {q[1]}, "
+                         f"__fmul2_rn({ops[0]}, {q[0]})));")
+            out[m] = v
+        return lines, out
+
+    rec = lambda n: f"R[{MSLOT[n]}]"
+    l, A3 = contract(4, "A3_", rec, True); L += l
+    l, A2 = contract(3, "A2_", lambda n: A3[n], False); L += l
+    l, A1 = contract(2, "A1_", lambda n: A2[n], False); L += l
+    l, A0 = contract(1, "A0_", lambda n: A1[n], False); L += l
+    l, B2 = contract(3, "B2_", rec, True); L += l
+    l, B1 = contract(2, "B1_", lambda n: B2[n], False); L += l
+    l, B0 = contract(1, "B0_", lambda n: B1[n], False); L += l
+    l, C1 = contract(2, "C1_", rec, True); L += l
+    l, C0 = contract(1, "C0_", lambda n: C1[n], False); L += l
+    l, T1 = contract(2, "T1_", lambda n: f"R[{TR4[n]}]", True); L += l
+    l, T0 = contract(1, "T0_", lambda n: T1[n], False); L += l
+    l, U0 = contract(1, "U0_", lambda n: f"R[{TR3[n.index(1)]}]", True); L += l
+    a0, b0, c0, t0, u0 = A0[(0, 0, 0)], B0[(0, 0, 0)], C0[(0, 0, 0)], T0[(0, 0, 0)], U0[(0, 0, 0)]
+    t2, tt4, M = f"R[{TR2}]", f"R[{TT4}]", "R[0]"
+    L += [
+        f"    const float2 p2 = __ffma2_rn({f2('1.5f')}, {c0}, {f2(f'-0.5f * {t2}')});",
+        f"    const float2 p3 = __ffma2_rn({f2('2.5f')}, {b0}, __fmul2_rn({f2('-1.5f')}, {u0}));",
+        f"    const float2 p4 = __ffma2_rn({f2('4.375f')}, {a0}, __ffma2_rn({f2('-3.75f')}, {t0}, {f2(f'0.375f * {tt4}')}));",
+        f"    const float2 s2 = __ffma2_rn({f2('-7.5f')}, {c0}, {f2(f'1.5f * {t2}')});",
+        f"    const float2 s3 = __ffma2_rn({f2('-17.5f')}, {b0}, __fmul2_rn({f2('7.5f')}, {u0}));",
+        f"    const float2 s4 = __ffma2_rn({f2('-39.375f')}, {a0}, __ffma2_rn({f2('26.25f')}, {t0}, {f2(f'-1.875f * {tt4}')}));",
+        f"    const float2 S = __ffma2_rn(ir2, __ffma2_rn(ir, __ffma2_rn(ir, s4, s3), s2), {f2(f'-{M}')});",
+        f"    phip = __ffma2_rn(ir, __ffma2_rn(ir2, __ffma2_rn(ir, __ffma2_rn(ir, p4, p3), p2), {f2(M)}), phip);",
+    ]
+    for a, c in enumerate("xyz"):
+        m = E[a]
+        L.append(f"    const float2 w{c} = __ffma2_rn({f2('17.5f')}, {A1[m]}, __fmul2_rn({f2('-7.5f')}, {T1[m]}));")
+        L.append(f"    const float2 v{c} = __ffma2_rn({f2('3.0f')}, {C1[m]}, __fmul2_rn(ir, __ffma2_rn(ir, w{c}, "
+                 f"__ffma2_rn({f2('7.5f')}, {B1[m]}, {f2(f'-1.5f * R[{TR3[a]}]')}))));")
+        L.append(f"    a{c} = __ffma2_rn(ir2, __ffma2_rn(S, q{c}, __fmul2_rn(ir2, v{c})), a{c});")
+    L.append("}")
+    return L
+
+
 def count_flops(lines):
     """FP32 flops of generated straight-line code: each binary '*', '+', '-' is 1 flop, fmaf is 2,
     an update 'x += e' / 'x -= e' adds 1; fmm_rsqrt is not counted (special-function unit)."""
@@ -422,7 +488,7 @@ def main():
     parts = {
         "green": gen_green_scaled(), "p2m": gen_p2m(), "m2m": gen_m2m(), "traces": gen_traces(),
         "norms": gen_norms(),
-        "m2l": gen_m2l(), "p2l": gen_p2l(), "l2l": gen_l2l(), "l2p": gen_l2p(), "pc": gen_pc(),
+        "m2l": gen_m2l(), "p2l": gen_p2l(), "l2l": gen_l2l(), "l2p": gen_l2p(), "pc": gen_pc(), "pc2": gen_pc2(),
     }
     out = ["// GENERATED by gen_expansions.py -- do not edit by hand.",
            "// Straight-line FP32 expansion operators for the Plummer-softened Green's function,",
@@ -452,7 +518,7 @@ def main():
     for k, v in parts.items():
         out += v
         out.append("")
-    flops = {k: count_flops(v) for k, v in parts.items()}
+    flops = {k: count_flops(v) for k, v in parts.items() if k != "pc2"}  # pc2: the pc arithmetic, paired
     out.append("/* FP32 flops of the generated bodies (fmaf = 2): " +
                ", ".join(f"{k} {v}" for k, v in flops.items()) + " */")
     out.append(f"#define FMM_FLOPS_PC {flops['pc']}")

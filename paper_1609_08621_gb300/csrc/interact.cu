@@ -22,8 +22,8 @@
 // splits' partial sums are added with warp shuffles.  Groups hold <= g particles (typically
 // 30-64), and a layout with more slots than active sinks idles lanes, so the slot count follows
 // the active count closely: PP uses one or two compile-time layouts in steps of 8 slots up to 48
-// (e.g. 32 + 8 for 40 sinks), each lane holding its sinks in pairs that share FP32x2
-// instructions; PC a runtime sequence of passes of 32, 16, 8 or 4 slots (at most 3 idle).
+// (e.g. 32 + 8 for 40 sinks), PC a runtime sequence of passes of 64, 32, 16 or 8 slots (at most 7
+// idle).  In both, each lane holds its sinks in pairs that share FP32x2 instructions.
 //
 // PP: a_i += m_j (s_j - u_i) / (|s_j - u_i|^2 + eps^2)^(3/2), phi_i -= m_j / (...)^(1/2)
 // over every particle of every PP source, the sink itself included: its force term is
@@ -31,7 +31,8 @@
 // by adding back the identically computed value.  Source particles are staged per warp in
 // shared memory (32 list entries at a time, <= 16 particles each).
 // PC: the order-4 moment record of each source cell evaluated at u_i - z_s
-// (fmm_pc_acc, trace form).  Records of 32 cells are staged per warp in shared memory.
+// (fmm_pc_acc2: the trace form of fmm_pc_acc for two sinks).  Records of 32 cells are staged
+// per warp in shared memory.
 // L2P: the group's order-5 local coefficients evaluated at u_i.
 #include <algorithm>
 
@@ -309,37 +310,42 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pp_pairs, pairs);
 }
 
-// PC sink passes: the group's active sinks [0, n) are covered by passes of S = 32, 16, 8 or 4
-// slots; in a pass lane l holds sink base + l % S and takes every Q-th staged cell (Q = 32 / S,
-// split l / S).  Full passes of 32 first, then the remainder r in passes of 16 (r > 12), 8 (r > 4)
-// or 4, so a group wastes at most 3 slots.
-#define PC_PMAX 4  // passes for n <= 64: 32 + 16 + 8 + 4 at most
+// PC sink passes: the group's active sinks [0, n) are covered by passes of 64, 32, 16 or 8 slots;
+// in a pass of 2S slots (S = 32, 16, 8, 4 lanes per split) lane l holds the sink pair base + l % S
+// and base + l % S + S, evaluated together in FP32x2 lanes, and takes every Q-th staged cell
+// (Q = 32 / S, split l / S).  The remainder r after full passes of 64 goes to passes of 32
+// (r > 24), 16 (r > 8) or 8, so a group idles at most 7 slots.
+#define PC_PMAX 3  // passes for n <= 64: 32 + 16 + 8 at most
 __device__ __forceinline__ int pc_pass_slots(int rem)
 {
-    return rem >= 32 ? 32 : rem > 12 ? 16 : rem > 4 ? 8 : 4;
+    return rem > 56 ? 64 : rem > 24 ? 32 : rem > 8 ? 16 : 8;
 }
 
-// PC for one work item: each pass sweeps every staged chunk of cell records; a lane's sink offset
-// and running sum per pass stay in shared memory (U, A: PC_PMAX x 32 per warp) between chunks, so
-// one copy of the particle-cell body serves every pass.
+// PC for one work item: each pass sweeps every staged chunk of cell records.  The sinks' offsets
+// (U, by slot) and each lane's running sums per pass (A: two float4 per lane and pass) stay in
+// shared memory between chunks, so one copy of the particle-cell body serves every pass.  Cell
+// centres are staged negated and duplicated ({-z, -z} per axis) for the FP32x2 differences.
 __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
                                         const Com4& ck,
                                         const unsigned int* __restrict__ pc, const Com4* __restrict__ com,
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
-                                        float4* __restrict__ part, float4* R4, float4* Z, int* ids, float4* U,
-                                        float4* A, float eps2, int lane, int csize)
+                                        float4* __restrict__ part, float4* R4, float4* Zxy, float2* Zz, int* ids,
+                                        float4* U, float4* A, float eps2, int lane, int csize)
 {
-    int npass = 0;
-    for (int base = 0; base < nact; npass++) {
-        const int S = pc_pass_slots(nact - base);
-        const int i = base + lane % S;
+    for (int i = lane; i < FMM_GMAX; i += 32) {
         float ux = 0.f, uy = 0.f, uz = 0.f, m;
         if (i < nact) load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
-        U[npass * 32 + lane] = make_float4(ux, uy, uz, 0.0f);
-        A[npass * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        base += S;
+        U[i] = make_float4(ux, uy, uz, 0.0f);
     }
+    int npass = 0;
+    for (int base = 0; base < nact; npass++) {
+        A[(npass * 32 + lane) * 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A[(npass * 32 + lane) * 2 + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        base += pc_pass_slots(nact - base);
+    }
+    __syncwarp();
+    const float2 e2 = make_float2(eps2, eps2);
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pc_len);
     for (int cbase = e0; cbase < e1; cbase += PC_CHUNK) {
         const int ne = min(PC_CHUNK, e1 - cbase);
@@ -347,8 +353,10 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
             const unsigned int c = pc[G.pc_off + cbase + lane];
             const Com4 cs = com[c];
             ids[lane] = (int)c;
-            Z[lane] = make_float4(__double2float_rn(cs.x - ck.x), __double2float_rn(cs.y - ck.y),
-                                  __double2float_rn(cs.z - ck.z), 0.0f);
+            const float zx = __double2float_rn(cs.x - ck.x), zy = __double2float_rn(cs.y - ck.y),
+                        zz = __double2float_rn(cs.z - ck.z);
+            Zxy[lane] = make_float4(-zx, -zx, -zy, -zy);
+            Zz[lane] = make_float2(-zz, -zz);
         }
         __syncwarp();
         const int nv = ne * (FMM_NREC / 4);
@@ -358,44 +366,58 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
         }
         __syncwarp();
         for (int p = 0, base = 0; p < npass; p++) {
-            const int S = pc_pass_slots(nact - base), Q = 32 / S, split = lane / S;
-            const float4 u = U[p * 32 + lane];
-            float bx = 0.f, by = 0.f, bz = 0.f, bp = 0.f;
+            const int P2 = pc_pass_slots(nact - base), S = P2 / 2, Q = 32 / S, split = lane / S;
+            const float4 u0 = U[base + lane % S], u1 = U[base + lane % S + S];
+            const float2 ux = make_float2(u0.x, u1.x), uy = make_float2(u0.y, u1.y), uz = make_float2(u0.z, u1.z);
+            float2 bx = make_float2(0.f, 0.f), by = bx, bz = bx, bp = bx;
 #pragma unroll 2
             for (int j = split; j < ne; j += Q) {
-                const float4 z = Z[j];
-                fmm_pc_acc(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]), u.x - z.x, u.y - z.y, u.z - z.z,
-                           eps2, bx, by, bz, bp);
+                const float4 zxy = Zxy[j];
+                const float2 zz = Zz[j];
+                fmm_pc_acc2(reinterpret_cast<const float*>(&R4[j * (FMM_NREC / 4)]),
+                            __fadd2_rn(ux, make_float2(zxy.x, zxy.y)), __fadd2_rn(uy, make_float2(zxy.z, zxy.w)),
+                            __fadd2_rn(uz, zz), e2, bx, by, bz, bp);
             }
-            float4 a = A[p * 32 + lane];
-            a.x += bx;
-            a.y += by;
-            a.z += bz;
-            a.w += bp;
-            A[p * 32 + lane] = a;
-            base += S;
+            float4 a0 = A[(p * 32 + lane) * 2], a1 = A[(p * 32 + lane) * 2 + 1];
+            a0.x += bx.x;
+            a0.y += bx.y;
+            a0.z += by.x;
+            a0.w += by.y;
+            a1.x += bz.x;
+            a1.y += bz.y;
+            a1.z += bp.x;
+            a1.w += bp.y;
+            A[(p * 32 + lane) * 2] = a0;
+            A[(p * 32 + lane) * 2 + 1] = a1;
+            base += P2;
         }
         __syncwarp();
     }
     // add each pass's Q split sums (lanes l, l ^ S, l ^ 2S, ...) and write the sinks' partials
     for (int p = 0, base = 0; p < npass; p++) {
-        const int S = pc_pass_slots(nact - base);
-        float4 a = A[p * 32 + lane];
+        const int P2 = pc_pass_slots(nact - base), S = P2 / 2;
+        float4 a0 = A[(p * 32 + lane) * 2], a1 = A[(p * 32 + lane) * 2 + 1];
         for (int o = S; o < 32; o <<= 1) {
-            a.x += __shfl_xor_sync(FMM_FULL_MASK, a.x, o);
-            a.y += __shfl_xor_sync(FMM_FULL_MASK, a.y, o);
-            a.z += __shfl_xor_sync(FMM_FULL_MASK, a.z, o);
-            a.w += __shfl_xor_sync(FMM_FULL_MASK, a.w, o);
+            a0.x += __shfl_xor_sync(FMM_FULL_MASK, a0.x, o);
+            a0.y += __shfl_xor_sync(FMM_FULL_MASK, a0.y, o);
+            a0.z += __shfl_xor_sync(FMM_FULL_MASK, a0.z, o);
+            a0.w += __shfl_xor_sync(FMM_FULL_MASK, a0.w, o);
+            a1.x += __shfl_xor_sync(FMM_FULL_MASK, a1.x, o);
+            a1.y += __shfl_xor_sync(FMM_FULL_MASK, a1.y, o);
+            a1.z += __shfl_xor_sync(FMM_FULL_MASK, a1.z, o);
+            a1.w += __shfl_xor_sync(FMM_FULL_MASK, a1.w, o);
         }
-        const int i = base + lane % S;
-        if (lane < S && i < nact) part[i] = a;
-        base += S;
+        const int i0 = base + lane % S, i1 = i0 + S;
+        if (lane < S && i0 < nact) part[i0] = make_float4(a0.x, a0.z, a1.x, -a1.z);
+        if (lane < S && i1 < nact) part[i1] = make_float4(a0.y, a0.w, a1.y, -a1.w);
+        base += P2;
     }
     __syncwarp();
 }
 
 // Persistent: each warp takes the next PC work item until none is left.
-__global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pc,
+// at least 4 blocks per SM: up to 128 registers for the paired particle-cell body
+__global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pc,
                                                  const unsigned int* __restrict__ base_pc,
                                                  const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
                                                  const Com4* __restrict__ com, const int* __restrict__ bucket_of,
@@ -406,8 +428,9 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
+    __shared__ float2 Zzs[IW][PC_CHUNK];
     __shared__ int idss[IW][PC_CHUNK];
-    __shared__ float4 Us[IW][PC_PMAX * 32], As[IW][PC_PMAX * 32];
+    __shared__ float4 Us[IW][FMM_GMAX], As[IW][PC_PMAX * 32 * 2];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
     const unsigned long long n_items =
@@ -424,7 +447,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pc(const Group* __restrict__ group
         const Com4 ck = com[G.cell];
         const int n = cnact[G.cell];  // active sinks of the group
         pc_item(G, n, act, k, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
-                idss[wl], Us[wl], As[wl], eps2, lane, csize);
+                Zzs[wl], idss[wl], Us[wl], As[wl], eps2, lane, csize);
         if (lane == 0) {
             const int nc = min(csize, G.pc_len - k * csize);
             pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nc;
