@@ -169,7 +169,7 @@ extern "C" double fmm_flops_per_pc(void) { return (double)FMM_FLOPS_PC; }
 static void free_all(fmm_ctx* c)
 {
     DevTree& t = c->t;
-    void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.off, t.bucket_of,
+    void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off, t.bucket_of,
                   t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
                   t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
                   t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
@@ -271,6 +271,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.sm, cap));
         CK(alloc(&t.sact, cap));
         CK(alloc(&t.posf, cap));
+        CK(alloc(&t.plo, cap));
         CK(alloc(&t.off, cap));
         CK(alloc(&t.accs, cap));
         CK(alloc(&t.act, cap));
@@ -298,6 +299,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
         CK(alloc(&t.bucket_cell, cap));
         CK(alloc(&t.arrive, cap));
         CK(alloc(&t.com, cap));
+        CK(alloc(&t.cen, 2 * cap));
         CK(alloc(&t.clo, 3 * cap));
         CK(alloc(&t.chi, 3 * cap));
         CK(alloc(&t.bmax, cap));

@@ -38,6 +38,16 @@ struct __align__(16) WalkNode {
     int4 d;
 };
 
+// Single-precision difference of two double-precision centres a - b without FP64 instructions
+// (FP64 issues at 1/64 of the FP32 rate on this GPU).  Each centre is held as the float pair
+// h = fl(c), l = fl(c - h), so c = h + l to about 2^-48 |c|, and the difference is formed as
+// (h_a - h_b) + (l_a - l_b): within about one unit in the last place of fl(a - b), the rounded
+// double difference it replaces.
+__device__ __forceinline__ float cen_diff(float ha, float la, float hb, float lb)
+{
+    return __fadd_rn(__fsub_rn(ha, hb), __fsub_rn(la, lb));
+}
+
 // A sink group after the walk.
 struct __align__(16) Group {
     int cell;
@@ -103,6 +113,7 @@ struct DevTree {
     float *sm = nullptr;
     unsigned char *sact = nullptr;
     float4 *posf = nullptr;  // single-precision position for the walk's decisions
+    float4 *plo = nullptr;   // per particle fl(x - fl(x)): with posf the centre pair of cen_diff
     float4 *off = nullptr;   // (x - com_bucket) in single precision, mass
     int *bucket_of = nullptr;
     float4 *accs = nullptr;  // accumulator in sorted order (ax, ay, az, pot)
@@ -117,6 +128,7 @@ struct DevTree {
     int *bucket_cell = nullptr;
     unsigned int *arrive = nullptr;
     Com4 *com = nullptr;      // centre of mass + mass
+    float4 *cen = nullptr;    // per cell [2c] = fl(com), [2c + 1] = fl(com - fl(com)) (cen_diff)
     double *clo = nullptr, *chi = nullptr;  // 3 per cell
     double *bmax = nullptr;
     float *rec = nullptr;        // FMM_NREC per cell

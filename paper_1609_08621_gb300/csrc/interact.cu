@@ -4,12 +4,13 @@
 //
 // All coordinates are single precision offsets from the group's centre of mass c_g
 // (Sec. 3.1: interactions in single precision):
-//   sink     u_i = fl(com_bucket(i) - c_g) + fl(x_i - com_bucket(i))
-//   source   s_j = fl(com_bucket(j) - c_g) + fl(x_j - com_bucket(j))
-//   cell     z_s = fl(com_s - c_g)
-// where the differences of double-precision centres are formed in FP64 and rounded once
-// per bucket or cell (never per interaction: FP64 issue is 1/64 of FP32 on this GPU),
-// and fl(x - com_bucket) is stored per particle by the upward pass.
+//   sink     u_i = d(com_bucket(i), c_g) + fl(x_i - com_bucket(i))
+//   source   s_j = d(com_bucket(j), c_g) + fl(x_j - com_bucket(j))
+//   cell     z_s = d(com_s, c_g)
+// where d(a, b) is the single-precision difference of two double-precision centres, taken from
+// their float pairs (hi, lo) by cen_diff within about one unit in the last place of fl(a - b),
+// without FP64 instructions (FP64 issues at 1/64 of the FP32 rate on this GPU), once per bucket
+// or cell; fl(x - com_bucket) is stored per particle by the upward pass.
 //
 // Work items: each group's PP list is cut into chunks of `chunk` entries and its PC list into
 // chunks of `chunk` cells (list_chunk, default 64); a persistent grid of warps takes items from an atomic
@@ -45,15 +46,16 @@
 #define PC_CHUNK 32
 
 // one sink's offset from the group centre and its mass
-__device__ __forceinline__ void load_sink(int s, const Com4& ck, const int* __restrict__ bucket_of,
-                                          const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+__device__ __forceinline__ void load_sink(int s, const float4& hk, const float4& lk, const int* __restrict__ bucket_of,
+                                          const int* __restrict__ bucket_cell, const float4* __restrict__ cen,
                                           const float4* __restrict__ off, float& ux, float& uy, float& uz, float& m)
 {
-    const Com4 cb = com[bucket_cell[bucket_of[s]]];
+    const int bc = bucket_cell[bucket_of[s]];
+    const float4 hb = cen[2 * bc], lb = cen[2 * bc + 1];
     const float4 o = off[s];
-    ux = __double2float_rn(cb.x - ck.x) + o.x;
-    uy = __double2float_rn(cb.y - ck.y) + o.y;
-    uz = __double2float_rn(cb.z - ck.z) + o.z;
+    ux = __fadd_rn(cen_diff(hb.x, lb.x, hk.x, lk.x), o.x);
+    uy = __fadd_rn(cen_diff(hb.y, lb.y, hk.y, lk.y), o.y);
+    uz = __fadd_rn(cen_diff(hb.z, lb.z, hk.z, lk.z), o.z);
     m = o.w;
 }
 
@@ -103,8 +105,8 @@ struct Sinks {
 
     // sink slot base + slot + r*S of the group is its active particle act[G.first + i], i < nact
     __device__ __forceinline__ void load(const Group& G, int nact, int base, const int* __restrict__ act,
-                                         const Com4& ck, const int* __restrict__ bucket_of,
-                                         const int* __restrict__ bucket_cell, const Com4* __restrict__ com,
+                                         const float4& hk, const float4& lk, const int* __restrict__ bucket_of,
+                                         const int* __restrict__ bucket_cell, const float4* __restrict__ cen,
                                          const float4* __restrict__ off, int lane)
     {
         split = lane / S;
@@ -113,8 +115,8 @@ struct Sinks {
         for (int p = 0; p < P; p++) {
             float ux0 = 0.f, uy0 = 0.f, uz0 = 0.f, ux1 = 0.f, uy1 = 0.f, uz1 = 0.f, m;
             const int i0 = base + slot + 2 * p * S, i1 = i0 + S;
-            if (i0 < nact) load_sink(act[G.first + i0], ck, bucket_of, bucket_cell, com, off, ux0, uy0, uz0, m);
-            if (i1 < nact) load_sink(act[G.first + i1], ck, bucket_of, bucket_cell, com, off, ux1, uy1, uz1, m);
+            if (i0 < nact) load_sink(act[G.first + i0], hk, lk, bucket_of, bucket_cell, cen, off, ux0, uy0, uz0, m);
+            if (i1 < nact) load_sink(act[G.first + i1], hk, lk, bucket_of, bucket_cell, cen, off, ux1, uy1, uz1, m);
             nux[p] = make_float2(-ux0, -ux1);
             nuy[p] = make_float2(-uy0, -uy1);
             nuz[p] = make_float2(-uz0, -uz1);
@@ -188,9 +190,9 @@ struct PPChunk {
 // 24 or 40 sinks takes 16 + 8 or 32 + 8 slots instead of 32 or 48.
 template <int R1, int Q1, int R2, int Q2>
 __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
-                                             const Com4& ck,
+                                             const float4& hk, const float4& lk,
                                              const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
-                                             const int* __restrict__ ccount, const Com4* __restrict__ com,
+                                             const int* __restrict__ ccount, const float4* __restrict__ cen,
                                              const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                              const float4* __restrict__ off, float4* __restrict__ part, float4* T,
                                              PPChunk& E, float eps2, int lane, int csize)
@@ -198,8 +200,8 @@ __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int
     constexpr int B2 = R1 * (32 / Q1);
     Sinks<R1, Q1> K;
     Sinks<(R2 > 0 ? R2 : 2), (R2 > 0 ? Q2 : 1)> K2;
-    K.load(G, nact, 0, act, ck, bucket_of, bucket_cell, com, off, lane);
-    if (R2 > 0) K2.load(G, nact, B2, act, ck, bucket_of, bucket_cell, com, off, lane);
+    K.load(G, nact, 0, act, hk, lk, bucket_of, bucket_cell, cen, off, lane);
+    if (R2 > 0) K2.load(G, nact, B2, act, hk, lk, bucket_of, bucket_cell, cen, off, lane);
     long long nsrc = 0;
     const int e0 = chunk * csize, e1 = min(e0 + csize, G.pp_len);
     for (int base = e0; base < e1; base += 32) {
@@ -218,10 +220,10 @@ __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int
                 cnt = ccount[e];
                 bc = (int)e;
             }
-            const Com4 cb = com[bc];
-            dx = __double2float_rn(cb.x - ck.x);
-            dy = __double2float_rn(cb.y - ck.y);
-            dz = __double2float_rn(cb.z - ck.z);
+            const float4 hb = cen[2 * bc], lb = cen[2 * bc + 1];
+            dx = cen_diff(hb.x, lb.x, hk.x, lk.x);
+            dy = cen_diff(hb.y, lb.y, hk.y, lk.y);
+            dz = cen_diff(hb.z, lb.z, hk.z, lk.z);
         }
         int incl = cnt;
 #pragma unroll
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
                                                  const unsigned int* __restrict__ base_pp,
                                                  const unsigned int* __restrict__ pp, const int* __restrict__ cfirst,
                                                  const int* __restrict__ ccount, const int* __restrict__ cnact,
-                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                                 const float4* __restrict__ cen, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  float4* __restrict__ part_pp, const int* __restrict__ act,
                                                  float eps2, int csize, long long cap_items,
@@ -290,12 +292,12 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
         const unsigned int gi = item_pp[i];
         const Group G = groups[gi];
         const int k = (int)(i - base_pp[gi]);
-        const Com4 ck = com[G.cell];
+        const float4 hk = cen[2 * G.cell], lk = cen[2 * G.cell + 1];
         const int n = cnact[G.cell];  // active sinks of the group
         float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
 #define PP_CALL(R1, Q1, R2, Q2) \
-    pp_item<R1, Q1, R2, Q2>(G, n, act, k, ck, pp, cfirst, ccount, com, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
+    pp_item<R1, Q1, R2, Q2>(G, n, act, k, hk, lk, pp, cfirst, ccount, cen, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
         // sink slots in steps of 8 up to 48 sinks, in pairs per lane
         if (n <= 8) nsrc = PP_CALL(2, 8, 0, 0);
         else if (n <= 16) nsrc = PP_CALL(2, 4, 0, 0);
@@ -326,8 +328,8 @@ __device__ __forceinline__ int pc_pass_slots(int rem)
 // shared memory between chunks, so one copy of the particle-cell body serves every pass.  Cell
 // centres are staged negated and duplicated ({-z, -z} per axis) for the FP32x2 differences.
 __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __restrict__ act, int chunk,
-                                        const Com4& ck,
-                                        const unsigned int* __restrict__ pc, const Com4* __restrict__ com,
+                                        const float4& hk, const float4& lk,
+                                        const unsigned int* __restrict__ pc, const float4* __restrict__ cen,
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
                                         float4* __restrict__ part, float4* R4, float4* Zxy, float2* Zz, int* ids,
@@ -335,7 +337,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
 {
     for (int i = lane; i < FMM_GMAX; i += 32) {
         float ux = 0.f, uy = 0.f, uz = 0.f, m;
-        if (i < nact) load_sink(act[G.first + i], ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
+        if (i < nact) load_sink(act[G.first + i], hk, lk, bucket_of, bucket_cell, cen, off, ux, uy, uz, m);
         U[i] = make_float4(ux, uy, uz, 0.0f);
     }
     int npass = 0;
@@ -351,10 +353,10 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
         const int ne = min(PC_CHUNK, e1 - cbase);
         if (lane < ne) {
             const unsigned int c = pc[G.pc_off + cbase + lane];
-            const Com4 cs = com[c];
+            const float4 hs = cen[2 * c], ls = cen[2 * c + 1];
             ids[lane] = (int)c;
-            const float zx = __double2float_rn(cs.x - ck.x), zy = __double2float_rn(cs.y - ck.y),
-                        zz = __double2float_rn(cs.z - ck.z);
+            const float zx = cen_diff(hs.x, ls.x, hk.x, lk.x), zy = cen_diff(hs.y, ls.y, hk.y, lk.y),
+                        zz = cen_diff(hs.z, ls.z, hk.z, lk.z);
             Zxy[lane] = make_float4(-zx, -zx, -zy, -zy);
             Zz[lane] = make_float2(-zz, -zz);
         }
@@ -420,7 +422,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
 __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ groups, const unsigned int* __restrict__ item_pc,
                                                  const unsigned int* __restrict__ base_pc,
                                                  const unsigned int* __restrict__ pc, const int* __restrict__ cnact,
-                                                 const Com4* __restrict__ com, const int* __restrict__ bucket_of,
+                                                 const float4* __restrict__ cen, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  const float* __restrict__ rec, float4* __restrict__ part_pc,
                                                  const int* __restrict__ act, float eps2, int csize, long long cap_items,
@@ -444,9 +446,9 @@ __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ gr
         const unsigned int gi = item_pc[i];
         const Group G = groups[gi];
         const int k = (int)(i - base_pc[gi]);
-        const Com4 ck = com[G.cell];
+        const float4 hk = cen[2 * G.cell], lk = cen[2 * G.cell + 1];
         const int n = cnact[G.cell];  // active sinks of the group
-        pc_item(G, n, act, k, ck, pc, com, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
+        pc_item(G, n, act, k, hk, lk, pc, cen, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
                 Zzs[wl], idss[wl], Us[wl], As[wl], eps2, lane, csize);
         if (lane == 0) {
             const int nc = min(csize, G.pc_len - k * csize);
@@ -463,7 +465,7 @@ template <typename T>
 __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ groups,
                                                       const unsigned long long* __restrict__ ngroups_dev, long long cap_groups,
                                                       long long cap_item_pp, long long cap_item_pc,
-                                                      const Com4* __restrict__ com,
+                                                      const float4* __restrict__ cen,
                                                       const int* __restrict__ bucket_of,
                                                       const int* __restrict__ bucket_cell,
                                                       const float4* __restrict__ off, const float* __restrict__ Lg,
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
     const long long n_groups = (long long)min(*ngroups_dev, (unsigned long long)cap_groups);
     for (long long gi = gw; gi < n_groups; gi += nw) {
         const Group G = groups[gi];
-        const Com4 ck = com[G.cell];
+        const float4 hk = cen[2 * G.cell], lk = cen[2 * G.cell + 1];
         for (int i = lane; i < FMM_NL; i += 32) Ls[wl][i] = Lg[gi * FMM_NL + i];
         __syncwarp();
         // items beyond the buffers (an overflow the host then repairs) are skipped
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
             }
             if (terms & 4) {
                 float ux, uy, uz, m;
-                load_sink(s, ck, bucket_of, bucket_cell, com, off, ux, uy, uz, m);
+                load_sink(s, hk, lk, bucket_of, bucket_cell, cen, off, ux, uy, uz, m);
                 float lx = 0.f, ly = 0.f, lz = 0.f, lw = 0.f;
                 fmm_l2p_acc(Ls[wl], ux, uy, uz, lx, ly, lz, lw);
                 ax += lx;
@@ -635,7 +637,7 @@ cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_pp);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
-    k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.com,
+    k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.cen,
                                      t.bucket_of, t.bucket_cell, t.off, w.part_pp, t.act, a.eps2, a.chunk, w.cap_item_pp, ctr);
     return cudaGetLastError();
 }
@@ -646,7 +648,7 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     static int blocks = 0;
     if (!blocks) blocks = persistent_blocks(k_pc);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
-    k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.com, t.bucket_of,
+    k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.cen, t.bucket_of,
                                      t.bucket_cell, t.off, t.rec, w.part_pc, t.act, a.eps2, a.chunk, w.cap_item_pc, ctr);
     return cudaGetLastError();
 }
@@ -657,12 +659,12 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
     const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     if (a.accumulate == 1)
         k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
-            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
+            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
             a.terms);
     else
         k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
-            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.com, t.bucket_of, t.bucket_cell,
+            w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
             a.terms);
     return cudaGetLastError();

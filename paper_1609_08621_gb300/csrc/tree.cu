@@ -54,7 +54,7 @@ __global__ void k_gather(const double* __restrict__ pos, const float* __restrict
                          const unsigned char* __restrict__ active, long long n, const unsigned int* __restrict__ idx,
                          double* __restrict__ sx, double* __restrict__ sy, double* __restrict__ sz,
                          float* __restrict__ sm, unsigned char* __restrict__ sact, float4* __restrict__ posf,
-                         unsigned long long* __restrict__ n_active)
+                         float4* __restrict__ plo, unsigned long long* __restrict__ n_active)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
@@ -68,7 +68,10 @@ __global__ void k_gather(const double* __restrict__ pos, const float* __restrict
         sm[i] = m;
         act = active ? (active[p] != 0) : true;
         sact[i] = act ? 1 : 0;
-        posf[i] = make_float4(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z), m);
+        const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
+        posf[i] = make_float4(hx, hy, hz, m);
+        plo[i] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
+                             __double2float_rn(z - (double)hz), 0.0f);
     }
     unsigned int b = __ballot_sync(FMM_FULL_MASK, act);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, (unsigned long long)__popc(b));
@@ -78,7 +81,7 @@ cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, 
                               long long n, DevCounters* ctr, cudaStream_t s)
 {
     k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, mass, active, n, t.idx, t.sx, t.sy, t.sz, t.sm,
-                                                           t.sact, t.posf, &ctr->n_active);
+                                                           t.sact, t.posf, t.plo, &ctr->n_active);
     return cudaGetLastError();
 }
 
@@ -527,7 +530,7 @@ __global__ void k_nodes(const unsigned int* __restrict__ ncell, float theta, con
                         const int* __restrict__ ccount,
                         const int* __restrict__ cchild, const Com4* __restrict__ com, const double* __restrict__ clo,
                         const double* __restrict__ chi, const double* __restrict__ bmax, const float* __restrict__ rec,
-                        WalkNode* __restrict__ node, float4* __restrict__ mnorm)
+                        WalkNode* __restrict__ node, float4* __restrict__ mnorm, float4* __restrict__ cen)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (int)*ncell) return;
@@ -536,7 +539,11 @@ __global__ void k_nodes(const unsigned int* __restrict__ ncell, float theta, con
     int cnt = ccount[c];
     float ro = (cnt == 1) ? 0.0f : __fdiv_rn(bm, theta);
     WalkNode w;
-    w.a = make_float4(__double2float_rn(cm.x), __double2float_rn(cm.y), __double2float_rn(cm.z), ro);
+    const float hx = __double2float_rn(cm.x), hy = __double2float_rn(cm.y), hz = __double2float_rn(cm.z);
+    w.a = make_float4(hx, hy, hz, ro);
+    cen[2 * c] = make_float4(hx, hy, hz, 0.0f);
+    cen[2 * c + 1] = make_float4(__double2float_rn(cm.x - (double)hx), __double2float_rn(cm.y - (double)hy),
+                                 __double2float_rn(cm.z - (double)hz), 0.0f);
     w.b = make_float4(__double2float_rn(clo[3 * c]), __double2float_rn(clo[3 * c + 1]),
                       __double2float_rn(clo[3 * c + 2]), bm);
     w.c = make_float4(__double2float_rn(chi[3 * c]), __double2float_rn(chi[3 * c + 1]),
@@ -560,7 +567,8 @@ cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s)
 {
     const long long nc = grid_cells(t);
     k_nodes<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.dcount, (float)theta, t.cfirst, t.ccount, t.cchild,
-                                                          t.com, t.clo, t.chi, t.bmax, t.rec, t.node, t.mnorm);
+                                                          t.com, t.clo, t.chi, t.bmax, t.rec, t.node, t.mnorm,
+                                                          t.cen);
     return cudaGetLastError();
 }
 

@@ -315,24 +315,26 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
 // list lies in the flat array or which warp took it.
 #define LF_ENTRIES FMM_LOCAL_RANGE
 
-__device__ __forceinline__ void local_entry(unsigned int e, const Com4& ck, const int* __restrict__ ccount,
-                                            const Com4* __restrict__ com, const double* __restrict__ sx,
-                                            const double* __restrict__ sy, const double* __restrict__ sz,
-                                            const float* __restrict__ sm, const float* __restrict__ rec, float eps2,
-                                            float* acc, int& ncc, int& ncp)
+// Centres enter as float pairs (cen_diff): the sink's (hk, lk), a cell's from cen, a particle's
+// from posf (hi, and its mass) and plo (lo).
+__device__ __forceinline__ void local_entry(unsigned int e, const float4& hk, const float4& lk,
+                                            const int* __restrict__ ccount, const float4* __restrict__ cen,
+                                            const float4* __restrict__ posf, const float4* __restrict__ plo,
+                                            const float* __restrict__ rec, float eps2, float* acc, int& ncc, int& ncp)
 {
     if (e & FMM_PARTICLE_BIT) {
         const unsigned int j = e & ~FMM_PARTICLE_BIT;
-        fmm_p2l_acc(sm[j], __double2float_rn(ck.x - sx[j]), __double2float_rn(ck.y - sy[j]),
-                    __double2float_rn(ck.z - sz[j]), eps2, acc);
+        const float4 hs = posf[j], ls = plo[j];
+        fmm_p2l_acc(hs.w, cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
+                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
         ncp++;
-    } else if (ccount[e] == 1) {  // a one-particle cell: its particle -> local expansion
-        const Com4 cs = com[e];
-        fmm_p2l_acc((float)cs.w, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y),
-                    __double2float_rn(ck.z - cs.z), eps2, acc);
+    } else if (ccount[e] == 1) {  // a one-particle cell: its particle (mass = moment M[0]) -> local expansion
+        const float4 hs = cen[2 * e], ls = cen[2 * e + 1];
+        fmm_p2l_acc(rec[(long long)e * FMM_NREC], cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
+                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
         ncp++;
     } else {
-        const Com4 cs = com[e];
+        const float4 hs = cen[2 * e], ls = cen[2 * e + 1];
         float M[FMM_NMOM];
         const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)e * FMM_NREC);
 #pragma unroll
@@ -343,8 +345,8 @@ __device__ __forceinline__ void local_entry(unsigned int e, const Com4& ck, cons
             M[4 * q + 2] = v.z;
             M[4 * q + 3] = v.w;
         }
-        fmm_m2l_acc(M, __double2float_rn(ck.x - cs.x), __double2float_rn(ck.y - cs.y), __double2float_rn(ck.z - cs.z),
-                    eps2, acc);
+        fmm_m2l_acc(M, cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
+                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
         ncc++;
     }
 }
@@ -362,9 +364,9 @@ __device__ __forceinline__ long long local_boundary(long long p, long long total
 
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
-    const int* __restrict__ lcc_len, const int* __restrict__ ccount, const Com4* __restrict__ com,
-    const double* __restrict__ sx, const double* __restrict__ sy, const double* __restrict__ sz,
-    const float* __restrict__ sm, const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
+    const int* __restrict__ lcc_len, const int* __restrict__ ccount, const float4* __restrict__ cen,
+    const float4* __restrict__ posf, const float4* __restrict__ plo,
+    const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
     float eps2, DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
             for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
             if (valid) {
                 sink = cc_sink[idx];
-                local_entry(cc[idx], com[sink], ccount, com, sx, sy, sz, sm, rec, eps2, acc, ncc, ncp);
+                local_entry(cc[idx], cen[2 * sink], cen[2 * sink + 1], ccount, cen, posf, plo, rec, eps2, acc, ncc, ncp);
             }
 #pragma unroll
             for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
@@ -556,8 +558,8 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s)
 {
     const int blocks = w.n_warps / LOCAL_WPB;
-    k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.com, t.sx, t.sy,
-                                                   t.sz, t.sm, t.rec, t.L, w.cap_cc, eps2, ctr);
+    k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.cen, t.posf,
+                                                   t.plo, t.rec, t.L, w.cap_cc, eps2, ctr);
     k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, ctr);
     return cudaGetLastError();
 }
