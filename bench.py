@@ -44,7 +44,7 @@ PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul,
 # buckets of 16, groups of 64 and work items of 128 list entries, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_pc_k_pp_nfw2m.md).  Reported only for
 # runs with those settings; set back to None whenever a kernel changes after that capture.
-NCU_TRAFFIC = None
+NCU_TRAFFIC = {"k_pc": 255633664, "k_pp": 121505280}
 NCU_TRAFFIC_PARAMS = (16, 64, 128)
 
 
