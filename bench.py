@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--params", default=None, help="bucket,group,list_chunk instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
+    ap.add_argument("--dual", type=int, default=None,
+                    help="rungs16m: fixed rung of the dual-tree scheme (rungs <= it form the fixed tree)")
     ap.add_argument("--n", type=int, default=None,
                     help="particle count override (profiling a smaller box of the same structure)")
     return ap.parse_args()
@@ -361,12 +363,37 @@ class Rungs:
         self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc))
         ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
         self.active_frac = []
+        # dual trees (Sec. 3.2): inside each interval of 2^(R - dual) substeps only rungs > dual are
+        # active; the particles of rungs <= dual are drifted to the interval's middle once and kept
+        # in a fixed tree, and each inner substep solves the active particles against both trees
+        self.dual = args.dual
+        self.fixed_interval = None
+        self.extra_launches = 0
+        if self.dual is not None:
+            if not 0 <= self.dual < self.R:
+                raise SystemExit(f"--dual must be in [0, {self.R - 1}]")
+            self.config["dual_fixed_rung"] = self.dual
+            self.config["dual_interval_substeps"] = 1 << (self.R - self.dual)
 
     def step(self, k):
         s = k % (1 << self.R)
         self.ctx.kick_drift(self.tpos, self.vel, self.acc, self.rung, self.act, self.eps, self.dt0, self.R, s,
                             1 if k > 0 else 0)
-        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
+        if self.dual is None:
+            self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
+            return
+        m = 1 << (self.R - self.dual)
+        t = k + 1  # the substep whose forces are solved (positions are there after the drift)
+        j = t % m
+        if j == 0:  # interval boundary: the slow rungs are active too
+            self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
+            return
+        if self.fixed_interval != t // m:
+            h = self.dt0 / (1 << self.R)
+            self.ctx.set_fixed_sources(self.tpos, self.tmass, self.rung, self.dual, self.vel, (0.5 * m - j) * h)
+            self.extra_launches += self.ctx.stats()["n_launches"]
+            self.fixed_interval = t // m
+        self.ctx.compute_forces_dual(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
 
     def e2e(self, steps):
         return None
@@ -567,6 +594,7 @@ def main():
     flops = {"pp": 0.0, "pc": 0.0}
     inter = []
     launches = 0
+    retries = 0
     active = []
     # workloads smaller than L2 get L2 flushed (a 256 MB write, outside the step's events) before
     # every step; larger ones rebuild a tree bigger than L2 each step
@@ -589,8 +617,11 @@ def main():
         flops["pp"] += st["kernel_flops_pp"]
         flops["pc"] += st["kernel_flops_pc"]
         inter.append(st["n_pp_pairs"] + st["n_pc_pairs"])
+        retries += st["retries"]
         active.append(st["n_active"])
-        launches += st["n_launches"] + (1 if args.workload != "batch64" else 0)
+        launches += st["n_launches"] + (1 if args.workload != "batch64" else 0) + getattr(wl, "extra_launches", 0)
+        if hasattr(wl, "extra_launches"):
+            wl.extra_launches = 0
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -621,7 +652,8 @@ def main():
             "config": wl.config, "phase_ms": {k: v / args.steps for k, v in kt.items()},
             "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
             "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
-            "active_per_step": float(np.mean(active)), "roofline": roof, "clocks": ck, "gpu_launches": launches}
+            "active_per_step": float(np.mean(active)), "walk_retries": retries, "roofline": roof, "clocks": ck,
+            "gpu_launches": launches}
     if hasattr(wl, "learned"):
         line["learned"] = wl.learned
     if not args.no_e2e:

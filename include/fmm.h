@@ -247,6 +247,42 @@ fmm_status fmm_kick_drift(fmm_ctx *ctx, double *pos, double *vel, const float *a
 fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung, long long n, double eps,
                             double dt0, int max_rung);
 
+/* ---------------- dual trees for multiple time steps (Sec. 3.2) ----------------
+ * On the substeps between two kicks of the slower rungs only the fast rungs need forces.  The
+ * particles of rungs <= r_fixed are not kicked there, so they move on straight lines; they are
+ * drifted to the middle of the interval once and a "fixed" tree of them is kept, and each
+ * substep builds a tree of the active particles only and walks it against both trees.  Both
+ * trees are radix trees over Morton keys of the same unit box, so their cells are the same
+ * dyadic boxes (the shared geometric structure the method asks for). */
+
+/* Build and keep the fixed tree: the particles i with rung[i] <= r_fixed (every particle when
+ * rung is NULL), at positions pos_i + vel_i * dt (FP64; pos_i when vel is NULL).  Which particles
+ * of the n are fixed is kept for the dual solves, which must pass the same n.
+ *   pos, vel  device, 3N doubles SoA (vel may be NULL); the drifted positions must lie in [0,1)
+ *   mass      device, N floats;  rung  device, N bytes or NULL
+ *   dt        the drift to the middle of the interval (finite)
+ * The tree uses the context's bucket size, which later dual solves must keep (FMM_ERR_ARG
+ * otherwise).  It replaces any earlier fixed tree; zero selected particles give an empty one.
+ * Uses the context's tree buffers (an earlier solve's exports are gone); afterwards fmm_get_stats
+ * reports the fixed tree's particles, cells, buckets and this call's kernel launches.  Synchronous. */
+fmm_status fmm_set_fixed_sources(fmm_ctx *ctx, const double *pos, const double *vel, const float *mass,
+                                 const unsigned char *rung, long long n, int r_fixed, double dt);
+
+/* Force solve on a substep inside the fixed tree's interval.  Every particle outside the fixed
+ * set (the fast rungs) goes into an active tree at its current position, built on each call; the
+ * fixed tree is appended to it and the walk starts with both roots on the checklist.  The sinks
+ * are the particles marked in active.
+ *   pos, mass  device, the caller's full arrays (3N doubles SoA, N floats), N as given to
+ *              fmm_set_fixed_sources (FMM_ERR_ARG otherwise)
+ *   active     device, N bytes: the sinks, particles outside the fixed set (NULL: all of them);
+ *              flags on fixed particles are ignored (they are not kicked inside the interval)
+ *   acc, pot   device, 3N / N floats (pot may be NULL): written for the sinks only
+ * Criterion 0 only (FMM_ERR_ARG otherwise); FMM_ERR_STATE when no fixed tree was set.  With no
+ * particle outside the fixed set nothing is written.  Statistics via fmm_get_stats (cells and
+ * buckets count both trees).  Synchronous; no CUDA graph. */
+fmm_status fmm_compute_forces_dual(fmm_ctx *ctx, const double *pos, const float *mass, const unsigned char *active,
+                                   long long n, double eps, double theta, float *acc, float *pot);
+
 /* ---------------- learned opening criterion (not in the paper; criterion = 1) ----------------
  * The network x (8) -> 64 -> 64 -> 64 -> 1 (ReLU) predicts log10 of the relative force error of
  * accepting a (sink cell, source cell) pair as a cell-cell interaction, from the features

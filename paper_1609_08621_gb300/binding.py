@@ -20,6 +20,7 @@ from . import build as _build
 FMM_OK = 0
 STATUS = {0: "FMM_OK", -1: "FMM_ERR_ARG", -2: "FMM_ERR_OOM", -3: "FMM_ERR_CUDA", -4: "FMM_ERR_TIMEOUT",
           -5: "FMM_ERR_STATE", -6: "FMM_ERR_NUMERIC"}
+FMM_OK, FMM_ERR_ARG, FMM_ERR_OOM, FMM_ERR_CUDA, FMM_ERR_TIMEOUT, FMM_ERR_STATE, FMM_ERR_NUMERIC = 0, -1, -2, -3, -4, -5, -6
 KIND = {"pp": 0, "pc": 1, "cc": 2, "cp": 3}
 
 
@@ -79,6 +80,8 @@ def load(build_if_missing: bool = True):
         "fmm_compute_forces_batch": (i, [vp, vp, vp, vp, ll, vp, i, d, d, vp, vp]),
         "fmm_kick_drift": (i, [vp, vp, vp, vp, vp, vp, ll, d, d, i, i, i]),
         "fmm_assign_rungs": (i, [vp, vp, vp, ll, d, d, i]),
+        "fmm_set_fixed_sources": (i, [vp, vp, vp, vp, vp, ll, i, d]),
+        "fmm_compute_forces_dual": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
         "fmm_get_stats": (i, [vp, C.POINTER(fmm_stats)]),
         "fmm_last_error": (C.c_char_p, []),
         "fmm_flops_per_pc": (d, []),
@@ -303,6 +306,30 @@ class Context:
                                      _ptr(rung, torch.uint8, n, "rung"),
                                      _ptr(active_next, torch.uint8, n, "active_next"), n, float(eps), float(dt0),
                                      int(max_rung), int(substep), int(closing)))
+
+    def set_fixed_sources(self, pos, mass, rung=None, r_fixed=0, vel=None, dt=0.0):
+        """Fixed tree of the dual-tree scheme: the particles with rung <= r_fixed (all when rung is
+        None) at pos + vel * dt (pos when vel is None).  CUDA tensors of the full particle set."""
+        import torch
+
+        n = mass.numel()
+        _check(load().fmm_set_fixed_sources(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                            _ptr(vel, torch.float64, 3 * n, "vel", True),
+                                            _ptr(mass, torch.float32, n, "mass"),
+                                            _ptr(rung, torch.uint8, n, "rung", True), n, int(r_fixed), float(dt)))
+
+    def compute_forces_dual(self, pos, mass, eps, theta, acc, pot=None, active=None):
+        """Forces on the sinks in active (every particle outside the fixed set when None) from all
+        particles: the fixed set as kept by set_fixed_sources, the others at pos.  acc/pot are
+        written for the sinks only; n must be the fixed set's."""
+        import torch
+
+        n = mass.numel()
+        _check(load().fmm_compute_forces_dual(self.h, _ptr(pos, torch.float64, 3 * n, "pos"),
+                                              _ptr(mass, torch.float32, n, "mass"),
+                                              _ptr(active, torch.uint8, n, "active", True), n, float(eps),
+                                              float(theta), _ptr(acc, torch.float32, 3 * n, "acc"),
+                                              _ptr(pot, torch.float32, n, "pot", True)))
 
     def assign_rungs(self, acc, rung, eps, dt0, max_rung):
         import torch

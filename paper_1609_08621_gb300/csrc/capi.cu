@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -92,6 +93,15 @@ struct fmm_ctx {
     bool have_tree = false, have_solve = false;
     int launches = 0;  // kernels launched by the current solve
     float theta_nodes = -1.0f;
+    // dual trees: the fixed tree, the subset scratch (flags, their scan, subset -> caller index,
+    // the subset's positions and masses, the composed output order) and the walk's second root
+    FixedTree fx;
+    unsigned int *d_flag = nullptr, *d_at = nullptr, *d_idx = nullptr, *d_perm = nullptr;
+    unsigned char* d_act = nullptr;
+    double* d_pos = nullptr;
+    float* d_mass = nullptr;
+    long long cap_d = 0;
+    int second_root = -1;
     // learned criterion: FP32 master parameters, Adam state, packed BF16 copy
     float *mlp_p = nullptr, *mlp_g = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_loss = nullptr;
     unsigned char* mlp_packed = nullptr;
@@ -116,6 +126,7 @@ struct fmm_ctx {
         double eps, theta;
     } gkey;
     int graph_levels = 0, graph_launches = 0;
+    std::vector<void*> graph_bufs;  // the context's buffer addresses when the graph was captured
     long long graph_replays = 0;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
@@ -166,19 +177,28 @@ extern "C" const char* fmm_last_error(void) { return g_err.c_str(); }
 
 extern "C" double fmm_flops_per_pc(void) { return (double)FMM_FLOPS_PC; }
 
+// The device buffers of the tree, the walk, the fixed tree and the subset scratch.
+static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
+{
+    const DevTree& t = c->t;
+    const DevWalk& w = c->w;
+    const FixedTree& f = c->fx;
+    return {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
+            t.bucket_of, t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
+            t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
+            t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
+            t.hist, t.box_off, t.box_root, t.sbox, t.key_orig,
+            w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
+            w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
+            w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch,
+            f.cfirst, f.ccount, f.cchild, f.cparent, f.bucket_cell, f.com, f.clo, f.chi, f.bmax, f.rec, f.posf, f.plo,
+            f.off, f.bucket_of, f.member, c->d_flag, c->d_at, c->d_idx, c->d_perm, c->d_act, c->d_pos, c->d_mass};
+}
+
 static void free_all(fmm_ctx* c)
 {
     DevTree& t = c->t;
-    void* ps[] = {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off, t.bucket_of,
-                  t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst, t.ccount,
-                  t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec, t.node,
-                  t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part, t.hist, t.box_off, t.box_root, t.sbox, t.key_orig};
-    for (void* p : ps)
-        if (p) cudaFree(p);
-    DevWalk& w = c->w;
-    void* qs[] = {w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off,
-                  w.lcc_len, w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc, w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch};
-    for (void* p : qs)
+    for (void* p : tree_walk_buffers(c))
         if (p) cudaFree(p);
     if (c->ctr) cudaFree(c->ctr);
     if (c->totals) cudaFree(c->totals);
@@ -532,7 +552,7 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
         // cells above a box's root are never walked: their local lists must read as empty
         CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.n_cells, s));
         CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
-        CK(fmm_launch_walk_seed(t, w, c->ctr, s));
+        CK(fmm_launch_walk_seed(t, w, c->ctr, s, c->second_root));
         c->launches += 1;
         for (int L = 0; L < levels; L++) {
             a.level = L;
@@ -562,6 +582,8 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
 }
 
 static fmm_status finish_stats(fmm_ctx* c, long long n);
+static fmm_status interact_and_finish(fmm_ctx* c, const fmm_params& q, double eps, float* acc, float* pot,
+                                      long long n_out, long long n_stats, const unsigned int* perm);
 
 static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active, long long n,
                         double eps, double theta, float* acc, float* pot, const long long* box_off = nullptr,
@@ -592,6 +614,17 @@ static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, 
     }
     st = run_walk(c, n, eps, q.bucket, q.group, q.criterion);
     if (st != FMM_OK) return st;
+    return interact_and_finish(c, q, eps, acc, pot, n, n, nullptr);
+}
+
+// After the walk: work items, PP, PC, and the sums plus local expansion written to acc/pot
+// (n_out particles long, in the order perm gives; NULL: the tree's own order); then the counters
+// and timing events are read back.
+static fmm_status interact_and_finish(fmm_ctx* c, const fmm_params& q, double eps, float* acc, float* pot,
+                                      long long n_out, long long n_stats, const unsigned int* perm)
+{
+    cudaStream_t s = c->stream;
+    fmm_status st;
     CK(cudaEventRecord(c->ev[2], s));
     InteractArgs ia;
     ia.eps2 = (float)(eps * eps);
@@ -619,7 +652,7 @@ static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, 
         CK(cudaEventRecord(c->ev[3], s));
         CK(fmm_launch_pc(c->t, c->w, c->ctr, ia, s));
         CK(cudaEventRecord(c->ev[4], s));
-        CK(fmm_launch_l2p_out(c->t, c->w, c->ctr, ia, acc, pot, n, s));
+        CK(fmm_launch_l2p_out(c->t, c->w, c->ctr, ia, acc, pot, n_out, s, perm));
         c->launches += ((q.terms & 1) ? 1 : 0) + ((q.terms & 2) ? 1 : 0) + 1;
     } else {
         CK(cudaEventRecord(c->ev[3], s));
@@ -630,7 +663,7 @@ static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, 
     CK(cudaStreamSynchronize(s));
     st = read_status(c, "fmm_compute_forces");
     if (st != FMM_OK) return st;
-    return finish_stats(c, n);
+    return finish_stats(c, n_stats);
 }
 
 static fmm_status finish_stats(fmm_ctx* c, long long n)
@@ -844,6 +877,7 @@ static void capture_graph(fmm_ctx* c, const fmm_ctx::GraphKey& key, const double
     if (cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
         c->gexec = ge;
         c->gkey = key;
+        c->graph_bufs = tree_walk_buffers(c);
     }
     cudaGraphDestroy(g);
     cudaGetLastError();
@@ -903,7 +937,9 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     st = set_boxes_check(n, box_off, nbox);
     if (st != FMM_OK) return st;
     const fmm_ctx::GraphKey key = make_key(pos, mass, active, acc, pot, n, box_off, nbox, q, eps, theta);
-    if (c->gexec && same_key(c->gkey, key)) {
+    // a graph holds the addresses of the context's buffers it was captured with: it replays only while
+    // none of them was reallocated since (another call may have grown them)
+    if (c->gexec && same_key(c->gkey, key) && c->graph_bufs == tree_walk_buffers(c)) {
         c->have_solve = false;
         int outcome = GRAPH_RETRY;
         st = replay_graph(c, n, &outcome);
@@ -1015,6 +1051,193 @@ extern "C" fmm_status fmm_autotune(fmm_ctx* c, const double* pos, const float* m
     if (best) *best = best_p;
     if (best_ms) *best_ms = best_t;
     return FMM_OK;
+}
+
+// ---------------------------------------------------------------- dual trees (Sec. 3.2)
+
+static fmm_status ensure_subset(fmm_ctx* c, long long n)
+{
+    if (n <= c->cap_d) return FMM_OK;
+    CK(alloc(&c->d_flag, n));
+    CK(alloc(&c->d_at, n));
+    CK(alloc(&c->d_idx, n));
+    CK(alloc(&c->d_perm, n));
+    CK(alloc(&c->d_act, n));
+    CK(alloc(&c->d_pos, 3 * n));
+    CK(alloc(&c->d_mass, n));
+    c->cap_d = n;
+    return FMM_OK;
+}
+
+// The particles with rung[i] <= r_max (with rungs), or outside the set flagged in flag_not (with
+// that array), or all, in input order, into d_pos (SoA, drifted by vel * dt when vel is given),
+// d_mass, d_idx (the caller's index) and, when sinks is given, d_act (their sink flags); *m is
+// their count.
+static fmm_status select_subset(fmm_ctx* c, const double* pos, const double* vel, double dt, const float* mass,
+                                const unsigned char* rung, int r_max, const unsigned int* flag_not,
+                                const unsigned char* sinks, long long n, long long* m)
+{
+    cudaStream_t s = c->stream;
+    fmm_status st = ensure_subset(c, n);
+    if (st != FMM_OK) return st;
+    CK(fmm_launch_subset_flags(rung, r_max, flag_not, n, c->d_flag, s));
+    CK(fmm_scan_exclusive(c->d_flag, c->d_at, n, c->totals + 2, c->t, s));
+    CK(cudaMemcpyAsync(c->totals_h + 2, c->totals + 2, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *m = (long long)c->totals_h[2];
+    c->launches += 4;
+    if (*m > 0) {
+        CK(fmm_launch_subset_gather(c->d_flag, c->d_at, n, pos, vel, dt, mass, sinks, *m, c->d_pos, c->d_mass, c->d_act,
+                                    c->d_idx, s));
+        c->launches += 1;
+    }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const double* vel, const float* mass,
+                                            const unsigned char* rung, long long n, int r_fixed, double dt)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!std::isfinite(dt)) return fail(FMM_ERR_ARG, "fmm_set_fixed_sources: dt must be finite");
+    st = check_params(&c->params);
+    if (st != FMM_OK) return st;
+    FixedTree& f = c->fx;
+    f.valid = false;
+    c->have_solve = false;
+    c->launches = 0;
+    long long m = 0;
+    st = select_subset(c, pos, vel, dt, mass, rung, r_fixed, nullptr, nullptr, n, &m);
+    if (st != FMM_OK) return st;
+    // membership of the fixed set, in the caller's order, for the dual solves
+    if (n > f.cap_member) {
+        CK(alloc(&f.member, n));
+        f.cap_member = n;
+    }
+    CK(cudaMemcpyAsync(f.member, c->d_flag, sizeof(unsigned int) * n, cudaMemcpyDeviceToDevice, c->stream));
+    f.n_all = n;
+    f.bucket = c->params.bucket;
+    f.n = m;
+    f.n_cells = f.n_buckets = 0;
+    if (m > 0) {
+        st = build_tree(c, c->d_pos, c->d_mass, nullptr, m, c->params.bucket);
+        if (st != FMM_OK) return st;
+        const DevTree& t = c->t;
+        cudaStream_t s = c->stream;
+        const long long nc = t.n_cells, nb = t.n_buckets;
+        if (nc > f.cap_cells) {
+            CK(alloc(&f.cfirst, nc));
+            CK(alloc(&f.ccount, nc));
+            CK(alloc(&f.cchild, 2 * nc));
+            CK(alloc(&f.cparent, nc));
+            CK(alloc(&f.bucket_cell, nc));
+            CK(alloc(&f.com, nc));
+            CK(alloc(&f.clo, 3 * nc));
+            CK(alloc(&f.chi, 3 * nc));
+            CK(alloc(&f.bmax, nc));
+            CK(alloc(&f.rec, (long long)FMM_NREC * nc));
+            f.cap_cells = nc;
+        }
+        if (m > f.cap_n) {
+            CK(alloc(&f.posf, m));
+            CK(alloc(&f.plo, m));
+            CK(alloc(&f.off, m));
+            CK(alloc(&f.bucket_of, m));
+            f.cap_n = m;
+        }
+        auto cp = [&](void* dst, const void* src, size_t bytes) {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+        };
+        CK(cp(f.cfirst, t.cfirst, sizeof(int) * nc));
+        CK(cp(f.ccount, t.ccount, sizeof(int) * nc));
+        CK(cp(f.cchild, t.cchild, sizeof(int) * 2 * nc));
+        CK(cp(f.cparent, t.cparent, sizeof(int) * nc));
+        CK(cp(f.bucket_cell, t.bucket_cell, sizeof(int) * nb));
+        CK(cp(f.com, t.com, sizeof(Com4) * nc));
+        CK(cp(f.clo, t.clo, sizeof(double) * 3 * nc));
+        CK(cp(f.chi, t.chi, sizeof(double) * 3 * nc));
+        CK(cp(f.bmax, t.bmax, sizeof(double) * nc));
+        CK(cp(f.rec, t.rec, sizeof(float) * FMM_NREC * nc));
+        CK(cp(f.posf, t.posf, sizeof(float4) * m));
+        CK(cp(f.plo, t.plo, sizeof(float4) * m));
+        CK(cp(f.off, t.off, sizeof(float4) * m));
+        CK(cp(f.bucket_of, t.bucket_of, sizeof(int) * m));
+        CK(cudaStreamSynchronize(s));
+        f.n_cells = nc;
+        f.n_buckets = nb;
+    }
+    f.valid = true;
+    // fmm_get_stats reports this call's kernel launches and the fixed tree's size
+    memset(&c->stats, 0, sizeof c->stats);
+    c->stats.n = m;
+    c->stats.n_cells = f.n_cells;
+    c->stats.n_buckets = f.n_buckets;
+    c->stats.n_launches = c->launches;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_compute_forces_dual(fmm_ctx* c, const double* pos, const float* mass,
+                                              const unsigned char* active, long long n, double eps, double theta,
+                                              float* acc, float* pot)
+{
+    fmm_status st = check_common(c, pos, mass, n);
+    if (st != FMM_OK) return st;
+    if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
+    const FixedTree& f = c->fx;
+    if (!f.valid) return fail(FMM_ERR_STATE, "fmm_compute_forces_dual: no fixed sources (fmm_set_fixed_sources first)");
+    fmm_params q = c->params;
+    q.eps = eps;
+    q.theta = theta;
+    st = check_params(&q);
+    if (st != FMM_OK) return st;
+    if (q.criterion != 0) return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: only the fixed criterion (criterion 0)");
+    if (q.bucket != f.bucket)
+        return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: bucket %d differs from the fixed tree's %d", q.bucket,
+                    f.bucket);
+    if (n != f.n_all)
+        return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: n = %lld, the fixed set was chosen from %lld particles", n,
+                    f.n_all);
+    cudaStream_t s = c->stream;
+    c->have_solve = false;
+    memset(&c->stats, 0, sizeof c->stats);
+    c->launches = 0;
+    CK(cudaEventRecord(c->ev[0], s));
+    // the active tree: every particle outside the fixed set, at its current position
+    long long na = 0;
+    st = select_subset(c, pos, nullptr, 0.0, mass, nullptr, 0, f.member, active, n, &na);
+    if (st != FMM_OK) return st;
+    if (na == 0) return FMM_OK;  // no particle outside the fixed set: nothing is written
+    // both trees' capacity before the active tree is built (buffers only grow)
+    st = ensure_tree(c, na + f.n + 64, q.bucket);
+    if (st != FMM_OK) return st;
+    st = build_tree(c, c->d_pos, c->d_mass, active ? c->d_act : nullptr, na, q.bucket);
+    if (st != FMM_OK) return st;
+    DevTree& t = c->t;
+    const long long ca = t.n_cells, ba = t.n_buckets;
+    c->stats.n_active = (long long)c->ctr_h->n_active;
+    if (ca + f.n_cells > t.cap_cells || na + f.n > t.cap_n)
+        return fail(FMM_ERR_STATE, "internal: the two trees exceed the tree capacity");
+    if (f.n > 0) {
+        CK(fmm_append_fixed(t, f, na, ca, ba, s));
+        c->launches += 3;
+        t.n_cells = ca + f.n_cells;
+        t.n_buckets = ba + f.n_buckets;
+        c->totals_h[0] = (unsigned int)t.n_cells;
+        c->totals_h[1] = (unsigned int)t.n_buckets;
+        CK(cudaMemcpyAsync(c->totals, c->totals_h, 2 * sizeof(unsigned int), cudaMemcpyHostToDevice, s));
+    }
+    CK(fmm_launch_nodes(t, theta, s));
+    c->launches += 1;
+    CK(cudaEventRecord(c->ev[1], s));
+    c->second_root = f.n > 0 ? (int)ca : -1;  // the fixed tree's root (its cell 0)
+    // the walk's list capacities follow the sources of both trees (as a plain solve's follow all
+    // its particles, sinks or not): sized for the active tree alone they overflow and re-run
+    st = run_walk(c, na + f.n, eps, q.bucket, q.group, 0);
+    c->second_root = -1;
+    if (st != FMM_OK) return st;
+    CK(fmm_launch_compose_perm(t.idx, c->d_idx, na, c->d_perm, s));
+    c->launches += 1;
+    return interact_and_finish(c, q, eps, acc, pot, n, na, c->d_perm);
 }
 
 extern "C" fmm_status fmm_compute_forces_batch(fmm_ctx* c, const double* pos, const float* mass,

@@ -179,6 +179,25 @@ struct DevWalk {
     long long n_groups = 0, pp_len = 0, pc_len = 0, cc_len = 0, n_levels = 0;
 };
 
+// The fixed tree of the dual-tree scheme (dual.cu): a copy of the source-side arrays of a tree
+// built from the particles of the slow rungs, in its own numbering (cells [0, n_cells), buckets
+// [0, n_buckets), sorted particles [0, n)), appended after each active tree.
+struct FixedTree {
+    bool valid = false;        // set by fmm_set_fixed_sources
+    int bucket = 0;            // bucket size it was built with (the active tree must use the same)
+    long long n_all = 0;       // particle count of the caller's arrays it was selected from
+    unsigned int* member = nullptr;  // n_all flags: 1 for the particles in the fixed set
+    long long cap_member = 0;
+    long long n = 0, n_cells = 0, n_buckets = 0;
+    long long cap_n = 0, cap_cells = 0;
+    int *cfirst = nullptr, *ccount = nullptr, *cchild = nullptr, *cparent = nullptr, *bucket_cell = nullptr;
+    Com4 *com = nullptr;
+    double *clo = nullptr, *chi = nullptr, *bmax = nullptr;
+    float *rec = nullptr;
+    float4 *posf = nullptr, *plo = nullptr, *off = nullptr;
+    int *bucket_of = nullptr;
+};
+
 // ---------------------------------------------------------------- launchers (host)
 
 // scan.cu / sort.cu
@@ -228,7 +247,7 @@ struct WalkArgs {
 };
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s);
-cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s);
+cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root = -1);
 int fmm_walk_warps(int device);
 
 // interact.cu
@@ -241,9 +260,21 @@ struct InteractArgs {
 cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk, cudaStream_t s);
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s);
+// perm: sorted sink -> index in acc/pot (NULL: the tree's own order t.idx)
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,
-                               float* pot, long long n, cudaStream_t s);
+                               float* pot, long long n, cudaStream_t s, const unsigned int* perm = nullptr);
 int fmm_interact_blocks(int device);
+
+// dual.cu
+cudaError_t fmm_launch_subset_flags(const unsigned char* rung, int r_max, const unsigned int* flag_not, long long n,
+                                    unsigned int* flag, cudaStream_t s);
+cudaError_t fmm_launch_subset_gather(const unsigned int* flag, const unsigned int* at, long long n, const double* pos,
+                                     const double* vel, double dt, const float* mass, const unsigned char* mask,
+                                     long long m, double* pos_out, float* mass_out, unsigned char* mask_out,
+                                     unsigned int* idx, cudaStream_t s);
+cudaError_t fmm_append_fixed(DevTree& t, const FixedTree& f, long long na, long long ca, long long ba, cudaStream_t s);
+cudaError_t fmm_launch_compose_perm(const unsigned int* perm, const unsigned int* sub, long long n, unsigned int* out,
+                                    cudaStream_t s);
 
 // kdk.cu
 cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, unsigned char* rung,

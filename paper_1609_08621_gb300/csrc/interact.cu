@@ -654,18 +654,19 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
 }
 
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,
-                               float* pot, long long n, cudaStream_t s)
+                               float* pot, long long n, cudaStream_t s, const unsigned int* perm)
 {
+    if (!perm) perm = t.idx;
     const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     if (a.accumulate == 1)
         k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
-            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
             a.terms);
     else
         k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
-            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, t.idx, n, acc, pot,
+            t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
             a.terms);
     return cudaGetLastError();
 }

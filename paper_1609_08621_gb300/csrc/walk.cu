@@ -496,9 +496,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
 // level 0 of the walk: every box's root cell as a sink, with that root alone on its checklist
 // (isolated boxes: sources of other boxes are never seen); boxes without an active particle
 // are not walked
+// Each box's root starts the walk with itself on its checklist.  With one box and second_root >= 0
+// (the root of an appended fixed tree, dual.cu) the checklist holds both roots.
 __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl,
                             const int* __restrict__ cnact, const int* __restrict__ box_root, int nbox,
-                            DevCounters* ctr)
+                            int second_root, DevCounters* ctr)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
@@ -506,16 +508,24 @@ __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cll
     if (r < 0 || cnact[r] <= 0) return;  // an empty box has no root cell
     const unsigned long long k = atomicAdd(&ctr->lv_front[0], 1ull);
     f_cell[k] = r;
+    if (second_root >= 0) {  // one box only: its entries are cl[0], cl[1]
+        f_cloff[k] = 0;
+        f_cllen[k] = 2;
+        cl[0] = (unsigned int)r;
+        cl[1] = (unsigned int)second_root;
+        return;
+    }
     f_cloff[k] = k;
     f_cllen[k] = 1;
     cl[k] = (unsigned int)r;
 }
 
-cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s)
+cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root)
 {
+    if (second_root >= 0 && t.nbox != 1) return cudaErrorInvalidValue;
     k_walk_seed<<<(unsigned)fmm_ceil_div(t.nbox, 128), 128, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0],
                                                                      t.cnact, t.nbox > 1 ? t.box_root : nullptr,
-                                                                     t.nbox, ctr);
+                                                                     t.nbox, second_root, ctr);
     return cudaGetLastError();
 }
 
