@@ -187,12 +187,12 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
             t.bucket_of, t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
             t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
-            t.hist, t.box_off, t.box_root, t.sbox, t.key_orig,
+            t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup,
             w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
             w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
             w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch,
             f.cfirst, f.ccount, f.cchild, f.cparent, f.bucket_cell, f.com, f.clo, f.chi, f.bmax, f.rec, f.posf, f.plo,
-            f.off, f.bucket_of, f.member, c->d_flag, c->d_at, c->d_idx, c->d_perm, c->d_act, c->d_pos, c->d_mass};
+            f.off, f.bucket_of, f.key, f.member, c->d_flag, c->d_at, c->d_idx, c->d_perm, c->d_act, c->d_pos, c->d_mass};
 }
 
 static void free_all(fmm_ctx* c)
@@ -276,7 +276,7 @@ extern "C" fmm_status fmm_get_params(const fmm_ctx* c, fmm_params* p)
     return FMM_OK;
 }
 
-static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
+static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1, long long min_cells = 0)
 {
     DevTree& t = c->t;
     if (n > t.cap_n) {
@@ -309,6 +309,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1)
     // most two bucket children; several boxes add their top levels (< 2 nbox nodes)
     long long need_cells = 6 * n / (bucket + 1) + 8 + 2LL * nbox;
     if (need_cells > 2 * n + 1) need_cells = 2 * n + 1;
+    if (need_cells < min_cells) need_cells = min_cells;
     if (need_cells > t.cap_cells) {
         long long cap = need_cells;
         CK(alloc(&t.cfirst, cap));
@@ -442,6 +443,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     // upward, exact b_max (count, scan, expand, two passes, final)
     c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
     t.depth = (int)c->ctr_h->depth;
+    t.graded = t.grade_key != nullptr && n > 1;
     c->have_tree = true;
     c->theta_nodes = -1.0f;
     return FMM_OK;
@@ -1143,6 +1145,7 @@ extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const
             CK(alloc(&f.plo, m));
             CK(alloc(&f.off, m));
             CK(alloc(&f.bucket_of, m));
+            CK(alloc(&f.key, m));
             f.cap_n = m;
         }
         auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -1162,6 +1165,7 @@ extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const
         CK(cp(f.plo, t.plo, sizeof(float4) * m));
         CK(cp(f.off, t.off, sizeof(float4) * m));
         CK(cp(f.bucket_of, t.bucket_of, sizeof(int) * m));
+        CK(cp(f.key, t.key, sizeof(unsigned long long) * m));
         CK(cudaStreamSynchronize(s));
         f.n_cells = nc;
         f.n_buckets = nb;
@@ -1207,12 +1211,21 @@ extern "C" fmm_status fmm_compute_forces_dual(fmm_ctx* c, const double* pos, con
     st = select_subset(c, pos, nullptr, 0.0, mass, nullptr, 0, f.member, active, n, &na);
     if (st != FMM_OK) return st;
     if (na == 0) return FMM_OK;  // no particle outside the fixed set: nothing is written
-    // both trees' capacity before the active tree is built (buffers only grow)
-    st = ensure_tree(c, na + f.n + 64, q.bucket);
-    if (st != FMM_OK) return st;
-    st = build_tree(c, c->d_pos, c->d_mass, active ? c->d_act : nullptr, na, q.bucket);
-    if (st != FMM_OK) return st;
+    // both trees' capacity before the active tree is built (buffers only grow); a graded active
+    // tree may keep every radix node (2 n_a - 1 cells)
     DevTree& t = c->t;
+    st = ensure_tree(c, na + f.n + 64, q.bucket, 1, 2 * na + f.n_cells + 16);
+    if (st != FMM_OK) return st;
+    if (f.n > 0) {
+        CK(grow(&t.split, &t.cap_split, 2 * na));
+        CK(grow(&t.nogroup, &t.cap_nogroup, t.cap_cells));
+        t.grade_key = f.key;  // the active tree takes the fixed tree's geometric structure
+        t.grade_n = f.n;
+        t.grade_group = q.group;
+    }
+    st = build_tree(c, c->d_pos, c->d_mass, active ? c->d_act : nullptr, na, q.bucket);
+    t.grade_key = nullptr;
+    if (st != FMM_OK) return st;
     const long long ca = t.n_cells, ba = t.n_buckets;
     c->stats.n_active = (long long)c->ctr_h->n_active;
     if (ca + f.n_cells > t.cap_cells || na + f.n > t.cap_n)

@@ -145,6 +145,16 @@ struct DevTree {
     unsigned long long *sbox = nullptr;      // sorted box id per particle (several boxes only)
     unsigned long long *key_orig = nullptr;  // Morton keys in input order (several boxes only)
     long long cap_box_n = 0;
+    // graded build (dual trees): with grade_key set, a radix node also splits where the fixed
+    // tree's sorted keys grade_key hold more than b particles in its Morton box, and a cell is no
+    // group where they hold more than g (split: per node, bit 0 split, bit 1 no group; nogroup:
+    // per cell, valid while graded)
+    const unsigned long long* grade_key = nullptr;
+    long long grade_n = 0;
+    int grade_group = 0;
+    bool graded = false;
+    unsigned char *split = nullptr, *nogroup = nullptr;
+    long long cap_split = 0, cap_nogroup = 0;
     // scan scratch
     unsigned int *scan_part = nullptr;
     long long cap_scan_part = 0;
@@ -196,6 +206,7 @@ struct FixedTree {
     float *rec = nullptr;
     float4 *posf = nullptr, *plo = nullptr, *off = nullptr;
     int *bucket_of = nullptr;
+    unsigned long long *key = nullptr;  // its sorted Morton keys (the graded build of the active tree)
 };
 
 // ---------------------------------------------------------------- launchers (host)

@@ -146,8 +146,56 @@ __device__ __forceinline__ int node_count(const int* ifirst, const int* ilast, i
     return x < n - 1 ? ilast[x] - ifirst[x] + 1 : 1;
 }
 
+// first index of a sorted key array k[0, n) that is >= v
+__device__ __forceinline__ long long lower_bound_u64(const unsigned long long* __restrict__ k, long long n,
+                                                     unsigned long long v)
+{
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (k[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Graded split flags of the radix nodes (dual trees, Sec. 3.2: the active tree takes the fixed
+// tree's geometric structure).  A node splits when it holds more than b particles, or more than
+// one while the fixed tree holds more than b in the node's Morton box (the dyadic box of its
+// keys' common prefix); it is no group when the fixed tree holds more than g there.  So the
+// active tree's leaves and groups are no larger than the fixed tree's around them.
+__global__ void k_split(const int* __restrict__ ifirst, const int* __restrict__ ilast,
+                        const unsigned long long* __restrict__ key, int n, int bucket, int group,
+                        const unsigned long long* __restrict__ fkey, long long nf, unsigned char* __restrict__ split)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= 2 * n - 1) return;
+    const int count = node_count(ifirst, ilast, n, x);
+    unsigned int f = count > bucket ? 1u : 0u;
+    if (count > 1 && count <= max(bucket, group)) {
+        const int first = x < n - 1 ? ifirst[x] : x - (n - 1);
+        const unsigned long long a = key[first], b = key[first + count - 1];
+        if (a != b) {  // equal keys are one point: no finer box exists
+            const int d = __clzll(a ^ b);                   // common leading bits, >= 1 (bit 63 is 0)
+            const unsigned long long span = 1ull << (64 - d);  // the box holds keys [lo, lo + span)
+            const unsigned long long lo = a & ~(span - 1);
+            const long long nb = lower_bound_u64(fkey, nf, lo + span) - lower_bound_u64(fkey, nf, lo);
+            if (nb > bucket) f |= 1u;
+            if (nb > group) f |= 2u;
+        }
+    }
+    split[x] = (unsigned char)f;
+}
+
+// a node's children are cells when it splits: more than b particles, or the graded flag
+__device__ __forceinline__ bool node_splits(const int* ifirst, const int* ilast, int n, int bucket,
+                                            const unsigned char* split, int x)
+{
+    return split ? (split[x] & 1u) != 0u : node_count(ifirst, ilast, n, x) > bucket;
+}
+
 __global__ void k_keep(const int* __restrict__ ifirst, const int* __restrict__ ilast, const int* __restrict__ nparent,
-                       int n, int bucket, unsigned int* __restrict__ keep)
+                       int n, int bucket, const unsigned char* __restrict__ split, unsigned int* __restrict__ keep)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= 2 * n - 1) return;
@@ -156,7 +204,7 @@ __global__ void k_keep(const int* __restrict__ ifirst, const int* __restrict__ i
         k = 1;
     } else {
         int p = nparent[x];
-        k = (p < 0) ? 1u : (node_count(ifirst, ilast, n, p) > bucket ? 1u : 0u);
+        k = (p < 0) ? 1u : (node_splits(ifirst, ilast, n, bucket, split, p) ? 1u : 0u);
     }
     keep[x] = k;
 }
@@ -164,9 +212,9 @@ __global__ void k_keep(const int* __restrict__ ifirst, const int* __restrict__ i
 // keep[] has been turned into exclusive cell ids in place; kept marks whether node x is kept
 __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ ilast, const int* __restrict__ ileft,
                         const int* __restrict__ iright, const int* __restrict__ nparent,
-                        const unsigned int* __restrict__ cid, int n, int bucket, int* __restrict__ cfirst,
-                        int* __restrict__ ccount, int* __restrict__ cparent, int* __restrict__ cchild,
-                        unsigned int* __restrict__ bflag)
+                        const unsigned int* __restrict__ cid, int n, int bucket, const unsigned char* __restrict__ split,
+                        int* __restrict__ cfirst, int* __restrict__ ccount, int* __restrict__ cparent,
+                        int* __restrict__ cchild, unsigned int* __restrict__ bflag, unsigned char* __restrict__ nogroup)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= 2 * n - 1) return;
@@ -175,7 +223,7 @@ __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ 
         kept = true;
     } else {
         int p = nparent[x];
-        kept = (p < 0) || node_count(ifirst, ilast, n, p) > bucket;
+        kept = (p < 0) || node_splits(ifirst, ilast, n, bucket, split, p);
     }
     if (!kept) return;
     int c = (int)cid[x];
@@ -185,7 +233,8 @@ __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ 
     ccount[c] = count;
     int p = n == 1 ? -1 : nparent[x];
     cparent[c] = p < 0 ? -1 : (int)cid[p];
-    if (count > bucket) {
+    if (split) nogroup[c] = (unsigned char)((split[x] >> 1) & 1u);
+    if (node_splits(ifirst, ilast, n, bucket, split, x)) {
         cchild[2 * c] = (int)cid[ileft[x]];
         cchild[2 * c + 1] = (int)cid[iright[x]];
     } else {
@@ -227,7 +276,13 @@ cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStrea
         k_radix_tree<<<(unsigned)fmm_ceil_div(ni - 1, TB), TB, 0, s>>>(t.key, t.nbox > 1 ? t.sbox : nullptr, ni,
                                                                        t.ifirst, t.ilast, t.ileft,
                                                                        t.iright, t.nparent);
-    k_keep<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.nparent, ni, bucket, t.keep);
+    const unsigned char* split = nullptr;
+    if (t.grade_key && ni > 1) {
+        k_split<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.key, ni, bucket,
+                                                                      t.grade_group, t.grade_key, t.grade_n, t.split);
+        split = t.split;
+    }
+    k_keep<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.nparent, ni, bucket, split, t.keep);
     return cudaGetLastError();
 }
 
@@ -481,9 +536,10 @@ __global__ void k_bm_final(const unsigned int* __restrict__ ncell, const int* __
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s)
 {
     int ni = (int)n;
+    const unsigned char* split = (t.grade_key && ni > 1) ? t.split : nullptr;
     k_cells<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.ileft, t.iright, t.nparent,
-                                                                  t.keep, ni, bucket, t.cfirst, t.ccount, t.cparent,
-                                                                  t.cchild, t.bflag);
+                                                                  t.keep, ni, bucket, split, t.cfirst, t.ccount,
+                                                                  t.cparent, t.cchild, t.bflag, t.nogroup);
     return cudaGetLastError();
 }
 

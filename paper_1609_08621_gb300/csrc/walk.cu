@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
     DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float4* __restrict__ mnorm,
     const float* __restrict__ amin,
     float eps, float band_lo, float band_hi, float tau, const unsigned char* __restrict__ mlp_packed,
-    int2* __restrict__ audit_pairs, long long audit_cap)
+    int2* __restrict__ audit_pairs, long long audit_cap, const unsigned char* __restrict__ nogroup)
 {
     extern __shared__ __align__(16) unsigned char walk_smem[];
     if (MODE == 1) {
@@ -85,7 +85,9 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
         if (fi >= n_front) break;
         const int k = f_cell[fi];
         const WalkNode K = node[k];
-        const bool kg = K.d.w <= group;
+        // a group holds <= g particles; in a graded tree (dual trees) it is also no larger than the
+        // fixed tree's groups around it
+        const bool kg = K.d.w <= group && !(nogroup && nogroup[k]);
         const float rk = K.a.w, bk = K.b.w;
         const float ak = MODE == 1 ? amin[k] : 0.0f;
         const unsigned long long cl0 = f_cloff[fi];
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
                     lox = S.b.x; loy = S.b.y; loz = S.b.z;
                     hix = S.c.x; hiy = S.c.y; hiz = S.c.z;
                     pointlike = S.d.w == 1;
-                    sleaf = S.d.w <= bucket;
+                    sleaf = S.d.x < 0;  // a leaf (bucket) has no children
                     c0 = S.d.x;
                     c1 = S.d.y;
                     sfirst = S.d.z;
@@ -546,7 +548,7 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
         w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
         w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
         a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
-        a.audit_cap
+        a.audit_cap, t.graded ? t.nogroup : nullptr
     if (a.mode == 1) {
         const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;
         static bool attr = false;
