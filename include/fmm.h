@@ -251,9 +251,12 @@ fmm_status fmm_assign_rungs(fmm_ctx *ctx, const float *acc, unsigned char *rung,
  * On the substeps between two kicks of the slower rungs only the fast rungs need forces.  The
  * particles of rungs <= r_fixed are not kicked there, so they move on straight lines; they are
  * drifted to the middle of the interval once and a "fixed" tree of them is kept, and each
- * substep builds a tree of the active particles only and walks it against both trees.  Both
+ * substep builds a tree of the other (fast) particles and walks it against both trees.  Both
  * trees are radix trees over Morton keys of the same unit box, so their cells are the same
- * dyadic boxes (the shared geometric structure the method asks for). */
+ * dyadic boxes; the active tree is moreover graded on the fixed one (the shared geometric
+ * structure the method asks for): a node keeps splitting while the fixed tree holds more than
+ * b particles in its box, and is no sink group while it holds more than g there, so active
+ * leaves and groups are never larger than the fixed tree's around them. */
 
 /* Build and keep the fixed tree: the particles i with rung[i] <= r_fixed (every particle when
  * rung is NULL), at positions pos_i + vel_i * dt (FP64; pos_i when vel is NULL).  Which particles
