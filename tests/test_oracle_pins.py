@@ -277,6 +277,45 @@ def test_p2l_and_m2l_converge_to_direct():
     assert pot == pytest.approx(rp1[0], rel=1e-13)
 
 
+def test_l2p_error_grows_as_fifth_power_of_the_offset():
+    """A local expansion to order 5 is the Taylor polynomial of degree 5 of the far field about
+    its centre: the potential's remainder is of order 6 in the offset u, so the force error grows
+    as |u|^5 (the expected slope is 5, the next term's order)."""
+    c = np.array([0.5, 0.5, 0.5])
+    src = c + np.array([0.31, -0.22, 0.27])
+    m = 0.8
+    L = oracle.p2l(m, src, c, 0.0)
+    dirn = np.array([0.36, 0.48, -0.8])
+    rs = np.array([0.02, 0.04, 0.08])
+    errs = []
+    for r in rs:
+        acc, _ = oracle.l2p(L, r * dirn)
+        ref, _ = oracle.direct(np.stack([src, c + r * dirn], axis=1), np.array([m, 0.0]), 0.0, [1])
+        errs.append(np.linalg.norm(acc - ref[:, 0]) / np.linalg.norm(ref[:, 0]))
+    slope = np.polyfit(np.log(rs), np.log(errs), 1)[0]
+    assert 4.8 < slope < 6.2, slope
+
+
+def test_plummer_sphere_far_field_is_a_point_mass():
+    """Far outside a Plummer sphere of scale a the field tends to M / r^2 along the radius; the
+    sampled sphere's residual quadrupole falls off as (a / r)^2 relative."""
+    rng = np.random.default_rng(31)
+    n, a = 4000, 0.01
+    r = a / np.sqrt(rng.random(n) ** (-2.0 / 3.0) - 1.0)
+    r = np.minimum(r, 0.2)
+    cz = 2.0 * rng.random(n) - 1.0
+    ph = 2.0 * np.pi * rng.random(n)
+    sz = np.sqrt(1.0 - cz * cz)
+    c = np.array([0.3, 0.3, 0.3])
+    pos = c[:, None] + r * np.stack([sz * np.cos(ph), sz * np.sin(ph), cz])
+    mass = np.full(n, 1.0 / n)
+    probe = c + 0.6 * np.array([0.6, 0.64, 0.48])
+    ref, _ = oracle.direct(np.concatenate([pos, probe[:, None]], axis=1), np.append(mass, 0.0), 0.0, [n])
+    d = probe - (pos * mass).sum(axis=1) / mass.sum()
+    point = -mass.sum() * d / np.linalg.norm(d) ** 3
+    assert np.linalg.norm(ref[:, 0] - point) <= 1e-3 * np.linalg.norm(point)
+
+
 # ---------------------------------------------------------------- plain FMM
 
 
