@@ -178,10 +178,12 @@ __global__ void k_split(const int* __restrict__ ifirst, const int* __restrict__ 
         if (a != b) {  // equal keys are one point: no finer box exists
             const int d = __clzll(a ^ b);                   // common leading bits, >= 1 (bit 63 is 0)
             const unsigned long long span = 1ull << (64 - d);  // the box holds keys [lo, lo + span)
-            const unsigned long long lo = a & ~(span - 1);
-            const long long nb = lower_bound_u64(fkey, nf, lo + span) - lower_bound_u64(fkey, nf, lo);
-            if (nb > bucket) f |= 1u;
-            if (nb > group) f |= 2u;
+            const unsigned long long lo = a & ~(span - 1), hi = lo + span;
+            // more than k fixed keys in [lo, hi) exactly when the k-th after the first one there
+            // exists and is below hi (the keys are sorted): one search instead of two
+            const long long p0 = lower_bound_u64(fkey, nf, lo);
+            if (p0 + bucket < nf && fkey[p0 + bucket] < hi) f |= 1u;
+            if (p0 + group < nf && fkey[p0 + group] < hi) f |= 2u;
         }
     }
     split[x] = (unsigned char)f;
