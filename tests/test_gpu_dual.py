@@ -184,3 +184,29 @@ def test_full_size_256cubed_fast_rungs(ctx):
     sinks = rng.choice(np.flatnonzero(active), 256, replace=False)
     ref, _ = oracle.direct(u, mass, eps, sinks)
     _assert_accuracy(_rel_err(a[:, sinks], ref))
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 100])
+def test_tiny_sets(ctx, n):
+    """Trees of one or a few particles on either side: the solve is still the direct sum of the
+    union (almost all of it PP at these sizes)."""
+    dt = 0.5
+    pos, mass, rung, vel = _particles(n, 40 + n, dt)
+    rung[0], rung[1] = 5, 0  # at least one fast and one fixed particle
+    fixed = rung <= 2
+    active = (~fixed).astype(np.uint8)
+    a, p = _solve_dual(ctx, pos, mass, rung, vel, dt, 2, active, 1e-3, 0.6)
+    assert np.all(np.isnan(a[:, fixed]))
+    sinks = np.flatnonzero(active)
+    ref, _ = oracle.direct(_union(pos, vel, dt, fixed), mass, 1e-3, sinks)
+    assert _rel_err(a[:, sinks], ref).max() <= 2e-3
+
+
+def test_everything_fixed_writes_nothing(ctx):
+    n = 500
+    pos, mass, _, _ = _particles(n, 26, 1.0)
+    tp, tm = _t(pos, torch.float64), _t(mass, torch.float32)
+    ctx.set_fixed_sources(tp, tm)  # no rungs: every particle is fixed
+    acc = torch.full((3 * n,), float("nan"), dtype=torch.float32, device="cuda:0")
+    ctx.compute_forces_dual(tp, tm, 1e-3, 0.6, acc)
+    assert bool(torch.isnan(acc).all())
