@@ -329,6 +329,19 @@ class Batch:
         return cpu_baseline(p, m, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / m.size))
 
 
+def dual_role(t, max_rung, fixed_rung):
+    """Role of the force solve at substep t (counted from the run's start) under dual trees
+    (Sec. 3.2) with the rungs <= fixed_rung fixed over intervals of m = 2^(max_rung - fixed_rung)
+    substeps: ("full", None, None) on an interval's boundary, where the slow rungs are active as
+    well; else ("dual", interval, to_mid), to_mid being the substeps from t to the interval's
+    middle, where the fixed particles are drifted to."""
+    m = 1 << (max_rung - fixed_rung)
+    j = t % m
+    if j == 0:
+        return "full", None, None
+    return "dual", t // m, 0.5 * m - j
+
+
 class Rungs:
     """256^3 Plummer-clustered box on rungs 0-5 (Sec. 3.2): a step is one substep of the KDK
     hierarchy -- kick-drift of the active particles and drift of all, then the force solve of the
@@ -382,17 +395,16 @@ class Rungs:
         if self.dual is None:
             self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
             return
-        m = 1 << (self.R - self.dual)
-        t = k + 1  # the substep whose forces are solved (positions are there after the drift)
-        j = t % m
-        if j == 0:  # interval boundary: the slow rungs are active too
+        # the substep whose forces are solved (positions are there after the drift)
+        role, interval, to_mid = dual_role(k + 1, self.R, self.dual)
+        if role == "full":  # interval boundary: the slow rungs are active too
             self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
             return
-        if self.fixed_interval != t // m:
+        if self.fixed_interval != interval:
             h = self.dt0 / (1 << self.R)
-            self.ctx.set_fixed_sources(self.tpos, self.tmass, self.rung, self.dual, self.vel, (0.5 * m - j) * h)
+            self.ctx.set_fixed_sources(self.tpos, self.tmass, self.rung, self.dual, self.vel, to_mid * h)
             self.extra_launches += self.ctx.stats()["n_launches"]
-            self.fixed_interval = t // m
+            self.fixed_interval = interval
         self.ctx.compute_forces_dual(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot, self.act)
 
     def e2e(self, steps):
