@@ -502,9 +502,13 @@ def main():
            "   around the special-function unit (PTX ISA, rsqrt.approx.ftz.f32) */",
            "__device__ __forceinline__ float fmm_rsqrt(float x)",
            "{",
+           "#ifdef __CUDA_ARCH__",
            "    float y;",
            '    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));',
            "    return y;",
+           "#else  /* host builds of these operators (tests): 1 / sqrt(x) in single precision */",
+           "    return 1.0f / sqrtf(x);",
+           "#endif",
            "}", "",
            "/* multi-index table (a, b, c) of the local coefficients, in storage order */",
            "static const int fmm_multi_index_table[FMM_NL * 3] = {"]
