@@ -1,8 +1,8 @@
 """The CUDA path's generated expansion operators (csrc/expansions.cuh), compiled for the host
 with g++ and checked against the oracle's independent FP64 operators.
 
-Covered: moment building (P2M and traces), the particle-cell body in its scalar and FP32x2
-forms, and M2L followed by L2P. The header is the one the kernels include. On the host:
+Covered: moment building (P2M, M2M and traces), the particle-cell body in its scalar and FP32x2
+forms, and the local expansions (M2L, P2L, L2L, each followed by L2P). The header is the one the kernels include. On the host:
 - the FP32x2 intrinsics are per-component fmaf / add / multiply, which is how the CUDA
   documentation defines them;
 - the reciprocal square root is 1/sqrtf.
@@ -55,6 +55,28 @@ void h_pc2(const float* R, const float* r0, const float* r1, float eps2, float* 
                 make_float2(eps2, eps2), ax, ay, az, pp);
     out[0] = ax.x; out[1] = ay.x; out[2] = az.x; out[3] = -pp.x;
     out[4] = ax.y; out[5] = ay.y; out[6] = az.y; out[7] = -pp.y;
+}
+void h_m2m(const float* Rc, float tx, float ty, float tz, float* Mp) {
+    fmm_m2m_acc(Rc, tx, ty, tz, Mp);
+}
+void h_traces(float* R) { fmm_moment_traces(R); }
+void h_p2l_l2p(float m, float rx, float ry, float rz, float eps2, float ux, float uy, float uz, float* out) {
+    float L[FMM_NL];
+    for (int i = 0; i < FMM_NL; i++) L[i] = 0.0f;
+    fmm_p2l_acc(m, rx, ry, rz, eps2, L);
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, phi = 0.0f;
+    fmm_l2p_acc(L, ux, uy, uz, ax, ay, az, phi);
+    out[0] = ax; out[1] = ay; out[2] = az; out[3] = phi;
+}
+void h_m2l_l2l_l2p(const float* R, float rx, float ry, float rz, float eps2, float tx, float ty, float tz, float ux,
+                   float uy, float uz, float* out) {
+    float L[FMM_NL], Lo[FMM_NL];
+    for (int i = 0; i < FMM_NL; i++) L[i] = 0.0f;
+    fmm_m2l_acc(R, rx, ry, rz, eps2, L);
+    fmm_l2l(L, tx, ty, tz, Lo);
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, phi = 0.0f;
+    fmm_l2p_acc(Lo, ux, uy, uz, ax, ay, az, phi);
+    out[0] = ax; out[1] = ay; out[2] = az; out[3] = phi;
 }
 void h_m2l_l2p(const float* R, float rx, float ry, float rz, float eps2, float ux, float uy, float uz, float* out) {
     float L[FMM_NL];
@@ -159,5 +181,69 @@ def test_m2l_then_l2p_matches_the_oracle(lib):
         lib.h_m2l_l2p(Rp, ctypes.c_float(rc[0]), ctypes.c_float(rc[1]), ctypes.c_float(rc[2]), ctypes.c_float(eps2),
                       ctypes.c_float(u[0]), ctypes.c_float(u[1]), ctypes.c_float(u[2]), op)
         ref, rp = oracle.l2p(L, u.astype(np.float64))
+        assert np.allclose(out[:3], ref, rtol=3e-6, atol=3e-6 * np.linalg.norm(ref)), (out[:3], ref)
+        assert out[3] == pytest.approx(rp, rel=3e-6)
+
+
+def _c(v):
+    return [ctypes.c_float(float(x)) for x in v]
+
+
+def test_m2m_shift_matches_the_parent_moments(lib):
+    """Two sub-clusters, each with moments about its own centre, shifted to the parent's centre:
+    the parent record gives the field of the oracle's moments of all particles about that centre."""
+    pos, m, zp = _cluster(7, k=40, b=0.012)
+    halves = (pos[0] < zp[0], pos[0] >= zp[0])
+    Mp, Mpp = _f(np.zeros(44))
+    for h in halves:
+        ph, mh = pos[:, h], m[h]
+        zc = (ph * mh).sum(axis=1) / mh.sum()
+        Rc, Rcp = _record(lib, ph, mh, zc)
+        lib.h_m2m(Rcp, *_c((zc - zp).astype(np.float32)), Mpp)
+    lib.h_traces(Mpp)
+    M = oracle.p2m(pos, m, zp)
+    rng = np.random.default_rng(8)
+    for d in (0.03, 0.1):
+        dirn = rng.normal(size=3)
+        r = (d * dirn / np.linalg.norm(dirn)).astype(np.float32)
+        out, op = _f(np.zeros(4))
+        lib.h_pc(Mpp, *_c(r), ctypes.c_float(1e-6), op)
+        ref, rp = oracle.m2p(M, zp, zp + r.astype(np.float64), 1e-6)
+        assert np.allclose(out[:3], ref, rtol=3e-6, atol=3e-6 * np.linalg.norm(ref)), (out[:3], ref)
+        assert out[3] == pytest.approx(rp, rel=3e-6)
+
+
+def test_p2l_then_l2p_matches_the_oracle(lib):
+    rng = np.random.default_rng(9)
+    c = np.array([0.5, 0.5, 0.5])
+    for _ in range(4):
+        x = c + rng.normal(size=3) * 0.1
+        m = float(rng.random() + 0.1)
+        r = (c - x).astype(np.float32)
+        u = (rng.normal(size=3) * 0.01).astype(np.float32)
+        out, op = _f(np.zeros(4))
+        lib.h_p2l_l2p(ctypes.c_float(m), *_c(r), ctypes.c_float(1e-6), *_c(u), op)
+        L = oracle.p2l(np.float32(m), c - r.astype(np.float64), c, 1e-6)
+        ref, rp = oracle.l2p(L, u.astype(np.float64))
+        assert np.allclose(out[:3], ref, rtol=3e-6, atol=3e-6 * np.linalg.norm(ref)), (out[:3], ref)
+        assert out[3] == pytest.approx(rp, rel=3e-6)
+
+
+def test_l2l_shift_then_l2p_matches_the_oracle(lib):
+    """A local expansion shifted to a child's centre (the groups' ancestor sums): exact for a
+    polynomial of degree 5, so it equals the oracle's expansion evaluated at t + u."""
+    pos, m, z = _cluster(10)
+    R, Rp = _record(lib, pos, m, z)
+    M = oracle.p2m(pos, m, z)
+    rc = np.array([0.15, 0.1, -0.07], np.float32)
+    c = z + rc.astype(np.float64)
+    L = oracle.m2l(M, z, c, 1e-6)
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        t = (rng.normal(size=3) * 0.01).astype(np.float32)
+        u = (rng.normal(size=3) * 0.004).astype(np.float32)
+        out, op = _f(np.zeros(4))
+        lib.h_m2l_l2l_l2p(Rp, *_c(rc), ctypes.c_float(1e-6), *_c(t), *_c(u), op)
+        ref, rp = oracle.l2p(L, t.astype(np.float64) + u.astype(np.float64))
         assert np.allclose(out[:3], ref, rtol=3e-6, atol=3e-6 * np.linalg.norm(ref)), (out[:3], ref)
         assert out[3] == pytest.approx(rp, rel=3e-6)
