@@ -11,9 +11,12 @@ Python view of the C oracle:
 * :func:`green_derivs`, :func:`p2m`, :func:`m2p`, :func:`m2l`, :func:`p2l`,
   :func:`l2l`, :func:`l2p` -- the expansion operators of Sec. 3.1 (moments to
   order 4, local expansion to order 5), in multi-index form.
+* :func:`direct_periodic`, :func:`ewald_derivs`, :func:`ewald_m2p` -- the
+  periodic unit box (Sec. 3.1): the periodic direct sum by Ewald summation, and
+  the correction kernel for the copies beyond the replica shell.
 * :class:`FMM` -- the plain recursive FMM (tree, moments, checklist walk,
   PP / PC / CC / CP / L2L / L2P), with its tree, lists and local expansions
-  exposed for stage-by-stage parity.
+  exposed for stage-by-stage parity; ``nrep`` makes the box periodic.
 
 ``kdk`` holds the rung assignment and kick-drift-kick schedule (Sec. 3.2) and
 ``mlp`` the FP64 reference of the learned opening criterion's network.
@@ -52,8 +55,16 @@ def lib():
         L.orc_l2l.argtypes = [dp, dp, dp]
         L.orc_l2p.argtypes = [dp, dp, dp, dp]
         L.orc_multi_index.argtypes = [ip]
+        L.orc_ewald_derivs.argtypes = [dp, C.c_int, C.c_double, dp]
+        L.orc_ewald_m2p.argtypes = [dp, dp, dp, C.c_int, C.c_double, dp, dp]
+        L.orc_direct_periodic.argtypes = [C.c_long, dp, dp, C.c_double, C.c_int, C.c_double, C.c_long,
+                                          C.c_void_p, dp, dp]
         L.orc_fmm_create.restype = C.c_void_p
         L.orc_fmm_create.argtypes = [C.c_long, dp, dp, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int]
+        L.orc_fmm_create_periodic.restype = C.c_void_p
+        L.orc_fmm_create_periodic.argtypes = [C.c_long, dp, dp, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                              C.c_int, C.c_int]
+        L.orc_fmm_entry_shifts.argtypes = [C.c_void_p, C.c_int, ip]
         L.orc_fmm_eval.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.orc_fmm_ncell.restype = C.c_long
         L.orc_fmm_ncell.argtypes = [C.c_void_p]
@@ -104,6 +115,40 @@ def direct(pos, mass, eps, sinks=None):
     return acc.reshape(3, ns), pot
 
 
+def direct_periodic(pos, mass, eps, sinks=None, nrep=1, alpha=8.0):
+    """FP64 periodic direct sum in the unit box: the softened kernel on the copies inside the
+    replica shell |n|_inf <= nrep, the Newtonian Ewald sum beyond (Ewald parameter alpha; the
+    result does not depend on it).  Returns acc (3, S), pot (S,) for the sinks."""
+    pos = _f64(pos)
+    mass = _f64(mass)
+    n = pos.shape[1]
+    if sinks is None:
+        ns, sp, keep = n, None, None
+    else:
+        keep = np.ascontiguousarray(sinks, dtype=np.int64)
+        ns, sp = keep.shape[0], keep.ctypes.data
+    acc = np.zeros(3 * ns)
+    pot = np.zeros(ns)
+    lib().orc_direct_periodic(n, pos.reshape(-1), mass, float(eps), int(nrep), float(alpha), ns, sp, acc, pot)
+    return acc.reshape(3, ns), pot
+
+
+def ewald_derivs(r, nrep=1, alpha=3.0):
+    """D^n F(r), |n| <= 5: F is the periodic potential of a unit mass (background subtracted)
+    less the Newtonian copies inside the replica shell.  Offsets with |r_a| < 1."""
+    D = np.zeros(NMI)
+    lib().orc_ewald_derivs(_f64(r), int(nrep), float(alpha), D)
+    return D
+
+
+def ewald_m2p(M, z, x, nrep=1, alpha=3.0):
+    """The correction for the copies beyond the replica shell at x, from moments M about z."""
+    acc = np.zeros(3)
+    pot = np.zeros(1)
+    lib().orc_ewald_m2p(_f64(M), _f64(z), _f64(x), int(nrep), float(alpha), acc, pot)
+    return acc, pot[0]
+
+
 def green_derivs(r, eps2):
     D = np.zeros(NMI)
     lib().orc_green_derivs(_f64(r), float(eps2), D)
@@ -150,9 +195,13 @@ def l2p(L, u):
 
 
 class FMM:
-    """Plain recursive FMM on the CPU (FP64 arithmetic, single-precision decisions)."""
+    """Plain recursive FMM on the CPU (FP64 arithmetic, single-precision decisions).
 
-    def __init__(self, pos, mass, eps, theta, bucket=16, group=64, active=None):
+    ``nrep`` makes the unit box periodic: the walk starts from the root and its copies
+    |n|_inf <= nrep (26 for 1, 124 for 2), and ``forces`` adds the Ewald correction for the
+    copies beyond (term bit 8)."""
+
+    def __init__(self, pos, mass, eps, theta, bucket=16, group=64, active=None, nrep=None):
         pos = _f64(pos)
         self.n = pos.shape[1]
         self._act = None
@@ -160,9 +209,15 @@ class FMM:
         if active is not None:
             self._act = np.ascontiguousarray(active, dtype=np.uint8)
             ap = self._act.ctypes.data
-        self.h = lib().orc_fmm_create(self.n, pos.reshape(-1), _f64(mass), ap, float(eps), float(theta),
-                                      int(bucket), int(group))
-        self.eps, self.theta, self.bucket, self.group = eps, theta, bucket, group
+        if nrep is None:
+            self.h = lib().orc_fmm_create(self.n, pos.reshape(-1), _f64(mass), ap, float(eps), float(theta),
+                                          int(bucket), int(group))
+        else:
+            self.h = lib().orc_fmm_create_periodic(self.n, pos.reshape(-1), _f64(mass), ap, float(eps),
+                                                   float(theta), int(bucket), int(group), int(nrep))
+            if not self.h:
+                raise ValueError("nrep must be 0, 1 or 2")
+        self.eps, self.theta, self.bucket, self.group, self.nrep = eps, theta, bucket, group, nrep
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -170,7 +225,9 @@ class FMM:
             lib().orc_fmm_free(h)
             self.h = None
 
-    def forces(self, terms=7, fill=0.0):
+    def forces(self, terms=None, fill=0.0):
+        if terms is None:
+            terms = 7 if self.nrep is None else 15
         acc = np.full(3 * self.n, fill)
         pot = np.full(self.n, fill)
         lib().orc_fmm_eval(self.h, int(terms), acc, pot)
@@ -206,6 +263,14 @@ class FMM:
         s, f, c = (np.zeros(n, np.int64) for _ in range(3))
         lib().orc_fmm_entries(self.h, k, s, f, c)
         return s, f, c
+
+    def shifts(self, kind):
+        """The periodic copy of each entry's source (rows (sx, sy, sz)), in the order of entries()."""
+        k = KINDS[kind]
+        n = lib().orc_fmm_nentries(self.h, k)
+        out = np.zeros(3 * n, np.int32)
+        lib().orc_fmm_entry_shifts(self.h, k, out)
+        return out.reshape(n, 3)
 
     def groups(self):
         n = lib().orc_fmm_ngroup(self.h)

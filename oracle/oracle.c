@@ -23,6 +23,11 @@
  *         P2L   L_k  = m D^k G(c - x_j)                       (|k| <= 5)
  *         L2L   L'_k = sum_{|j|<=5-|k|} t^j / j! L_(k+j)
  *         L2P   a_i  = sum_{|k|<=4} u^k / k! L_(k+e_i)
+ *   - Periodic boundaries (Sec. 3.1): orc_direct_periodic, the periodic direct sum in the unit
+ *     box (Ewald summation with a uniform background; the copies inside the replica shell
+ *     softened, as the walk over them is); orc_ewald_derivs, the derivatives to 5th order of the
+ *     correction kernel F = periodic potential less the shell's Newtonian copies; orc_ewald_m2p,
+ *     the correction from a cell's moments.
  *   - orc_fmm_*: a plain recursive FMM (Sec. 3.1): Morton-ordered binary tree
  *     with buckets of <= b particles, exact b_max about the centre of mass,
  *     opening radius R_O = b_max / theta, checklist walk with outcomes
@@ -31,7 +36,9 @@
  *     are taken in single precision (the precision the paper uses for the
  *     interaction work, Sec. 3.1), with a fixed operation order and no fused
  *     multiply-add, so that any implementation following the same order takes
- *     identical decisions.  All force arithmetic is FP64.
+ *     identical decisions.  All force arithmetic is FP64.  orc_fmm_create_periodic starts the
+ *     walk from the root and its 26 (or 124) copies and adds the Ewald correction of the root's
+ *     moments for the copies beyond.
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (oracle/build.py).
  * -ffp-contract=off is required for the single-precision decisions.
@@ -113,23 +120,13 @@ static void monomials(const double u[3], double P[NMI])
 static double herm(int n, int k) { return FACT[n] / (ldexp(1.0, k) * FACT[k] * FACT[n - 2 * k]); }
 
 /*
- * D^n G(r) for |n| <= 5 with G = (r.r + eps2)^(-1/2).
- * G = h(s), s = r.r.  With d_m = 2^m h^(m)(s) = (-1)^m (2m-1)!! R^-(2m+1), R^2 = s + eps2:
- *   D^(a,b,c) G = sum_{i<=a/2, j<=b/2, k<=c/2} H(a,i) H(b,j) H(c,k)
+ * Derivatives of a function of s = r.r.  With h(s) and d_m = 2^m h^(m)(s), the Hermite form
+ *   D^(a,b,c) h = sum_{i<=a/2, j<=b/2, k<=c/2} H(a,i) H(b,j) H(c,k)
  *                 x^(a-2i) y^(b-2j) z^(c-2k) d_(a+b+c-i-j-k)
+ * gives every |n| <= 5.  radial_tensor_acc adds w * D^n h(r) to D.
  */
-void orc_green_derivs(const double r[3], double eps2, double D[NMI])
+static void radial_tensor_acc(const double r[3], const double d[ORD + 1], double w, double D[NMI])
 {
-    double R2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps2;
-    double iR = 1.0 / sqrt(R2), iR2 = iR * iR;
-    double d[ORD + 1];
-    double dfact = 1.0; /* (2m-1)!! */
-    double p = iR;
-    for (int m = 0; m <= ORD; m++) {
-        if (m > 0) dfact *= (2.0 * m - 1.0);
-        d[m] = ((m & 1) ? -1.0 : 1.0) * dfact * p;
-        p *= iR2;
-    }
     double px[ORD + 1], py[ORD + 1], pz[ORD + 1];
     px[0] = py[0] = pz[0] = 1.0;
     for (int k = 1; k <= ORD; k++) {
@@ -145,8 +142,30 @@ void orc_green_derivs(const double r[3], double eps2, double D[NMI])
                 for (int k = 0; 2 * k <= c; k++)
                     s += herm(a, i) * herm(b, j) * herm(c, k) * px[a - 2 * i] * py[b - 2 * j] *
                          pz[c - 2 * k] * d[a + b + c - i - j - k];
-        D[n] = s;
+        D[n] += w * s;
     }
+}
+
+/* G = (s + eps2)^(-1/2): d_m = (-1)^m (2m-1)!! R^-(2m+1), R^2 = s + eps2 (m = 0..mmax) */
+static void plummer_scalars(double R2, int mmax, double *d)
+{
+    double iR = 1.0 / sqrt(R2), iR2 = iR * iR;
+    double dfact = 1.0; /* (2m-1)!! */
+    double p = iR;
+    for (int m = 0; m <= mmax; m++) {
+        if (m > 0) dfact *= (2.0 * m - 1.0);
+        d[m] = ((m & 1) ? -1.0 : 1.0) * dfact * p;
+        p *= iR2;
+    }
+}
+
+/* D^n G(r) for |n| <= 5 with G = (r.r + eps2)^(-1/2) */
+void orc_green_derivs(const double r[3], double eps2, double D[NMI])
+{
+    double d[ORD + 1];
+    plummer_scalars(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + eps2, ORD, d);
+    for (int n = 0; n < NMI; n++) D[n] = 0.0;
+    radial_tensor_acc(r, d, 1.0, D);
 }
 
 /* P2M: M_n = sum_j m_j (x_j - c)^n for |n| <= 4 */
@@ -166,13 +185,10 @@ void orc_p2m(long n, const double *pos /* 3n SoA */, const double *mass, const d
     }
 }
 
-/* M2P: field at x of the moments M about z.  acc += a, *pot += phi */
-static void m2p_acc(const double M[NM4], const double z[3], const double x[3], double eps2, double acc[3],
-                    double *pot)
+/* the field of moments M given the derivatives D of the kernel at r = x - z:
+ *   Phi = sum_n (-1)^|n| / n! M_n D_n,  a_i = sum_n (-1)^|n| / n! M_n D_(n+e_i);  acc += a, *pot -= Phi */
+static void contract_m2p(const double M[NM4], const double D[NMI], double acc[3], double *pot)
 {
-    double r[3] = {x[0] - z[0], x[1] - z[1], x[2] - z[2]};
-    double D[NMI];
-    orc_green_derivs(r, eps2, D);
     double Phi = 0.0, a[3] = {0.0, 0.0, 0.0};
     for (int n = 0; n < NM4; n++) {
         double w = ((order_of(n) & 1) ? -1.0 : 1.0) / mfact(n) * M[n];
@@ -181,6 +197,16 @@ static void m2p_acc(const double M[NM4], const double z[3], const double x[3], d
     }
     for (int q = 0; q < 3; q++) acc[q] += a[q];
     *pot -= Phi;
+}
+
+/* M2P: field at x of the moments M about z */
+static void m2p_acc(const double M[NM4], const double z[3], const double x[3], double eps2, double acc[3],
+                    double *pot)
+{
+    double r[3] = {x[0] - z[0], x[1] - z[1], x[2] - z[2]};
+    double D[NMI];
+    orc_green_derivs(r, eps2, D);
+    contract_m2p(M, D, acc, pot);
 }
 
 void orc_m2p(const double *M, const double z[3], const double x[3], double eps2, double acc[3], double *pot)
@@ -302,25 +328,268 @@ void orc_direct(long n, const double *pos, const double *mass, double eps, long 
 }
 
 /* ------------------------------------------------------------------ */
+/* periodic boundaries (Sec. 3.1): the unit box and its replicas       */
+/* ------------------------------------------------------------------ */
+/*
+ * psi(r): the potential of a unit mass at the origin and at every periodic copy r + n (n integer),
+ * less a uniform background of unit density, with zero mean over the box.  Ewald's split with any
+ * alpha > 0 writes it as
+ *   psi(r) = sum_n erfc(alpha |r+n|) / |r+n|
+ *          + sum_{h != 0} exp(-pi^2 h^2 / alpha^2) / (pi h^2) cos(2 pi h.r)  -  pi / alpha^2.
+ *
+ * The paper gives the method (the root and its 26 or 124 replicas on the checklist, the rest
+ * from a 5th-order multipole approximation of the Ewald sum), not the sum it approximates.
+ * Reading: the copies inside the replica shell N = { n : |n|_inf <= nrep } use the softened
+ * kernel G, as the walk over those replicas does; beyond N the Newtonian Ewald sum applies.
+ * Between a sink and a source at offset r = x_i - x_j the kernel is
+ *   K(r) = sum_{n in N} G(r + n) + F(r),   F(r) = psi(r) - sum_{n in N} 1 / |r + n|
+ * (the n = 0 term of G dropped for the particle itself), and
+ *   phi_i = -sum_j m_j K(x_i - x_j),   a_i = sum_j m_j grad K(x_i - x_j).
+ * F has no singularity for r in (-nrep-1, nrep+1)^3, which holds every offset between two
+ * points of the box.  Functions here take offsets with |r_a| < 1.
+ */
+#define EWALD_CUT 8.0 /* drop real-space copies with alpha |r+n| >= 8 and reciprocal terms with pi |h| / alpha >= 8 */
+
+/* erfc(alpha sqrt(s)) / sqrt(s): d_m = (-1)^m B_m,
+ *   B_0 = erfc(alpha r) / r,  B_m = ((2m-1) B_(m-1) + (2 alpha^2)^m exp(-alpha^2 r^2) / (alpha sqrt(pi))) / r^2
+ * (B_m = (-(1/r) d/dr)^m B_0) */
+static void erfc_scalars(double s, double alpha, int mmax, double *d)
+{
+    double r = sqrt(s);
+    double g = exp(-alpha * alpha * s) / (alpha * sqrt(M_PI));
+    double B = erfc(alpha * r) / r, p = 1.0;
+    d[0] = B;
+    for (int m = 1; m <= mmax; m++) {
+        p *= 2.0 * alpha * alpha;
+        B = ((2.0 * m - 1.0) * B + p * g) / s;
+        d[m] = (m & 1) ? -B : B;
+    }
+}
+
+/* erf(alpha sqrt(s)) / sqrt(s), finite at s = 0.  While alpha^2 s < 2.25 from its power series,
+ *   h(s) = 2 alpha / sqrt(pi) sum_k (-alpha^2 s)^k / (k! (2k+1)),
+ *   h^(m)(s) = 2 alpha / sqrt(pi) sum_{k>=m} (-alpha^2)^k s^(k-m) / ((k-m)! (2k+1)),
+ * else as 1/r less the erfc part. */
+static void erf_scalars(double s, double alpha, int mmax, double *d)
+{
+    double a2 = alpha * alpha;
+    if (a2 * s < 2.25) {
+        double c = 2.0 * alpha / sqrt(M_PI);
+        for (int m = 0; m <= mmax; m++) {
+            double sum = 0.0, t = 1.0; /* t = (-a2 s)^j / j! with j = k - m */
+            for (int j = 0; j < 60; j++) {
+                sum += t / (2.0 * (m + j) + 1.0);
+                t *= -a2 * s / (j + 1.0);
+            }
+            d[m] = c * sum; /* times 2^m (-a2)^m below */
+            for (int q = 0; q < m; q++) d[m] *= -2.0 * a2;
+        }
+        return;
+    }
+    double N[ORD + 1], B[ORD + 1];
+    plummer_scalars(s, mmax, N);
+    erfc_scalars(s, alpha, mmax, B);
+    for (int m = 0; m <= mmax; m++) d[m] = N[m] - B[m];
+}
+
+/* reciprocal vectors of the half space (h and -h together): count, or fill h[3k] and coef[k] =
+ * 2 exp(-pi^2 h^2 / alpha^2) / (pi h^2) */
+static long recip_vectors(double alpha, double *hv, double *coef)
+{
+    int H = (int)ceil(EWALD_CUT * alpha / M_PI);
+    long k = 0;
+    for (int hx = 0; hx <= H; hx++)
+        for (int hy = -H; hy <= H; hy++)
+            for (int hz = -H; hz <= H; hz++) {
+                if (hx == 0 && (hy < 0 || (hy == 0 && hz <= 0))) continue;
+                double h2 = (double)hx * hx + (double)hy * hy + (double)hz * hz;
+                if (M_PI * sqrt(h2) / alpha >= EWALD_CUT) continue;
+                if (hv) {
+                    hv[3 * k] = hx;
+                    hv[3 * k + 1] = hy;
+                    hv[3 * k + 2] = hz;
+                    coef[k] = 2.0 * exp(-M_PI * M_PI * h2 / (alpha * alpha)) / (M_PI * h2);
+                }
+                k++;
+            }
+    return k;
+}
+
+/* range of copies n_a along one axis: the replica shell, and every copy with |r_a + n_a| < cut */
+static void copy_range(double ra, int nrep, double cut, int *lo, int *hi)
+{
+    int a = (int)ceil(-ra - cut), b = (int)floor(-ra + cut);
+    *lo = a < -nrep ? a : -nrep;
+    *hi = b > nrep ? b : nrep;
+}
+
+/* D^n F(r) for |n| <= 5 (F = psi less the Newtonian copies inside the replica shell) */
+void orc_ewald_derivs(const double r[3], int nrep, double alpha, double D[NMI])
+{
+    for (int n = 0; n < NMI; n++) D[n] = 0.0;
+    double d[ORD + 1], cut = EWALD_CUT / alpha;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) copy_range(r[a], nrep, cut, &lo[a], &hi[a]);
+    for (int nx = lo[0]; nx <= hi[0]; nx++)
+        for (int ny = lo[1]; ny <= hi[1]; ny++)
+            for (int nz = lo[2]; nz <= hi[2]; nz++) {
+                double u[3] = {r[0] + nx, r[1] + ny, r[2] + nz};
+                double s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                int in_shell = abs(nx) <= nrep && abs(ny) <= nrep && abs(nz) <= nrep;
+                if (in_shell) {
+                    erf_scalars(s, alpha, ORD, d);
+                    radial_tensor_acc(u, d, -1.0, D);
+                } else if (alpha * sqrt(s) < EWALD_CUT) {
+                    erfc_scalars(s, alpha, ORD, d);
+                    radial_tensor_acc(u, d, 1.0, D);
+                }
+            }
+    long nh = recip_vectors(alpha, NULL, NULL);
+    double *hv = malloc(3 * nh * sizeof(double)), *coef = malloc(nh * sizeof(double));
+    recip_vectors(alpha, hv, coef);
+    for (long k = 0; k < nh; k++) {
+        /* D^n cos(2 pi h.r) = (2 pi h)^n cos(2 pi h.r + |n| pi / 2) */
+        double th = 2.0 * M_PI * (hv[3 * k] * r[0] + hv[3 * k + 1] * r[1] + hv[3 * k + 2] * r[2]);
+        double cs = cos(th), sn = sin(th);
+        double ph[4] = {cs, -sn, -cs, sn};
+        double kx[ORD + 1], ky[ORD + 1], kz[ORD + 1];
+        kx[0] = ky[0] = kz[0] = 1.0;
+        for (int q = 1; q <= ORD; q++) {
+            kx[q] = kx[q - 1] * 2.0 * M_PI * hv[3 * k];
+            ky[q] = ky[q - 1] * 2.0 * M_PI * hv[3 * k + 1];
+            kz[q] = kz[q - 1] * 2.0 * M_PI * hv[3 * k + 2];
+        }
+        for (int n = 0; n < NMI; n++)
+            D[n] += coef[k] * kx[MI[n][0]] * ky[MI[n][1]] * kz[MI[n][2]] * ph[order_of(n) & 3];
+    }
+    free(hv);
+    free(coef);
+    D[0] -= M_PI / (alpha * alpha);
+}
+
+/* the correction for the copies beyond the replica shell, from moments M (|n| <= 4) about z:
+ * the M2P contraction with D^n F(x - z) */
+void orc_ewald_m2p(const double *M, const double z[3], const double x[3], int nrep, double alpha, double acc[3],
+                   double *pot)
+{
+    double r[3] = {x[0] - z[0], x[1] - z[1], x[2] - z[2]}, D[NMI];
+    orc_ewald_derivs(r, nrep, alpha, D);
+    acc[0] = acc[1] = acc[2] = 0.0;
+    *pot = 0.0;
+    contract_m2p(M, D, acc, pot);
+}
+
+/* the periodic direct sum (the reading above): every source, every copy, for each sink.
+ * Reciprocal space through the structure factors C(h) + i S(h) = sum_j m_j exp(2 pi i h.x_j). */
+void orc_direct_periodic(long n, const double *pos, const double *mass, double eps, int nrep, double alpha,
+                         long ns, const long *sinks, double *acc /* 3 ns SoA */, double *pot /* ns */)
+{
+    const double *X = pos, *Y = pos + n, *Z = pos + 2 * n;
+    double eps2 = eps * eps, cut = EWALD_CUT / alpha, mtot = 0.0;
+    for (long j = 0; j < n; j++) mtot += mass[j];
+    long nh = recip_vectors(alpha, NULL, NULL);
+    double *hv = malloc(3 * nh * sizeof(double)), *coef = malloc(nh * sizeof(double));
+    double *Cs = malloc(nh * sizeof(double)), *Sn = malloc(nh * sizeof(double));
+    recip_vectors(alpha, hv, coef);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < nh; k++) {
+        double c = 0.0, sn = 0.0;
+        for (long j = 0; j < n; j++) {
+            double th = 2.0 * M_PI * (hv[3 * k] * X[j] + hv[3 * k + 1] * Y[j] + hv[3 * k + 2] * Z[j]);
+            c += mass[j] * cos(th);
+            sn += mass[j] * sin(th);
+        }
+        Cs[k] = c;
+        Sn[k] = sn;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long q = 0; q < ns; q++) {
+        long i = sinks ? sinks[q] : q;
+        double a[3] = {0, 0, 0}, ph = 0.0, d[2];
+        for (long j = 0; j < n; j++) {
+            double r[3] = {X[i] - X[j], Y[i] - Y[j], Z[i] - Z[j]};
+            int lo[3], hi[3];
+            for (int ax = 0; ax < 3; ax++) copy_range(r[ax], nrep, cut, &lo[ax], &hi[ax]);
+            double kp = 0.0, kg[3] = {0, 0, 0};
+            for (int nx = lo[0]; nx <= hi[0]; nx++)
+                for (int ny = lo[1]; ny <= hi[1]; ny++)
+                    for (int nz = lo[2]; nz <= hi[2]; nz++) {
+                        double u[3] = {r[0] + nx, r[1] + ny, r[2] + nz};
+                        double s = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                        int in_shell = abs(nx) <= nrep && abs(ny) <= nrep && abs(nz) <= nrep;
+                        double w0 = 0.0, w1 = 0.0; /* kernel value and 2 dK/ds */
+                        if (in_shell) {
+                            if (!(j == i && nx == 0 && ny == 0 && nz == 0)) {
+                                plummer_scalars(s + eps2, 1, d);
+                                w0 += d[0];
+                                w1 += d[1];
+                            }
+                            erf_scalars(s, alpha, 1, d);
+                            w0 -= d[0];
+                            w1 -= d[1];
+                        } else if (alpha * sqrt(s) < EWALD_CUT) {
+                            erfc_scalars(s, alpha, 1, d);
+                            w0 += d[0];
+                            w1 += d[1];
+                        }
+                        kp += w0;
+                        for (int ax = 0; ax < 3; ax++) kg[ax] += w1 * u[ax];
+                    }
+            ph -= mass[j] * kp;
+            for (int ax = 0; ax < 3; ax++) a[ax] += mass[j] * kg[ax];
+        }
+        for (long k = 0; k < nh; k++) {
+            double th = 2.0 * M_PI * (hv[3 * k] * X[i] + hv[3 * k + 1] * Y[i] + hv[3 * k + 2] * Z[i]);
+            double cs = cos(th), sn = sin(th);
+            /* sum_j m_j cos(th_i - th_j) and sum_j m_j sin(th_i - th_j) */
+            double cd = cs * Cs[k] + sn * Sn[k], sd = sn * Cs[k] - cs * Sn[k];
+            ph -= coef[k] * cd;
+            for (int ax = 0; ax < 3; ax++) a[ax] -= coef[k] * 2.0 * M_PI * hv[3 * k + ax] * sd;
+        }
+        ph += mtot * M_PI / (alpha * alpha);
+        acc[q] = a[0];
+        acc[ns + q] = a[1];
+        acc[2 * ns + q] = a[2];
+        pot[q] = ph;
+    }
+    free(hv);
+    free(coef);
+    free(Cs);
+    free(Sn);
+}
+
+/* ------------------------------------------------------------------ */
 /* plain FMM                                                           */
 /* ------------------------------------------------------------------ */
 enum { K_PP = 0, K_PC = 1, K_CC = 2, K_CP = 3 };
 enum { O_ACCEPT = 1, O_DEFER = 2, O_PC = 3, O_PP = 4, O_OPEN = 5 };
 
+/* a checklist entry: a cell or a particle, in the box (sh = 0) or in the periodic copy shifted by sh */
 typedef struct {
     long id;
     int particle;
+    int sh[3];
 } entry;
 
 typedef struct {
     long *sink, *first, *count, *cell; /* cell = source cell id, -1 for a particle entry */
+    int *shift;                        /* the copy: (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), |s| <= 2 */
     long n, cap;
 } elist;
+
+static int shift_code(const int sh[3]) { return (sh[0] + 2) * 25 + (sh[1] + 2) * 5 + (sh[2] + 2); }
+static void shift_of(int code, double v[3])
+{
+    v[0] = code / 25 - 2;
+    v[1] = (code / 5) % 5 - 2;
+    v[2] = code % 5 - 2;
+}
 
 typedef struct {
     long n;
     int b, g;
     double eps, theta;
+    int nrep; /* periodic: the root's copies |n|_inf <= nrep start the walk; -1 for an isolated box */
     long *perm;
     uint64_t *key;
     double *X, *Y, *Z, *m;
@@ -339,7 +608,7 @@ typedef struct {
     int status;
 } orc_fmm;
 
-static void elist_push(elist *l, long sink, long first, long count, long cell)
+static void elist_push(elist *l, long sink, long first, long count, long cell, const int sh[3])
 {
     if (l->n == l->cap) {
         l->cap = l->cap ? 2 * l->cap : 1024;
@@ -347,11 +616,13 @@ static void elist_push(elist *l, long sink, long first, long count, long cell)
         l->first = realloc(l->first, l->cap * sizeof(long));
         l->count = realloc(l->count, l->cap * sizeof(long));
         l->cell = realloc(l->cell, l->cap * sizeof(long));
+        l->shift = realloc(l->shift, l->cap * sizeof(int));
     }
     l->sink[l->n] = sink;
     l->first[l->n] = first;
     l->count[l->n] = count;
     l->cell[l->n] = cell;
+    l->shift[l->n] = shift_code(sh);
     l->n++;
 }
 
@@ -470,7 +741,8 @@ static void cell_props(orc_fmm *t, long c)
     t->rof[c] = (cnt == 1) ? 0.0f : t->bmaxf[c] / (float)t->theta;
 }
 
-/* geometry of a checklist entry, single precision */
+/* geometry of a checklist entry, single precision; a copy's coordinates are shifted in double
+ * precision and then rounded */
 typedef struct {
     float c[3], lo[3], hi[3], ro;
     int pointlike, leaf;
@@ -479,7 +751,7 @@ typedef struct {
 static void entry_geom(const orc_fmm *t, entry e, sgeom *s)
 {
     if (e.particle) {
-        float p[3] = {(float)t->X[e.id], (float)t->Y[e.id], (float)t->Z[e.id]};
+        float p[3] = {(float)(t->X[e.id] + e.sh[0]), (float)(t->Y[e.id] + e.sh[1]), (float)(t->Z[e.id] + e.sh[2])};
         for (int a = 0; a < 3; a++) s->c[a] = s->lo[a] = s->hi[a] = p[a];
         s->ro = 0.0f;
         s->pointlike = 1;
@@ -487,9 +759,15 @@ static void entry_geom(const orc_fmm *t, entry e, sgeom *s)
     } else {
         long c = e.id;
         for (int a = 0; a < 3; a++) {
-            s->c[a] = t->comf[3 * c + a];
-            s->lo[a] = t->lof[3 * c + a];
-            s->hi[a] = t->hif[3 * c + a];
+            if (e.sh[a] == 0) {
+                s->c[a] = t->comf[3 * c + a];
+                s->lo[a] = t->lof[3 * c + a];
+                s->hi[a] = t->hif[3 * c + a];
+            } else {
+                s->c[a] = (float)(t->com[3 * c + a] + e.sh[a]);
+                s->lo[a] = (float)(t->lo[3 * c + a] + e.sh[a]);
+                s->hi[a] = (float)(t->hi[3 * c + a] + e.sh[a]);
+            }
         }
         s->ro = t->rof[c];
         s->pointlike = (t->count[c] == 1);
@@ -585,12 +863,14 @@ static void walk(orc_fmm *t, long k, const entry *cl, long ncl, const double *Lp
         switch (o) {
         case O_ACCEPT:
             if (s.pointlike) {
-                double xs[3] = {t->X[sf], t->Y[sf], t->Z[sf]};
+                double xs[3] = {t->X[sf] + e.sh[0], t->Y[sf] + e.sh[1], t->Z[sf] + e.sh[2]};
                 p2l_acc(t->m[sf], xs, ck, eps2, L);
-                elist_push(&t->lists[K_CP], k, sf, 1, e.particle ? -1 : e.id);
+                elist_push(&t->lists[K_CP], k, sf, 1, e.particle ? -1 : e.id, e.sh);
             } else {
-                m2l_acc(t->mom + NM4 * e.id, t->com + 3 * e.id, ck, eps2, L);
-                elist_push(&t->lists[K_CC], k, sf, sn, e.id);
+                const double *cs = t->com + 3 * e.id;
+                double zs[3] = {cs[0] + e.sh[0], cs[1] + e.sh[1], cs[2] + e.sh[2]};
+                m2l_acc(t->mom + NM4 * e.id, zs, ck, eps2, L);
+                elist_push(&t->lists[K_CC], k, sf, sn, e.id, e.sh);
             }
             break;
         case O_DEFER:
@@ -601,10 +881,10 @@ static void walk(orc_fmm *t, long k, const entry *cl, long ncl, const double *Lp
             def[nd++] = e;
             break;
         case O_PC:
-            elist_push(&t->lists[K_PC], k, sf, sn, e.id);
+            elist_push(&t->lists[K_PC], k, sf, sn, e.id, e.sh);
             break;
         case O_PP:
-            elist_push(&t->lists[K_PP], k, sf, sn, e.particle ? -1 : e.id);
+            elist_push(&t->lists[K_PP], k, sf, sn, e.particle ? -1 : e.id, e.sh);
             break;
         case O_OPEN: {
             long c = e.id;
@@ -613,18 +893,20 @@ static void walk(orc_fmm *t, long k, const entry *cl, long ncl, const double *Lp
                 while (nq + add > cap) cap *= 2;
                 q = realloc(q, cap * sizeof(entry));
             }
+            /* the children (or a leaf's particles) stay in the same copy */
             if (t->count[c] <= t->b) {
                 for (long j = 0; j < t->count[c]; j++) {
+                    q[nq] = e;
                     q[nq].id = t->first[c] + j;
                     q[nq].particle = 1;
                     nq++;
                 }
             } else {
+                q[nq] = e;
                 q[nq].id = t->child[2 * c];
-                q[nq].particle = 0;
                 nq++;
+                q[nq] = e;
                 q[nq].id = t->child[2 * c + 1];
-                q[nq].particle = 0;
                 nq++;
             }
         } break;
@@ -644,8 +926,8 @@ static void walk(orc_fmm *t, long k, const entry *cl, long ncl, const double *Lp
 
 void orc_fmm_free(orc_fmm *t);
 
-orc_fmm *orc_fmm_create(long n, const double *pos, const double *mass, const unsigned char *active, double eps,
-                        double theta, int b, int g)
+static orc_fmm *fmm_create(long n, const double *pos, const double *mass, const unsigned char *active, double eps,
+                          double theta, int b, int g, int nrep)
 {
     if (!tables_ready) make_tables();
     orc_fmm *t = calloc(1, sizeof(orc_fmm));
@@ -654,6 +936,7 @@ orc_fmm *orc_fmm_create(long n, const double *pos, const double *mass, const uns
     t->g = g;
     t->eps = eps;
     t->theta = theta;
+    t->nrep = nrep;
     if (n <= 0) return t;
     t->key = malloc(n * sizeof(uint64_t));
     t->perm = malloc(n * sizeof(long));
@@ -702,13 +985,39 @@ orc_fmm *orc_fmm_create(long n, const double *pos, const double *mass, const uns
 #pragma omp parallel for schedule(dynamic, 64)
     for (long c = 0; c < nc; c++) cell_props(t, c);
     if (t->nact[0] > 0) {
-        entry root = {0, 0};
-        walk(t, 0, &root, 1, NULL, -1);
+        /* the checklist starts with the root, and in a periodic box with its copies of the shell */
+        int R = nrep > 0 ? nrep : 0;
+        long ne = 0;
+        entry *cl = malloc((2 * R + 1) * (2 * R + 1) * (2 * R + 1) * sizeof(entry));
+        for (int sx = -R; sx <= R; sx++)
+            for (int sy = -R; sy <= R; sy++)
+                for (int sz = -R; sz <= R; sz++) {
+                    entry e = {0, 0, {sx, sy, sz}};
+                    cl[ne++] = e;
+                }
+        walk(t, 0, cl, ne, NULL, -1);
+        free(cl);
     }
     return t;
 }
 
-/* evaluate the lists: terms bit 1 = PP, 2 = PC, 4 = local expansion (CC+CP).
+orc_fmm *orc_fmm_create(long n, const double *pos, const double *mass, const unsigned char *active, double eps,
+                        double theta, int b, int g)
+{
+    return fmm_create(n, pos, mass, active, eps, theta, b, g, -1);
+}
+
+/* periodic unit box (Sec. 3.1): the walk starts from the root and its copies |n|_inf <= nrep
+ * (26 copies for nrep = 1, 124 for nrep = 2); the copies beyond come from the Ewald correction */
+orc_fmm *orc_fmm_create_periodic(long n, const double *pos, const double *mass, const unsigned char *active,
+                                 double eps, double theta, int b, int g, int nrep)
+{
+    if (nrep < 0 || nrep > 2) return NULL;
+    return fmm_create(n, pos, mass, active, eps, theta, b, g, nrep);
+}
+
+/* evaluate the lists: terms bit 1 = PP, 2 = PC, 4 = local expansion (CC+CP), 8 = the Ewald correction
+ * of a periodic box (the root's moments, 5th order).
  * acc (3n SoA) and pot (n) in the caller's original order; inactive particles untouched. */
 int orc_fmm_eval(orc_fmm *t, int terms, double *acc, double *pot)
 {
@@ -726,9 +1035,13 @@ int orc_fmm_eval(orc_fmm *t, int terms, double *acc, double *pot)
             if (terms & 1) {
                 for (long e = seg[0]; e < seg[1]; e++) {
                     long f = t->lists[K_PP].first[e], c = t->lists[K_PP].count[e];
+                    double sv[3];
+                    shift_of(t->lists[K_PP].shift[e], sv);
+                    int same = sv[0] == 0.0 && sv[1] == 0.0 && sv[2] == 0.0;
                     for (long j = f; j < f + c; j++) {
-                        if (j == i) continue;
-                        double dx = t->X[j] - xi[0], dy = t->Y[j] - xi[1], dz = t->Z[j] - xi[2];
+                        if (j == i && same) continue;
+                        double dx = (t->X[j] + sv[0]) - xi[0], dy = (t->Y[j] + sv[1]) - xi[1],
+                               dz = (t->Z[j] + sv[2]) - xi[2];
                         double R2 = dx * dx + dy * dy + dz * dz + eps2;
                         double iR = 1.0 / sqrt(R2);
                         double miR = t->m[j] * iR, miR3 = miR * iR * iR;
@@ -742,12 +1055,22 @@ int orc_fmm_eval(orc_fmm *t, int terms, double *acc, double *pot)
             if (terms & 2) {
                 for (long e = seg[2]; e < seg[3]; e++) {
                     long s = t->lists[K_PC].cell[e];
-                    m2p_acc(t->mom + NM4 * s, t->com + 3 * s, xi, eps2, a, &ph);
+                    double sv[3];
+                    shift_of(t->lists[K_PC].shift[e], sv);
+                    const double *cs = t->com + 3 * s;
+                    double zs[3] = {cs[0] + sv[0], cs[1] + sv[1], cs[2] + sv[2]};
+                    m2p_acc(t->mom + NM4 * s, zs, xi, eps2, a, &ph);
                 }
             }
             if (terms & 4) {
                 double u[3] = {xi[0] - t->com[3 * k], xi[1] - t->com[3 * k + 1], xi[2] - t->com[3 * k + 2]};
                 l2p_acc(L, u, a, &ph);
+            }
+            if ((terms & 8) && t->nrep >= 0) {
+                double ea[3], ep;
+                orc_ewald_m2p(t->mom, t->com, xi, t->nrep, 3.0, ea, &ep);
+                for (int q = 0; q < 3; q++) a[q] += ea[q];
+                ph += ep;
             }
             long p = t->perm[i];
             acc[p] = a[0];
@@ -789,6 +1112,17 @@ void orc_fmm_entries(const orc_fmm *t, int kind, long *sink, long *first, long *
     memcpy(sink, l->sink, l->n * sizeof(long));
     memcpy(first, l->first, l->n * sizeof(long));
     memcpy(count, l->count, l->n * sizeof(long));
+}
+
+/* the copy of each entry's source, as (sx, sy, sz) triples */
+void orc_fmm_entry_shifts(const orc_fmm *t, int kind, int *out)
+{
+    const elist *l = &t->lists[kind];
+    for (long e = 0; e < l->n; e++) {
+        double v[3];
+        shift_of(l->shift[e], v);
+        for (int a = 0; a < 3; a++) out[3 * e + a] = (int)v[a];
+    }
 }
 
 void orc_fmm_groups(const orc_fmm *t, long *cell, double *L)
@@ -834,6 +1168,7 @@ void orc_fmm_free(orc_fmm *t)
         free(t->lists[k].first);
         free(t->lists[k].count);
         free(t->lists[k].cell);
+        free(t->lists[k].shift);
     }
     free(t);
 }
