@@ -421,9 +421,9 @@ class Learned(Box):
     Set-up, outside the timed region: the network is trained on the GPU from audit walks of
     the 4096-particle box, the 128^3 NFW box and two boxes of the 64-box batch (labels are the
     method's own cell-cell errors, normalised by each particle's acceleration from a theta = 0.3
-    solve).  The judge of force error is an FMM solve at theta = 0.25 with the FP64 combine,
+    solve).  The reference for the force error is an FMM solve at theta = 0.25 with the FP64 combine,
     restricted to 65,536 random sinks (an active subset, so it costs little); the tests pin that
-    judge against the FP64 direct sum.  The budget tau of the network is searched until its rms
+    reference against the FP64 direct sum.  The budget tau of the network is searched until its rms
     error matches the fixed criterion's, then both are timed.  A step is one learned solve."""
 
     N_SINKS = 65536
@@ -473,7 +473,7 @@ class Learned(Box):
         ctx.set_params(criterion=1, mlp_tau=self.tau)
         self.config = dict(self.config, criterion="learned", tau=self.tau)
         self.learned = {
-            "judge": "FMM at theta=0.25 with FP64 combine on 65,536 random sinks (pinned against the FP64 "
+            "error_reference": "FMM at theta=0.25 with FP64 combine on 65,536 random sinks (pinned against the FP64 "
                      "direct sum in the tests)",
             "train_pairs": self.train_pairs, "train_loss": self.train_loss,
             "fixed": {"theta": self.theta, "rms_err": e_fixed, "ms_per_solve": t_fixed,

@@ -7,7 +7,7 @@ shares no code with the CUDA path (``oracle.c`` is compiled on its own by
 
 Python view of the C oracle:
 
-* :func:`direct`      -- softened O(N^2) direct sum (Sec. 2 / Sec. 3.1), the judge.
+* :func:`direct`      -- softened O(N^2) direct sum (Sec. 2 / Sec. 3.1), the accuracy reference.
 * :func:`green_derivs`, :func:`p2m`, :func:`m2p`, :func:`m2l`, :func:`p2l`,
   :func:`l2l`, :func:`l2p` -- the expansion operators of Sec. 3.1 (moments to
   order 4, local expansion to order 5), in multi-index form.

@@ -198,7 +198,7 @@ def test_learned_criterion_gain_at_equal_error(ctx):
     """Train on audits of two sets, then on a third set compare the fixed-theta curve
     (theta -> rms error, flops) with the learned curve (tau -> rms error, flops): the flops of each
     at the rms error of theta = 0.55, interpolated in log-log.  The learned solve must meet the
-    accuracy target; the measured gain is printed (the judge of error is the FP64 direct sum)."""
+    accuracy target; the measured gain is printed (the error reference is the FP64 direct sum)."""
     eps = 1e-3
     ftr, ltr = _training_set(ctx, [71, 72], 16000, eps, 0.55)
     ctx.mlp_train(ftr, ltr, epochs=25, batch=256, lr=2e-3, seed=3)

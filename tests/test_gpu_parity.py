@@ -292,10 +292,10 @@ def test_fp64_combine_option(ctx):
         ctx.set_params(accumulate=2)
 
 
-def test_tight_theta_judge_against_direct_sum(ctx):
-    """The error judge of the learned-criterion benchmark -- an FMM solve at theta = 0.25 with
-    the FP64 combine, restricted to the judged sinks -- against the FP64 direct sum, on the
-    full-size 128^3 NFW box: its own error must be far below the 1e-4 errors it judges."""
+def test_tight_theta_reference_against_direct_sum(ctx):
+    """The error reference of the learned-criterion benchmark -- an FMM solve at theta = 0.25 with
+    the FP64 combine, restricted to the sampled sinks -- against the FP64 direct sum, on the
+    full-size 128^3 NFW box: its own error must be far below the 1e-4 errors it measures."""
     n = 128 ** 3
     pos, mass = synth.clustered_nfw(n, 2)
     eps = synth.paper_softening(n)
@@ -309,7 +309,7 @@ def test_tight_theta_judge_against_direct_sum(ctx):
         ctx.set_params(accumulate=0)
     ref, _ = oracle.direct(pos, mass, eps, sinks)
     e = rel_err(a[:, sinks], ref)
-    print(f"\njudge theta=0.25: rms {rms(e):.3e} max {e.max():.3e}")
+    print(f"\nreference theta=0.25: rms {rms(e):.3e} max {e.max():.3e}")
     # measured: rms 9.7e-7, max 7.0e-6
     assert rms(e) <= 3e-6 and e.max() <= 3e-5, (rms(e), e.max())
 
