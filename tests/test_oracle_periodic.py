@@ -333,3 +333,25 @@ def test_periodic_fmm_rejects_a_shell_out_of_range():
     pos, m = synth.clustered_plummer(50, 12)
     with pytest.raises(ValueError):
         oracle.FMM(pos, m, 1e-3, 0.55, nrep=3)
+
+
+def test_ewald_correction_is_a_low_degree_polynomial_on_sub_cubes():
+    """The correction field of the root's moments is smooth across the box (its nearest singularity
+    lies >= 1 outside): on a sub-cube of side 1/4 the best degree-5 polynomial reproduces its force
+    to 1e-6 of its size, which is what a grid of order-5 local expansions relies on."""
+    import itertools
+
+    pos, m = synth.clustered_plummer(1000, 13)
+    z = (pos * m).sum(axis=1) / m.sum()
+    M = oracle.p2m(pos, m, z)
+    exps = [e for e in itertools.product(range(6), repeat=3) if sum(e) <= 5]
+    rng = np.random.default_rng(14)
+    h = 0.25
+    c = np.array([0.125, 0.125, 0.875])  # a corner sub-cube, the farthest from the centre of mass
+    X = c + (rng.random((150, 3)) - 0.5) * h
+    acc = np.array([oracle.ewald_m2p(M, z, x)[0] for x in X])
+    A = np.array([[np.prod(((x - c) / h) ** np.array(e)) for e in exps] for x in X])
+    scale = np.max(np.linalg.norm(acc, axis=1))
+    for q in range(3):
+        coef, *_ = np.linalg.lstsq(A, acc[:, q], rcond=None)
+        assert np.max(np.abs(acc[:, q] - A @ coef)) < 1e-6 * scale
