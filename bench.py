@@ -12,6 +12,10 @@ larger than L2 for the tree-build phase and every step rebuilds the tree from th
 positions, so no state is reused across steps.  ``e2e`` repeats the measurement through
 fmm_compute_forces_host with host buffers (copies inside the timed region).
 
+With the CPU baseline (rank 0, one GPU), ``force_error`` reports one more, untimed solve of
+the synthetic input against the oracle's FP64 direct sum at 1024 random sinks (rms,
+nearest-rank 99th percentile, maximum of the relative error).
+
 ``--impl reference`` times the CPU oracle (plain FP64 FMM, OpenMP) on a bounded sample of
 the same workload and prints the same JSON line with "impl": "reference".
 
@@ -170,6 +174,23 @@ def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
             "seconds": dt}
 
 
+def force_error(pos, mass, eps, acc, nsinks=1024, seed=7):
+    """Relative force error |a - a_ref| / |a_ref| of a solve's accelerations acc (3, N) against
+    the oracle's FP64 direct sum at random sinks: rms, nearest-rank 99th percentile and maximum."""
+    import oracle
+
+    n = mass.size
+    sinks = np.sort(np.random.default_rng(seed).choice(n, min(nsinks, n), replace=False))
+    t0 = time.perf_counter()
+    ref, _ = oracle.direct(pos, mass, eps, sinks)
+    dt = time.perf_counter() - t0
+    e = np.sort(np.linalg.norm(np.asarray(acc, np.float64)[:, sinks] - ref, axis=0) / np.linalg.norm(ref, axis=0))
+    return {"rms": float(np.sqrt(np.mean(e * e))), "p99": float(e[int(np.ceil(0.99 * e.size)) - 1]),
+            "max": float(e[-1]), "sinks": int(sinks.size),
+            "reference": "FP64 direct sum (oracle) of the synthetic input, %.1f s on %d threads"
+                         % (dt, oracle.num_threads())}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as it stands, timed on the host cores on bounded samples of the workload."""
     if rank != 0:
@@ -268,6 +289,16 @@ class Box:
 
     def cpu_sample(self, frac):
         return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac)
+
+    def force_error(self, nsinks=1024):
+        """One more solve, outside the timed region, of the synthetic input as generated (the timed
+        steps drift the particles), checked against the FP64 direct sum at random sinks."""
+        import torch
+
+        tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
+        acc = torch.zeros_like(self.acc)
+        self.ctx.compute_forces(tpos, self.tmass, self.eps, self.theta, acc, None)
+        return force_error(self.pos, self.mass, self.eps, acc.cpu().numpy().reshape(3, self.n), nsinks)
 
 
 class Batch:
@@ -427,6 +458,7 @@ class Learned(Box):
     error matches the fixed criterion's, then both are timed.  A step is one learned solve."""
 
     N_SINKS = 65536
+    force_error = None  # the line's "learned" entry reports both criteria's errors against the reference
 
     def __init__(self, args, rank, dev, ctx):
         import torch
@@ -678,6 +710,12 @@ def main():
                            "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in wl.cpu_sample(args.cpu_sample).items() if k != "seconds"}
+        fe = getattr(wl, "force_error", None)
+        if fe is not None:
+            try:
+                line["force_error"] = fe()
+            except Exception as ex:  # the accuracy report is auxiliary: keep the line
+                line["force_error"] = {"error": repr(ex)}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
