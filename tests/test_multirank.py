@@ -37,7 +37,7 @@ def _rank_main(rank, world, port, out):
 def test_two_gloo_ranks_aggregate_and_get_distinct_boxes():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork: earlier tests may have started OpenMP threads
         out = m.dict()
         mp.start_processes(_rank_main, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
