@@ -14,7 +14,13 @@
  *     particles;
  *   - PP, PC and local-expansion (order 5) evaluation for each group (Sec. 3.1,
  *     Sec. 3.3);
- *   - kick-drift-kick on individual time-step rungs (Sec. 3.2).
+ *   - kick-drift-kick on individual time-step rungs (Sec. 3.2), with dual trees
+ *     for the substeps: a tree of the slow rungs kept over their interval and
+ *     a tree of the other particles per substep (Sec. 3.2);
+ *   - independent boxes solved together in one pass, CUDA-graph replay of the
+ *     solve and an autotuner of bucket, group and work-item size;
+ *   - an opening criterion learned by a small network trained on the GPU (not
+ *     in the paper; it replaces the fixed-theta test of Sec. 3.1 inside a band).
  *
  * Physics conventions (all entry points): G = 1, Plummer softening,
  *     a_i   =  sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2)
