@@ -63,6 +63,35 @@ def test_direct_two_body_newton():
     assert pot[1] == pytest.approx(-2.0 / math.sqrt(d * d + eps * eps), rel=1e-14)
 
 
+@pytest.mark.parametrize("n", [3, 5, 8])
+def test_direct_tiny_n_against_extended_precision(n):
+    """N <= 8 summed term by term in 40-digit arithmetic: the FP64 sums agree to a few ulp."""
+    mpmath = pytest.importorskip("mpmath")
+    rng = np.random.default_rng(100 + n)
+    pos = rng.random((3, n))
+    mass = 0.2 + rng.random(n)
+    eps = 0.01
+    acc, pot = oracle.direct(pos, mass, eps)
+    with mpmath.workdps(40):
+        P = [[mpmath.mpf(float(v)) for v in row] for row in pos]
+        M = [mpmath.mpf(float(v)) for v in mass]
+        e2 = mpmath.mpf(eps) ** 2
+        for i in range(n):
+            a = [mpmath.mpf(0)] * 3
+            ph = mpmath.mpf(0)
+            for j in range(n):
+                if j == i:
+                    continue
+                d = [P[q][j] - P[q][i] for q in range(3)]
+                R = mpmath.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2 + e2)
+                for q in range(3):
+                    a[q] += M[j] * d[q] / R ** 3
+                ph -= M[j] / R
+            for q in range(3):
+                assert acc[q, i] == pytest.approx(float(a[q]), rel=1e-14, abs=1e-14 * float(mpmath.fabs(ph)))
+            assert pot[i] == pytest.approx(float(ph), rel=1e-15)
+
+
 def test_direct_momentum_translation_linearity_scaling():
     pos, mass = synth.clustered_plummer(600, 5)
     mass = mass.astype(np.float64) * (1 + np.arange(600) % 3)
