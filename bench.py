@@ -359,6 +359,22 @@ class Batch:
         p, m = self.boxes[b]
         return cpu_baseline(p, m, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / m.size))
 
+    def force_error(self, nsinks=1024):
+        """One more batched solve of the boxes as generated, outside the timed region; the largest
+        box is checked against its own FP64 direct sum at random sinks (the boxes are independent)."""
+        import torch
+
+        tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
+        acc = torch.zeros_like(self.acc)
+        pot = torch.zeros_like(self.pot)
+        self.ctx.compute_forces_batch(tpos, self.tmass, self.off, self.eps, self.theta, acc, pot)
+        b = int(np.argmax(np.diff(self.off)))
+        p, m = self.boxes[b]
+        a = acc.cpu().numpy().reshape(3, self.n)[:, int(self.off[b]):int(self.off[b + 1])]
+        r = force_error(p, m, self.eps, a, nsinks)
+        r["box"] = b
+        return r
+
 
 def dual_role(t, max_rung, fixed_rung):
     """Role of the force solve at substep t (counted from the run's start) under dual trees
@@ -443,6 +459,17 @@ class Rungs:
 
     def cpu_sample(self, frac):
         return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / self.n))
+
+    def force_error(self, nsinks=512):
+        """One more solve of the box as generated (every particle active), outside the timed region,
+        against the FP64 direct sum at random sinks (512: the direct sum over 16.8M sources is the
+        cost)."""
+        import torch
+
+        tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
+        acc = torch.zeros_like(self.acc)
+        self.ctx.compute_forces(tpos, self.tmass, self.eps, self.theta, acc, None)
+        return force_error(self.pos, self.mass, self.eps, acc.cpu().numpy().reshape(3, self.n), nsinks)
 
 
 class Learned(Box):

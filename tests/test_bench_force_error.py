@@ -2,10 +2,13 @@
 rms, nearest-rank 99th percentile and maximum.  Checked on the CPU with accelerations of known
 error, built from the oracle's own direct sum."""
 import numpy as np
+import pytest
 
 import bench
 import oracle
 from paper_1609_08621_gb300 import synth
+
+torch = pytest.importorskip("torch")
 
 
 def _with_errors(ref, rel, seed=1):
@@ -41,3 +44,43 @@ def test_force_error_samples_distinct_sinks():
     assert r["sinks"] == 400
     # a sample of distinct sinks from both halves: rms between the extremes, max at the carried error
     assert 1e-3 < r["rms"] < 1e-2 and abs(r["max"] - 1e-2) < 1e-12
+
+
+class _ExactCtx:
+    """Stands in for the library with exact answers: acc is the oracle's direct sum of the given
+    positions (per box for a batch), rounded to FP32.  A correct force_error then reports only that
+    rounding; a wrong box, slice or layout reports errors of order one."""
+
+    def compute_forces(self, tpos, tmass, eps, theta, acc, pot=None, active=None):
+        a, _ = oracle.direct(tpos.numpy().reshape(3, -1), tmass.numpy(), eps)
+        acc.copy_(torch.from_numpy(a.reshape(-1).astype(np.float32)))
+
+    def compute_forces_batch(self, tpos, tmass, off, eps, theta, acc, pot):
+        pos, m = tpos.numpy().reshape(3, -1), tmass.numpy()
+        out = np.zeros_like(pos)
+        for b in range(len(off) - 1):
+            sl = slice(int(off[b]), int(off[b + 1]))
+            out[:, sl] = oracle.direct(pos[:, sl], m[sl], eps)[0]
+        acc.copy_(torch.from_numpy(out.reshape(-1).astype(np.float32)))
+
+
+def test_workload_force_error_slices_and_layouts():
+    from types import SimpleNamespace
+
+    t = torch
+    eps = 1e-3
+    boxes = [synth.clustered_plummer(n, 20 + n) for n in (300, 900, 500)]
+    off = np.concatenate([[0], np.cumsum([b[1].size for b in boxes])])
+    pos = np.concatenate([b[0] for b in boxes], axis=1)
+    mass = np.concatenate([b[1] for b in boxes])
+    n = mass.size
+    w = SimpleNamespace(ctx=_ExactCtx(), dev="cpu", pos=pos, mass=mass, boxes=boxes, off=off, n=n, eps=eps,
+                        theta=0.7, tmass=t.from_numpy(mass), acc=t.zeros(3 * n, dtype=t.float32),
+                        pot=t.zeros(n, dtype=t.float32))
+    r = bench.Batch.force_error(w, nsinks=200)
+    assert r["box"] == 1 and r["sinks"] == 200 and r["max"] < 1e-6
+    one = SimpleNamespace(ctx=_ExactCtx(), dev="cpu", pos=boxes[0][0], mass=boxes[0][1], n=300, eps=eps,
+                          theta=0.7, tmass=t.from_numpy(boxes[0][1]), acc=t.zeros(900, dtype=t.float32))
+    for cls in (bench.Box, bench.Rungs):
+        r = cls.force_error(one, nsinks=100)
+        assert r["sinks"] == 100 and r["max"] < 1e-6
