@@ -13,8 +13,9 @@ positions, so no state is reused across steps.  ``e2e`` repeats the measurement 
 fmm_compute_forces_host with host buffers (copies inside the timed region).
 
 With the CPU baseline (rank 0, one GPU), ``force_error`` reports one more, untimed solve of
-the synthetic input against the oracle's FP64 direct sum at 1024 random sinks (rms,
-nearest-rank 99th percentile, maximum of the relative error).
+the synthetic input against the oracle's FP64 direct sum at random sinks (rms, nearest-rank
+99th percentile, maximum of the relative error); the learned workload reports its errors in its
+"learned" entry instead.
 
 ``--impl reference`` times the CPU oracle (plain FP64 FMM, OpenMP) on a bounded sample of
 the same workload and prints the same JSON line with "impl": "reference".
