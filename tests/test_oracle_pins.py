@@ -410,6 +410,57 @@ def test_fmm_tree_invariants():
         assert cl["bmax"][c] == pytest.approx(d, rel=1e-12, abs=1e-300)
 
 
+@pytest.mark.parametrize("theta", [0.4, 0.7])
+def test_fmm_lists_satisfy_the_opening_rule(theta):
+    """Every list entry against the rule that produced it (Sec. 3.1, R4), re-checked in FP64 from
+    the tree's own geometry: CC/CP entries pass the acceptance test; PC entries fail it and have
+    every sink particle outside the source's opening sphere; PP entries fail both (or are
+    point-like sources).  Decisions are taken in FP32, so comparisons allow a relative 1e-5."""
+    pos, mass = synth.clustered_plummer(3000, 15)
+    eps, b, g = 1e-3, 16, 64
+    f = oracle.FMM(pos, mass, eps, theta, bucket=b, group=g)
+    cl = f.cells()
+    first, count, com, lo, hi, bmax = cl["first"], cl["count"], cl["com"], cl["lo"], cl["hi"], cl["bmax"]
+    cell_of = {(int(a), int(c)): i for i, (a, c) in enumerate(zip(first, count))}
+    ro = np.where(count == 1, 0.0, bmax / theta)
+    sp = pos[:, f.perm()]
+    tol = 1e-5
+
+    def source(fi, ci):
+        """(centre, lo, hi, R_O, b_max, point-like) of an entry's source: a cell, or one particle."""
+        c = cell_of.get((fi, ci)) if ci > 1 or (fi, ci) in cell_of else None
+        if ci == 1:
+            x = sp[:, fi]
+            return x, x, x, 0.0, 0.0, True
+        return com[c], lo[c], hi[c], ro[c], bmax[c], False
+
+    def accepted(k, src):
+        x, slo, shi, sro, _, _ = src
+        d = np.linalg.norm(com[k] - x)
+        gap = np.linalg.norm(np.maximum(np.maximum(slo - hi[k], lo[k] - shi), 0.0))
+        return d, gap, d > (1.5 * ro[k] + sro) * (1 - tol) and gap >= 2 * eps * (1 - tol), \
+            d <= (1.5 * ro[k] + sro) * (1 + tol) or gap < 2 * eps * (1 + tol)
+
+    for kind in ("cc", "cp"):
+        sink, fi, ci = f.entries(kind)
+        for k, a, c in zip(sink, fi, ci):
+            _, _, ok, _ = accepted(k, source(int(a), int(c)))
+            assert ok, (kind, k, a, c)
+    for kind in ("pc", "pp"):
+        sink, fi, ci = f.entries(kind)
+        for k, a, c in zip(sink, fi, ci):
+            assert count[k] <= g  # interactions are listed at groups only
+            src = source(int(a), int(c))
+            d, _, _, rejected = accepted(k, src)
+            assert rejected, (kind, k, a, c)
+            outside = d > (src[3] + bmax[k]) * (1 - tol)
+            if kind == "pc":
+                assert not src[5] and outside, (k, a, c)
+            else:
+                # a particle, or a bucket too close for PC
+                assert src[5] or (c <= b and d <= (src[3] + bmax[k]) * (1 + tol)), (k, a, c)
+
+
 def test_fmm_morton_keys_known_points():
     """Level l bisects axis l mod 3 (x, y, z): the key's top three bits are x, y, z halves."""
     pos = np.array([[0.75, 0.25, 0.25, 0.25, 0.0], [0.25, 0.75, 0.25, 0.25, 0.0], [0.25, 0.25, 0.75, 0.25, 0.0]])
