@@ -461,6 +461,39 @@ def test_fmm_lists_satisfy_the_opening_rule(theta):
                 assert src[5] or (c <= b and d <= (src[3] + bmax[k]) * (1 + tol)), (k, a, c)
 
 
+def test_fmm_group_locals_are_the_sum_of_their_accepted_sources():
+    """A group's local expansion is every CC/CP entry of the group and of its ancestors, each
+    expanded about the centre of mass of the cell that accepted it and shifted to the group's
+    (L2L is exact on the degree-5 polynomial).  Rebuilt here from the exported lists and tree."""
+    pos, mass = synth.clustered_plummer(2000, 16)
+    eps = 1e-3
+    f = oracle.FMM(pos, mass, eps, 0.6, bucket=8, group=32)
+    cl = f.cells()
+    first, count, parent, com = cl["first"], cl["count"], cl["parent"], cl["com"]
+    cell_of = {(int(a), int(c)): i for i, (a, c) in enumerate(zip(first, count))}
+    sp, sm = pos[:, f.perm()], mass[f.perm()]
+    own = {}
+    for kind in ("cc", "cp"):
+        sink, fi, ci = f.entries(kind)
+        for k, a, c in zip(sink, fi, ci):
+            if c == 1:
+                L = oracle.p2l(sm[a], sp[:, a], com[k], eps * eps)
+            else:
+                s_ = cell_of[(int(a), int(c))]
+                L = oracle.m2l(cl["mom"][s_], com[s_], com[k], eps * eps)
+            own[int(k)] = own.get(int(k), 0.0) + L
+    gcell, gL = f.groups()
+    assert len(own) > 10
+    for g, Lg in zip(gcell[::7], gL[::7]):
+        want = np.zeros(oracle.NMI)
+        k = int(g)
+        while k >= 0:
+            if k in own:
+                want += oracle.l2l(own[k], com[g] - com[k])
+            k = int(parent[k])
+        assert np.allclose(Lg, want, rtol=1e-10, atol=1e-10 * np.max(np.abs(want))), g
+
+
 def test_fmm_morton_keys_known_points():
     """Level l bisects axis l mod 3 (x, y, z): the key's top three bits are x, y, z halves."""
     pos = np.array([[0.75, 0.25, 0.25, 0.25, 0.0], [0.25, 0.75, 0.25, 0.25, 0.0], [0.25, 0.25, 0.75, 0.25, 0.0]])
