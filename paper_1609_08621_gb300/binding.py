@@ -200,6 +200,7 @@ class Context:
             self.set_params(**params)
 
     def close(self):
+        """fmm_destroy: release everything the context owns (idempotent)."""
         if getattr(self, "h", None):
             load().fmm_destroy(self.h)
             self.h = None
@@ -212,11 +213,14 @@ class Context:
 
     # -- parameters
     def get_params(self) -> fmm_params:
+        """fmm_get_params: the context's current parameters."""
         p = fmm_params()
         _check(load().fmm_get_params(self.h, C.byref(p)))
         return p
 
     def set_params(self, **kw):
+        """fmm_set_params with the given fields changed (bucket, group, list_chunk, criterion,
+        accumulate, mlp_tau, ...); the others keep their values."""
         p = self.get_params()
         for k, v in kw.items():
             setattr(p, k, v)
@@ -224,6 +228,8 @@ class Context:
 
     # -- solve
     def build_tree(self, pos, mass, active=None, params=None):
+        """fmm_build_tree: keys, sort, tree and upward pass only.  pos (3N float64 SoA), mass (N
+        float32), active (N uint8 or None) -- CUDA tensors."""
         import torch
 
         n = mass.numel()
@@ -257,9 +263,12 @@ class Context:
                                                _ptr(pot, torch.float32, n, "pot", True)))
 
     def set_graphs(self, enable=True):
+        """fmm_set_graphs: replay the whole solve as a CUDA graph while its arguments and buffers
+        stay the same (captured after an eager solve)."""
         _check(load().fmm_set_graphs(self.h, 1 if enable else 0))
 
     def graph_info(self):
+        """fmm_graph_info: whether a graph is captured, and how many solves replayed it."""
         cap, rep = C.c_int(), C.c_longlong()
         _check(load().fmm_graph_info(self.h, C.byref(cap), C.byref(rep)))
         return {"captured": bool(cap.value), "replays": rep.value}
@@ -298,6 +307,10 @@ class Context:
                                               _hptr(pot, np.float32, n, "pot", True)))
 
     def kick_drift(self, pos, vel, acc, rung, active_next, eps, dt0, max_rung, substep, closing):
+        """fmm_kick_drift: one substep of the hierarchical KDK (Sec. 3.2) -- closing half kick (when
+        closing), rung reassignment and opening half kick of the particles active at substep, then
+        the drift of all; active_next marks the particles whose forces come next.  pos, vel (3N
+        float64), acc (3N float32), rung and active_next (N uint8) -- CUDA tensors, in place."""
         import torch
 
         n = rung.numel()
@@ -332,6 +345,8 @@ class Context:
                                               _ptr(pot, torch.float32, n, "pot", True)))
 
     def assign_rungs(self, acc, rung, eps, dt0, max_rung):
+        """fmm_assign_rungs: rung = the smallest r <= max_rung with dt0 / 2^r <= 0.2 sqrt(eps / |a|)
+        (Sec. 3.2).  acc (3N float32), rung (N uint8 out) -- CUDA tensors."""
         import torch
 
         n = rung.numel()
@@ -340,6 +355,7 @@ class Context:
                                        int(max_rung)))
 
     def stats(self) -> dict:
+        """fmm_get_stats of the last solve (pair counts, phase times, launches) as a dict."""
         s = fmm_stats()
         _check(load().fmm_get_stats(self.h, C.byref(s)))
         return s.as_dict()
@@ -349,15 +365,18 @@ class Context:
     MLP_NW = 8961
 
     def mlp_load(self, params):
+        """fmm_mlp_load: the learned criterion's FMM_MLP_NP parameters (host float32)."""
         p = np.ascontiguousarray(params, dtype=np.float32)
         _check(load().fmm_mlp_load(self.h, p.ctypes.data, p.size))
 
     def mlp_get(self):
+        """fmm_mlp_get: the learned criterion's parameters (host float32 array)."""
         p = np.zeros(self.MLP_NP, np.float32)
         _check(load().fmm_mlp_get(self.h, p.ctypes.data, p.size))
         return p
 
     def mlp_predict(self, feats):
+        """fmm_mlp_predict: predicted log10 error for feature rows feats (n x 8 float32, CUDA)."""
         import torch
 
         n = feats.shape[0]
@@ -366,6 +385,7 @@ class Context:
         return out
 
     def mlp_gradient(self, feats, labels):
+        """fmm_mlp_gradient: (gradient over the FMM_MLP_NW weights, loss) of 0.5 mean((y - label)^2)."""
         import torch
 
         n = labels.numel()
@@ -376,6 +396,7 @@ class Context:
         return g, float(loss[0])
 
     def mlp_train(self, feats, labels, epochs=30, batch=256, lr=1e-3, seed=1):
+        """fmm_mlp_train on labelled rows (CUDA tensors); returns the last epoch's mean loss."""
         import torch
 
         n = labels.numel()
@@ -401,23 +422,28 @@ class Context:
         return feats[:8 * m].reshape(m, 8), labels[:m]
 
     def mlp_audit_pairs(self, n):
+        """fmm_mlp_audit_pairs: the last audit's (sink first, sink count, source first, source count)
+        as particle ranges in the sorted order."""
         arrs = [np.zeros(max(n, 1), np.int32) for _ in range(4)]
         _check(load().fmm_mlp_audit_pairs(self.h, *[a.ctypes.data for a in arrs], n))
         return [a[:n] for a in arrs]
 
     # -- introspection (host numpy outputs)
     def tree_info(self):
+        """fmm_tree_info: counts of cells, groups and PP / PC / local entries."""
         v = [C.c_longlong() for _ in range(5)]
         _check(load().fmm_tree_info(self.h, *[C.byref(x) for x in v]))
         return dict(zip(("cells", "groups", "pp", "pc", "local"), (x.value for x in v)))
 
     def export_order(self, n):
+        """fmm_export_order: the sort permutation and the sorted Morton keys."""
         perm = np.zeros(n, np.uint32)
         keys = np.zeros(n, np.uint64)
         _check(load().fmm_export_order(self.h, perm.ctypes.data, keys.ctypes.data))
         return perm, keys
 
     def export_cells(self):
+        """fmm_export_cells: the tree's cells (ranges, links, mass, centre, box, b_max, moments)."""
         nc = self.tree_info()["cells"]
         d = dict(first=np.zeros(nc, np.int32), count=np.zeros(nc, np.int32), parent=np.zeros(nc, np.int32),
                  child=np.zeros(2 * nc, np.int32), nact=np.zeros(nc, np.int32), mass=np.zeros(nc),
@@ -432,6 +458,7 @@ class Context:
         return d
 
     def export_lists(self, kind):
+        """fmm_export_lists: (sink cell, source first, source count) of the kind's entries."""
         k = KIND[kind]
         n = C.c_longlong()
         _check(load().fmm_export_lists(self.h, k, C.byref(n), None, None, None, 0))
@@ -442,12 +469,15 @@ class Context:
         return sink[:m], first[:m], count[:m]
 
     def export_walk_levels(self):
+        """fmm_export_walk_levels: per level of the walk, the sink cells walked, the checklist
+        entries they examined and the most examined by one sink."""
         counts = np.zeros(3 * 256, np.int64)
         nl = C.c_int()
         _check(load().fmm_export_walk_levels(self.h, counts.ctypes.data, 256, C.byref(nl)))
         return counts[:3 * nl.value].reshape(-1, 3)
 
     def export_locals(self):
+        """fmm_export_locals: (group cell, 56 local coefficients) of every group."""
         g = self.tree_info()["groups"]
         cell = np.zeros(max(g, 1), np.int32)
         L = np.zeros(max(g, 1) * 56, np.float32)
