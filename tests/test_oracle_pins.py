@@ -411,13 +411,15 @@ def test_fmm_tree_invariants():
 
 
 @pytest.mark.parametrize("theta", [0.4, 0.7])
-def test_fmm_lists_satisfy_the_opening_rule(theta):
+def test_fmm_lists_satisfy_the_opening_rule(theta, paper):
     """Every list entry against the rule that produced it (Sec. 3.1, R4), re-checked in FP64 from
     the tree's own geometry: CC/CP entries pass the acceptance test; PC entries fail it and have
     every sink particle outside the source's opening sphere; PP entries fail both (or are
-    point-like sources).  Decisions are taken in FP32, so comparisons allow a relative 1e-5."""
+    point-like sources).  Decisions are taken in FP32, so comparisons allow a relative 1e-5.
+    The factor of the sink's radius and the gap in softenings are the paper's printed values."""
     pos, mass = synth.clustered_plummer(3000, 15)
     eps, b, g = 1e-3, 16, 64
+    fk, fgap = paper["sink_radius_factor"], paper["bbox_gap_softenings"]
     f = oracle.FMM(pos, mass, eps, theta, bucket=b, group=g)
     cl = f.cells()
     first, count, com, lo, hi, bmax = cl["first"], cl["count"], cl["com"], cl["lo"], cl["hi"], cl["bmax"]
@@ -438,8 +440,8 @@ def test_fmm_lists_satisfy_the_opening_rule(theta):
         x, slo, shi, sro, _, _ = src
         d = np.linalg.norm(com[k] - x)
         gap = np.linalg.norm(np.maximum(np.maximum(slo - hi[k], lo[k] - shi), 0.0))
-        return d, gap, d > (1.5 * ro[k] + sro) * (1 - tol) and gap >= 2 * eps * (1 - tol), \
-            d <= (1.5 * ro[k] + sro) * (1 + tol) or gap < 2 * eps * (1 + tol)
+        return d, gap, d > (fk * ro[k] + sro) * (1 - tol) and gap >= fgap * eps * (1 - tol), \
+            d <= (fk * ro[k] + sro) * (1 + tol) or gap < fgap * eps * (1 + tol)
 
     for kind in ("cc", "cp"):
         sink, fi, ci = f.entries(kind)
