@@ -118,6 +118,20 @@ def _nfw_mu(x):
     return np.log1p(x) - x / (1.0 + x)
 
 
+def _nfw_radius(rng, c: float, rvir: float, k: int) -> np.ndarray:
+    """Radii inside r_vir from the NFW enclosed mass M(<r)/M(<r_vir) = mu(r c / r_vir) / mu(c),
+    mu(x) = ln(1 + x) - x / (1 + x), inverted by bisection (60 halvings of [0, c])."""
+    target = rng.random(k) * _nfw_mu(c)
+    a = np.zeros(k)
+    b = np.full(k, c)
+    for _ in range(60):
+        mid = 0.5 * (a + b)
+        below = _nfw_mu(mid) < target
+        a = np.where(below, mid, a)
+        b = np.where(below, b, mid)
+    return 0.5 * (a + b) * (rvir / c)
+
+
 def clustered_nfw(n: int, seed: int, n_halos: int = 200, uniform_frac: float = 0.3,
                   slope: float = 1.9, decades: float = 3.0, rvir_max: float = 0.05):
     """Uniform background plus NFW halos.
@@ -151,16 +165,7 @@ def clustered_nfw(n: int, seed: int, n_halos: int = 200, uniform_frac: float = 0
         ch, rv = conc[h], rvir[h]
 
         def draw(g, kk, c=c, ch=ch, rv=rv):
-            target = g.random(kk) * _nfw_mu(ch)
-            a = np.zeros(kk)
-            b = np.full(kk, ch)
-            for _ in range(60):
-                mid = 0.5 * (a + b)
-                below = _nfw_mu(mid) < target
-                a = np.where(below, mid, a)
-                b = np.where(below, b, mid)
-            r = 0.5 * (a + b) * (rv / ch)
-            return c + _isotropic(g, r)
+            return c + _isotropic(g, _nfw_radius(g, ch, rv, kk))
 
         parts.append(_resample(rng, draw, k))
     pos = np.concatenate(parts, axis=1)
