@@ -46,9 +46,10 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul, 3 fma, 1 add)
 
 # DRAM bytes (read + write) per launch of the interaction kernels on the 128^3 NFW box with
-# buckets of 16, groups of 64 and work items of 128 list entries, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_pc_k_pp_nfw2m.md).  Reported only for
-# runs with those settings; set back to None whenever a kernel changes after that capture.
+# buckets of 16, groups of 64 and work items of 128 list entries, stored from one earlier ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), not measured by this run.  Reported,
+# labelled as stored, only for runs with those settings; set back to None whenever a kernel
+# changes after that capture.
 NCU_TRAFFIC = {"k_pc": 255633664, "k_pp": 121505280}
 NCU_TRAFFIC_PARAMS = (16, 64, 128)
 
@@ -718,6 +719,9 @@ def main():
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "pp_pc_frac": ((fpp + fpc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
             if pp_ms + pc_ms > 0 else 0.0}
+    roof["traffic_source"] = ("stored from an earlier ncu capture of this kernel and these settings, not measured "
+                              "in this run" if roof["traffic"] is not None else
+                              "no ncu capture of this kernel at these settings")
     line = {"metric": "interactions/s (PP + PC) per force solve", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -176,11 +176,16 @@ def morton_order_static(pos, keys, order, stream=None):
     import torch
 
     n = keys.numel()
-    if stream is None:
-        stream = torch.cuda.current_stream(keys.device)
-    _check(load().fmm_morton_order_static(_ptr(pos, torch.float64, 3 * n, "pos"), n,
-                                          _ptr(keys, torch.int64, n, "keys"), _ptr(order, torch.int32, n, "order"),
-                                          C.c_void_p(stream.cuda_stream)))
+    devs = {t.device for t in (pos, keys, order)}
+    if len(devs) != 1:
+        raise ValueError(f"pos, keys and order must be on one device, got {sorted(str(d) for d in devs)}")
+    # the C call runs on the current device: make it the tensors' device for the call
+    with torch.cuda.device(keys.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(keys.device)
+        _check(load().fmm_morton_order_static(_ptr(pos, torch.float64, 3 * n, "pos"), n,
+                                              _ptr(keys, torch.int64, n, "keys"),
+                                              _ptr(order, torch.int32, n, "order"), C.c_void_p(stream.cuda_stream)))
 
 
 class Context:

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "fmm.h"
 
 #define FMM_FULL_MASK 0xffffffffu
@@ -293,6 +295,24 @@ cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, un
                                   int substep, int closing, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_assign_rungs(const float* acc, unsigned char* rung, long long n, double eps, double dt0,
                                     int max_rung, cudaStream_t s);
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the calling thread's current
+// device, once per device.  Function attributes belong to each device's context, so a flag for
+// the whole process would skip the call on the second device; `done` holds one bit per device
+// (devices 0-63; others set the attribute on every call).  Setting it twice is harmless, so two
+// threads that race on the first call only repeat the call.
+template <typename F>
+cudaError_t fmm_smem_attr_once(F* func, int bytes, std::atomic<unsigned long long>& done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // ---------------------------------------------------------------- device helpers
 

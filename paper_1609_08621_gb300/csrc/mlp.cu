@@ -173,12 +173,9 @@ static size_t grad_smem() { return (size_t)(TB_ROWS * MLP_F + 5 * TB_ROWS * TPAD
 cudaError_t fmm_mlp_grad(const float* params, const float* feats, const float* labels, const unsigned int* idx,
                          long long nrows, float inv_b, float loss_scale, float* grad, float* loss, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    cudaError_t e = fmm_smem_attr_once(k_mlp_grad, (int)grad_smem(), attr);
+    if (e != cudaSuccess) return e;
     k_mlp_grad<<<(unsigned)fmm_ceil_div(nrows, TB_ROWS), 64, grad_smem(), s>>>(params, feats, labels, idx, nrows, inv_b,
                                                                              loss_scale, grad, loss);
     return cudaGetLastError();
@@ -234,13 +231,9 @@ size_t fmm_mlp_predict_smem(int warps) { return MLPP_SIZE + (size_t)warps * MLP_
 
 cudaError_t fmm_mlp_predict(const unsigned char* packed, const float* feats, long long n, float* out, cudaStream_t s)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_predict, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)fmm_mlp_predict_smem(4));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    cudaError_t e = fmm_smem_attr_once(k_mlp_predict, (int)fmm_mlp_predict_smem(4), attr);
+    if (e != cudaSuccess) return e;
     long long blocks = fmm_ceil_div(n, 128);
     if (blocks > 152LL * 16) blocks = 152LL * 16;
     if (blocks < 1) blocks = 1;

@@ -234,18 +234,16 @@ static size_t rs_smem_bytes()
     return (size_t)RS_TILE * 8 + (size_t)RS_TILE * 4 + (RS_WARPS * 256 + 256 + 256 + 32) * 4;
 }
 
+// Lets the scatter kernel use its shared-memory tile on the current device.
+static std::atomic<unsigned long long> g_rs_attr{0};
+cudaError_t fmm_sort_prepare() { return fmm_smem_attr_once(k_rs_scatter, (int)rs_smem_bytes(), g_rs_attr); }
+
 cudaError_t fmm_sort_ensure(DevTree& t, long long n)
 {
     long long nblk = fmm_ceil_div(n, RS_TILE);
     cudaError_t e = ensure_u32(&t.hist, &t.cap_hist, 256 * nblk);
     if (e != cudaSuccess) return e;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem_bytes());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    return cudaSuccess;
+    return fmm_sort_prepare();
 }
 
 // Stable LSD sort of n (key, value) pairs on the low 8 * passes key bits (passes even): the
@@ -287,7 +285,6 @@ long long fmm_sort_hist_entries(long long n) { return 256LL * fmm_ceil_div(n, RS
 long long fmm_sort_part_entries(long long n) { return fmm_ceil_div(fmm_sort_hist_entries(n), SCAN_TILE); }
 
 // Lets the scatter kernel use its shared-memory tile on the current device.
-cudaError_t fmm_sort_prepare() { return cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem_bytes()); }
 
 // The same stable LSD sort as fmm_radix_sort_kv, with every scratch buffer supplied by the
 // caller (hist, part of the sizes above; kb, vb of n entries) and nothing allocated here.

@@ -551,12 +551,9 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
         a.audit_cap, t.graded ? t.nogroup : nullptr
     if (a.mode == 1) {
         const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_walk_level<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static std::atomic<unsigned long long> attr{0};
+        cudaError_t e = fmm_smem_attr_once(k_walk_level<1>, (int)smem, attr);
+        if (e != cudaSuccess) return e;
         k_walk_level<1><<<blocks, WALK_THREADS, smem, s>>>(WALK_ARGS);
     } else if (a.mode == 2) {
         k_walk_level<2><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
