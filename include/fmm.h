@@ -20,13 +20,18 @@
  *   - independent boxes solved together in one pass, CUDA-graph replay of the
  *     solve and an autotuner of bucket, group and work-item size;
  *   - an opening criterion learned by a small network trained on the GPU (not
- *     in the paper; it replaces the fixed-theta test of Sec. 3.1 inside a band).
+ *     in the paper; it replaces the fixed-theta test of Sec. 3.1 inside a band);
+ *   - the periodic unit box: the root's 26 or 124 copies on the checklist and the
+ *     5th-order Ewald multipole correction for the copies beyond (Sec. 3.1, Sec. 3.3).
  *
  * Physics conventions (all entry points): G = 1, Plummer softening,
  *     a_i   =  sum_{j != i} m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2)
  *     phi_i = -sum_{j != i} m_j / (|x_j - x_i|^2 + eps^2)^(1/2)
- * which the method approximates.  Positions must lie in [0,1)^3 (isolated box,
- * no periodic replicas), masses must be finite and > 0, eps > 0, 0 < theta <= 1.
+ * which the method approximates in the isolated unit box.  With fmm_params.nrep > 0
+ * the box is periodic (Sec. 3.1): the sum runs over every periodic copy of the sources,
+ * softened within the replica shell |n|_inf <= nrep and Newtonian (Ewald, with a uniform
+ * background of the mean density) beyond it.  Positions must lie in [0,1)^3, masses
+ * must be finite and > 0, eps > 0, 0 < theta <= 1.
  *
  * Memory and ownership:
  *   - "device" arguments are CUDA device pointers on the context's device;
@@ -82,7 +87,8 @@ typedef struct fmm_params {
     int criterion;         /* 0: fixed theta (Sec. 3.1); 1: learned (MLP, requires fmm_mlp_load) */
     int accumulate;        /* 0: a particle's partial sums (one per list chunk of <= 64 entries, and the
                               local expansion) are added in FP32; 1: they are added in FP64 */
-    int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion; default 7 */
+    int terms;             /* bit mask of evaluated terms: 1 PP, 2 PC, 4 local expansion of the walk,
+                              8 Ewald correction (periodic box only); default 15 */
     int list_chunk;        /* list entries per PP / PC work item: 0 (default, 64) or a multiple of
                               32 in [32, 1024] */
     long long spin_limit;  /* iteration cap of any device-side wait (default 1<<26) */
@@ -95,6 +101,16 @@ typedef struct fmm_params {
     double mlp_tau;
     double band_lo;
     double band_hi;
+    /* Periodic unit box (Sec. 3.1, periodic boundaries): 0 (default) for the isolated box; 1 or 2
+     * for the periodic box, whose walk starts from the root and its copies shifted by the integer
+     * vectors n with |n|_inf <= nrep (26 or 124 copies, softened like the box itself), and whose
+     * copies beyond that shell enter as the 5th-order Ewald multipole correction (Sec. 3.1,
+     * Sec. 3.3): the periodic Newtonian sum with a uniform background of the mean density, from the
+     * root's moments, evaluated in FP64 once per solve as order-5 local expansions about the
+     * centres of 4^3 sub-cubes.  Periodic solves take one box (not fmm_compute_forces_batch), the
+     * fixed criterion only, no dual trees, and n <= 2^26 (nrep 1) or 2^24 (nrep 2): list entries
+     * carry the copy in their upper bits. */
+    int nrep;
 } fmm_params;
 
 /* Per-solve statistics of the last fmm_compute_forces on a context. */
@@ -126,7 +142,7 @@ typedef struct fmm_stats {
 } fmm_stats;
 
 /* Fill *p with the defaults: theta 0.55, eps 1e-3, bucket 16, group 64, criterion 0,
- * accumulate 0, terms 7, spin_limit 1<<26.  Returns FMM_ERR_ARG for p == NULL. */
+ * accumulate 0, terms 15, spin_limit 1<<26, nrep 0.  Returns FMM_ERR_ARG for p == NULL. */
 fmm_status fmm_default_params(fmm_params *p);
 
 /* Create a context on CUDA device `device`, enqueuing all work on `cuda_stream`
@@ -379,6 +395,12 @@ fmm_status fmm_export_cells(const fmm_ctx *ctx, int *first, int *count, int *par
  * PP and PC entries belong to groups; CC and CP entries to any walked sink cell. */
 fmm_status fmm_export_lists(const fmm_ctx *ctx, int kind, long long *n_entries, int *sink, int *src_first,
                             int *src_count, long long capacity);
+
+/* The periodic copy of each entry's source, in the order of fmm_export_lists for the same kind:
+ * shift[3i..3i+2] = the integer vector n of the copy the source lies in (Sec. 3.1, periodic
+ * boundaries; all zero for an isolated box).  *n_entries receives the entry count; with
+ * capacity < *n_entries (or shift NULL) the call only reports it.  shift: host, 3 * capacity ints. */
+fmm_status fmm_export_list_shifts(const fmm_ctx *ctx, int kind, long long *n_entries, int *shift, long long capacity);
 
 /* Local expansions of the groups: group_cell[i] and 56 coefficients L_k = D^k Phi at the
  * group's centre of mass, in the order of fmm_multi_index. */

@@ -34,7 +34,7 @@ class fmm_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("bucket", C.c_int), ("group", C.c_int),
                 ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("list_chunk", C.c_int),
                 ("spin_limit", C.c_longlong), ("mlp_tau", C.c_double), ("band_lo", C.c_double),
-                ("band_hi", C.c_double)]
+                ("band_hi", C.c_double), ("nrep", C.c_int)]
 
 
 class fmm_stats(C.Structure):
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         "fmm_export_order": (i, [vp, vp, vp]),
         "fmm_export_cells": (i, [vp] + [vp] * 11),
         "fmm_export_lists": (i, [vp, i, C.POINTER(ll), vp, vp, vp, ll]),
+        "fmm_export_list_shifts": (i, [vp, i, C.POINTER(ll), vp, ll]),
         "fmm_export_locals": (i, [vp, vp, vp, ll]),
         "fmm_multi_index": (i, [vp, vp]),
         "fmm_export_walk_levels": (i, [vp, vp, i, C.POINTER(i)]),
@@ -472,6 +473,17 @@ class Context:
         _check(load().fmm_export_lists(self.h, k, C.byref(n), sink.ctypes.data, first.ctypes.data,
                                        count.ctypes.data, m))
         return sink[:m], first[:m], count[:m]
+
+    def export_list_shifts(self, kind):
+        """fmm_export_list_shifts: the periodic copy (n_x, n_y, n_z) of each entry's source, rows in
+        the order of export_lists(kind)."""
+        k = KIND[kind]
+        n = C.c_longlong()
+        _check(load().fmm_export_list_shifts(self.h, k, C.byref(n), None, 0))
+        m = n.value
+        out = np.zeros(3 * max(m, 1), np.int32)
+        _check(load().fmm_export_list_shifts(self.h, k, C.byref(n), out.ctypes.data, m))
+        return out[:3 * m].reshape(m, 3)
 
     def export_walk_levels(self):
         """fmm_export_walk_levels: per level of the walk, the sink cells walked, the checklist

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfmm_gb300.so")
-SOURCES = ["capi.cu", "sort.cu", "tree.cu", "walk.cu", "interact.cu", "kdk.cu", "mlp.cu", "noalloc.cu", "dual.cu"]
+SOURCES = ["capi.cu", "sort.cu", "tree.cu", "walk.cu", "interact.cu", "kdk.cu", "mlp.cu", "noalloc.cu", "dual.cu", "ewald.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -128,6 +128,10 @@ struct fmm_ctx {
     int graph_levels = 0, graph_launches = 0;
     std::vector<void*> graph_bufs;  // the context's buffer addresses when the graph was captured
     long long graph_replays = 0;
+    // periodic box: the Ewald sub-cube expansions run on a side stream beside the walk (fork after
+    // the tree, join before the groups add them)
+    cudaStream_t ew_stream = nullptr;
+    cudaEvent_t ew_fork = nullptr, ew_join = nullptr;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
     float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
@@ -148,7 +152,8 @@ static fmm_status check_params(const fmm_params* p)
         return fail(FMM_ERR_ARG, "band must satisfy 0 < band_lo <= band_hi <= 2");
     if (!isfinite(p->mlp_tau)) return fail(FMM_ERR_ARG, "mlp_tau must be finite");
     if (p->accumulate != 0 && p->accumulate != 1) return fail(FMM_ERR_ARG, "accumulate must be 0 or 1, got %d", p->accumulate);
-    if (p->terms < 0 || p->terms > 7) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4, got %d", p->terms);
+    if (p->terms < 0 || p->terms > 15) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4|8, got %d", p->terms);
+    if (p->nrep < 0 || p->nrep > 2) return fail(FMM_ERR_ARG, "nrep must be 0 (isolated), 1 or 2, got %d", p->nrep);
     if (p->list_chunk != 0 && (p->list_chunk < 32 || p->list_chunk > 1024 || p->list_chunk % 32 != 0))
         return fail(FMM_ERR_ARG, "list_chunk must be 0 or a multiple of 32 in [32, 1024], got %d", p->list_chunk);
     if (p->spin_limit < 1) return fail(FMM_ERR_ARG, "spin_limit must be >= 1");
@@ -165,8 +170,9 @@ extern "C" fmm_status fmm_default_params(fmm_params* p)
     p->group = 64;
     p->criterion = 0;
     p->accumulate = 0;
-    p->terms = 7;
+    p->terms = 15;
     p->spin_limit = 1LL << 26;
+    p->nrep = 0;
     p->mlp_tau = -3.5;
     p->band_lo = 0.35;
     p->band_hi = 1.0;
@@ -187,7 +193,7 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
             t.bucket_of, t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
             t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
-            t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup,
+            t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
             w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
             w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
             w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch,
@@ -216,6 +222,11 @@ static void free_all(fmm_ctx* c)
     c->gexec = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
+    if (c->ew_stream) cudaStreamDestroy(c->ew_stream);
+    if (c->ew_fork) cudaEventDestroy(c->ew_fork);
+    if (c->ew_join) cudaEventDestroy(c->ew_join);
+    c->ew_stream = nullptr;
+    c->ew_fork = c->ew_join = nullptr;
 }
 
 extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
@@ -335,6 +346,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.L, (long long)FMM_NL * cap));
         t.cap_cells = cap;
     }
+    if (!t.ewald_L) CK(alloc(&t.ewald_L, fmm_ewald_floats()));
     CK(fmm_sort_ensure(t, n));
     return FMM_OK;
 }
@@ -524,6 +536,69 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
     return FMM_OK;
 }
 
+// The periodic state of the coming walk (Sec. 3.1, periodic boundaries): the replica shell and
+// the index bits of list entries, which must leave room for the copy code above them.  Isolated
+// solves reset it.
+static fmm_status set_periodic(fmm_ctx* c, const fmm_params& q, long long n, int nbox)
+{
+    DevTree& t = c->t;
+    t.per_R = 0;
+    t.per_ib = 31;
+    if (q.nrep == 0) return FMM_OK;
+    if (nbox != 1) return fail(FMM_ERR_ARG, "a periodic solve (nrep %d) takes one box, got %d", q.nrep, nbox);
+    if (q.criterion != 0) return fail(FMM_ERR_ARG, "a periodic solve (nrep %d) takes the fixed criterion", q.nrep);
+    const long long W = 2 * q.nrep + 1, copies = W * W * W;
+    const long long span = std::max(n, t.cap_cells);
+    int ib = 1;
+    while ((1LL << ib) < span) ib++;
+    if (((copies - 1) << ib) >= (1LL << 31))
+        return fail(FMM_ERR_ARG, "a periodic solve with nrep %d holds at most %lld particles and cells, got %lld", q.nrep,
+                    (1LL << 31) / copies, span);
+    t.per_R = q.nrep;
+    t.per_ib = ib;
+    return FMM_OK;
+}
+
+// The shifted-geometry tables of a periodic walk, sized for the tree's capacity (eager solves
+// only: a captured graph reuses what the eager solve before it allocated).
+static fmm_status ensure_periodic(fmm_ctx* c)
+{
+    DevTree& t = c->t;
+    if (t.per_R <= 0) return FMM_OK;
+    const long long w2 = 2 * t.per_R;
+    CK(grow(&t.cshift, &t.cap_cshift, t.cap_cells * 3 * w2));
+    CK(grow(&t.pshift, &t.cap_pshift, t.cap_n * 3 * w2));
+    return FMM_OK;
+}
+
+// Fork the Ewald sub-cube expansions onto the side stream once the tree (the root's moments) is
+// on the context's stream; ewald_join makes the context's stream wait for them.  Nothing to do for
+// an isolated box or without the correction term.
+static bool ewald_on(const fmm_ctx* c, int terms) { return c->t.per_R > 0 && (terms & 8); }
+
+static fmm_status ewald_fork(fmm_ctx* c, int terms)
+{
+    if (!ewald_on(c, terms)) return FMM_OK;
+    if (!c->ew_stream) CK(cudaStreamCreateWithFlags(&c->ew_stream, cudaStreamNonBlocking));
+    if (!c->ew_fork) CK(cudaEventCreateWithFlags(&c->ew_fork, cudaEventDisableTiming));
+    if (!c->ew_join) CK(cudaEventCreateWithFlags(&c->ew_join, cudaEventDisableTiming));
+    CK(cudaEventRecord(c->ew_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->ew_stream, c->ew_fork, 0));
+    CK(fmm_launch_ewald_grid(c->t, terms, c->ew_stream));
+    CK(cudaEventRecord(c->ew_join, c->ew_stream));
+    c->launches += 1;
+    return FMM_OK;
+}
+
+static fmm_status ewald_join(fmm_ctx* c, int terms)
+{
+    if (!ewald_on(c, terms)) return FMM_OK;
+    CK(cudaStreamWaitEvent(c->stream, c->ew_join, 0));
+    CK(fmm_launch_ewald_groups(c->t, c->w, c->ctr, terms, c->stream));
+    c->launches += 1;
+    return FMM_OK;
+}
+
 static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int group, int mode = 0)
 {
     DevTree& t = c->t;
@@ -564,6 +639,10 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
         }
         CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
         c->launches += 2;
+        {
+            const fmm_status se = ewald_join(c, c->params.terms);
+            if (se != FMM_OK) return se;
+        }
         CK(cudaMemcpyAsync(c->ctr_h, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (!c->ctr_h->overflow) {
@@ -604,9 +683,18 @@ static fmm_status solve_eager(fmm_ctx* c, const double* pos, const float* mass, 
     CK(cudaEventRecord(c->ev[0], s));
     st = build_tree(c, pos, mass, active, n, q.bucket, box_off, nbox);
     if (st != FMM_OK) return st;
+    st = set_periodic(c, q, n, nbox);
+    if (st == FMM_OK) st = ensure_periodic(c);
+    if (st != FMM_OK) return st;
     c->stats.n_active = (long long)c->ctr_h->n_active;
     CK(fmm_launch_nodes(c->t, theta, s));
     c->launches += 1;
+    if (c->t.per_R > 0) {
+        CK(fmm_launch_shift_tables(c->t, s));
+        c->launches += 1;
+    }
+    st = ewald_fork(c, q.terms);
+    if (st != FMM_OK) return st;
     CK(cudaEventRecord(c->ev[1], s));
     if (q.criterion == 1) {
         if (!c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
@@ -722,6 +810,8 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
     fmm_status st = set_boxes(c, n, box_off, nbox);
     if (st != FMM_OK) return st;
+    st = set_periodic(c, q, n, nbox);
+    if (st != FMM_OK) return st;
     CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
     CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
     if (nbox > 1) {
@@ -747,6 +837,15 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
     CK(fmm_launch_nodes(t, q.theta, s));
     c->launches += 1;
+    if (t.per_R > 0) {
+        if (!t.cshift || !t.pshift || t.cap_cshift < t.cap_cells * 3 * 2 * t.per_R ||
+            t.cap_pshift < t.cap_n * 3 * 2 * t.per_R)
+            return fail(FMM_ERR_STATE, "internal: periodic tables missing at capture");
+        CK(fmm_launch_shift_tables(t, s));
+        c->launches += 1;
+    }
+    st = ewald_fork(c, q.terms);
+    if (st != FMM_OK) return st;
     CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     if (q.criterion == 1) {
         CK(fmm_launch_cell_amin(t, acc, n, s));
@@ -779,6 +878,8 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     }
     CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
     c->launches += 2;
+    st = ewald_join(c, q.terms);
+    if (st != FMM_OK) return st;
     CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
     InteractArgs ia;
     ia.eps2 = (float)(q.eps * q.eps);
@@ -1195,6 +1296,9 @@ extern "C" fmm_status fmm_compute_forces_dual(fmm_ctx* c, const double* pos, con
     st = check_params(&q);
     if (st != FMM_OK) return st;
     if (q.criterion != 0) return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: only the fixed criterion (criterion 0)");
+    if (q.nrep != 0) return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: isolated boxes only (nrep 0)");
+    c->t.per_R = 0;
+    c->t.per_ib = 31;
     if (q.bucket != f.bucket)
         return fail(FMM_ERR_ARG, "fmm_compute_forces_dual: bucket %d differs from the fixed tree's %d", q.bucket,
                     f.bucket);
@@ -1404,31 +1508,38 @@ extern "C" fmm_status fmm_export_cells(const fmm_ctx* c, int* first, int* count,
     return FMM_OK;
 }
 
-extern "C" fmm_status fmm_export_lists(const fmm_ctx* c, int kind, long long* n_entries, int* sink, int* src_first,
-                                       int* src_count, long long capacity)
+// The kind's list entries of the last solve (0 PP, 1 PC, 2 CC, 3 CP) as (sink cell, source first,
+// source count, source copy n) in list order; n = 0 for an isolated box.
+static fmm_status collect_lists(const fmm_ctx* c, int kind, std::vector<long long>& out_sink,
+                                std::vector<long long>& out_first, std::vector<long long>& out_count,
+                                std::vector<int>& out_shift)
 {
-    if (!c || !n_entries) return fail(FMM_ERR_ARG, "NULL argument");
     if (kind < 0 || kind > 3) return fail(FMM_ERR_ARG, "kind must be 0..3");
     if (!c->have_solve) return fail(FMM_ERR_STATE, "no solve yet");
     CK(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     const DevTree& t = c->t;
     const DevWalk& w = c->w;
+    const int ib = t.per_ib, R = t.per_R;
     long long nc = t.n_cells;
     std::vector<int> cf((size_t)nc), cn((size_t)nc);
     CK(d2h(cf.data(), t.cfirst, nc, s));
     CK(d2h(cn.data(), t.ccount, nc, s));
-    std::vector<long long> out_sink, out_first, out_count;
     auto push = [&](int sk, unsigned int e) {
+        const unsigned int j = entry_index(e, ib);
+        int nx = 0, ny = 0, nz = 0;
+        copy_shift(entry_copy(e, ib), R, nx, ny, nz);
+        out_sink.push_back(sk);
         if (e & FMM_PARTICLE_BIT) {
-            out_sink.push_back(sk);
-            out_first.push_back((int)(e & ~FMM_PARTICLE_BIT));
+            out_first.push_back((int)j);
             out_count.push_back(1);
         } else {
-            out_sink.push_back(sk);
-            out_first.push_back(cf[e]);
-            out_count.push_back(cn[e]);
+            out_first.push_back(cf[j]);
+            out_count.push_back(cn[j]);
         }
+        out_shift.push_back(nx);
+        out_shift.push_back(ny);
+        out_shift.push_back(nz);
     };
     if (kind <= 1) {
         std::vector<Group> g((size_t)w.n_groups);
@@ -1450,10 +1561,21 @@ extern "C" fmm_status fmm_export_lists(const fmm_ctx* c, int kind, long long* n_
         CK(cudaStreamSynchronize(s));
         for (long long i = 0; i < w.cc_len; i++) {
             unsigned int e = L[i];
-            bool pointlike = (e & FMM_PARTICLE_BIT) || cn[e] == 1;
+            bool pointlike = (e & FMM_PARTICLE_BIT) || cn[entry_index(e, ib)] == 1;
             if ((kind == 3) == pointlike) push(sk[i], e);
         }
     }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_lists(const fmm_ctx* c, int kind, long long* n_entries, int* sink, int* src_first,
+                                       int* src_count, long long capacity)
+{
+    if (!c || !n_entries) return fail(FMM_ERR_ARG, "NULL argument");
+    std::vector<long long> out_sink, out_first, out_count;
+    std::vector<int> out_shift;
+    fmm_status st = collect_lists(c, kind, out_sink, out_first, out_count, out_shift);
+    if (st != FMM_OK) return st;
     *n_entries = (long long)out_sink.size();
     if (capacity < *n_entries) return FMM_OK;  // size query
     for (long long i = 0; i < *n_entries; i++) {
@@ -1461,6 +1583,20 @@ extern "C" fmm_status fmm_export_lists(const fmm_ctx* c, int kind, long long* n_
         if (src_first) src_first[i] = (int)out_first[i];
         if (src_count) src_count[i] = (int)out_count[i];
     }
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_export_list_shifts(const fmm_ctx* c, int kind, long long* n_entries, int* shift,
+                                             long long capacity)
+{
+    if (!c || !n_entries) return fail(FMM_ERR_ARG, "NULL argument");
+    std::vector<long long> out_sink, out_first, out_count;
+    std::vector<int> out_shift;
+    fmm_status st = collect_lists(c, kind, out_sink, out_first, out_count, out_shift);
+    if (st != FMM_OK) return st;
+    *n_entries = (long long)out_sink.size();
+    if (capacity < *n_entries || !shift) return FMM_OK;  // size query
+    memcpy(shift, out_shift.data(), sizeof(int) * out_shift.size());
     return FMM_OK;
 }
 
@@ -1771,6 +1907,9 @@ extern "C" fmm_status fmm_mlp_audit(fmm_ctx* c, const double* pos, const float* 
     q.criterion = 0;
     st = check_params(&q);
     if (st != FMM_OK) return st;
+    if (q.nrep != 0) return fail(FMM_ERR_ARG, "fmm_mlp_audit: isolated boxes only (nrep 0)");
+    c->t.per_R = 0;
+    c->t.per_ib = 31;
     const fmm_params saved = c->params;
     c->params = q;
     cudaStream_t s = c->stream;

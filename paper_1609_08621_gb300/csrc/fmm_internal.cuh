@@ -50,6 +50,60 @@ __device__ __forceinline__ float cen_diff(float ha, float la, float hb, float lb
     return __fadd_rn(__fsub_rn(ha, hb), __fsub_rn(la, lb));
 }
 
+// Periodic unit box (Sec. 3.1, periodic boundaries): the walk starts from the root and its copies
+// shifted by n, |n|_inf <= R (R = nrep, 26 or 124 copies), and every checklist and list entry
+// carries the copy its source lies in.  An entry is
+//   bit 31: particle (else cell) | bits 30..ib: copy code q | bits ib-1..0: index,
+// q = (n_x + R) W^2 + (n_y + R) W + (n_z + R) with W = 2R + 1, so the box itself is
+// q0 = R (W^2 + W + 1).  An isolated box has R = 0 and ib = 31: q is always 0 and the index is
+// the whole entry, as before.
+//
+// The walk decides on a copy's geometry shifted in FP64 and then rounded, fl(x + n_a) per axis, as
+// for the box itself.  FP64 issues at 1/64 of the FP32 rate, so those values are tabulated once
+// per solve (k_shift_tables) for every cell and particle, axis and non-zero shift value v in
+// [-R, R]: slot (i * 3 + axis) * 2R + shift_slot(v).
+struct PeriodicArgs {
+    int ib;        // index bits
+    int R;         // replica shell radius (0: isolated)
+    const float4* cshift;  // per cell, axis and shift: (fl(com + v), fl(lo + v), fl(hi + v), 0)
+    const float* pshift;   // per particle, axis and shift: fl(x + v)
+};
+
+__host__ __device__ __forceinline__ int shift_slot(int v, int R) { return v < 0 ? v + R : v + R - 1; }
+
+__host__ __device__ __forceinline__ unsigned int entry_index(unsigned int e, int ib)
+{
+    return e & ((1u << ib) - 1u);
+}
+__host__ __device__ __forceinline__ unsigned int entry_copy(unsigned int e, int ib)
+{
+    return (e & ~FMM_PARTICLE_BIT) >> ib;
+}
+__host__ __device__ __forceinline__ unsigned int copy_centre(int R)
+{
+    const int W = 2 * R + 1;
+    return (unsigned int)(R * (W * W + W + 1));
+}
+// the shift n of copy code q
+__host__ __device__ __forceinline__ void copy_shift(unsigned int q, int R, int& nx, int& ny, int& nz)
+{
+    const int W = 2 * R + 1;
+    nx = (int)q / (W * W) - R;
+    ny = ((int)q / W) % W - R;
+    nz = (int)q % W - R;
+}
+
+// Shift the float pair (h, l) of a centre c = h + l by an integer n (|n| <= 2, |h| < 1): the
+// rounded sum t = fl(n + h) and its exact rounding error h - (t - n) (|n| >= |h|, so the error is
+// representable and computed exactly), added into the low part.  n = 0 leaves the pair unchanged.
+__device__ __forceinline__ void cen_shift(float& h, float& l, float n)
+{
+    const float t = __fadd_rn(n, h);
+    const float err = __fsub_rn(h, __fsub_rn(t, n));
+    h = t;
+    l = __fadd_rn(l, err);
+}
+
 // A sink group after the walk.
 struct __align__(16) Group {
     int cell;
@@ -157,12 +211,29 @@ struct DevTree {
     bool graded = false;
     unsigned char *split = nullptr, *nogroup = nullptr;
     long long cap_split = 0, cap_nogroup = 0;
+    // periodic box (nrep > 0): the replica shell radius and the index bits of list entries;
+    // R = 0, ib = 31 for an isolated box
+    int per_R = 0, per_ib = 31;
+    float* ewald_L = nullptr;  // FP32 local coefficients of the Ewald correction per sub-cube
+    float4* cshift = nullptr;  // shifted cell geometry (PeriodicArgs), 3 * 2R per cell
+    float* pshift = nullptr;   // shifted particle positions, 3 * 2R per particle
+    long long cap_cshift = 0, cap_pshift = 0;
     // scan scratch
     unsigned int *scan_part = nullptr;
     long long cap_scan_part = 0;
     unsigned int *hist = nullptr;
     long long cap_hist = 0;
 };
+
+__host__ __forceinline__ PeriodicArgs periodic_args(const DevTree& t)
+{
+    PeriodicArgs a;
+    a.ib = t.per_ib;
+    a.R = t.per_R;
+    a.cshift = t.cshift;
+    a.pshift = t.pshift;
+    return a;
+}
 
 struct DevWalk {
     long long cap_front = 0, cap_cl = 0, cap_pp = 0, cap_pc = 0, cap_cc = 0, cap_groups = 0;
@@ -261,6 +332,7 @@ struct WalkArgs {
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s);
 cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root = -1);
+cudaError_t fmm_launch_shift_tables(DevTree& t, cudaStream_t s);
 int fmm_walk_warps(int device);
 
 // interact.cu
@@ -288,6 +360,11 @@ cudaError_t fmm_launch_subset_gather(const unsigned int* flag, const unsigned in
 cudaError_t fmm_append_fixed(DevTree& t, const FixedTree& f, long long na, long long ca, long long ba, cudaStream_t s);
 cudaError_t fmm_launch_compose_perm(const unsigned int* perm, const unsigned int* sub, long long n, unsigned int* out,
                                     cudaStream_t s);
+
+// ewald.cu
+long long fmm_ewald_floats();
+cudaError_t fmm_launch_ewald_grid(DevTree& t, int terms, cudaStream_t s);
+cudaError_t fmm_launch_ewald_groups(DevTree& t, DevWalk& w, DevCounters* ctr, int terms, cudaStream_t s);
 
 // kdk.cu
 cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, unsigned char* rung,

@@ -195,7 +195,7 @@ __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int
                                              const int* __restrict__ ccount, const float4* __restrict__ cen,
                                              const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                              const float4* __restrict__ off, float4* __restrict__ part, float4* T,
-                                             PPChunk& E, float eps2, int lane, int csize)
+                                             PPChunk& E, float eps2, int lane, int csize, int ib, int R)
 {
     constexpr int B2 = R1 * (32 / Q1);
     Sinks<R1, Q1> K;
@@ -210,17 +210,26 @@ __device__ __forceinline__ long long pp_item(const Group& G, int nact, const int
         float dx = 0.f, dy = 0.f, dz = 0.f;
         if (lane < ne) {
             const unsigned int e = pp[G.pp_off + base + lane];
+            const unsigned int j = entry_index(e, ib);
             int bc;
             if (e & FMM_PARTICLE_BIT) {
-                first = (int)(e & ~FMM_PARTICLE_BIT);
+                first = (int)j;
                 cnt = 1;
                 bc = bucket_cell[bucket_of[first]];
             } else {
-                first = cfirst[e];
-                cnt = ccount[e];
-                bc = (int)e;
+                first = cfirst[j];
+                cnt = ccount[j];
+                bc = (int)j;
             }
-            const float4 hb = cen[2 * bc], lb = cen[2 * bc + 1];
+            float4 hb = cen[2 * bc], lb = cen[2 * bc + 1];
+            const unsigned int q = entry_copy(e, ib);
+            if (q != copy_centre(R)) {  // a source in a periodic copy: its bucket's centre shifted
+                int nx, ny, nz;
+                copy_shift(q, R, nx, ny, nz);
+                cen_shift(hb.x, lb.x, (float)nx);
+                cen_shift(hb.y, lb.y, (float)ny);
+                cen_shift(hb.z, lb.z, (float)nz);
+            }
             dx = cen_diff(hb.x, lb.x, hk.x, lk.x);
             dy = cen_diff(hb.y, lb.y, hk.y, lk.y);
             dz = cen_diff(hb.z, lb.z, hk.z, lk.z);
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
                                                  const float4* __restrict__ cen, const int* __restrict__ bucket_of,
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  float4* __restrict__ part_pp, const int* __restrict__ act,
-                                                 float eps2, int csize, long long cap_items,
+                                                 float eps2, int csize, long long cap_items, int ib, int R,
                                                  DevCounters* __restrict__ ctr)
 {
     __shared__ float4 tile[IW][PP_TILE];
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
         float4* part = part_pp + i * FMM_GMAX;
         long long nsrc;
 #define PP_CALL(R1, Q1, R2, Q2) \
-    pp_item<R1, Q1, R2, Q2>(G, n, act, k, hk, lk, pp, cfirst, ccount, cen, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize)
+    pp_item<R1, Q1, R2, Q2>(G, n, act, k, hk, lk, pp, cfirst, ccount, cen, bucket_of, bucket_cell, off, part, T, chunk[wl], eps2, lane, csize, ib, R)
         // sink slots in steps of 8 up to 48 sinks, in pairs per lane
         if (n <= 8) nsrc = PP_CALL(2, 8, 0, 0);
         else if (n <= 16) nsrc = PP_CALL(2, 4, 0, 0);
@@ -333,7 +342,7 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
                                         const int* __restrict__ bucket_of, const int* __restrict__ bucket_cell,
                                         const float4* __restrict__ off, const float4* __restrict__ rec4,
                                         float4* __restrict__ part, float4* R4, float4* Zxy, float2* Zz, int* ids,
-                                        float4* U, float4* A, float eps2, int lane, int csize)
+                                        float4* U, float4* A, float eps2, int lane, int csize, int ib, int R)
 {
     for (int i = lane; i < FMM_GMAX; i += 32) {
         float ux = 0.f, uy = 0.f, uz = 0.f, m;
@@ -352,8 +361,17 @@ __device__ __forceinline__ void pc_item(const Group& G, int nact, const int* __r
     for (int cbase = e0; cbase < e1; cbase += PC_CHUNK) {
         const int ne = min(PC_CHUNK, e1 - cbase);
         if (lane < ne) {
-            const unsigned int c = pc[G.pc_off + cbase + lane];
-            const float4 hs = cen[2 * c], ls = cen[2 * c + 1];
+            const unsigned int e = pc[G.pc_off + cbase + lane];
+            const unsigned int c = entry_index(e, ib);
+            float4 hs = cen[2 * c], ls = cen[2 * c + 1];
+            const unsigned int q = entry_copy(e, ib);
+            if (q != copy_centre(R)) {  // a cell in a periodic copy: its centre shifted
+                int nx, ny, nz;
+                copy_shift(q, R, nx, ny, nz);
+                cen_shift(hs.x, ls.x, (float)nx);
+                cen_shift(hs.y, ls.y, (float)ny);
+                cen_shift(hs.z, ls.z, (float)nz);
+            }
             ids[lane] = (int)c;
             const float zx = cen_diff(hs.x, ls.x, hk.x, lk.x), zy = cen_diff(hs.y, ls.y, hk.y, lk.y),
                         zz = cen_diff(hs.z, ls.z, hk.z, lk.z);
@@ -426,7 +444,7 @@ __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ gr
                                                  const int* __restrict__ bucket_cell, const float4* __restrict__ off,
                                                  const float* __restrict__ rec, float4* __restrict__ part_pc,
                                                  const int* __restrict__ act, float eps2, int csize, long long cap_items,
-                                                 DevCounters* __restrict__ ctr)
+                                                 int ib, int R, DevCounters* __restrict__ ctr)
 {
     __shared__ float4 R4s[IW][PC_CHUNK * FMM_NREC / 4];
     __shared__ float4 Zs[IW][PC_CHUNK];
@@ -449,7 +467,7 @@ __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ gr
         const float4 hk = cen[2 * G.cell], lk = cen[2 * G.cell + 1];
         const int n = cnact[G.cell];  // active sinks of the group
         pc_item(G, n, act, k, hk, lk, pc, cen, bucket_of, bucket_cell, off, rec4, part_pc + i * FMM_GMAX, R4s[wl], Zs[wl],
-                Zzs[wl], idss[wl], Us[wl], As[wl], eps2, lane, csize);
+                Zzs[wl], idss[wl], Us[wl], As[wl], eps2, lane, csize, ib, R);
         if (lane == 0) {
             const int nc = min(csize, G.pc_len - k * csize);
             pairs += (unsigned long long)cnact[G.cell] * (unsigned long long)nc;
@@ -638,7 +656,8 @@ cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pp);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
     k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.cen,
-                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, t.act, a.eps2, a.chunk, w.cap_item_pp, ctr);
+                                     t.bucket_of, t.bucket_cell, t.off, w.part_pp, t.act, a.eps2, a.chunk, w.cap_item_pp,
+                                     t.per_ib, t.per_R, ctr);
     return cudaGetLastError();
 }
 
@@ -649,24 +668,28 @@ cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
     if (!blocks) blocks = persistent_blocks(k_pc);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
     k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.cen, t.bucket_of,
-                                     t.bucket_cell, t.off, t.rec, w.part_pc, t.act, a.eps2, a.chunk, w.cap_item_pc, ctr);
+                                     t.bucket_cell, t.off, t.rec, w.part_pc, t.act, a.eps2, a.chunk, w.cap_item_pc,
+                                     t.per_ib, t.per_R, ctr);
     return cudaGetLastError();
 }
 
 cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, float* acc,
                                float* pot, long long n, cudaStream_t s, const unsigned int* perm)
 {
+    // the group expansions also carry the Ewald correction of a periodic box (terms & 8), so they
+    // are evaluated when either part is asked for
+    const int terms = (t.per_R > 0 && (a.terms & 8)) ? (a.terms | 4) : a.terms;
     if (!perm) perm = t.idx;
     const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     if (a.accumulate == 1)
         k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
-            a.terms);
+            terms);
     else
         k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
-            a.terms);
+            terms);
     return cudaGetLastError();
 }

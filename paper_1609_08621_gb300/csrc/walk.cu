@@ -21,6 +21,8 @@
 //
 // The local expansion of a walked cell is L_k = L2L(L_parent) + sum of M2L (CC) and P2L
 // (CP) terms, computed by a second kernel per level after the walk kernel of that level.
+#include <algorithm>
+
 #include "expansions.cuh"
 #include "fmm_internal.cuh"
 #include "mlp.cuh"
@@ -45,8 +47,30 @@ __device__ __forceinline__ float gap_axis(float lo_s, float hi_s, float lo_k, fl
 // MODE 0: fixed-theta criterion.  MODE 1: learned criterion for source cells (the network
 // decides inside the band, see mlp.cuh).  MODE 2: fixed criterion, and every (sink, source cell)
 // pair of the band is recorded for labelling (audit).
+//
+// A warp examines up to E * 32 entries of its sink's queue per step: lane l takes entries
+// base + s * 32 + l for slots s < E, the loads of every slot are in flight together, and the
+// outcomes are ranked slot by slot, so each list comes out in queue order, exactly as with one
+// entry per lane.  A sink's serial chain of steps (its checklist and what it opens, 32 entries
+// at a time) set each level's duration; E entries per lane shorten it E-fold where the queue is
+// long, and cost nothing extra where it is short (slots past the queue are skipped, warp-uniformly).
+//
+// Measured on the 128^3 NFW box: 2 to 4 entries per lane made the walk slower (3.93 ms with one,
+// 4.09 with two, 4.41 with four), because the extra registers halve the resident warps and each
+// entry's chain of dependent instructions does not shorten; one entry per lane is the default.
+#ifndef FMM_WALK_SLOTS
+#define FMM_WALK_SLOTS 1  // entries per lane and step
+#endif
+#ifndef FMM_WALK_MINB
+#define FMM_WALK_MINB 6  // resident blocks per SM the fixed-theta walk is compiled for
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
+struct WalkSlots {
+    static constexpr int E = FMM_WALK_SLOTS;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k_walk_level(
     const WalkNode* __restrict__ node, const float4* __restrict__ posf, const int* __restrict__ cnact,
     const int* __restrict__ f_cell, const unsigned long long* __restrict__ f_cloff, const int* __restrict__ f_cllen,
     int level, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
@@ -59,8 +83,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
     DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float4* __restrict__ mnorm,
     const float* __restrict__ amin,
     float eps, float band_lo, float band_hi, float tau, const unsigned char* __restrict__ mlp_packed,
-    int2* __restrict__ audit_pairs, long long audit_cap, const unsigned char* __restrict__ nogroup)
+    int2* __restrict__ audit_pairs, long long audit_cap, const unsigned char* __restrict__ nogroup, PeriodicArgs pa)
 {
+    constexpr int E = WalkSlots<MODE>::E;
+    const unsigned int q0 = copy_centre(pa.R);
     extern __shared__ __align__(16) unsigned char walk_smem[];
     if (MODE == 1) {
         mlp_load_smem(mlp_packed, walk_smem);
@@ -97,129 +123,213 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
         bool overflow = false;
         long long base = 0;
         while (base < ncl + nq) {
-            // entries appended while this batch runs get indices >= ncl + nq (batch start), so the
-            // next batch begins right after the entries that were actually available here
+            // entries appended while this step runs get indices >= ncl + nq (step start), so the
+            // next step begins right after the entries that were actually available here
             const long long avail = ncl + nq - base;
-            const long long vi = base + lane;
-            const bool valid = lane < avail;
-            base += avail < 32 ? avail : 32;
-            unsigned int e = 0;
-            if (valid) e = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
-            int out = OUT_NONE, nadd = 0, sfirst = 0, c0 = -1, c1 = -1, nsrc_cell = 0;
-            float f[MLP_F];  // learned criterion: the pair's features (set for band pairs)
-            bool sleaf = false, pointlike = false, acc = false, need = false;
-            float d2 = 0.0f, ro = 0.0f;
-            WalkNode S;
-            if (valid) {
-                float cx, cy, cz, lox, loy, loz, hix, hiy, hiz;
-                if (e & FMM_PARTICLE_BIT) {
-                    float4 p = posf[e & ~FMM_PARTICLE_BIT];
-                    cx = lox = hix = p.x;
-                    cy = loy = hiy = p.y;
-                    cz = loz = hiz = p.z;
-                    ro = 0.0f;
-                    pointlike = true;
-                } else {
-                    S = node[e];
-                    cx = S.a.x; cy = S.a.y; cz = S.a.z; ro = S.a.w;
-                    lox = S.b.x; loy = S.b.y; loz = S.b.z;
-                    hix = S.c.x; hiy = S.c.y; hiz = S.c.z;
-                    pointlike = S.d.w == 1;
-                    sleaf = S.d.x < 0;  // a leaf (bucket) has no children
-                    c0 = S.d.x;
-                    c1 = S.d.y;
-                    sfirst = S.d.z;
-                    nsrc_cell = S.d.w;
-                    nadd = sleaf ? S.d.w : 2;
+            const int ns = avail >= 32 * E ? E : (int)((avail + 31) >> 5);  // slots in use (warp-uniform)
+            unsigned int e[E];
+            bool valid[E];
+#pragma unroll
+            for (int s = 0; s < E; s++) {
+                const long long vi = base + s * 32 + lane;
+                valid[s] = s < ns && s * 32 + lane < avail;
+                e[s] = 0;
+                if (valid[s]) e[s] = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
+            }
+            base += avail < 32 * E ? avail : 32 * E;
+            WalkNode S[E];
+#pragma unroll
+            for (int s = 0; s < E; s++) {
+                if (valid[s]) {
+                    const unsigned int j = entry_index(e[s], pa.ib);
+                    if (e[s] & FMM_PARTICLE_BIT) S[s].a = posf[j];
+                    else S[s] = node[j];
                 }
-                d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
-                const float thr = __fadd_rn(__fmul_rn(1.5f, rk), ro);
-                const float gx = gap_axis(lox, hix, K.b.x, K.c.x);
-                const float gy = gap_axis(loy, hiy, K.b.y, K.c.y);
-                const float gz = gap_axis(loz, hiz, K.b.z, K.c.z);
-                const float gap2 = d2_ordered(gx, gy, gz);
-                acc = d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2;
-                if (MODE != 0 && !pointlike) {
-                    float te;
-                    int band = mlp_band(K, S, d2, gap2, four_eps2, band_lo, band_hi, te);
-                    if (MODE == 1) {
-                        if (band == 3 && !(ak > 0.0f)) {
-                            band = acc ? 1 : 2;  // no acceleration estimate: the fixed criterion decides
-                        } else if (band == 3) {
-                            mlp_pair_features(K, S, mnorm[e], ak, eps, f);
-                            band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau);
+            }
+            // a source in a periodic copy: its centre and box shifted in FP64, then rounded, read from
+            // the tables of those values (the axes with a non-zero shift)
+#pragma unroll
+            for (int s = 0; s < E; s++) {
+                if (valid[s] && entry_copy(e[s], pa.ib) != q0) {
+                    const unsigned int j = entry_index(e[s], pa.ib);
+                    int nv[3];
+                    copy_shift(entry_copy(e[s], pa.ib), pa.R, nv[0], nv[1], nv[2]);
+                    const int w2 = 2 * pa.R;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ax++) {
+                        if (nv[ax] == 0) continue;
+                        const long long slot = ((long long)j * 3 + ax) * w2 + shift_slot(nv[ax], pa.R);
+                        if (e[s] & FMM_PARTICLE_BIT) {
+                            const float x = pa.pshift[slot];
+                            if (ax == 0) S[s].a.x = x;
+                            else if (ax == 1) S[s].a.y = x;
+                            else S[s].a.z = x;
+                        } else {
+                            const float4 g = pa.cshift[slot];
+                            if (ax == 0) {
+                                S[s].a.x = g.x;
+                                S[s].b.x = g.y;
+                                S[s].c.x = g.z;
+                            } else if (ax == 1) {
+                                S[s].a.y = g.x;
+                                S[s].b.y = g.y;
+                                S[s].c.y = g.z;
+                            } else {
+                                S[s].a.z = g.x;
+                                S[s].b.z = g.y;
+                                S[s].c.z = g.z;
+                            }
                         }
-                        acc = band == 1;
-                        need = band == 3;
-                    } else if (band == 3) {
-                        const unsigned long long q = atomicAdd(&ctr->n_audit, 1ull);
-                        if ((long long)q < audit_cap) audit_pairs[q] = make_int2(k, (int)e);
                     }
                 }
             }
-            if (MODE == 1) {
-                const unsigned int nm = __ballot_sync(FMM_FULL_MASK, need);
-                if (nm) {
-                    if (!need) {
+            int out[E], nadd[E], sfirst[E], c0[E], c1[E], nsrc_cell[E];
+            bool sleaf[E];
 #pragma unroll
-                        for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
+            for (int s = 0; s < E; s++) {
+                out[s] = OUT_NONE;
+                nadd[s] = 0;
+                sfirst[s] = 0;
+                c0[s] = c1[s] = -1;
+                nsrc_cell[s] = 0;
+                sleaf[s] = false;
+                if (s >= ns) continue;
+                float f[MLP_F];  // learned criterion: the pair's features (set for band pairs)
+                bool pointlike = false, acc = false, need = false;
+                float d2 = 0.0f, ro = 0.0f;
+                if (valid[s]) {
+                    float cx, cy, cz, lox, loy, loz, hix, hiy, hiz;
+                    if (e[s] & FMM_PARTICLE_BIT) {
+                        const float4 p = S[s].a;
+                        cx = lox = hix = p.x;
+                        cy = loy = hiy = p.y;
+                        cz = loz = hiz = p.z;
+                        ro = 0.0f;
+                        pointlike = true;
+                    } else {
+                        cx = S[s].a.x; cy = S[s].a.y; cz = S[s].a.z; ro = S[s].a.w;
+                        lox = S[s].b.x; loy = S[s].b.y; loz = S[s].b.z;
+                        hix = S[s].c.x; hiy = S[s].c.y; hiz = S[s].c.z;
+                        pointlike = S[s].d.w == 1;
+                        sleaf[s] = S[s].d.x < 0;  // a leaf (bucket) has no children
+                        c0[s] = S[s].d.x;
+                        c1[s] = S[s].d.y;
+                        sfirst[s] = S[s].d.z;
+                        nsrc_cell[s] = S[s].d.w;
+                        nadd[s] = sleaf[s] ? S[s].d.w : 2;
                     }
-                    const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane, nm);
-                    if (need) acc = pred < tau;
-                    n_mlp += __popc(nm);
+                    d2 = d2_ordered(__fsub_rn(K.a.x, cx), __fsub_rn(K.a.y, cy), __fsub_rn(K.a.z, cz));
+                    const float thr = __fadd_rn(__fmul_rn(1.5f, rk), ro);
+                    const float gx = gap_axis(lox, hix, K.b.x, K.c.x);
+                    const float gy = gap_axis(loy, hiy, K.b.y, K.c.y);
+                    const float gz = gap_axis(loz, hiz, K.b.z, K.c.z);
+                    const float gap2 = d2_ordered(gx, gy, gz);
+                    acc = d2 > __fmul_rn(thr, thr) && gap2 >= four_eps2;
+                    if (MODE != 0 && !pointlike) {
+                        float te;
+                        int band = mlp_band(K, S[s], d2, gap2, four_eps2, band_lo, band_hi, te);
+                        if (MODE == 1) {
+                            if (band == 3 && !(ak > 0.0f)) {
+                                band = acc ? 1 : 2;  // no acceleration estimate: the fixed criterion decides
+                            } else if (band == 3) {
+                                mlp_pair_features(K, S[s], mnorm[entry_index(e[s], pa.ib)], ak, eps, f);
+                                band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau);
+                            }
+                            acc = band == 1;
+                            need = band == 3;
+                        } else if (band == 3) {
+                            const unsigned long long q = atomicAdd(&ctr->n_audit, 1ull);
+                            if ((long long)q < audit_cap) audit_pairs[q] = make_int2(k, (int)e[s]);
+                        }
+                    }
                 }
-            }
-            if (valid) {
-                if (acc) {
-                    out = OUT_ACCEPT;
-                } else if (!kg) {
-                    out = (pointlike || ro <= rk) ? OUT_DEFER : OUT_OPEN;
-                } else if (pointlike) {
-                    out = OUT_PP;
-                } else {
-                    const float u = __fadd_rn(ro, bk);
-                    if (d2 > __fmul_rn(u, u)) out = OUT_PC;
-                    else out = sleaf ? OUT_PP : OUT_OPEN;
-                }
-                if (out != OUT_OPEN) nadd = 0;
-            }
-            const unsigned int mA = __ballot_sync(FMM_FULL_MASK, out == OUT_ACCEPT);
-            const unsigned int mD = __ballot_sync(FMM_FULL_MASK, out == OUT_DEFER);
-            const unsigned int mC = __ballot_sync(FMM_FULL_MASK, out == OUT_PC);
-            const unsigned int mP = __ballot_sync(FMM_FULL_MASK, out == OUT_PP);
-            int incl = nadd;
+                if (MODE == 1) {
+                    const unsigned int nm = __ballot_sync(FMM_FULL_MASK, need);
+                    if (nm) {
+                        if (!need) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(FMM_FULL_MASK, incl, o);
-                if (lane >= o) incl += t;
+                            for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
+                        }
+                        const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane, nm);
+                        if (need) acc = pred < tau;
+                        n_mlp += __popc(nm);
+                    }
+                }
+                if (valid[s]) {
+                    if (acc) {
+                        out[s] = OUT_ACCEPT;
+                    } else if (!kg) {
+                        out[s] = (pointlike || ro <= rk) ? OUT_DEFER : OUT_OPEN;
+                    } else if (pointlike) {
+                        out[s] = OUT_PP;
+                    } else {
+                        const float u = __fadd_rn(ro, bk);
+                        if (d2 > __fmul_rn(u, u)) out[s] = OUT_PC;
+                        else out[s] = sleaf[s] ? OUT_PP : OUT_OPEN;
+                    }
+                    if (out[s] != OUT_OPEN) nadd[s] = 0;
+                }
             }
-            const int tot = __shfl_sync(FMM_FULL_MASK, incl, 31);
-            if (na + __popc(mA) > cap_scr || nd + __popc(mD) > cap_scr || npc + __popc(mC) > cap_scr ||
-                npp + __popc(mP) > cap_scr || nq + tot > cap_scr) {
+            // ranks in queue order: slot by slot, lanes in order within a slot
+            unsigned int mA[E], mD[E], mC[E], mP[E];
+            int incl[E], tot[E];
+            long long tA = 0, tD = 0, tC = 0, tP = 0, tQ = 0;
+#pragma unroll
+            for (int s = 0; s < E; s++) {
+                mA[s] = mD[s] = mC[s] = mP[s] = 0u;
+                incl[s] = tot[s] = 0;
+                if (s >= ns) continue;
+                mA[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_ACCEPT);
+                mD[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_DEFER);
+                mC[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_PC);
+                mP[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_PP);
+                int v = nadd[s];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FMM_FULL_MASK, v, o);
+                    if (lane >= o) v += t;
+                }
+                incl[s] = v;
+                tot[s] = __shfl_sync(FMM_FULL_MASK, v, 31);
+                tA += __popc(mA[s]);
+                tD += __popc(mD[s]);
+                tC += __popc(mC[s]);
+                tP += __popc(mP[s]);
+                tQ += tot[s];
+            }
+            if (na + tA > cap_scr || nd + tD > cap_scr || npc + tC > cap_scr || npp + tP > cap_scr ||
+                nq + tQ > cap_scr) {
                 overflow = true;
                 break;
             }
-            if (out == OUT_ACCEPT) A[na + __popc(mA & lt)] = e;
-            if (out == OUT_DEFER) D[nd + __popc(mD & lt)] = e;
-            if (out == OUT_PC) C[npc + __popc(mC & lt)] = e;
-            if (out == OUT_PP) {
-                P[npp + __popc(mP & lt)] = e;
-                srcpp += (e & FMM_PARTICLE_BIT) ? 1 : nsrc_cell;
-            }
-            if (out == OUT_OPEN) {
-                long long pos = nq + incl - nadd;
-                if (sleaf) {
-                    for (int j = 0; j < nadd; j++) Q[pos + j] = (unsigned int)(sfirst + j) | FMM_PARTICLE_BIT;
-                } else {
-                    Q[pos] = (unsigned int)c0;
-                    Q[pos + 1] = (unsigned int)c1;
+#pragma unroll
+            for (int s = 0; s < E; s++) {
+                if (s >= ns) continue;
+                if (out[s] == OUT_ACCEPT) A[na + __popc(mA[s] & lt)] = e[s];
+                if (out[s] == OUT_DEFER) D[nd + __popc(mD[s] & lt)] = e[s];
+                if (out[s] == OUT_PC) C[npc + __popc(mC[s] & lt)] = e[s];
+                if (out[s] == OUT_PP) {
+                    P[npp + __popc(mP[s] & lt)] = e[s];
+                    srcpp += (e[s] & FMM_PARTICLE_BIT) ? 1 : nsrc_cell[s];
                 }
+                if (out[s] == OUT_OPEN) {
+                    // the children, or a leaf's particles, stay in the source's copy
+                    const long long pos = nq + incl[s] - nadd[s];
+                    const unsigned int qb = entry_copy(e[s], pa.ib) << pa.ib;
+                    if (sleaf[s]) {
+                        for (int j = 0; j < nadd[s]; j++)
+                            Q[pos + j] = ((unsigned int)(sfirst[s] + j) | qb) | FMM_PARTICLE_BIT;
+                    } else {
+                        Q[pos] = (unsigned int)c0[s] | qb;
+                        Q[pos + 1] = (unsigned int)c1[s] | qb;
+                    }
+                }
+                na += __popc(mA[s]);
+                nd += __popc(mD[s]);
+                npc += __popc(mC[s]);
+                npp += __popc(mP[s]);
+                nq += tot[s];
             }
-            na += __popc(mA);
-            nd += __popc(mD);
-            npc += __popc(mC);
-            npp += __popc(mP);
-            nq += tot;
             __syncwarp();
         }
         if (overflow) {
@@ -318,37 +428,52 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : 6) k_walk_level(
 #define LF_ENTRIES FMM_LOCAL_RANGE
 
 // Centres enter as float pairs (cen_diff): the sink's (hk, lk), a cell's from cen, a particle's
-// from posf (hi, and its mass) and plo (lo).
+// from posf (hi, and its mass) and plo (lo); a source in a periodic copy has its pair shifted
+// (cen_shift) by the copy's integer offset.
 __device__ __forceinline__ void local_entry(unsigned int e, const float4& hk, const float4& lk,
                                             const int* __restrict__ ccount, const float4* __restrict__ cen,
                                             const float4* __restrict__ posf, const float4* __restrict__ plo,
-                                            const float* __restrict__ rec, float eps2, float* acc, int& ncc, int& ncp)
+                                            const float* __restrict__ rec, float eps2, int ib, int R, float* acc,
+                                            int& ncc, int& ncp)
 {
+    const unsigned int j = entry_index(e, ib);
+    const unsigned int q = entry_copy(e, ib);
+    const bool shifted = q != copy_centre(R);
+    int nx = 0, ny = 0, nz = 0;
+    if (shifted) copy_shift(q, R, nx, ny, nz);
+    float4 hs, ls;
     if (e & FMM_PARTICLE_BIT) {
-        const unsigned int j = e & ~FMM_PARTICLE_BIT;
-        const float4 hs = posf[j], ls = plo[j];
-        fmm_p2l_acc(hs.w, cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
-                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
+        hs = posf[j];
+        ls = plo[j];
+    } else {
+        hs = cen[2 * j];
+        ls = cen[2 * j + 1];
+    }
+    if (shifted) {
+        cen_shift(hs.x, ls.x, (float)nx);
+        cen_shift(hs.y, ls.y, (float)ny);
+        cen_shift(hs.z, ls.z, (float)nz);
+    }
+    const float rx = cen_diff(hk.x, lk.x, hs.x, ls.x), ry = cen_diff(hk.y, lk.y, hs.y, ls.y),
+                rz = cen_diff(hk.z, lk.z, hs.z, ls.z);
+    if (e & FMM_PARTICLE_BIT) {
+        fmm_p2l_acc(hs.w, rx, ry, rz, eps2, acc);
         ncp++;
-    } else if (ccount[e] == 1) {  // a one-particle cell: its particle (mass = moment M[0]) -> local expansion
-        const float4 hs = cen[2 * e], ls = cen[2 * e + 1];
-        fmm_p2l_acc(rec[(long long)e * FMM_NREC], cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
-                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
+    } else if (ccount[j] == 1) {  // a one-particle cell: its particle (mass = moment M[0]) -> local expansion
+        fmm_p2l_acc(rec[(long long)j * FMM_NREC], rx, ry, rz, eps2, acc);
         ncp++;
     } else {
-        const float4 hs = cen[2 * e], ls = cen[2 * e + 1];
         float M[FMM_NMOM];
-        const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)e * FMM_NREC);
+        const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)j * FMM_NREC);
 #pragma unroll
-        for (int q = 0; q < FMM_NMOM / 4; q++) {
-            const float4 v = r4[q];
-            M[4 * q] = v.x;
-            M[4 * q + 1] = v.y;
-            M[4 * q + 2] = v.z;
-            M[4 * q + 3] = v.w;
+        for (int q4 = 0; q4 < FMM_NMOM / 4; q4++) {
+            const float4 v = r4[q4];
+            M[4 * q4] = v.x;
+            M[4 * q4 + 1] = v.y;
+            M[4 * q4 + 2] = v.z;
+            M[4 * q4 + 3] = v.w;
         }
-        fmm_m2l_acc(M, cen_diff(hk.x, lk.x, hs.x, ls.x), cen_diff(hk.y, lk.y, hs.y, ls.y),
-                    cen_diff(hk.z, lk.z, hs.z, ls.z), eps2, acc);
+        fmm_m2l_acc(M, rx, ry, rz, eps2, acc);
         ncc++;
     }
 }
@@ -369,7 +494,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const int* __restrict__ lcc_len, const int* __restrict__ ccount, const float4* __restrict__ cen,
     const float4* __restrict__ posf, const float4* __restrict__ plo,
     const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
-    float eps2, DevCounters* __restrict__ ctr)
+    float eps2, int ib, int R, DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -393,7 +518,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
             for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
             if (valid) {
                 sink = cc_sink[idx];
-                local_entry(cc[idx], cen[2 * sink], cen[2 * sink + 1], ccount, cen, posf, plo, rec, eps2, acc, ncc, ncp);
+                local_entry(cc[idx], cen[2 * sink], cen[2 * sink + 1], ccount, cen, posf, plo, rec, eps2, ib, R, acc,
+                            ncc, ncp);
             }
 #pragma unroll
             for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
@@ -495,14 +621,56 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
     }
 }
 
+// The shifted geometry of a periodic box's copies (PeriodicArgs): per cell and particle, axis and
+// non-zero shift v, the FP64 sum rounded once to FP32 -- the values the walk's decisions use.
+__global__ void k_shift_tables(const unsigned int* __restrict__ ncell, long long n, int R, const Com4* __restrict__ com,
+                               const double* __restrict__ clo, const double* __restrict__ chi,
+                               const double* __restrict__ sx, const double* __restrict__ sy,
+                               const double* __restrict__ sz, float4* __restrict__ cshift, float* __restrict__ pshift)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int w2 = 2 * R;
+    if (i < (long long)*ncell) {
+        const Com4 c = com[i];
+        const double cc[3] = {c.x, c.y, c.z};
+        for (int ax = 0; ax < 3; ax++)
+            for (int v = -R; v <= R; v++) {
+                if (v == 0) continue;
+                cshift[(i * 3 + ax) * w2 + shift_slot(v, R)] =
+                    make_float4(__double2float_rn(cc[ax] + v), __double2float_rn(clo[3 * i + ax] + v),
+                                __double2float_rn(chi[3 * i + ax] + v), 0.0f);
+            }
+    }
+    if (i < n) {
+        const double x[3] = {sx[i], sy[i], sz[i]};
+        for (int ax = 0; ax < 3; ax++)
+            for (int v = -R; v <= R; v++) {
+                if (v == 0) continue;
+                pshift[(i * 3 + ax) * w2 + shift_slot(v, R)] = __double2float_rn(x[ax] + v);
+            }
+    }
+}
+
+cudaError_t fmm_launch_shift_tables(DevTree& t, cudaStream_t s)
+{
+    if (t.per_R <= 0) return cudaSuccess;
+    if (!t.cshift || !t.pshift) return cudaErrorInvalidValue;
+    const long long span = std::max(t.cap_grid ? t.cap_cells : t.n_cells, t.n);
+    k_shift_tables<<<(unsigned)fmm_ceil_div(span, 256), 256, 0, s>>>(t.dcount, t.n, t.per_R, t.com, t.clo, t.chi, t.sx,
+                                                                     t.sy, t.sz, t.cshift, t.pshift);
+    return cudaGetLastError();
+}
+
 // level 0 of the walk: every box's root cell as a sink, with that root alone on its checklist
 // (isolated boxes: sources of other boxes are never seen); boxes without an active particle
 // are not walked
 // Each box's root starts the walk with itself on its checklist.  With one box and second_root >= 0
 // (the root of an appended fixed tree, dual.cu) the checklist holds both roots.
+// In a periodic box (R > 0, one box) the checklist holds the root and its (2R + 1)^3 - 1 copies,
+// in the order of their copy codes.
 __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cllen, unsigned int* cl,
                             const int* __restrict__ cnact, const int* __restrict__ box_root, int nbox,
-                            int second_root, DevCounters* ctr)
+                            int second_root, int R, int ib, DevCounters* ctr)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbox) return;
@@ -510,6 +678,13 @@ __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cll
     if (r < 0 || cnact[r] <= 0) return;  // an empty box has no root cell
     const unsigned long long k = atomicAdd(&ctr->lv_front[0], 1ull);
     f_cell[k] = r;
+    if (R > 0) {  // one box only
+        const int W = 2 * R + 1, nc = W * W * W;
+        f_cloff[k] = 0;
+        f_cllen[k] = nc;
+        for (int q = 0; q < nc; q++) cl[q] = ((unsigned int)q << ib) | (unsigned int)r;
+        return;
+    }
     if (second_root >= 0) {  // one box only: its entries are cl[0], cl[1]
         f_cloff[k] = 0;
         f_cllen[k] = 2;
@@ -525,9 +700,10 @@ __global__ void k_walk_seed(int* f_cell, unsigned long long* f_cloff, int* f_cll
 cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root)
 {
     if (second_root >= 0 && t.nbox != 1) return cudaErrorInvalidValue;
+    if (t.per_R > 0 && (t.nbox != 1 || second_root >= 0)) return cudaErrorInvalidValue;
     k_walk_seed<<<(unsigned)fmm_ceil_div(t.nbox, 128), 128, 0, s>>>(w.f_cell[0], w.f_cloff[0], w.f_cllen[0], w.cl[0],
                                                                      t.cnact, t.nbox > 1 ? t.box_root : nullptr,
-                                                                     t.nbox, second_root, ctr);
+                                                                     t.nbox, second_root, t.per_R, t.per_ib, ctr);
     return cudaGetLastError();
 }
 
@@ -548,7 +724,7 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
         w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
         w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
         a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
-        a.audit_cap, t.graded ? t.nogroup : nullptr
+        a.audit_cap, t.graded ? t.nogroup : nullptr, periodic_args(t)
     if (a.mode == 1) {
         const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;
         static std::atomic<unsigned long long> attr{0};
@@ -568,7 +744,7 @@ cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps
 {
     const int blocks = w.n_warps / LOCAL_WPB;
     k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.cen, t.posf,
-                                                   t.plo, t.rec, t.L, w.cap_cc, eps2, ctr);
+                                                   t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
     k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, ctr);
     return cudaGetLastError();
 }

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol():
 def test_library_loads_and_host_only_calls_work():
     L = binding.load()
     p = binding.fmm_default_params()
-    assert p.theta == 0.55 and p.bucket == 16 and p.group == 64 and p.terms == 7
+    assert p.theta == 0.55 and p.bucket == 16 and p.group == 64 and p.terms == 15 and p.nrep == 0
     assert binding.fmm_flops_per_pc() > 200
     loc, mom = binding.fmm_multi_index()
     assert loc.shape == (56, 3) and mom.shape == (32, 3)
