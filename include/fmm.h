@@ -97,7 +97,11 @@ typedef struct fmm_params {
      * interaction when theta_eff < band_lo, rejected when theta_eff >= band_hi, and in between
      * accepted when the network's predicted log10 relative force error is < mlp_tau.  A guard
      * (d > 1.1 (b_max(sink) + b_max(source)), bounding boxes >= 2 eps apart) always applies.
-     * Defaults: band 0.35 .. 1.0, mlp_tau = -3.5. */
+     * Defaults: band 0.35 .. 1.0, mlp_tau = -3.5.  Inside the band a linear surrogate fitted
+     * to the network at training time decides the pairs whose prediction lies clear of mlp_tau:
+     * mlp_margin in [0, 1] scales the surrogate's residual range on the training rows (1: the
+     * network decides every pair the surrogate could have got wrong there; 0: the surrogate
+     * decides alone); default 0.1. */
     double mlp_tau;
     double band_lo;
     double band_hi;
@@ -111,6 +115,7 @@ typedef struct fmm_params {
      * fixed criterion only, no dual trees, and n <= 2^26 (nrep 1) or 2^24 (nrep 2): list entries
      * carry the copy in their upper bits. */
     int nrep;
+    double mlp_margin;
 } fmm_params;
 
 /* Per-solve statistics of the last fmm_compute_forces on a context. */
@@ -415,6 +420,24 @@ fmm_status fmm_export_walk_levels(const fmm_ctx *ctx, long long *counts, int cap
 /* The 56 multi-indices (a, b, c) of the local coefficients in storage order (168 ints),
  * and the 32 multi-indices of the moment slots (96 ints).  Either may be NULL. */
 fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
+
+/* ---------------------------------------------------------------- test hooks
+ *
+ * Not in the paper: they let tests drive the library's recovery paths from the host, with no GPU
+ * fault.
+ *
+ * fmm_debug_fail_allocations: the calling thread's next `after` device allocations of any context
+ * succeed and the ones after them fail as out of memory (FMM_ERR_OOM from the call that needed
+ * them); after < 0 switches the hook off.  A context whose allocation failed stays usable: the
+ * buffers involved are allocated again by its next call.
+ *
+ * fmm_debug_walk_capacity: the walk's first capacities for a context whose buffers have not been
+ * sized yet: scratch_entries per warp and list (default 8192) and list_scale checklist, CC and PC
+ * entries per particle (default 16; PP half of it); 0 keeps a default.  Each overflow grows them
+ * x4 and repeats the walk, up to 6 times, so small values exercise that path.  Returns
+ * FMM_ERR_ARG for ctx == NULL or negative values. */
+fmm_status fmm_debug_fail_allocations(long long after);
+fmm_status fmm_debug_walk_capacity(fmm_ctx *ctx, long long scratch_entries, long long list_scale);
 
 /* ---------------------------------------------------------------- allocation-free Morton order
  *

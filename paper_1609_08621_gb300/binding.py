@@ -34,7 +34,7 @@ class fmm_params(C.Structure):
     _fields_ = [("theta", C.c_double), ("eps", C.c_double), ("bucket", C.c_int), ("group", C.c_int),
                 ("criterion", C.c_int), ("accumulate", C.c_int), ("terms", C.c_int), ("list_chunk", C.c_int),
                 ("spin_limit", C.c_longlong), ("mlp_tau", C.c_double), ("band_lo", C.c_double),
-                ("band_hi", C.c_double), ("nrep", C.c_int)]
+                ("band_hi", C.c_double), ("nrep", C.c_int), ("mlp_margin", C.c_double)]
 
 
 class fmm_stats(C.Structure):
@@ -101,6 +101,8 @@ def load(build_if_missing: bool = True):
         "fmm_mlp_audit": (i, [vp, vp, vp, ll, d, d, d, d, vp, ll, vp, vp, C.POINTER(ll)]),
         "fmm_mlp_audit_pairs": (i, [vp, vp, vp, vp, vp, ll]),
         "fmm_morton_order_static": (i, [vp, ll, vp, vp, vp]),
+        "fmm_debug_fail_allocations": (i, [ll]),
+        "fmm_debug_walk_capacity": (i, [vp, ll, ll]),
         "fmm_set_graphs": (i, [vp, i]),
         "fmm_graph_info": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
         "fmm_autotune": (i, [vp, vp, vp, ll, vp, i, d, d, vp, i, i, vp, C.POINTER(fmm_params), C.POINTER(C.c_float)]),
@@ -187,6 +189,12 @@ def morton_order_static(pos, keys, order, stream=None):
         _check(load().fmm_morton_order_static(_ptr(pos, torch.float64, 3 * n, "pos"), n,
                                               _ptr(keys, torch.int64, n, "keys"),
                                               _ptr(order, torch.int32, n, "order"), C.c_void_p(stream.cuda_stream)))
+
+
+def debug_fail_allocations(after):
+    """fmm_debug_fail_allocations: the calling thread's device allocations after the next `after`
+    fail as out of memory (after < 0: off).  A test hook for the recovery path."""
+    _check(load().fmm_debug_fail_allocations(int(after)))
 
 
 class Context:
@@ -473,6 +481,11 @@ class Context:
         _check(load().fmm_export_lists(self.h, k, C.byref(n), sink.ctypes.data, first.ctypes.data,
                                        count.ctypes.data, m))
         return sink[:m], first[:m], count[:m]
+
+    def debug_walk_capacity(self, scratch_entries=0, list_scale=0):
+        """fmm_debug_walk_capacity: the walk's first scratch and list capacities (0: default), a
+        test hook that makes the walk overflow and regrow."""
+        _check(load().fmm_debug_walk_capacity(self.h, int(scratch_entries), int(list_scale)))
 
     def export_list_shifts(self, kind):
         """fmm_export_list_shifts: the periodic copy (n_x, n_y, n_z) of each entry's source, rows in

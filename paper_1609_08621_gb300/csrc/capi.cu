@@ -46,6 +46,12 @@ fmm_status fail(fmm_status st, const char* fmt, ...)
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
     } while (0)
 
+// Buffer growth.  A block that regrows a group of buffers first sets their capacity to 0, so an
+// allocation that fails part-way (FMM_ERR_OOM) leaves every buffer of the group to be allocated
+// again by the next call: the context stays usable.  fmm_debug_fail_allocations makes the calling
+// thread's next allocations fail, to test exactly that.
+thread_local long long g_fail_allocs_after = -1;  // < 0: off; else successful allocations left
+
 template <typename T>
 cudaError_t grow(T** p, long long* cap, long long need)
 {
@@ -54,6 +60,8 @@ cudaError_t grow(T** p, long long* cap, long long need)
     *p = nullptr;
     *cap = 0;
     if (need < 1) need = 1;
+    if (g_fail_allocs_after == 0) return cudaErrorMemoryAllocation;
+    if (g_fail_allocs_after > 0) g_fail_allocs_after--;
     cudaError_t e = cudaMalloc((void**)p, (size_t)need * sizeof(T));
     if (e == cudaSuccess) *cap = need;
     return e;
@@ -132,6 +140,8 @@ struct fmm_ctx {
     // the tree, join before the groups add them)
     cudaStream_t ew_stream = nullptr;
     cudaEvent_t ew_fork = nullptr, ew_join = nullptr;
+    // test hook (fmm_debug_walk_capacity): the walk's first per-warp scratch and list capacities
+    long long dbg_scratch = 0, dbg_list_scale = 0;
     // staging for the host-buffer entry point
     double* hpos = nullptr;
     float *hmass = nullptr, *hacc = nullptr, *hpot = nullptr;
@@ -151,6 +161,7 @@ static fmm_status check_params(const fmm_params* p)
     if (!(p->band_lo > 0.0 && p->band_lo <= p->band_hi && p->band_hi <= 2.0))
         return fail(FMM_ERR_ARG, "band must satisfy 0 < band_lo <= band_hi <= 2");
     if (!isfinite(p->mlp_tau)) return fail(FMM_ERR_ARG, "mlp_tau must be finite");
+    if (!(p->mlp_margin >= 0.0 && p->mlp_margin <= 1.0)) return fail(FMM_ERR_ARG, "mlp_margin must be in [0, 1]");
     if (p->accumulate != 0 && p->accumulate != 1) return fail(FMM_ERR_ARG, "accumulate must be 0 or 1, got %d", p->accumulate);
     if (p->terms < 0 || p->terms > 15) return fail(FMM_ERR_ARG, "terms must be a mask of 1|2|4|8, got %d", p->terms);
     if (p->nrep < 0 || p->nrep > 2) return fail(FMM_ERR_ARG, "nrep must be 0 (isolated), 1 or 2, got %d", p->nrep);
@@ -176,10 +187,26 @@ extern "C" fmm_status fmm_default_params(fmm_params* p)
     p->mlp_tau = -3.5;
     p->band_lo = 0.35;
     p->band_hi = 1.0;
+    p->mlp_margin = 0.1;
     return FMM_OK;
 }
 
 extern "C" const char* fmm_last_error(void) { return g_err.c_str(); }
+
+extern "C" fmm_status fmm_debug_fail_allocations(long long after)
+{
+    g_fail_allocs_after = after < 0 ? -1 : after;
+    return FMM_OK;
+}
+
+extern "C" fmm_status fmm_debug_walk_capacity(fmm_ctx* c, long long scratch_entries, long long list_scale)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (scratch_entries < 0 || list_scale < 0) return fail(FMM_ERR_ARG, "capacities must be >= 0");
+    c->dbg_scratch = scratch_entries;
+    c->dbg_list_scale = list_scale;
+    return FMM_OK;
+}
 
 extern "C" double fmm_flops_per_pc(void) { return (double)FMM_FLOPS_PC; }
 
@@ -291,6 +318,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
 {
     DevTree& t = c->t;
     if (n > t.cap_n) {
+        t.cap_n = 0;
         long long cap = n;
         CK(alloc(&t.key, cap));
         CK(alloc(&t.key_alt, cap));
@@ -322,6 +350,7 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
     if (need_cells > 2 * n + 1) need_cells = 2 * n + 1;
     if (need_cells < min_cells) need_cells = min_cells;
     if (need_cells > t.cap_cells) {
+        t.cap_cells = 0;
         long long cap = need_cells;
         CK(alloc(&t.cfirst, cap));
         CK(alloc(&t.ccount, cap));
@@ -382,6 +411,7 @@ static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int n
     t.nbox = nbox;
     if (nbox == 1) return FMM_OK;
     if (nbox + 1 > t.cap_box) {
+        t.cap_box = 0;
         CK(alloc(&t.box_off, nbox + 1));
         CK(alloc(&t.box_root, nbox + 1));
         if (t.box_off_h) cudaFreeHost(t.box_off_h);
@@ -390,6 +420,7 @@ static fmm_status set_boxes(fmm_ctx* c, long long n, const long long* off, int n
         t.cap_box = nbox + 1;
     }
     if (n > t.cap_box_n) {
+        t.cap_box_n = 0;
         CK(alloc(&t.sbox, n));
         CK(alloc(&t.key_orig, n));
         t.cap_box_n = n;
@@ -441,6 +472,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     {
         const long long need = fmm_bmax_items_bound(n, (int)c->ctr_h->depth, t.n_cells);
         if (need > t.cap_bm_items) {
+            t.cap_bm_items = 0;
             CK(alloc(&t.bm_item, need));
             CK(alloc(&t.bm_imax, need));
             t.cap_bm_items = need;
@@ -488,12 +520,16 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
     DevWalk& w = c->w;
     long long cells = c->t.cap_cells;
     long long need_front = cells;
-    long long need_cl = (long long)scale * 16 * n + 4096;
-    long long need_pp = (long long)scale * 8 * n + 4096;
-    long long need_pc = (long long)scale * 16 * n + 4096;
-    long long need_cc = (long long)scale * 16 * n + 4096;
-    long long need_scr = 8192LL * scale;
+    // per particle: checklist 16, PP 8, PC 16, local 16 entries, and 8192 scratch entries per warp
+    // and list (fmm_debug_walk_capacity may start them smaller); each retry grows them x4
+    const long long ls = c->dbg_list_scale > 0 ? c->dbg_list_scale : 16;
+    long long need_cl = (long long)scale * ls * n + 4096;
+    long long need_pp = (long long)scale * (ls / 2) * n + 4096;
+    long long need_pc = (long long)scale * ls * n + 4096;
+    long long need_cc = (long long)scale * ls * n + 4096;
+    long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * scale;
     if (need_front > w.cap_front) {
+        w.cap_front = 0;
         for (int i = 0; i < 2; i++) {
             CK(alloc(&w.f_cell[i], need_front));
             CK(alloc(&w.f_cloff[i], need_front));
@@ -512,38 +548,46 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
         w.cap_groups = need_front;
     }
     if (need_cl > w.cap_cl) {
+        w.cap_cl = 0;
         CK(alloc(&w.cl[0], need_cl));
         CK(alloc(&w.cl[1], need_cl));
         w.cap_cl = need_cl;
     }
     if (need_pp > w.cap_pp) {
+        w.cap_pp = 0;
         CK(alloc(&w.pp, need_pp));
         w.cap_pp = need_pp;
     }
     if (need_pc > w.cap_pc) {
+        w.cap_pc = 0;
         CK(alloc(&w.pc, need_pc));
         w.cap_pc = need_pc;
     }
     if (need_cc > w.cap_cc) {
+        w.cap_cc = 0;
         CK(alloc(&w.cc, need_cc));
         CK(alloc(&w.cc_sink, need_cc));
         w.cap_cc = need_cc;
     }
     if (need_scr > w.cap_scratch) {
+        w.cap_scratch = 0;
         CK(alloc(&w.scratch, (long long)w.n_warps * 5 * need_scr));
         w.cap_scratch = need_scr;
     }
     return FMM_OK;
 }
 
-// The periodic state of the coming walk (Sec. 3.1, periodic boundaries): the replica shell and
-// the index bits of list entries, which must leave room for the copy code above them.  Isolated
-// solves reset it.
+// The encoding of the coming walk's list entries: for a periodic box (Sec. 3.1, periodic
+// boundaries) the replica shell and the index bits, which must leave room for the copy code above
+// them; isolated solves reset it.
 static fmm_status set_periodic(fmm_ctx* c, const fmm_params& q, long long n, int nbox)
 {
     DevTree& t = c->t;
     t.per_R = 0;
     t.per_ib = 31;
+    // the learned walk marks cell entries with the network's decision in bits 29 and 30
+    if (q.criterion == 1 && t.cap_cells >= (1LL << 29))
+        return fail(FMM_ERR_ARG, "the learned criterion holds at most 2^29 cells, the tree may have %lld", t.cap_cells);
     if (q.nrep == 0) return FMM_OK;
     if (nbox != 1) return fail(FMM_ERR_ARG, "a periodic solve (nrep %d) takes one box, got %d", q.nrep, nbox);
     if (q.criterion != 0) return fail(FMM_ERR_ARG, "a periodic solve (nrep %d) takes the fixed criterion", q.nrep);
@@ -615,6 +659,7 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     a.band_lo = (float)c->params.band_lo;
     a.band_hi = (float)c->params.band_hi;
     a.tau = (float)c->params.mlp_tau;
+    a.margin = (float)c->params.mlp_margin;
     a.mlp_packed = c->mlp_packed;
     a.audit_pairs = c->audit_pairs;
     a.audit_cap = c->audit_cap;
@@ -727,11 +772,13 @@ static fmm_status interact_and_finish(fmm_ctx* c, const fmm_params& q, double ep
         long long need_pp = w.pp_len / ia.chunk + w.n_groups + 1;
         long long need_pc = w.pc_len / ia.chunk + w.n_groups + 1;
         if (need_pp > w.cap_item_pp) {
+            w.cap_item_pp = 0;
             CK(alloc(&w.item_pp, need_pp));
             CK(alloc(&w.part_pp, need_pp * FMM_GMAX));
             w.cap_item_pp = need_pp;
         }
         if (need_pc > w.cap_item_pc) {
+            w.cap_item_pc = 0;
             CK(alloc(&w.item_pc, need_pc));
             CK(alloc(&w.part_pc, need_pc * FMM_GMAX));
             w.cap_item_pc = need_pc;
@@ -862,6 +909,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     a.band_lo = (float)q.band_lo;
     a.band_hi = (float)q.band_hi;
     a.tau = (float)q.mlp_tau;
+    a.margin = (float)q.mlp_margin;
     a.mlp_packed = c->mlp_packed;
     a.audit_pairs = c->audit_pairs;
     a.audit_cap = c->audit_cap;
@@ -905,7 +953,7 @@ static bool same_params(const fmm_params& a, const fmm_params& b)
     return a.theta == b.theta && a.eps == b.eps && a.bucket == b.bucket && a.group == b.group &&
            a.criterion == b.criterion && a.accumulate == b.accumulate && a.terms == b.terms &&
            a.list_chunk == b.list_chunk && a.spin_limit == b.spin_limit && a.mlp_tau == b.mlp_tau &&
-           a.band_lo == b.band_lo && a.band_hi == b.band_hi;
+           a.band_lo == b.band_lo && a.band_hi == b.band_hi && a.nrep == b.nrep && a.mlp_margin == b.mlp_margin;
 }
 
 static fmm_ctx::GraphKey make_key(const double* pos, const float* mass, const unsigned char* active, float* acc,
@@ -1214,6 +1262,7 @@ extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const
     if (st != FMM_OK) return st;
     // membership of the fixed set, in the caller's order, for the dual solves
     if (n > f.cap_member) {
+        f.cap_member = 0;
         CK(alloc(&f.member, n));
         f.cap_member = n;
     }
@@ -1229,6 +1278,7 @@ extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const
         cudaStream_t s = c->stream;
         const long long nc = t.n_cells, nb = t.n_buckets;
         if (nc > f.cap_cells) {
+            f.cap_cells = 0;
             CK(alloc(&f.cfirst, nc));
             CK(alloc(&f.ccount, nc));
             CK(alloc(&f.cchild, 2 * nc));
@@ -1242,6 +1292,7 @@ extern "C" fmm_status fmm_set_fixed_sources(fmm_ctx* c, const double* pos, const
             f.cap_cells = nc;
         }
         if (m > f.cap_n) {
+            f.cap_n = 0;
             CK(alloc(&f.posf, m));
             CK(alloc(&f.plo, m));
             CK(alloc(&f.off, m));
@@ -1376,6 +1427,7 @@ extern "C" fmm_status fmm_compute_forces_host(fmm_ctx* c, const double* pos, con
     if (!acc) return fail(FMM_ERR_ARG, "acc must not be NULL");
     cudaStream_t s = c->stream;
     if (n > c->hcap) {
+        c->hcap = 0;
         CK(alloc(&c->hpos, 3 * n));
         CK(alloc(&c->hmass, n));
         CK(alloc(&c->hacc, 3 * n));
@@ -1763,6 +1815,7 @@ extern "C" fmm_status fmm_mlp_train(fmm_ctx* c, const float* feats, const float*
     CK(cudaMemsetAsync(c->mlp_m, 0, sizeof(float) * MLP_NW, s));
     CK(cudaMemsetAsync(c->mlp_v, 0, sizeof(float) * MLP_NW, s));
     if (n > c->mlp_idx_cap) {
+        c->mlp_idx_cap = 0;
         CK(alloc(&c->mlp_idx, n));
         c->mlp_idx_cap = n;
     }
@@ -1794,6 +1847,7 @@ extern "C" fmm_status fmm_mlp_train(fmm_ctx* c, const float* feats, const float*
     // labels by least squares (normal equations in FP64, columns scaled to unit RMS), then the
     // 0.05% and 99.95% quantiles of the network's residual y_net - y_lin
     if (n > c->mlp_pred_cap) {
+        c->mlp_pred_cap = 0;
         CK(alloc(&c->mlp_pred, n));
         c->mlp_pred_cap = n;
     }
@@ -1914,6 +1968,7 @@ extern "C" fmm_status fmm_mlp_audit(fmm_ctx* c, const double* pos, const float* 
     c->params = q;
     cudaStream_t s = c->stream;
     if (max_pairs > c->audit_cap) {
+        c->audit_cap = 0;
         CK(alloc(&c->audit_pairs, max_pairs));
         c->audit_cap = max_pairs;
     }

@@ -324,7 +324,7 @@ struct WalkArgs {
     float eps;
     // learned criterion (mode 1) and audit (mode 2); mode 0 is the fixed-theta criterion
     int mode;
-    float band_lo, band_hi, tau;
+    float band_lo, band_hi, tau, margin;
     const unsigned char* mlp_packed;
     int2* audit_pairs;
     long long audit_cap;

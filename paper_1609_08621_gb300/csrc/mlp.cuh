@@ -199,18 +199,20 @@ __device__ __forceinline__ void mlp_pair_features(const WalkNode& K, const WalkN
 // f[3], times a power of the opening angle):
 //   y_lin = f[3] + alpha log10(theta_eff) + beta + sum_i gamma_i f[i].
 // Training fits it to the labels by least squares and records the range [r_lo, r_hi] of the
-// network's residual y_net - y_lin over its training rows (0.05% quantiles).  A pair with
-// y_lin + r_hi < tau is accepted and one with y_lin + r_lo >= tau rejected without running the
-// network; the network decides the rest.  sur: the MLP_NSUR floats.  Returns 1 accept, 2 reject,
-// 3 ask the network.
-__device__ __forceinline__ int mlp_surrogate(const float* sur, const float* f, float te, float tau)
+// network's residual y_net - y_lin over its training rows (0.05% quantiles).  With the margin m in
+// [0, 1] (fmm_params.mlp_margin), a pair with y_lin + m r_hi < tau is accepted and one with
+// y_lin + m r_lo >= tau rejected without running the network; the network decides the pairs in
+// between, where the surrogate's prediction lies near the budget.  m = 1 leaves the network every
+// pair the surrogate could get wrong on the training rows; m = 0 lets the surrogate decide alone.
+// sur: the MLP_NSUR floats.  Returns 1 accept, 2 reject, 3 ask the network.
+__device__ __forceinline__ int mlp_surrogate(const float* sur, const float* f, float te, float tau, float margin)
 {
     const float r_lo = sur[2], r_hi = sur[3];
-    if (!(r_hi > r_lo)) return 3;
+    if (!(r_hi > r_lo)) return 3;  // no surrogate fitted: the network decides every band pair
     float y = f[3] + sur[0] * log10f(te) + sur[1];
 #pragma unroll
     for (int i = 0; i < MLP_F; i++) y = fmaf(sur[4 + i], f[i], y);
-    if (y + r_hi < tau) return 1;
-    if (y + r_lo >= tau) return 2;
+    if (y + margin * r_hi < tau) return 1;
+    if (y + margin * r_lo >= tau) return 2;
     return 3;
 }

@@ -32,6 +32,17 @@
 
 enum { OUT_NONE = 0, OUT_ACCEPT = 1, OUT_DEFER = 2, OUT_PC = 3, OUT_PP = 4, OUT_OPEN = 5 };
 
+// Learned criterion (MODE 1): the pairs the network must decide are not evaluated one step at a
+// time, where a step has a few of them and the tensor-core tile of 16 rows runs mostly empty.  They
+// wait in a per-warp buffer (entry and features) until 32 of them fill two tiles, or the sink's
+// queue runs dry; the evaluated entries return to the queue marked with their decision, and the
+// next steps sort them like any other entry.  Marks: bit 30 accepted, bit 29 rejected (cell entries
+// of an isolated box, whose indices stay below 2^29).
+#define WALK_NET_ACC (1u << 30)
+#define WALK_NET_REJ (1u << 29)
+#define WALK_PEND 64  // pending pairs per warp: fewer than 32 left after a flush, plus one step's 32
+#define WALK_PEND_BYTES (WALK_PEND * 4 + WALK_PEND * MLP_F * 4)
+
 __device__ __forceinline__ float d2_ordered(float dx, float dy, float dz)
 {
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
@@ -82,7 +93,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
     Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
     DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float4* __restrict__ mnorm,
     const float* __restrict__ amin,
-    float eps, float band_lo, float band_hi, float tau, const unsigned char* __restrict__ mlp_packed,
+    float eps, float band_lo, float band_hi, float tau, float margin, const unsigned char* __restrict__ mlp_packed,
     int2* __restrict__ audit_pairs, long long audit_cap, const unsigned char* __restrict__ nogroup, PeriodicArgs pa)
 {
     constexpr int E = WalkSlots<MODE>::E;
@@ -93,6 +104,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         __syncthreads();
     }
     unsigned char* mlp_scratch = walk_smem + MLPP_SIZE + (threadIdx.x >> 5) * MLP_WARP_SCRATCH;
+    unsigned int* pend_e = reinterpret_cast<unsigned int*>(walk_smem + MLPP_SIZE + WALK_WPB * MLP_WARP_SCRATCH +
+                                                           (threadIdx.x >> 5) * WALK_PEND_BYTES);
+    float* pend_f = reinterpret_cast<float*>(pend_e + WALK_PEND);
+    static_assert(MODE != 1 || E == 1, "the learned walk takes one entry per lane and step");
     unsigned long long n_mlp = 0;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -119,6 +134,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         const unsigned long long cl0 = f_cloff[fi];
         const long long ncl = f_cllen[fi];
         long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
+        int npend = 0;  // learned criterion: pairs waiting for the network
         int srcpp = 0;  // this lane's PP source particles
         bool overflow = false;
         long long base = 0;
@@ -135,6 +151,11 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 valid[s] = s < ns && s * 32 + lane < avail;
                 e[s] = 0;
                 if (valid[s]) e[s] = vi < ncl ? cl_cur[cl0 + vi] : Q[vi - ncl];
+            }
+            unsigned int decided = 0u;  // learned criterion: the network's decision carried by the entry
+            if (MODE == 1 && valid[0] && !(e[0] & FMM_PARTICLE_BIT)) {
+                decided = e[0] & (WALK_NET_ACC | WALK_NET_REJ);
+                e[0] &= ~(WALK_NET_ACC | WALK_NET_REJ);
             }
             base += avail < 32 * E ? avail : 32 * E;
             WalkNode S[E];
@@ -229,11 +250,14 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                         float te;
                         int band = mlp_band(K, S[s], d2, gap2, four_eps2, band_lo, band_hi, te);
                         if (MODE == 1) {
-                            if (band == 3 && !(ak > 0.0f)) {
+                            if (band == 3 && decided) {
+                                band = decided == WALK_NET_ACC ? 1 : 2;  // the network has decided
+                            } else if (band == 3 && !(ak > 0.0f)) {
                                 band = acc ? 1 : 2;  // no acceleration estimate: the fixed criterion decides
                             } else if (band == 3) {
                                 mlp_pair_features(K, S[s], mnorm[entry_index(e[s], pa.ib)], ak, eps, f);
-                                band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau);
+                                band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau,
+                                                     margin);
                             }
                             acc = band == 1;
                             need = band == 3;
@@ -244,15 +268,18 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                     }
                 }
                 if (MODE == 1) {
+                    // a pair for the network waits in the buffer and gives no output this step
                     const unsigned int nm = __ballot_sync(FMM_FULL_MASK, need);
-                    if (nm) {
-                        if (!need) {
+                    if (need) {
+                        const int slot = npend + __popc(nm & lt);
+                        pend_e[slot] = e[s];
 #pragma unroll
-                            for (int q = 0; q < MLP_F; q++) f[q] = 0.0f;
-                        }
-                        const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane, nm);
-                        if (need) acc = pred < tau;
-                        n_mlp += __popc(nm);
+                        for (int q = 0; q < MLP_F; q++) pend_f[slot * MLP_F + q] = f[q];
+                    }
+                    npend += __popc(nm);
+                    if (need) {
+                        valid[s] = false;
+                        nadd[s] = 0;
                     }
                 }
                 if (valid[s]) {
@@ -331,6 +358,45 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 nq += tot[s];
             }
             __syncwarp();
+            if (MODE == 1) {
+                // evaluate 32 waiting pairs (or the rest once the queue is dry) and return them
+                // to the queue with their decisions
+                while (npend >= 32 || (npend > 0 && base >= ncl + nq)) {
+                    const int cnt = npend < 32 ? npend : 32;
+                    if (nq + cnt > cap_scr) {
+                        overflow = true;
+                        break;
+                    }
+                    float f[MLP_F];
+                    const bool have = lane < cnt;
+#pragma unroll
+                    for (int q = 0; q < MLP_F; q++) f[q] = have ? pend_f[lane * MLP_F + q] : 0.0f;
+                    const unsigned int pe = have ? pend_e[lane] : 0u;
+                    const float pred = mlp_predict_warp(walk_smem, mlp_scratch, f, lane,
+                                                        cnt == 32 ? FMM_FULL_MASK : (1u << cnt) - 1u);
+                    if (have) Q[nq + lane] = pe | (pred < tau ? WALK_NET_ACC : WALK_NET_REJ);
+                    n_mlp += cnt;
+                    nq += cnt;
+                    // move the rest (fewer than 32) to the front of the buffer
+                    const int rest = npend - cnt;
+                    unsigned int me = 0u;
+                    float mf[MLP_F];
+                    if (lane < rest) {
+                        me = pend_e[cnt + lane];
+#pragma unroll
+                        for (int q = 0; q < MLP_F; q++) mf[q] = pend_f[(cnt + lane) * MLP_F + q];
+                    }
+                    __syncwarp();
+                    if (lane < rest) {
+                        pend_e[lane] = me;
+#pragma unroll
+                        for (int q = 0; q < MLP_F; q++) pend_f[lane * MLP_F + q] = mf[q];
+                    }
+                    npend = rest;
+                    __syncwarp();
+                }
+                if (overflow) break;
+            }
         }
         if (overflow) {
             if (lane == 0) atomicOr(&ctr->overflow, 1u);
@@ -723,10 +789,10 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],      \
         w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
         w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
-        a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.mlp_packed, a.audit_pairs,  \
+        a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.margin, a.mlp_packed, a.audit_pairs, \
         a.audit_cap, t.graded ? t.nogroup : nullptr, periodic_args(t)
     if (a.mode == 1) {
-        const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * MLP_WARP_SCRATCH;
+        const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * (MLP_WARP_SCRATCH + WALK_PEND_BYTES);
         static std::atomic<unsigned long long> attr{0};
         cudaError_t e = fmm_smem_attr_once(k_walk_level<1>, (int)smem, attr);
         if (e != cudaSuccess) return e;

@@ -127,3 +127,61 @@ def test_rungs_256cubed_active_subset(ctx):
     sinks = np.random.default_rng(13).choice(np.flatnonzero(act), 256, replace=False)
     ref, _ = oracle.direct(pos, mass, eps, sinks)
     _assert_accuracy(_rel_err(a[:, sinks].astype(np.float64), ref))
+
+
+def test_nfw_128cubed_lists_and_locals_match_the_oracle(ctx):
+    """The bench's 128^3 NFW box and settings with 4096 random active sinks on both sides (the tree
+    is the whole box's, 37 levels deep): PP, PC, CC and CP list sets identical to the oracle's, and
+    every group's local expansion (evaluated by the oracle's FP64 L2P at the group's active sinks)
+    and PP + PC + local forces at FP32 tolerance of the oracle FMM's."""
+    n = 128 ** 3
+    pos, mass = synth.clustered_nfw(n, 2)
+    eps, theta = synth.paper_softening(n), 0.55
+    act = np.zeros(n, np.uint8)
+    act[np.random.default_rng(17).choice(n, 4096, replace=False)] = 1
+    tp, tm, ta = _t(pos, torch.float64), _t(mass, torch.float32), _t(act, torch.uint8)
+    acc = torch.full((3 * n,), float("nan"), dtype=torch.float32, device="cuda:0")
+    ctx.compute_forces(tp, tm, eps, theta, acc, None, ta)
+    torch.cuda.synchronize()
+    orc = oracle.FMM(pos, mass, eps, theta, bucket=16, group=64, active=act)
+    g = ctx.export_cells()
+    o = orc.cells()
+    grng = np.stack([g["first"], g["count"]], axis=1)
+    orng = np.stack([o["first"], o["count"]], axis=1)
+    for kind in ("pp", "pc", "cc", "cp"):
+        s, f, c = ctx.export_lists(kind)
+        os_, of, oc = orc.entries(kind)
+        gs = set(zip(map(tuple, grng[s]), f.tolist(), c.tolist()))
+        ost = set(zip(map(tuple, orng[os_]), of.tolist(), oc.tolist()))
+        assert len(gs) == len(s) and gs == ost, (kind, len(gs - ost), len(ost - gs))
+    # group local expansions: matched by the group cell's particle range
+    gcell, gL = ctx.export_locals()
+    ocell, oL = orc.groups()
+    # the GPU's coefficients in the oracle's multi-index order
+    loc_idx, _ = binding.fmm_multi_index()
+    mi = oracle.multi_index()
+    gL = gL[:, [int(np.where((loc_idx == m).all(axis=1))[0][0]) for m in mi]]
+    okey = {(int(o["first"][c]), int(o["count"][c])): i for i, c in enumerate(ocell)}
+    perm = orc.perm()
+    ra, _ = orc.forces()
+    scale = np.linalg.norm(ra, axis=0)
+    errs = []
+    for i, c in enumerate(gcell):
+        key = (int(g["first"][c]), int(g["count"][c]))
+        j = okey[key]
+        com = o["com"][ocell[j]]
+        for q in range(key[0], key[0] + key[1]):
+            p = int(perm[q])
+            if not act[p]:
+                continue
+            u = pos[:, p] - com
+            ag, _ = oracle.l2p(gL[i].astype(np.float64), u)
+            ao, _ = oracle.l2p(oL[j], u)
+            errs.append(np.linalg.norm(ag - ao) / scale[p])
+    assert len(okey) == len(gcell) and len(errs) == int(act.sum())
+    errs = np.array(errs)
+    assert float(np.sqrt(np.mean(errs ** 2))) <= 2e-5 and errs.max() <= 2e-3
+    a = acc.cpu().numpy().reshape(3, n).astype(np.float64)
+    sel = act.astype(bool)
+    e = np.linalg.norm(a[:, sel] - ra[:, sel], axis=0) / scale[sel]
+    assert float(np.sqrt(np.mean(e ** 2))) <= 2e-5 and e.max() <= 2e-3
