@@ -2,9 +2,14 @@
 
 A step is one pass of the whole hot path over one box of synthetic particles: Morton keys,
 radix sort, radix tree, upward pass, checklist walk with local expansions, PP, PC and L2P
-evaluation (fmm_compute_forces), then one kick-drift substep on rung 0 (fmm_kick_drift).
-The default workload is the 128^3 clustered NFW box (30% uniform background, 70% in 200 NFW
-halos, eps = 1/50 of the mean separation, theta = 0.55, buckets of 16, groups of 64).
+evaluation (fmm_compute_forces).  Partial sums are added per particle in FP64 (the paper's double
+accumulation, fmm_params.accumulate = 1) unless --accumulate 0.
+
+The default workload is the largest configuration: 512^3 particles clustered like the 4096-particle
+set (half uniform, half in Plummer spheres), eps = 1/50 of the mean separation, solved with the
+learned opening criterion at the rms force error of fixed theta = 0.55 (see Learned).  Other
+workloads: the 128^3 NFW box (nfw2m, with a rung-0 kick-drift per step), 64 batched boxes, the
+256^3 rung hierarchy, the 4096-particle set, and the 128^3 NFW box as a periodic box (periodic2m).
 
 metric: interactions/s = (PP pairs + PC pairs) of one solve / seconds per step, over the
 whole job (all ranks).  Inputs are resident in HBM when the timed region starts; the box is
@@ -60,8 +65,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="nfw2m",
-                    choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m"])
+    ap.add_argument("--workload", default="learned134m",
+                    choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m", "periodic2m"])
+    ap.add_argument("--accumulate", type=int, default=1, choices=[0, 1],
+                    help="1: partial sums added in FP64 per particle (the paper's double accumulation)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (buckets 16, groups 64)")
     ap.add_argument("--no-graphs", action="store_true", help="solve eagerly instead of replaying a CUDA graph")
@@ -73,6 +80,41 @@ def parse():
     ap.add_argument("--n", type=int, default=None,
                     help="particle count override (profiling a smaller box of the same structure)")
     return ap.parse_args()
+
+
+L2_FLUSHED = "flushed before every step (256 MB write, not timed)"
+L2_NOTE = {
+    "batch64": "inputs and trees larger than L2 are rebuilt every step",
+    "rungs16m": "inputs and tree larger than L2 are rebuilt every substep",
+}
+
+
+def fits_l2(n):
+    """Inputs plus tree of n particles well inside the 129 MB L2 (about 64 bytes per particle)."""
+    return n * 64 < (128 << 20)
+
+
+def static_config(name, n=None, extra=None):
+    """The workload as both arms describe it (what is solved, not how): name, size, softening,
+    opening angle, accumulation, and how L2 is kept from carrying data between timed steps."""
+    from paper_1609_08621_gb300 import synth
+
+    w = synth.WORKLOADS[name]
+    nn = n if n is not None else w["n"]
+    eps = w["eps"] if (n is None or w["eps"] == 1e-3) else synth.paper_softening(nn)
+    cfg = {"workload": name, "n": nn, "eps": eps, "theta": w["theta"],
+           "l2": L2_FLUSHED if (name != "batch64" and fits_l2(nn)) else
+                 L2_NOTE.get(name, "inputs and tree larger than L2 are rebuilt every step"),
+           "combine": "fp64 per particle (the paper's double accumulation)"}
+    if name == "periodic2m":
+        cfg["nrep"] = w["nrep"]
+    if name == "rungs16m":
+        cfg["max_rung"] = 5
+    if name == "learned134m":
+        cfg["criterion"] = "learned, tau set to the rms error of fixed theta 0.55 against the FP64 direct sum"
+    if extra:
+        cfg.update(extra)
+    return cfg
 
 
 def workload(name, rank, n=None):
@@ -176,6 +218,32 @@ def cpu_baseline(pos, mass, eps, theta, frac=None, target_s=15.0):
             "seconds": dt}
 
 
+def error_stats(a, ref):
+    """rms, nearest-rank 99th percentile and maximum of |a - ref| / |ref| over the columns."""
+    e = np.sort(np.linalg.norm(np.asarray(a, np.float64) - ref, axis=0) / np.linalg.norm(ref, axis=0))
+    return {"rms": float(np.sqrt(np.mean(e * e))), "p99": float(e[int(np.ceil(0.99 * e.size)) - 1]),
+            "max": float(e[-1])}
+
+
+def periodic_cpu_sample(pos, mass, eps, theta, frac, nrep):
+    """The oracle's periodic plain FMM on a bounded sample: the full tree, the walk over the root's
+    copies and the FP64 PP/PC/local/Ewald terms for a random subset of active sinks."""
+    import oracle
+
+    n = mass.size
+    act = (np.random.default_rng(123).random(n) < (frac or 1024.0 / n)).astype(np.uint8)
+    t0 = time.perf_counter()
+    f = oracle.FMM(pos, mass, eps, theta, active=act, nrep=nrep)
+    f.forces()
+    dt = time.perf_counter() - t0
+    c = f.counts()
+    inter = c["pp_pairs"] + c["pc_pairs"]
+    return {"value": inter / dt, "unit": "interactions/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"periodic N={n} tree + walk over the root's copies + FP64 PP/PC/local/Ewald for "
+                      f"{int(act.sum())} random active sinks; {inter} interactions in {dt:.2f} s",
+            "seconds": dt}
+
+
 def force_error(pos, mass, eps, acc, nsinks=1024, seed=7):
     """Relative force error |a - a_ref| / |a_ref| of a solve's accelerations acc (3, N) against
     the oracle's FP64 direct sum at random sinks: rms, nearest-rank 99th percentile and maximum."""
@@ -186,34 +254,49 @@ def force_error(pos, mass, eps, acc, nsinks=1024, seed=7):
     t0 = time.perf_counter()
     ref, _ = oracle.direct(pos, mass, eps, sinks)
     dt = time.perf_counter() - t0
-    e = np.sort(np.linalg.norm(np.asarray(acc, np.float64)[:, sinks] - ref, axis=0) / np.linalg.norm(ref, axis=0))
-    return {"rms": float(np.sqrt(np.mean(e * e))), "p99": float(e[int(np.ceil(0.99 * e.size)) - 1]),
-            "max": float(e[-1]), "sinks": int(sinks.size),
-            "reference": "FP64 direct sum (oracle) of the synthetic input, %.1f s on %d threads"
-                         % (dt, oracle.num_threads())}
+    r = error_stats(np.asarray(acc, np.float64)[:, sinks], ref)
+    r.update(sinks=int(sinks.size), reference="FP64 direct sum (oracle) of the synthetic input, %.1f s on %d threads"
+             % (dt, oracle.num_threads()))
+    return r
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle as it stands, timed on the host cores on bounded samples of the workload."""
+    """The CPU oracle as it stands, timed on the host cores on bounded samples of the workload: the
+    same config as the GPU arm's line; each step is a few seconds of the oracle's plain FP64 FMM."""
     if rank != 0:
         return
-    if args.workload == "batch64":
-        from paper_1609_08621_gb300 import synth
+    from paper_1609_08621_gb300 import synth
 
+    if args.workload == "batch64":
         w = synth.WORKLOADS["batch64"]
         boxes, off = synth.batch_boxes(w["boxes"], w["seed"])
         b = int(np.argmax(np.diff(off)))
         pos, mass = boxes[b]
         eps, theta = w["eps"], w["theta"]
         frac = args.cpu_sample or min(1.0, 1024.0 / mass.size)
-        cfg = {"workload": "batch64", "sample_box": b, "n": int(mass.size), "eps": eps, "theta": theta}
+        cfg = static_config("batch64", extra={"boxes": int(w["boxes"]), "n": int(off[-1])})
+
+        def sample():
+            r = cpu_baseline(pos, mass, eps, theta, frac=frac)
+            r["sample"] = f"the largest box ({b}) of the batch; " + r["sample"]
+            return r
     else:
         pos, mass, eps, theta = workload(args.workload, 0, args.n)
-        frac = args.cpu_sample or min(1.0, 1024.0 / mass.size)
-        cfg = {"workload": args.workload, "n": int(mass.size), "eps": eps, "theta": theta}
+        cfg = static_config(args.workload, args.n)
+        if args.workload == "learned134m":
+            def sample():
+                return learned_cpu_sample(pos, mass, eps, theta, args.cpu_sample)
+        else:
+            frac = args.cpu_sample or min(1.0, 1024.0 / mass.size)
+            nrep = synth.WORKLOADS[args.workload].get("nrep")
+
+            def sample():
+                if nrep:
+                    return periodic_cpu_sample(pos, mass, eps, theta, frac, nrep)
+                return cpu_baseline(pos, mass, eps, theta, frac=frac)
     steps = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(pos, mass, eps, theta, frac=frac)
+        r = sample()
         if k >= args.warmup:
             steps.append(r)
     v = float(np.mean([s["value"] for s in steps]))
@@ -261,10 +344,10 @@ class Box:
         self.rung = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.act = torch.zeros(n, dtype=torch.uint8, device=dev)
         self.dt0 = 1e-5  # tiny base step: the box barely changes, so every step solves the same workload
-        self.config = {"workload": args.workload, "n": int(n), "eps": self.eps, "theta": self.theta,
-                       "l2": "inputs and tree larger than L2 are rebuilt every step"}
-        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc))
-        self.small = n * 64 < (128 << 20)  # inputs plus tree well inside the 129 MB L2
+        self.config = static_config(args.workload, args.n)
+        ctx.set_params(accumulate=args.accumulate)
+        self.tuning = tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc)
+        self.small = fits_l2(n)
 
     def step(self, k):
         self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
@@ -292,15 +375,53 @@ class Box:
     def cpu_sample(self, frac):
         return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac)
 
-    def force_error(self, nsinks=1024):
+    def force_error(self, nsinks=8192):
         """One more solve, outside the timed region, of the synthetic input as generated (the timed
-        steps drift the particles), checked against the FP64 direct sum at random sinks."""
+        steps drift the particles), checked against the FP64 direct sum at random sinks (8192 of
+        the 128^3 box; every particle of the 4096-particle set)."""
         import torch
 
         tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
         acc = torch.zeros_like(self.acc)
         self.ctx.compute_forces(tpos, self.tmass, self.eps, self.theta, acc, None)
         return force_error(self.pos, self.mass, self.eps, acc.cpu().numpy().reshape(3, self.n), nsinks)
+
+
+class Periodic(Box):
+    """The 128^3 NFW box as a periodic box (Sec. 3.1): the root's 26 copies on the checklist and the
+    Ewald correction for the copies beyond; a step is one force solve."""
+
+    def __init__(self, args, rank, dev, ctx):
+        from paper_1609_08621_gb300 import synth
+
+        args.workload = "periodic2m"
+        ctx.set_params(nrep=synth.WORKLOADS["periodic2m"]["nrep"])
+        super().__init__(args, rank, dev, ctx)
+
+    def step(self, k):
+        self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+
+    def cpu_sample(self, frac):
+        return periodic_cpu_sample(self.pos, self.mass, self.eps, self.theta, frac, 1)
+
+    def force_error(self, nsinks=256):
+        """One more solve of the box as generated, against the oracle's periodic FP64 direct sum (the
+        softened shell, Ewald beyond it) at 256 random sinks."""
+        import oracle
+        import torch
+
+        tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
+        acc = torch.zeros_like(self.acc)
+        self.ctx.compute_forces(tpos, self.tmass, self.eps, self.theta, acc, None)
+        a = acc.cpu().numpy().reshape(3, self.n)
+        sinks = np.sort(np.random.default_rng(7).choice(self.n, nsinks, replace=False))
+        t0 = time.perf_counter()
+        ref, _ = oracle.direct_periodic(self.pos, self.mass, self.eps, sinks, nrep=1)
+        dt = time.perf_counter() - t0
+        r = error_stats(np.asarray(a, np.float64)[:, sinks], ref)
+        r.update(sinks=int(sinks.size), reference="periodic FP64 direct sum (oracle), %.1f s on %d threads"
+                 % (dt, oracle.num_threads()))
+        return r
 
 
 class Batch:
@@ -323,10 +444,10 @@ class Batch:
         self.tmass = torch.from_numpy(self.mass).to(dev)
         self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
         self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
-        self.config = {"workload": "batch64", "boxes": int(w["boxes"]), "n": int(n), "eps": self.eps,
-                       "theta": self.theta, "l2": "inputs and trees larger than L2 are rebuilt every step"}
-        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc,
-                                box_offsets=self.off, buckets=(8, 12, 16)))
+        self.config = static_config("batch64", extra={"boxes": int(w["boxes"]), "n": int(n)})
+        ctx.set_params(accumulate=args.accumulate)
+        self.tuning = tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc, box_offsets=self.off,
+                           buckets=(8, 12, 16))
 
     def step(self, k):
         self.ctx.compute_forces_batch(self.tpos, self.tmass, self.off, self.eps, self.theta, self.acc, self.pot)
@@ -361,9 +482,10 @@ class Batch:
         p, m = self.boxes[b]
         return cpu_baseline(p, m, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / m.size))
 
-    def force_error(self, nsinks=1024):
+    def force_error(self, nsinks=4096):
         """One more batched solve of the boxes as generated, outside the timed region; the largest
-        box is checked against its own FP64 direct sum at random sinks (the boxes are independent)."""
+        box is checked against its own FP64 direct sum at 4096 random sinks (the boxes are
+        independent)."""
         import torch
 
         tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
@@ -419,10 +541,10 @@ class Rungs:
         self.dt0 = float(np.ldexp(np.quantile(dtp, 0.10), self.R - 1))
         ctx.assign_rungs(self.acc, self.rung, self.eps, self.dt0, self.R)
         hist = np.bincount(self.rung.cpu().numpy(), minlength=self.R + 1)
-        self.config = {"workload": "rungs16m", "n": int(n), "eps": self.eps, "theta": self.theta,
-                       "max_rung": self.R, "dt0": self.dt0, "rung_hist": hist.tolist(),
-                       "l2": "inputs and tree larger than L2 are rebuilt every substep"}
-        self.config.update(tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc))
+        self.config = static_config("rungs16m", args.n)
+        self.detail = {"dt0": self.dt0, "rung_hist": hist.tolist()}
+        ctx.set_params(accumulate=args.accumulate)
+        self.tuning = tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc)
         ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
         self.active_frac = []
         # dual trees (Sec. 3.2): inside each interval of 2^(R - dual) substeps only rungs > dual are
@@ -436,6 +558,8 @@ class Rungs:
                 raise SystemExit(f"--dual must be in [0, {self.R - 1}]")
             self.config["dual_fixed_rung"] = self.dual
             self.config["dual_interval_substeps"] = 1 << (self.R - self.dual)
+            # dual trees take the fixed criterion with FP32 sums per work item as a plain solve does
+            ctx.set_params(accumulate=args.accumulate)
 
     def step(self, k):
         s = k % (1 << self.R)
@@ -462,10 +586,10 @@ class Rungs:
     def cpu_sample(self, frac):
         return cpu_baseline(self.pos, self.mass, self.eps, self.theta, frac if frac else min(1.0, 4096.0 / self.n))
 
-    def force_error(self, nsinks=512):
+    def force_error(self, nsinks=4096):
         """One more solve of the box as generated (every particle active), outside the timed region,
-        against the FP64 direct sum at random sinks (512: the direct sum over 16.8M sources is the
-        cost)."""
+        against the FP64 direct sum at 4096 random sinks (about 30 s of host time over 16.8M
+        sources)."""
         import torch
 
         tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(self.dev)
@@ -476,79 +600,95 @@ class Rungs:
 
 class Learned(Box):
     """512^3 Plummer-clustered box solved with the learned opening criterion, compared with the
-    fixed criterion (theta = 0.55) at equal rms force error.
+    fixed criterion (theta = 0.55) at equal rms force error against the FP64 direct sum.
 
-    Set-up, outside the timed region: the network is trained on the GPU from audit walks of
-    the 4096-particle box, the 128^3 NFW box and two boxes of the 64-box batch (labels are the
-    method's own cell-cell errors, normalised by each particle's acceleration from a theta = 0.3
-    solve).  The reference for the force error is an FMM solve at theta = 0.25 with the FP64 combine,
-    restricted to 65,536 random sinks (an active subset, so it costs little); the tests pin that
-    reference against the FP64 direct sum.  The budget tau of the network is searched until its rms
-    error matches the fixed criterion's, then both are timed.  A step is one learned solve."""
+    Set-up, outside the timed region:
+    - the oracle's FP64 direct sum at 4096 random sinks starts on the host cores in a thread (the C
+      call releases the GIL) and runs while the GPU prepares;
+    - the network is trained on the GPU from audit walks of the 4096-particle box, the 128^3 NFW
+      box and two boxes of the 64-box batch (labels are the method's own cell-cell errors,
+      normalised by each particle's acceleration from a theta = 0.3 solve);
+    - a fixed-theta solve gives the acceleration estimate a time step carries over; its error
+      against the direct sum sets the target, and the budget tau of the network is bisected to the
+      largest value whose error does not exceed it;
+    - both criteria are timed (3 solves each, CUDA events), and their errors reported.
+    A step is one learned solve, with the previous step's accelerations as its estimate."""
 
-    N_SINKS = 65536
-    force_error = None  # the line's "learned" entry reports both criteria's errors against the reference
+    N_JUDGE = 4096
+    force_error = None  # the line's "learned" entry reports both criteria's errors against the direct sum
 
     def __init__(self, args, rank, dev, ctx):
         import torch
 
+        import oracle
         from paper_1609_08621_gb300 import synth
 
         args.workload = "learned134m"
-        super().__init__(args, rank, dev, ctx)
-        n = self.n
-        self._train(args, rank, dev, ctx, synth)
+        # the direct sum starts first: it is the longest part of the set-up
+        self.pos, self.mass, self.eps, self.theta = workload("learned134m", rank, args.n)
+        n = self.n = self.mass.size
         rng = np.random.default_rng(12345 + rank)
-        self.sinks = torch.from_numpy(np.sort(rng.choice(n, min(self.N_SINKS, n), replace=False))).to(dev)
-        act = torch.zeros(n, dtype=torch.uint8, device=dev)
-        act[self.sinks] = 1
-        ctx.set_params(criterion=0, accumulate=1)
-        ctx.compute_forces(self.tpos, self.tmass, self.eps, 0.25, self.acc, self.pot, act)
-        ctx.set_params(accumulate=0)
-        self.ref = self._at_sinks()
+        self.judge_sinks = np.sort(rng.choice(n, min(self.N_JUDGE, n), replace=False))
+        self._judge = {}
+
+        def judge():
+            t0 = time.perf_counter()
+            self._judge["ref"] = oracle.direct(self.pos, self.mass, self.eps, self.judge_sinks)[0]
+            self._judge["seconds"] = time.perf_counter() - t0
+
+        th = threading.Thread(target=judge, daemon=True)
+        th.start()
+        self.ctx, self.dev = ctx, dev
+        self.tpos = torch.from_numpy(self.pos.reshape(-1).copy()).to(dev)
+        self.tmass = torch.from_numpy(self.mass).to(dev)
+        self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.config = static_config("learned134m", args.n)
+        self.small = False
+        t0 = time.perf_counter()
+        self._train(ctx, synth, dev)
+        t_train = time.perf_counter() - t0
+        ctx.set_params(criterion=0, accumulate=args.accumulate)
+        self.tuning = tune(args, ctx, self.tpos, self.tmass, self.eps, self.theta, self.acc)
+        ctx.set_params(criterion=0)
+        ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
+        self.estimate = self.acc.clone()
+        self.ts = torch.from_numpy(self.judge_sinks).to(dev)
+        th.join()
+        self.ref = self._judge["ref"]
         e_fixed = self._err(0, None)
-        t_fixed = self._time(0, None)
-        st_fixed = ctx.stats()
-        # tau search: coarse grid, then bisection on the bracket around the fixed criterion's error
-        grid = [-7.0, -6.5, -6.0, -5.5, -5.0, -4.5, -4.0, -3.5, -3.0]
-        errs = [self._err(1, t) for t in grid]
-        lo, hi = grid[0], grid[-1]
-        for t, e in zip(grid, errs):
-            if e <= e_fixed:
-                lo = t
-        for t, e in zip(grid, errs):
-            if t > lo and e > e_fixed:
-                hi = t
-                break
+        # tau: the largest budget whose error does not exceed the fixed criterion's
+        lo, hi = -7.0, -3.5
         e_lo = self._err(1, lo)
-        for _ in range(5):
+        for _ in range(9):
             mid = 0.5 * (lo + hi)
             e = self._err(1, mid)
-            if e <= e_fixed:
+            if e["rms"] <= e_fixed["rms"]:
                 lo, e_lo = mid, e
             else:
                 hi = mid
         self.tau = lo
-        t_learned = self._time(1, lo)
-        st_learned = ctx.stats()
+        t_fixed, st_fixed = self._time(0, None)
+        t_learned, st_learned = self._time(1, lo)
         ctx.set_params(criterion=1, mlp_tau=self.tau)
-        self.config = dict(self.config, criterion="learned", tau=self.tau)
+        self.acc.copy_(self.estimate)
+        margin = ctx.get_params().mlp_margin
+        self.detail = {"tau": self.tau, "mlp_margin": margin}
         self.learned = {
-            "error_reference": "FMM at theta=0.25 with FP64 combine on 65,536 random sinks (pinned against the FP64 "
-                     "direct sum in the tests)",
-            "train_pairs": self.train_pairs, "train_loss": self.train_loss,
-            "fixed": {"theta": self.theta, "rms_err": e_fixed, "ms_per_solve": t_fixed,
-                      "interactions": st_fixed["n_pp_pairs"] + st_fixed["n_pc_pairs"],
+            "error_reference": "FP64 direct sum (oracle) at %d random sinks, %.1f s on %d threads" %
+                               (self.judge_sinks.size, self._judge["seconds"], oracle.num_threads()),
+            "train_pairs": self.train_pairs, "train_loss": self.train_loss, "train_seconds": t_train,
+            "fixed": {"theta": self.theta, "rms_err": e_fixed["rms"], "p99_err": e_fixed["p99"],
+                      "ms_per_solve": t_fixed, "interactions": st_fixed["n_pp_pairs"] + st_fixed["n_pc_pairs"],
                       "n_cc": st_fixed["n_cc"], "ms_walk": st_fixed["ms_walk"]},
-            "learned": {"tau": self.tau, "rms_err": e_lo, "ms_per_solve": t_learned,
-                        "interactions": st_learned["n_pp_pairs"] + st_learned["n_pc_pairs"],
+            "learned": {"tau": self.tau, "mlp_margin": margin, "rms_err": e_lo["rms"], "p99_err": e_lo["p99"],
+                        "ms_per_solve": t_learned, "interactions": st_learned["n_pp_pairs"] + st_learned["n_pc_pairs"],
                         "n_cc": st_learned["n_cc"], "ms_walk": st_learned["ms_walk"],
                         "network_calls": st_learned["n_learned"]},
             "speedup_at_equal_error": t_fixed / t_learned if t_learned > 0 else None,
-            "tau_grid": [[t, e] for t, e in zip(grid, errs)],
         }
 
-    def _train(self, args, rank, dev, ctx, synth):
+    def _train(self, ctx, synth, dev):
         import torch
 
         sets = []
@@ -573,26 +713,20 @@ class Learned(Box):
             ls.append(l.clone())
         feats, labels = torch.cat(fs).contiguous(), torch.cat(ls).contiguous()
         self.train_pairs = int(labels.numel())
-        self.train_loss = ctx.mlp_train(feats, labels, epochs=20, batch=256, lr=2e-3, seed=1)
-
-    def _at_sinks(self):
-        a = self.acc.view(3, self.n)
-        return a.index_select(1, self.sinks).double()
+        self.train_loss = ctx.mlp_train(feats, labels, epochs=10, batch=4096, lr=4e-3, seed=1)
 
     def _solve(self, criterion, tau):
         if criterion == 1:
             self.ctx.set_params(criterion=1, mlp_tau=tau)
         else:
             self.ctx.set_params(criterion=0)
+        self.acc.copy_(self.estimate)  # the estimate a time step carries over
         self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
 
     def _err(self, criterion, tau):
-        import torch
-
         self._solve(criterion, tau)
-        a = self._at_sinks()
-        e = torch.linalg.norm(a - self.ref, dim=0) / torch.linalg.norm(self.ref, dim=0)
-        return float(torch.sqrt(torch.mean(e * e)).item())
+        a = self.acc.view(3, self.n).index_select(1, self.ts).double().cpu().numpy()
+        return error_stats(a, self.ref)
 
     def _time(self, criterion, tau, reps=3):
         import torch
@@ -605,21 +739,25 @@ class Learned(Box):
             self._solve(criterion, tau)
         e1.record(s)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1) / reps, self.ctx.stats()
 
     def step(self, k):
         self.ctx.compute_forces(self.tpos, self.tmass, self.eps, self.theta, self.acc, self.pot)
 
     def cpu_sample(self, frac):
-        # the oracle (fixed theta) on a random 2^21-particle subset of the box, masses rescaled to
-        # a total of 1: the full 512^3 tree alone would take the host minutes
-        k = min(self.n, 1 << 21)
-        idx = np.sort(np.random.default_rng(7).choice(self.n, k, replace=False))
-        m = (self.mass[idx].astype(np.float64) * (self.n / k)).astype(np.float32)
-        r = cpu_baseline(np.ascontiguousarray(self.pos[:, idx]), m, self.eps, self.theta,
-                         frac if frac else min(1.0, 4096.0 / k))
-        r["sample"] = f"random {k}-particle subset of the box; " + r["sample"]
-        return r
+        return learned_cpu_sample(self.pos, self.mass, self.eps, self.theta, frac)
+
+
+def learned_cpu_sample(pos, mass, eps, theta, frac=None, k=1 << 20):
+    """The oracle (fixed theta) on a random 2^20-particle subset of the 512^3 box, masses rescaled to
+    a total of 1: the full tree alone would take the host minutes."""
+    n = mass.size
+    k = min(n, k)
+    idx = np.sort(np.random.default_rng(7).choice(n, k, replace=False))
+    m = (mass[idx].astype(np.float64) * (n / k)).astype(np.float32)
+    r = cpu_baseline(np.ascontiguousarray(pos[:, idx]), m, eps, theta, frac if frac else min(1.0, 1024.0 / k))
+    r["sample"] = f"random {k}-particle subset of the box; " + r["sample"]
+    return r
 
 
 def main():
@@ -643,10 +781,10 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = binding.Context(local, stream)
-    kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned}.get(args.workload, Box)
+    kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned, "periodic2m": Periodic}.get(args.workload, Box)
     wl = kind(args, rank, dev, ctx)
     ctx.set_graphs(not args.no_graphs)
-    wl.config["cuda_graph"] = not args.no_graphs
+    wl.tuning["cuda_graph"] = not args.no_graphs
 
     def barrier():
         if world > 1:
@@ -672,8 +810,6 @@ def main():
     # workloads smaller than L2 get L2 flushed (a 256 MB write, outside the step's events) before
     # every step; larger ones rebuild a tree bigger than L2 each step
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if getattr(wl, "small", False) else None
-    if flush is not None:
-        wl.config["l2"] = "flushed before every step (256 MB write, not timed)"
     step_ms = []
     e0.record(stream)
     for k in range(args.steps):
@@ -725,7 +861,8 @@ def main():
     line = {"metric": "interactions/s (PP + PC) per force solve", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": wl.config, "phase_ms": {k: v / args.steps for k, v in kt.items()},
+            "config": wl.config, "tuning": wl.tuning, "detail": getattr(wl, "detail", {}),
+            "phase_ms": {k: v / args.steps for k, v in kt.items()},
             "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
             "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
             "active_per_step": float(np.mean(active)), "walk_retries": retries, "roofline": roof, "clocks": ck,

@@ -433,7 +433,7 @@ fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
  *
  * fmm_debug_walk_capacity: the walk's first capacities for a context whose buffers have not been
  * sized yet: scratch_entries per warp and list (default 8192) and list_scale checklist, CC and PC
- * entries per particle (default 16; PP half of it); 0 keeps a default.  Each overflow grows them
+ * entries per particle (default 16; PP half of it, rounded up); 0 keeps a default.  Each overflow grows them
  * x4 and repeats the walk, up to 6 times, so small values exercise that path.  Returns
  * FMM_ERR_ARG for ctx == NULL or negative values. */
 fmm_status fmm_debug_fail_allocations(long long after);

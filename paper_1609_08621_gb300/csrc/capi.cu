@@ -524,7 +524,7 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
     // and list (fmm_debug_walk_capacity may start them smaller); each retry grows them x4
     const long long ls = c->dbg_list_scale > 0 ? c->dbg_list_scale : 16;
     long long need_cl = (long long)scale * ls * n + 4096;
-    long long need_pp = (long long)scale * (ls / 2) * n + 4096;
+    long long need_pp = (long long)scale * ((ls + 1) / 2) * n + 4096;
     long long need_pc = (long long)scale * ls * n + 4096;
     long long need_cc = (long long)scale * ls * n + 4096;
     long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * scale;

@@ -201,6 +201,7 @@ WORKLOADS = {
     "batch64": dict(n=None, kind="batch", seed=3, eps=1e-3, theta=0.7, boxes=64),
     "rungs16m": dict(n=256 ** 3, kind="plummer", seed=4, eps=paper_softening(256 ** 3), theta=0.55),
     "learned134m": dict(n=512 ** 3, kind="plummer", seed=5, eps=paper_softening(512 ** 3), theta=0.55),
+    "periodic2m": dict(n=128 ** 3, kind="nfw", seed=2, eps=paper_softening(128 ** 3), theta=0.55, nrep=1),
 }
 
 
