@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="learned134m",
-                    choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m", "periodic2m"])
+                    choices=["nfw2m", "plummer4096", "batch64", "rungs16m", "learned134m", "periodic2m",
+                             "compressed704"])
     ap.add_argument("--accumulate", type=int, default=1, choices=[0, 1],
                     help="1: partial sums added in FP64 per particle (the paper's double accumulation)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -112,6 +113,8 @@ def static_config(name, n=None, extra=None):
         cfg["max_rung"] = 5
     if name == "learned134m":
         cfg["criterion"] = "learned, tau set to the rms error of fixed theta 0.55 against the FP64 direct sum"
+    if name == "compressed704":
+        cfg["positions"] = "3 x uint32 fixed point (x = u 2^-32), fmm_compute_forces_i32"
     if extra:
         cfg.update(extra)
     return cfg
@@ -283,7 +286,7 @@ def run_reference(args, rank, world):
     else:
         pos, mass, eps, theta = workload(args.workload, 0, args.n)
         cfg = static_config(args.workload, args.n)
-        if args.workload == "learned134m":
+        if args.workload in ("learned134m", "compressed704"):
             def sample():
                 return learned_cpu_sample(pos, mass, eps, theta, args.cpu_sample)
         else:
@@ -422,6 +425,55 @@ class Periodic(Box):
         r.update(sinks=int(sinks.size), reference="periodic FP64 direct sum (oracle), %.1f s on %d threads"
                  % (dt, oracle.num_threads()))
         return r
+
+
+class Compressed(Box):
+    """704^3 = 348,913,664 particles clustered like the 4096-particle set, positions stored as
+    32-bit fixed-point coordinates (Sec. 3.4: 12 bytes per particle), fixed theta = 0.55: the
+    largest box the context's buffers let one GB300 hold.  A step is one fmm_compute_forces_i32."""
+
+    def __init__(self, args, rank, dev, ctx):
+        import torch
+
+        from paper_1609_08621_gb300 import synth
+
+        args.workload = "compressed704"
+        pos, self.mass, self.eps, self.theta = workload("compressed704", rank, args.n)
+        n = self.n = self.mass.size
+        u = synth.to_fixed(pos)
+        del pos
+        self.ipos = u  # the FP64 positions the solve sees are u 2^-32 (force_error)
+        self.ctx, self.dev = ctx, dev
+        self.tu = torch.from_numpy(u.reshape(-1).view(np.int32)).to(dev)
+        self.tmass = torch.from_numpy(self.mass).to(dev)
+        self.acc = torch.zeros(3 * n, dtype=torch.float32, device=dev)
+        self.pot = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.config = static_config("compressed704", args.n)
+        ctx.set_params(accumulate=args.accumulate, bucket=16, group=64, list_chunk=128)
+        self.tuning = {"bucket": 16, "group": 64, "list_chunk": 128, "tuned": False,
+                       "note": "the bench's tuned settings of the 512^3 box (autotuning would hold a second box)"}
+        self.small = False
+        ctx.compute_forces_i32(self.tu, self.tmass, self.eps, self.theta, self.acc, self.pot)
+        d, _ = ctx.memory_info()
+        free, total = torch.cuda.mem_get_info(dev)
+        self.detail = {"context_device_bytes": d, "context_bytes_per_particle": d / n,
+                       "device_used_gib": (total - free) / 2 ** 30, "device_total_gib": total / 2 ** 30}
+
+    def step(self, k):
+        self.ctx.compute_forces_i32(self.tu, self.tmass, self.eps, self.theta, self.acc, self.pot)
+
+    def e2e(self, steps):
+        return None
+
+    def cpu_sample(self, frac):
+        return learned_cpu_sample(self.ipos.astype(np.float64) * (1.0 / 4294967296.0), self.mass, self.eps,
+                                  self.theta, frac)
+
+    def force_error(self, nsinks=256):
+        """The last step's solve against the FP64 direct sum at 256 random sinks (about 45 s of host
+        time over 3.5e8 sources)."""
+        x = self.ipos.astype(np.float64) * (1.0 / 4294967296.0)
+        return force_error(x, self.mass, self.eps, self.acc.cpu().numpy().reshape(3, self.n), nsinks)
 
 
 class Batch:
@@ -781,7 +833,8 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     ctx = binding.Context(local, stream)
-    kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned, "periodic2m": Periodic}.get(args.workload, Box)
+    kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned, "periodic2m": Periodic,
+            "compressed704": Compressed}.get(args.workload, Box)
     wl = kind(args, rank, dev, ctx)
     ctx.set_graphs(not args.no_graphs)
     wl.tuning["cuda_graph"] = not args.no_graphs

@@ -268,6 +268,36 @@ fmm_status fmm_kick_drift(fmm_ctx *ctx, double *pos, double *vel, const float *a
                           unsigned char *active_next, long long n, double eps, double dt0, int max_rung,
                           int substep, int closing);
 
+/* ---------------------------------------------------------------- compressed storage (Sec. 3.4)
+ *
+ * The paper stores positions as 32-bit integer coordinates of the box (converted from and to
+ * doubles, a resolution well below the softening length) and velocities as single-precision
+ * floats.  These calls take that storage directly:
+ *   ipos  device, 3N unsigned 32-bit SoA (x then y then z): the coordinate is u * 2^-32 of the
+ *         unit box (exact in FP64), always inside [0, 1)
+ *   vel   device, 3N floats SoA
+ *
+ * fmm_compute_forces_i32: fmm_compute_forces on those positions; the results are bit for bit those
+ * of fmm_compute_forces on the FP64 positions u * 2^-32.  Graph replay, periodic boxes and the
+ * learned criterion work as there; FMM_ERR_ARG for NULL ipos or mass or n out of range. */
+fmm_status fmm_compute_forces_i32(fmm_ctx *ctx, const unsigned int *ipos, const float *mass,
+                                  const unsigned char *active, long long n, double eps, double theta, float *acc,
+                                  float *pot);
+
+/* fmm_kick_drift_i32: the substep of fmm_kick_drift on compressed storage.  The kicks of a substep
+ * are FP64 from the stored FP32 velocity (each product and sum rounded once), and the velocity is
+ * stored rounded to FP32; the drift adds to u the nearest integer of v h 2^32 (FP64, ties to even).
+ * In a periodic box (fmm_params.nrep > 0) u wraps modulo 2^32, the box's period; in the isolated box
+ * a particle that would leave [0, 1) keeps its position and the next synchronising call reports
+ * FMM_ERR_ARG.  Asynchronous; the other arguments as for fmm_kick_drift. */
+fmm_status fmm_kick_drift_i32(fmm_ctx *ctx, unsigned int *ipos, float *vel, const float *acc, unsigned char *rung,
+                              unsigned char *active_next, long long n, double eps, double dt0, int max_rung,
+                              int substep, int closing);
+
+/* Device memory the context holds: *device_bytes = its buffers (tree, lists, scratch, staging,
+ * network) as allocated so far, *host_bytes = its pinned host mirrors; either may be NULL. */
+fmm_status fmm_memory_info(const fmm_ctx *ctx, long long *device_bytes, long long *host_bytes);
+
 /* Assign rungs from accelerations: the smallest r in [0, max_rung] with dt0 / 2^r <= Delta T,
  * Delta T = 0.2 sqrt(eps / |a|) (Sec. 3.2).  acc device 3N floats SoA, rung device N bytes out.
  * Asynchronous. */
@@ -432,10 +462,10 @@ fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
  * buffers involved are allocated again by its next call.
  *
  * fmm_debug_walk_capacity: the walk's first capacities for a context whose buffers have not been
- * sized yet: scratch_entries per warp and list (default 8192) and list_scale checklist, CC and PC
- * entries per particle (default 16; PP half of it, rounded up); 0 keeps a default.  Each overflow grows them
- * x4 and repeats the walk, up to 6 times, so small values exercise that path.  Returns
- * FMM_ERR_ARG for ctx == NULL or negative values. */
+ * sized yet: scratch_entries per warp and list (default 8192) and list_scale checklist, local and
+ * PC entries per particle (defaults 8, 12 and 8; PP half of list_scale, rounded up, default 3);
+ * 0 keeps the defaults.  Each overflow doubles them and repeats the walk, up to 8 times, so small
+ * values exercise that path.  Returns FMM_ERR_ARG for ctx == NULL or negative values. */
 fmm_status fmm_debug_fail_allocations(long long after);
 fmm_status fmm_debug_walk_capacity(fmm_ctx *ctx, long long scratch_entries, long long list_scale);
 

@@ -108,3 +108,63 @@ def close(vel, acc, rung, dt0):
     vel = np.array(vel, dtype=np.float64)
     a = np.asarray(acc, dtype=np.float32).astype(np.float64)
     return vel + a * np.ldexp(dt0, -np.asarray(rung, dtype=np.int64) - 1)
+
+
+# ---------------------------------------------------------------- compressed storage (Sec. 3.4)
+#
+# The paper keeps positions as 32-bit integer coordinates of the box and velocities as single
+# precision floats.  Reading of the substep on that storage (the same schedule as kick_drift):
+#   - a position component is u (uint32), the coordinate u * 2^-32 of the unit box;
+#   - the half kicks of a substep run in FP64 from the stored FP32 velocity, v += a hk, each
+#     product and each sum rounded once, and the velocity is stored rounded to FP32;
+#   - the drift moves u by the nearest integer (ties to even) of (v32 h) 2^32, computed in FP64;
+#   - in a periodic box u wraps modulo 2^32; in the isolated box a component that would leave
+#     [0, 2^32) leaves the particle where it was and is reported.
+
+
+def kick_drift_i32(ipos, vel, acc, rung, eps, dt0, max_rung, s, closing, periodic=False):
+    """One substep on compressed storage; returns (ipos uint32 (3, N), vel float32 (3, N), rung,
+    active_next, out) where out flags the particles an isolated box would lose (left in place)."""
+    u = np.array(ipos, dtype=np.uint32).astype(np.int64)
+    v = np.asarray(vel, dtype=np.float32).astype(np.float64)
+    rung = np.array(rung, dtype=np.int64)
+    a = np.asarray(acc, dtype=np.float32).astype(np.float64)
+    act = active(rung, s, max_rung)
+    if closing:
+        v[:, act] = v[:, act] + a[:, act] * np.ldexp(dt0, -rung[act] - 1)
+    tgt = target_rungs(acc, eps, dt0, max_rung)
+    new = rung.copy()
+    for i in np.nonzero(act)[0]:
+        rt, r = int(tgt[i]), int(rung[i])
+        if rt >= r:
+            new[i] = rt
+        else:
+            rn = rt
+            while rn < r and s % (1 << (max_rung - rn)) != 0:
+                rn += 1
+            new[i] = rn
+    rung = new
+    v[:, act] = v[:, act] + a[:, act] * np.ldexp(dt0, -rung[act] - 1)
+    v32 = np.asarray(vel, dtype=np.float32).copy()
+    v32[:, act] = v[:, act].astype(np.float32)
+    h = math.ldexp(dt0, -max_rung)
+    d = np.rint((v32.astype(np.float64) * h) * 4294967296.0).astype(np.int64)
+    un = u + d
+    if periodic:
+        un &= 0xFFFFFFFF
+        out = np.zeros(u.shape[1], dtype=bool)
+    else:
+        out = np.any((un < 0) | (un > 0xFFFFFFFF), axis=0)
+        un[:, out] = u[:, out]
+    return un.astype(np.uint32), v32, rung, active(rung, s + 1, max_rung), out
+
+
+def to_fixed(pos):
+    """Nearest 32-bit coordinates of FP64 positions in [0, 1): u = rint(x 2^32), capped at 2^32 - 1."""
+    u = np.rint(np.asarray(pos, dtype=np.float64) * 4294967296.0)
+    return np.minimum(u, 4294967295.0).astype(np.uint32)
+
+
+def from_fixed(ipos):
+    """The FP64 coordinates u 2^-32 of 32-bit ones (exact)."""
+    return np.asarray(ipos, dtype=np.uint32).astype(np.float64) * (1.0 / 4294967296.0)

@@ -102,6 +102,9 @@ def load(build_if_missing: bool = True):
         "fmm_mlp_audit_pairs": (i, [vp, vp, vp, vp, vp, ll]),
         "fmm_morton_order_static": (i, [vp, ll, vp, vp, vp]),
         "fmm_debug_fail_allocations": (i, [ll]),
+        "fmm_compute_forces_i32": (i, [vp, vp, vp, vp, ll, d, d, vp, vp]),
+        "fmm_kick_drift_i32": (i, [vp, vp, vp, vp, vp, vp, ll, d, d, i, i, i]),
+        "fmm_memory_info": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
         "fmm_debug_walk_capacity": (i, [vp, ll, ll]),
         "fmm_set_graphs": (i, [vp, i]),
         "fmm_graph_info": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
@@ -481,6 +484,36 @@ class Context:
         _check(load().fmm_export_lists(self.h, k, C.byref(n), sink.ctypes.data, first.ctypes.data,
                                        count.ctypes.data, m))
         return sink[:m], first[:m], count[:m]
+
+    def compute_forces_i32(self, ipos, mass, eps, theta, acc, pot=None, active=None):
+        """fmm_compute_forces_i32: ipos a 3n int32 CUDA tensor holding the uint32 fixed-point
+        coordinates (x = u * 2^-32), otherwise as compute_forces."""
+        import torch
+
+        n = mass.numel()
+        _check(load().fmm_compute_forces_i32(self.h, _ptr(ipos, torch.int32, 3 * n, "ipos"),
+                                             _ptr(mass, torch.float32, n, "mass"),
+                                             _ptr(active, torch.uint8, n, "active", allow_none=True), n,
+                                             float(eps), float(theta), _ptr(acc, torch.float32, 3 * n, "acc"),
+                                             _ptr(pot, torch.float32, n, "pot", allow_none=True)))
+
+    def kick_drift_i32(self, ipos, vel, acc, rung, active_next, eps, dt0, max_rung, substep, closing):
+        """fmm_kick_drift_i32: fixed-point positions (3n int32 holding uint32) and FP32 velocities
+        (3n float32), updated in place."""
+        import torch
+
+        n = rung.numel()
+        _check(load().fmm_kick_drift_i32(self.h, _ptr(ipos, torch.int32, 3 * n, "ipos"),
+                                         _ptr(vel, torch.float32, 3 * n, "vel"), _ptr(acc, torch.float32, 3 * n, "acc"),
+                                         _ptr(rung, torch.uint8, n, "rung"),
+                                         _ptr(active_next, torch.uint8, n, "active_next"), n, float(eps), float(dt0),
+                                         int(max_rung), int(substep), 1 if closing else 0))
+
+    def memory_info(self):
+        """fmm_memory_info: (device bytes, pinned host bytes) the context holds."""
+        d, h = C.c_longlong(), C.c_longlong()
+        _check(load().fmm_memory_info(self.h, C.byref(d), C.byref(h)))
+        return d.value, h.value
 
     def debug_walk_capacity(self, scratch_entries=0, list_scale=0):
         """fmm_debug_walk_capacity: the walk's first scratch and list capacities (0: default), a

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include <math.h>
@@ -52,18 +54,43 @@ fmm_status fail(fmm_status st, const char* fmt, ...)
 // thread's next allocations fail, to test exactly that.
 thread_local long long g_fail_allocs_after = -1;  // < 0: off; else successful allocations left
 
+// Sizes of the device buffers allocated here, by address (fmm_memory_info sums a context's).
+std::mutex g_size_mutex;
+std::unordered_map<void*, size_t> g_sizes;
+
+void dev_free(void* p)
+{
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> lock(g_size_mutex);
+    g_sizes.erase(p);
+}
+
+size_t dev_size(const void* p)
+{
+    if (!p) return 0;
+    std::lock_guard<std::mutex> lock(g_size_mutex);
+    auto it = g_sizes.find(const_cast<void*>(p));
+    return it == g_sizes.end() ? 0 : it->second;
+}
+
 template <typename T>
 cudaError_t grow(T** p, long long* cap, long long need)
 {
     if (need <= *cap && *p) return cudaSuccess;
-    if (*p) cudaFree(*p);
+    dev_free(*p);
     *p = nullptr;
     *cap = 0;
     if (need < 1) need = 1;
     if (g_fail_allocs_after == 0) return cudaErrorMemoryAllocation;
     if (g_fail_allocs_after > 0) g_fail_allocs_after--;
-    cudaError_t e = cudaMalloc((void**)p, (size_t)need * sizeof(T));
-    if (e == cudaSuccess) *cap = need;
+    const size_t bytes = (size_t)need * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) {
+        *cap = need;
+        std::lock_guard<std::mutex> lock(g_size_mutex);
+        g_sizes[(void*)*p] = bytes;
+    }
     return e;
 }
 
@@ -71,7 +98,7 @@ template <typename T>
 cudaError_t alloc(T** p, long long need)
 {
     long long cap = 0;
-    if (*p) cudaFree(*p);
+    dev_free(*p);
     *p = nullptr;
     return grow(p, &cap, need);
 }
@@ -123,10 +150,11 @@ struct fmm_ctx {
     // CUDA graph of the whole solve (fmm_set_graphs): captured after an eager solve and replayed
     // while the call's inputs, buffers and parameters stay the same
     bool graphs = false;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_head = nullptr, gexec = nullptr;  // the solve's head and the rest
     cudaStream_t cap_stream = nullptr;  // capture needs a stream of its own (the caller's may be the legacy one)
     struct GraphKey {
         const void *pos, *mass, *active, *acc, *pot;
+        bool i32;  // pos holds 32-bit fixed-point coordinates
         long long n;
         int nbox;
         std::vector<long long> off;
@@ -140,6 +168,9 @@ struct fmm_ctx {
     // the tree, join before the groups add them)
     cudaStream_t ew_stream = nullptr;
     cudaEvent_t ew_fork = nullptr, ew_join = nullptr;
+    // positions of the current call as 32-bit fixed-point coordinates (fmm_compute_forces_i32), else
+    // NULL and the call's FP64 positions are used
+    const unsigned int* cur_ipos = nullptr;
     // test hook (fmm_debug_walk_capacity): the walk's first per-warp scratch and list capacities
     long long dbg_scratch = 0, dbg_list_scale = 0;
     // staging for the host-buffer entry point
@@ -217,7 +248,7 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
     const DevWalk& w = c->w;
     const FixedTree& f = c->fx;
     return {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
-            t.bucket_of, t.accs, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
+            t.bucket_of, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
             t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
             t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
@@ -231,8 +262,7 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
 static void free_all(fmm_ctx* c)
 {
     DevTree& t = c->t;
-    for (void* p : tree_walk_buffers(c))
-        if (p) cudaFree(p);
+    for (void* p : tree_walk_buffers(c)) dev_free(p);
     if (c->ctr) cudaFree(c->ctr);
     if (c->totals) cudaFree(c->totals);
     if (c->seed) cudaFree(c->seed);
@@ -241,10 +271,11 @@ static void free_all(fmm_ctx* c)
     if (c->totals_h) cudaFreeHost(c->totals_h);
     void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact, c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v, c->mlp_loss,
                   c->mlp_packed, c->audit_pairs, c->mlp_idx, c->mlp_pred};
-    for (void* p : hs)
-        if (p) cudaFree(p);
+    for (void* p : hs) dev_free(p);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->gexec_head) cudaGraphExecDestroy(c->gexec_head);
+    c->gexec_head = nullptr;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -254,6 +285,20 @@ static void free_all(fmm_ctx* c)
     if (c->ew_join) cudaEventDestroy(c->ew_join);
     c->ew_stream = nullptr;
     c->ew_fork = c->ew_join = nullptr;
+}
+
+extern "C" fmm_status fmm_memory_info(const fmm_ctx* c, long long* device_bytes, long long* host_bytes)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    long long d = 0;
+    for (void* p : tree_walk_buffers(c)) d += (long long)dev_size(p);
+    const void* hs[] = {c->hpos, c->hmass, c->hacc, c->hpot, c->hact, c->mlp_p, c->mlp_g, c->mlp_m, c->mlp_v,
+                        c->mlp_loss, c->mlp_packed, c->audit_pairs, c->mlp_idx, c->mlp_pred};
+    for (const void* p : hs) d += (long long)dev_size(p);
+    d += (long long)(sizeof(DevCounters) + 12 * sizeof(unsigned int));
+    if (device_bytes) *device_bytes = d;
+    if (host_bytes) *host_bytes = (long long)sizeof(DevCounters) + 2 * (long long)sizeof(unsigned int);
+    return FMM_OK;
 }
 
 extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
@@ -277,6 +322,10 @@ extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
     for (auto& ev : c->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaMemset(c->seed, 0, 8 * sizeof(unsigned int));
+    // every counter starts at zero, the compressed kick-drift's status word included (it is kept
+    // across solves, so memory left by an earlier context must not read as a report)
+    if (e == cudaSuccess) e = cudaMemset(c->ctr, 0, sizeof(DevCounters));
+    if (e == cudaSuccess) memset(c->ctr_h, 0, sizeof(DevCounters));
     if (e != cudaSuccess) {
         free_all(c);
         delete c;
@@ -314,6 +363,8 @@ extern "C" fmm_status fmm_get_params(const fmm_ctx* c, fmm_params* p)
     return FMM_OK;
 }
 
+static fmm_status ensure_cells(fmm_ctx* c, long long need_cells);
+
 static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1, long long min_cells = 0)
 {
     DevTree& t = c->t;
@@ -332,7 +383,6 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.posf, cap));
         CK(alloc(&t.plo, cap));
         CK(alloc(&t.off, cap));
-        CK(alloc(&t.accs, cap));
         CK(alloc(&t.act, cap));
         CK(alloc(&t.bucket_of, cap));
         CK(alloc(&t.bflag, cap));
@@ -344,11 +394,17 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.keep, 2 * cap));
         t.cap_n = cap;
     }
-    // nodes holding > b particles form a binary tree with at most n / (b + 1) leaves, each with at
-    // most two bucket children; several boxes add their top levels (< 2 nbox nodes)
-    long long need_cells = 6 * n / (bucket + 1) + 8 + 2LL * nbox;
-    if (need_cells > 2 * n + 1) need_cells = 2 * n + 1;
-    if (need_cells < min_cells) need_cells = min_cells;
+    // the cells themselves are sized by build_tree once the tree's cell count is known; callers
+    // that append more cells (the dual trees' fixed tree) ask for min_cells here
+    CK(fmm_sort_ensure(t, n));
+    return ensure_cells(c, min_cells);
+}
+
+// Cell arrays for at least need cells.
+static fmm_status ensure_cells(fmm_ctx* c, long long need_cells)
+{
+    DevTree& t = c->t;
+    if (!t.ewald_L) CK(alloc(&t.ewald_L, fmm_ewald_floats()));
     if (need_cells > t.cap_cells) {
         t.cap_cells = 0;
         long long cap = need_cells;
@@ -375,13 +431,29 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.L, (long long)FMM_NL * cap));
         t.cap_cells = cap;
     }
-    if (!t.ewald_L) CK(alloc(&t.ewald_L, fmm_ewald_floats()));
-    CK(fmm_sort_ensure(t, n));
     return FMM_OK;
+}
+
+// Every counter of a solve starts at zero, except the compressed kick-drift's status word, which
+// waits for the next solve to report it.
+static cudaError_t clear_counters(fmm_ctx* c, cudaStream_t s)
+{
+    const size_t k = offsetof(DevCounters, kdk_status);
+    cudaError_t e = cudaMemsetAsync(c->ctr, 0, k, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(reinterpret_cast<char*>(c->ctr) + k + sizeof(unsigned int), 0,
+                            sizeof(DevCounters) - k - sizeof(unsigned int), s);
+    return e;
 }
 
 static fmm_status read_status(fmm_ctx* c, const char* where)
 {
+    if (c->ctr_h->kdk_status & FMM_DEV_ERR_ARG) {
+        c->ctr_h->kdk_status = 0;
+        CK(cudaMemsetAsync(&c->ctr->kdk_status, 0, sizeof(unsigned int), c->stream));
+        return fail(FMM_ERR_ARG, "%s: the last fmm_kick_drift_i32 kept a particle from leaving the isolated box",
+                    where);
+    }
     unsigned int st = c->ctr_h->status;
     if (st & FMM_DEV_ERR_ARG)
         return fail(FMM_ERR_ARG, "%s: a position outside [0,1), or a mass that is not finite and > 0", where);
@@ -442,8 +514,8 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     st = set_boxes(c, n, box_off, nbox);
     if (st != FMM_OK) return st;
     c->have_tree = false;
-    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
-    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
+    CK(clear_counters(c, s));
+    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s, c->cur_ipos));
     if (nbox > 1) {
         CK(fmm_launch_box_sort(t, n, s));
         c->launches += 8 * 5 + 1 + 2 * 5 + 1;
@@ -451,9 +523,19 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
         CK(fmm_radix_sort(t, n, s));
         c->launches += 8 * 5;
     }
-    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s));
+    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
     CK(fmm_launch_radix_tree(t, n, bucket, s));
     CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
+    // the cell count, then cell arrays for it (a small margin lets graph replays of a slowly
+    // changing box keep their buffers; a replay with more cells than that is solved eagerly)
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    {
+        const long long nc = c->totals_h[0];
+        const fmm_status se = ensure_cells(c, nc + nc / 32 + 64);
+        if (se != FMM_OK) return se;
+        if (t.grade_key) CK(grow(&t.nogroup, &t.cap_nogroup, t.cap_cells));  // a graded build's per-cell flags
+    }
     CK(cudaMemsetAsync(t.bflag, 0, sizeof(unsigned int) * (size_t)n, s));
     CK(fmm_launch_cells(t, n, bucket, s));
     // bucket ids: exclusive scan of the bucket start flags into keep[] (free after k_cells)
@@ -515,19 +597,28 @@ extern "C" fmm_status fmm_build_tree(fmm_ctx* c, const double* pos, const float*
     return build_tree(c, pos, mass, active, n, q->bucket);
 }
 
-static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
+static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
 {
     DevWalk& w = c->w;
-    long long cells = c->t.cap_cells;
-    long long need_front = cells;
-    // per particle: checklist 16, PP 8, PC 16, local 16 entries, and 8192 scratch entries per warp
-    // and list (fmm_debug_walk_capacity may start them smaller); each retry grows them x4
-    const long long ls = c->dbg_list_scale > 0 ? c->dbg_list_scale : 16;
-    long long need_cl = (long long)scale * ls * n + 4096;
-    long long need_pp = (long long)scale * ((ls + 1) / 2) * n + 4096;
-    long long need_pc = (long long)scale * ls * n + 4096;
-    long long need_cc = (long long)scale * ls * n + 4096;
+    const long long cells = c->t.cap_cells;
+    const long long need_front = cells;
+    // Capacities per particle, from the NFW and clustered boxes measured here (per particle:
+    // PP entries 1.8, PC 5.2, local 7.9, a level's checklists under 5): checklists 8, PP 3, PC 8,
+    // local entries 12, and 8192 scratch entries per warp and list (fmm_debug_walk_capacity may
+    // start them smaller).  Groups: in a plain tree they are one more than the cells with more
+    // than g particles, which no multiple of n / (g + 1) bounds (a chain of such cells may shed a
+    // few particles per level); measured 2.3 n / (g + 1) in a 20000-particle NFW halo and 1.7 in
+    // one of 2^21, so they start at 4 n / (g + 1) (graded trees take the cell count).  A walk that
+    // overflows any of them doubles them all and runs again.
+    const long long ls = c->dbg_list_scale > 0 ? c->dbg_list_scale : 8;
+    const long long floor = c->dbg_list_scale > 0 ? 4096 : 65536;  // small boxes have longer lists per particle
+    long long need_cl = (long long)scale * (ls * n + floor);
+    long long need_pp = (long long)scale * ((c->dbg_list_scale > 0 ? (ls + 1) / 2 : 3) * n + floor);
+    long long need_pc = (long long)scale * (ls * n + floor);
+    long long need_cc = (long long)scale * ((c->dbg_list_scale > 0 ? ls : 12) * n + floor);
     long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * scale;
+    long long need_groups = c->t.graded ? cells : (long long)scale * (4 * n / (group + 1) + 64 + 2LL * c->t.nbox);
+    if (need_groups > cells) need_groups = cells;
     if (need_front > w.cap_front) {
         w.cap_front = 0;
         for (int i = 0; i < 2; i++) {
@@ -538,14 +629,17 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale)
         CK(alloc(&w.lcc_off, need_front));
         CK(alloc(&w.lcc_len, need_front));
         CK(alloc(&w.lcells, need_front));
-        CK(alloc(&w.groups, need_front));
-        CK(alloc(&w.Lg, (long long)FMM_NL * need_front));
-        CK(alloc(&w.cnt_pp, need_front));
-        CK(alloc(&w.cnt_pc, need_front));
-        CK(alloc(&w.base_pp, need_front));
-        CK(alloc(&w.base_pc, need_front));
         w.cap_front = need_front;
-        w.cap_groups = need_front;
+    }
+    if (need_groups > w.cap_groups) {
+        w.cap_groups = 0;
+        CK(alloc(&w.groups, need_groups));
+        CK(alloc(&w.Lg, (long long)FMM_NL * need_groups));
+        CK(alloc(&w.cnt_pp, need_groups));
+        CK(alloc(&w.cnt_pc, need_groups));
+        CK(alloc(&w.base_pp, need_groups));
+        CK(alloc(&w.base_pc, need_groups));
+        w.cap_groups = need_groups;
     }
     if (need_cl > w.cap_cl) {
         w.cap_cl = 0;
@@ -668,7 +762,7 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     if (levels + 1 > FMM_MAX_LEVELS) return fail(FMM_ERR_STATE, "tree depth %d exceeds the walk's levels", t.depth);
     int scale = 1;
     for (int attempt = 0;; attempt++) {
-        fmm_status st = ensure_walk(c, n, scale);
+        fmm_status st = ensure_walk(c, n, scale, group);
         if (st != FMM_OK) return st;
         CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
         // cells above a box's root are never walked: their local lists must read as empty
@@ -702,8 +796,8 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
             c->stats.retries = attempt;
             return FMM_OK;
         }
-        if (attempt >= 6) return fail(FMM_ERR_OOM, "walk lists keep overflowing after %d grows", attempt);
-        scale *= 4;
+        if (attempt >= 8) return fail(FMM_ERR_OOM, "walk lists keep overflowing after %d grows", attempt);
+        scale *= 2;
     }
 }
 
@@ -837,30 +931,26 @@ static fmm_status finish_stats(fmm_ctx* c, long long n)
 
 // ---------------------------------------------------------------- CUDA graph of a solve
 
-// Enqueue the whole solve without a host synchronisation: the same launches as solve_eager, with
-// every launch over cells, buckets or groups covering the capacity (kernels read the counts on the
-// device) and the walk run for graph_levels levels (levels past the deepest cell find an empty
-// front).  Used only inside stream capture, after an eager solve has sized every buffer.
-static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
-                                     long long n, const fmm_params& q, float* acc, float* pot,
-                                     const long long* box_off, int nbox)
+// Enqueue the solve for capture in two parts.  The head (keys, sort, gather, radix tree and the
+// scan of the kept nodes) ends with the cell count copied to the host: a replay checks it against
+// the cell buffers before the rest runs, since every later kernel indexes cells by that count.  The
+// rest makes the same launches as solve_eager, with every launch over cells, buckets or groups
+// covering the capacity (kernels read the counts on the device) and the walk run for graph_levels
+// levels (levels past the deepest cell find an empty front).  Used only inside stream capture,
+// after an eager solve has sized every buffer.
+static fmm_status enqueue_graph_head(fmm_ctx* c, const double* pos, const float* mass, const unsigned char* active,
+                                     long long n, const fmm_params& q, const long long* box_off, int nbox)
 {
     DevTree& t = c->t;
-    DevWalk& w = c->w;
     cudaStream_t s = c->stream;
     c->launches = 0;
-    t.cap_grid = true;
-    struct Reset {
-        DevTree& t;
-        ~Reset() { t.cap_grid = false; }
-    } reset{t};
     CK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
     fmm_status st = set_boxes(c, n, box_off, nbox);
     if (st != FMM_OK) return st;
     st = set_periodic(c, q, n, nbox);
     if (st != FMM_OK) return st;
-    CK(cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s));
-    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s));
+    CK(clear_counters(c, s));
+    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s, c->cur_ipos));
     if (nbox > 1) {
         CK(fmm_launch_box_sort(t, n, s));
         c->launches += 8 * 5 + 1 + 2 * 5 + 1;
@@ -868,9 +958,24 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
         CK(fmm_radix_sort(t, n, s));
         c->launches += 8 * 5;
     }
-    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s));
+    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
     CK(fmm_launch_radix_tree(t, n, q.bucket, s));
     CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
+    CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3;
+    return FMM_OK;
+}
+
+static fmm_status enqueue_graph_rest(fmm_ctx* c, long long n, const fmm_params& q, float* acc, float* pot, int nbox)
+{
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    cudaStream_t s = c->stream;
+    t.cap_grid = true;
+    struct Reset {
+        DevTree& t;
+        ~Reset() { t.cap_grid = false; }
+    } reset{t};
     CK(cudaMemsetAsync(t.bflag, 0, sizeof(unsigned int) * (size_t)n, s));
     CK(fmm_launch_cells(t, n, q.bucket, s));
     CK(fmm_scan_exclusive(t.bflag, t.keep, n, c->totals + 1, t, s));
@@ -881,7 +986,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
         CK(fmm_launch_box_roots(t, s));
         c->launches += 1;
     }
-    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
+    c->launches += 1 + 3 + 1 + 1 + 2 + 8;
     CK(fmm_launch_nodes(t, q.theta, s));
     c->launches += 1;
     if (t.per_R > 0) {
@@ -891,7 +996,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
         CK(fmm_launch_shift_tables(t, s));
         c->launches += 1;
     }
-    st = ewald_fork(c, q.terms);
+    fmm_status st = ewald_fork(c, q.terms);
     if (st != FMM_OK) return st;
     CK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     if (q.criterion == 1) {
@@ -913,7 +1018,7 @@ static fmm_status enqueue_graph_body(fmm_ctx* c, const double* pos, const float*
     a.mlp_packed = c->mlp_packed;
     a.audit_pairs = c->audit_pairs;
     a.audit_cap = c->audit_cap;
-    CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
+    // the overflow flag is not cleared here: the b_max items may have set it (the head cleared it)
     CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.cap_cells, s));
     CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
     CK(fmm_launch_walk_seed(t, w, c->ctr, s));
@@ -962,6 +1067,7 @@ static fmm_ctx::GraphKey make_key(const double* pos, const float* mass, const un
 {
     fmm_ctx::GraphKey k;
     k.pos = pos;
+    k.i32 = false;
     k.mass = mass;
     k.active = active;
     k.acc = acc;
@@ -977,15 +1083,40 @@ static fmm_ctx::GraphKey make_key(const double* pos, const float* mass, const un
 
 static bool same_key(const fmm_ctx::GraphKey& a, const fmm_ctx::GraphKey& b)
 {
-    return a.pos == b.pos && a.mass == b.mass && a.active == b.active && a.acc == b.acc && a.pot == b.pot &&
+    return a.pos == b.pos && a.i32 == b.i32 && a.mass == b.mass && a.active == b.active && a.acc == b.acc &&
+           a.pot == b.pot &&
            a.n == b.n && a.nbox == b.nbox && a.off == b.off && same_params(a.p, b.p) && a.eps == b.eps &&
            a.theta == b.theta;
 }
 
 static void drop_graph(fmm_ctx* c)
 {
+    if (c->gexec_head) cudaGraphExecDestroy(c->gexec_head);
+    c->gexec_head = nullptr;
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
+}
+
+// One part of the solve captured on the context's capture stream and instantiated; null on any
+// failure (the context then keeps solving eagerly).
+template <class F>
+static cudaGraphExec_t capture_part(fmm_ctx* c, F&& enqueue)
+{
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    const fmm_status st = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->stream = user;
+    cudaGraphExec_t ge = nullptr;
+    if (st != FMM_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return ge;
 }
 
 // Capture the solve just done eagerly (same arguments) into a graph; on any failure the context
@@ -1006,32 +1137,20 @@ static void capture_graph(fmm_ctx* c, const fmm_ctx::GraphKey& key, const double
         return;
     }
     // the work is recorded on the context's capture stream; replays launch on the caller's stream
-    const cudaStream_t user = c->stream;
-    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    c->stream = c->cap_stream;
     const int saved_launches = c->launches;
-    fmm_status st = enqueue_graph_body(c, pos, mass, active, n, q, acc, pot, box_off, nbox);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    c->stream = user;
-    c->graph_launches = c->launches;
+    cudaGraphExec_t head = capture_part(c, [&] { return enqueue_graph_head(c, pos, mass, active, n, q, box_off, nbox); });
+    cudaGraphExec_t rest = head ? capture_part(c, [&] { return enqueue_graph_rest(c, n, q, acc, pot, nbox); }) : nullptr;
+    c->graph_launches = c->launches;  // both parts
     c->launches = saved_launches;
-    if (st != FMM_OK || e != cudaSuccess || !g) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
+    if (!head || !rest) {
+        if (head) cudaGraphExecDestroy(head);
+        if (rest) cudaGraphExecDestroy(rest);
         return;
     }
-    cudaGraphExec_t ge = nullptr;
-    if (cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
-        c->gexec = ge;
-        c->gkey = key;
-        c->graph_bufs = tree_walk_buffers(c);
-    }
-    cudaGraphDestroy(g);
-    cudaGetLastError();
+    c->gexec_head = head;
+    c->gexec = rest;
+    c->gkey = key;
+    c->graph_bufs = tree_walk_buffers(c);
 }
 
 enum { GRAPH_DONE = 0, GRAPH_RETRY = 1 };
@@ -1042,14 +1161,18 @@ static fmm_status replay_graph(fmm_ctx* c, long long n, int* outcome)
 {
     *outcome = GRAPH_RETRY;
     cudaStream_t s = c->stream;
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    CK(cudaGraphLaunch(c->gexec_head, s));
+    CK(cudaStreamSynchronize(s));
+    if ((long long)c->totals_h[0] > t.cap_cells) return FMM_OK;  // more cells than the buffers hold
     CK(cudaGraphLaunch(c->gexec, s));
     CK(cudaStreamSynchronize(s));
     fmm_status st = read_status(c, "fmm_compute_forces");
     if (st != FMM_OK) return st;
     const DevCounters& h = *c->ctr_h;
-    DevTree& t = c->t;
-    DevWalk& w = c->w;
-    if (h.overflow || h.lv_front[c->graph_levels] != 0 || (long long)h.n_groups > w.cap_groups) return FMM_OK;
+    if (h.overflow || h.lv_front[c->graph_levels] != 0 || (long long)h.n_groups > w.cap_groups)
+        return FMM_OK;
     t.n = n;
     t.n_cells = c->totals_h[0];
     t.n_buckets = c->totals_h[1];
@@ -1087,7 +1210,11 @@ static fmm_status solve(fmm_ctx* c, const double* pos, const float* mass, const 
     if (q.criterion == 1 && !c->mlp_ready) return fail(FMM_ERR_STATE, "criterion 1 needs network parameters");
     st = set_boxes_check(n, box_off, nbox);
     if (st != FMM_OK) return st;
-    const fmm_ctx::GraphKey key = make_key(pos, mass, active, acc, pot, n, box_off, nbox, q, eps, theta);
+    fmm_ctx::GraphKey key = make_key(pos, mass, active, acc, pot, n, box_off, nbox, q, eps, theta);
+    if (c->cur_ipos) {
+        key.pos = c->cur_ipos;
+        key.i32 = true;
+    }
     // a graph holds the addresses of the context's buffers it was captured with: it replays only while
     // none of them was reallocated since (another call may have grown them)
     if (c->gexec && same_key(c->gkey, key) && c->graph_bufs == tree_walk_buffers(c)) {
@@ -1465,6 +1592,37 @@ extern "C" fmm_status fmm_kick_drift(fmm_ctx* c, double* pos, double* vel, const
     CK(cudaSetDevice(c->device));
     CK(fmm_launch_kick_drift(pos, vel, acc, rung, active_next, n, eps, dt0, max_rung, substep, closing ? 1 : 0,
                              c->ctr, c->stream));
+    return FMM_OK;
+}
+
+// Sec. 3.4, memory: the solve on positions stored as 32-bit fixed-point coordinates.
+extern "C" fmm_status fmm_compute_forces_i32(fmm_ctx* c, const unsigned int* ipos, const float* mass,
+                                             const unsigned char* active, long long n, double eps, double theta,
+                                             float* acc, float* pot)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!ipos || !mass) return fail(FMM_ERR_ARG, "ipos and mass must not be NULL");
+    if (n < 1 || n >= (1LL << 31)) return fail(FMM_ERR_ARG, "n must be in [1, 2^31), got %lld", n);
+    CK(cudaSetDevice(c->device));
+    c->cur_ipos = ipos;
+    const fmm_status st = solve(c, nullptr, mass, active, n, eps, theta, acc, pot);
+    c->cur_ipos = nullptr;
+    return st;
+}
+
+extern "C" fmm_status fmm_kick_drift_i32(fmm_ctx* c, unsigned int* ipos, float* vel, const float* acc,
+                                         unsigned char* rung, unsigned char* active_next, long long n, double eps,
+                                         double dt0, int max_rung, int substep, int closing)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    if (!ipos || !vel || !acc || !rung || !active_next) return fail(FMM_ERR_ARG, "NULL array");
+    if (n < 1 || n >= (1LL << 31)) return fail(FMM_ERR_ARG, "n must be in [1, 2^31)");
+    if (!(eps > 0.0) || !(dt0 > 0.0)) return fail(FMM_ERR_ARG, "eps and dt0 must be > 0");
+    if (max_rung < 0 || max_rung > 30) return fail(FMM_ERR_ARG, "max_rung must be in [0, 30]");
+    if (substep < 0 || substep >= (1 << max_rung)) return fail(FMM_ERR_ARG, "substep out of range");
+    CK(cudaSetDevice(c->device));
+    CK(fmm_launch_kick_drift_i32(ipos, vel, acc, rung, active_next, n, eps, dt0, max_rung, substep, closing ? 1 : 0,
+                                 c->params.nrep > 0 ? 1 : 0, c->ctr, c->stream));
     return FMM_OK;
 }
 

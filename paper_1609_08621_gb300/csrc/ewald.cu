@@ -350,8 +350,9 @@ __global__ void __launch_bounds__(EWG_WARPS * 32) k_ewald_groups(const Group* __
                                                                  const unsigned long long* __restrict__ ngroups_dev,
                                                                  long long cap_groups, const Com4* __restrict__ com,
                                                                  const float* __restrict__ E, float* __restrict__ Lg,
-                                                                 int keep_walk)
+                                                                 int keep_walk, const DevCounters* __restrict__ ctr)
 {
+    if (fmm_overflowed(ctr)) return;
     __shared__ float mono[EWG_WARPS][EW_NP], coef[EWG_WARPS][EW_NP];
     __shared__ short pk[EWG_PAIRS], pj[EWG_PAIRS];
     __shared__ int poff[FMM_NL + 1];
@@ -431,6 +432,6 @@ cudaError_t fmm_launch_ewald_groups(DevTree& t, DevWalk& w, DevCounters* ctr, in
     if (t.per_R <= 0 || !(terms & 8)) return cudaSuccess;
     const long long blocks = std::min<long long>(std::max<long long>(fmm_ceil_div(w.cap_groups, EWG_WARPS), 1), 152 * 16);
     k_ewald_groups<<<(unsigned)blocks, EWG_WARPS * 32, 0, s>>>(w.groups, &ctr->n_groups, w.cap_groups, t.com,
-                                                                t.ewald_L, w.Lg, (terms & 4) ? 1 : 0);
+                                                                t.ewald_L, w.Lg, (terms & 4) ? 1 : 0, ctr);
     return cudaGetLastError();
 }

@@ -124,7 +124,8 @@ struct DevCounters {
     unsigned int status;    // FMM_DEV_ERR_* bits of invalid input or failed waits
     unsigned int overflow;  // a walk list or scratch capacity was exceeded (host grows and retries)
     unsigned int depth;     // deepest cell level
-    unsigned int pad0;
+    unsigned int kdk_status;  // FMM_DEV_ERR_ARG: a compressed kick-drift kept a particle from leaving the
+                              // isolated box (kept across solves until a solve reports it)
     unsigned long long n_active;
     // walk totals
     unsigned long long n_groups, n_lcells;
@@ -132,7 +133,8 @@ struct DevCounters {
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
-    unsigned int n_bm_items, pad1;        // (cell, particle chunk) items of the exact b_max
+    unsigned int n_bm_items;              // (cell, particle chunk) items of the exact b_max
+    unsigned int pad1;
     unsigned long long n_audit;           // (sink, source) pairs recorded by an audit walk
     unsigned long long n_mlp;             // learned decisions taken
     // per walk level: frontier size, work counters of the walk and local kernels, and the
@@ -143,6 +145,13 @@ struct DevCounters {
     unsigned long long lv_entries[FMM_MAX_LEVELS];      // checklist entries examined (incl. opened)
     unsigned long long lv_max_entries[FMM_MAX_LEVELS];  // largest per-sink count
 };
+
+// A walk (or the b_max items before it) that ran past a capacity left holes in the lists: the
+// kernels after it read nothing and return, and the host grows the buffers and solves again.
+__device__ __forceinline__ bool fmm_overflowed(const DevCounters* ctr)
+{
+    return *(const volatile unsigned int*)&ctr->overflow != 0u;
+}
 
 // Device buffers of a context.  Capacities are in elements.
 struct DevTree {
@@ -172,7 +181,6 @@ struct DevTree {
     float4 *plo = nullptr;   // per particle fl(x - fl(x)): with posf the centre pair of cen_diff
     float4 *off = nullptr;   // (x - com_bucket) in single precision, mass
     int *bucket_of = nullptr;
-    float4 *accs = nullptr;  // accumulator in sorted order (ax, ay, az, pot)
     int *act = nullptr;      // per group, its active particles compacted (see k_group_active)
     // radix tree (nodes 0..n-2 internal, leaf p is node n-1+p)
     int *ifirst = nullptr, *ilast = nullptr, *ileft = nullptr, *iright = nullptr;  // child node ids
@@ -300,10 +308,11 @@ cudaError_t fmm_radix_sort_kv_scratch(unsigned long long* ka, unsigned long long
                                       unsigned int* part, cudaStream_t s);
 
 // tree.cu
+// positions: pos (FP64 SoA) or, when ipos is given, 32-bit fixed-point coordinates x = u 2^-32
 cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
-                            cudaStream_t s);
+                            cudaStream_t s, const unsigned int* ipos = nullptr);
 cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
-                              long long n, DevCounters* ctr, cudaStream_t s);
+                              long long n, DevCounters* ctr, cudaStream_t s, const unsigned int* ipos = nullptr);
 cudaError_t fmm_launch_bucket_index(DevTree& t, long long n, cudaStream_t s);
 cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s);
@@ -372,6 +381,9 @@ cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, un
                                   int substep, int closing, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_assign_rungs(const float* acc, unsigned char* rung, long long n, double eps, double dt0,
                                     int max_rung, cudaStream_t s);
+cudaError_t fmm_launch_kick_drift_i32(unsigned int* ipos, float* vel, const float* acc, unsigned char* rung,
+                                      unsigned char* active_next, long long n, double eps, double dt0, int max_rung,
+                                      int substep, int closing, int periodic, DevCounters* ctr, cudaStream_t s);
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` on the calling thread's current
 // device, once per device.  Function attributes belong to each device's context, so a flag for

@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(ITHREADS) k_pp(const Group* __restrict__ group
     __shared__ PPChunk chunk[IW];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     float4* T = tile[wl];
+    if (fmm_overflowed(ctr)) return;
     const unsigned long long n_items =
         min((unsigned long long)*(volatile unsigned int*)&ctr->n_item_pp, (unsigned long long)cap_items);
     unsigned long long pairs = 0;
@@ -453,6 +454,7 @@ __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ gr
     __shared__ float4 Us[IW][FMM_GMAX], As[IW][PC_PMAX * 32 * 2];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const float4* rec4 = reinterpret_cast<const float4*>(rec);
+    if (fmm_overflowed(ctr)) return;
     const unsigned long long n_items =
         min((unsigned long long)*(volatile unsigned int*)&ctr->n_item_pc, (unsigned long long)cap_items);
     unsigned long long pairs = 0;
@@ -495,9 +497,11 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
                                                       const float4* __restrict__ part_pc,
                                                       const int* __restrict__ act, const int* __restrict__ cnact,
                                                       const unsigned int* __restrict__ perm, long long n,
-                                                      float* __restrict__ acc, float* __restrict__ pot, int terms)
+                                                      float* __restrict__ acc, float* __restrict__ pot, int terms,
+                                                      const DevCounters* __restrict__ ctr)
 {
     __shared__ float Ls[IW][FMM_NL];
+    if (fmm_overflowed(ctr)) return;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -580,8 +584,10 @@ static int persistent_blocks(K kernel)
 // Active sinks of every group, compacted in particle order: act[G.first + i] = the group's i-th
 // active particle (with no inactive particles, the identity).  One warp per group.
 __global__ void k_group_active(const Group* __restrict__ groups, const unsigned long long* __restrict__ ngroups_dev,
-                               long long cap_groups, const unsigned char* __restrict__ sact, int* __restrict__ act)
+                               long long cap_groups, const unsigned char* __restrict__ sact, int* __restrict__ act,
+                               const DevCounters* __restrict__ ctr)
 {
+    if (fmm_overflowed(ctr)) return;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -602,11 +608,13 @@ __global__ void k_group_active(const Group* __restrict__ groups, const unsigned 
 
 // Work items: per group ceil(pp_len / chunk) PP items and ceil(pc_len / chunk) PC items; exclusive scans give each group's first item, and every item learns its group.
 __global__ void k_item_counts(const Group* __restrict__ groups, long long grid, const unsigned long long* __restrict__ ng,
-                              unsigned int* __restrict__ cnt_pp, unsigned int* __restrict__ cnt_pc, int csize)
+                              unsigned int* __restrict__ cnt_pp, unsigned int* __restrict__ cnt_pc, int csize,
+                              const DevCounters* __restrict__ ctr)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= grid) return;
-    if (i >= (long long)*ng) {  // slots past the group count (capacity-sized launches) add nothing
+    // slots past the group count (capacity-sized launches) add nothing, nor does a walk that overflowed
+    if (i >= (long long)*ng || fmm_overflowed(ctr)) {
         cnt_pp[i] = 0u;
         cnt_pc[i] = 0u;
         return;
@@ -638,14 +646,14 @@ cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk
     // under graph capture the group count is known only on the device: cover the capacity
     const long long ng = t.cap_grid ? w.cap_groups : w.n_groups;
     const unsigned blocks = (unsigned)fmm_ceil_div(ng, 256);
-    k_item_counts<<<blocks, 256, 0, s>>>(w.groups, ng, &ctr->n_groups, w.cnt_pp, w.cnt_pc, chunk);
+    k_item_counts<<<blocks, 256, 0, s>>>(w.groups, ng, &ctr->n_groups, w.cnt_pp, w.cnt_pc, chunk, ctr);
     cudaError_t e = fmm_scan_exclusive(w.cnt_pp, w.base_pp, ng, &ctr->n_item_pp, t, s);
     if (e == cudaSuccess) e = fmm_scan_exclusive(w.cnt_pc, w.base_pc, ng, &ctr->n_item_pc, t, s);
     if (e != cudaSuccess) return e;
     k_item_expand<<<blocks, 256, 0, s>>>(ng, w.cnt_pp, w.base_pp, w.cnt_pc, w.base_pc, w.item_pp, w.item_pc,
                                          w.cap_item_pp, w.cap_item_pc, &ctr->overflow);
     k_group_active<<<(unsigned)std::max(1LL, std::min(fmm_ceil_div(ng, ITHREADS / 32), 152LL * 16)), ITHREADS, 0, s>>>(
-        w.groups, &ctr->n_groups, w.cap_groups, t.sact, t.act);
+        w.groups, &ctr->n_groups, w.cap_groups, t.sact, t.act, ctr);
     return cudaGetLastError();
 }
 
@@ -685,11 +693,11 @@ cudaError_t fmm_launch_l2p_out(DevTree& t, DevWalk& w, DevCounters* ctr, const I
         k_l2p_out<double><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
-            terms);
+            terms, ctr);
     else
         k_l2p_out<float><<<grid_for(ng), ITHREADS, 0, s>>>(
             w.groups, &ctr->n_groups, w.cap_groups, w.cap_item_pp, w.cap_item_pc, t.cen, t.bucket_of, t.bucket_cell,
             t.off, w.Lg, w.cnt_pp, w.base_pp, w.part_pp, w.cnt_pc, w.base_pc, w.part_pc, t.act, t.cnact, perm, n, acc, pot,
-            terms);
+            terms, ctr);
     return cudaGetLastError();
 }

@@ -90,6 +90,72 @@ cudaError_t fmm_launch_kick_drift(double* pos, double* vel, const float* acc, un
     return cudaGetLastError();
 }
 
+// The same schedule on compressed storage (Sec. 3.4, memory): positions as 32-bit fixed-point
+// coordinates x = u 2^-32 of the unit box, velocities as FP32.  Within a substep the kicks are FP64
+// (v = fl64(v32), v += a hk for each half kick, each product and sum rounded once: no fused
+// operations), and the velocity is stored rounded to FP32.  The drift moves u by the nearest integer
+// of v32 h 2^32, computed in FP64 (x 2^32 is exact), ties to even.  In the periodic box (periodic != 0)
+// u wraps modulo 2^32, which is the box's periodicity; in the isolated box a particle leaving
+// [0, 1) sets the argument error bit and keeps its old position.
+__global__ void k_kick_drift_i32(unsigned int* __restrict__ ipos, float* __restrict__ vel,
+                                 const float* __restrict__ acc, unsigned char* __restrict__ rung,
+                                 unsigned char* __restrict__ active_next, long long n, double eps, double dt0, int R,
+                                 long long s, int closing, int periodic, unsigned int* __restrict__ status)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = rung[i];
+    float v32[3] = {vel[i], vel[n + i], vel[2 * n + i]};
+    if ((s & ((1LL << (R - r)) - 1)) == 0) {
+        const float f[3] = {acc[i], acc[n + i], acc[2 * n + i]};
+        double v[3] = {v32[0], v32[1], v32[2]};
+        if (closing) {
+            const double hk = ldexp(dt0, -r - 1);
+            for (int a = 0; a < 3; a++) v[a] = __dadd_rn(v[a], __dmul_rn((double)f[a], hk));
+        }
+        int rt = target_rung(f[0], f[1], f[2], eps, dt0, R);
+        int rn = rt;
+        if (rt < r) {
+            rn = rt;
+            while (rn < r && (s & ((1LL << (R - rn)) - 1)) != 0) rn++;
+        }
+        r = rn;
+        rung[i] = (unsigned char)r;
+        const double hk = ldexp(dt0, -r - 1);
+        for (int a = 0; a < 3; a++) {
+            v[a] = __dadd_rn(v[a], __dmul_rn((double)f[a], hk));
+            v32[a] = __double2float_rn(v[a]);
+            vel[a * n + i] = v32[a];
+        }
+    }
+    const double h = ldexp(dt0, -R);
+    long long u[3];
+    bool out = false;
+    for (int a = 0; a < 3; a++) {
+        const long long d = __double2ll_rn(__dmul_rn(__dmul_rn((double)v32[a], h), 4294967296.0));
+        u[a] = (long long)ipos[a * n + i] + d;
+        if (periodic) u[a] &= 0xffffffffLL;
+        else if (u[a] < 0 || u[a] > 0xffffffffLL) out = true;
+    }
+    if (out) {
+        atomicOr(status, FMM_DEV_ERR_ARG);
+    } else {
+        for (int a = 0; a < 3; a++) ipos[a * n + i] = (unsigned int)u[a];
+    }
+    long long s1 = s + 1;
+    active_next[i] = ((s1 & ((1LL << (R - r)) - 1)) == 0) ? 1 : 0;
+}
+
+cudaError_t fmm_launch_kick_drift_i32(unsigned int* ipos, float* vel, const float* acc, unsigned char* rung,
+                                      unsigned char* active_next, long long n, double eps, double dt0, int max_rung,
+                                      int substep, int closing, int periodic, DevCounters* ctr, cudaStream_t s)
+{
+    k_kick_drift_i32<<<(unsigned)fmm_ceil_div(n, 256), 256, 0, s>>>(ipos, vel, acc, rung, active_next, n, eps, dt0,
+                                                                    max_rung, substep, closing, periodic,
+                                                                    &ctr->kdk_status);
+    return cudaGetLastError();
+}
+
 cudaError_t fmm_launch_assign_rungs(const float* acc, unsigned char* rung, long long n, double eps, double dt0,
                                     int max_rung, cudaStream_t s)
 {

@@ -28,13 +28,21 @@
 
 // ---------------------------------------------------------------- keys
 
-__global__ void k_keys(const double* __restrict__ pos, const float* __restrict__ mass, long long n,
-                       unsigned long long* __restrict__ key, unsigned int* __restrict__ idx,
-                       unsigned int* __restrict__ status)
+// A position given as FP64 coordinates, or as 32-bit fixed-point ones (Sec. 3.4: x = u 2^-32, exact
+// in FP64), component a of particle i of n.
+__device__ __forceinline__ double pos_at(const double* __restrict__ pos, const unsigned int* __restrict__ ipos,
+                                         long long n, int a, long long i)
+{
+    return ipos ? __dmul_rn(__uint2double_rn(ipos[a * n + i]), 0x1p-32) : pos[a * n + i];
+}
+
+__global__ void k_keys(const double* __restrict__ pos, const unsigned int* __restrict__ ipos,
+                       const float* __restrict__ mass, long long n, unsigned long long* __restrict__ key,
+                       unsigned int* __restrict__ idx, unsigned int* __restrict__ status)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
+    double x = pos_at(pos, ipos, n, 0, i), y = pos_at(pos, ipos, n, 1, i), z = pos_at(pos, ipos, n, 2, i);
     float m = mass[i];
     bool ok = (x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0 && m > 0.0f && isfinite(m));
     if (!ok) atomicOr(status, FMM_DEV_ERR_ARG);
@@ -44,14 +52,15 @@ __global__ void k_keys(const double* __restrict__ pos, const float* __restrict__
 }
 
 cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
-                            cudaStream_t s)
+                            cudaStream_t s, const unsigned int* ipos)
 {
-    k_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, mass, n, t.key, t.idx, &ctr->status);
+    k_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, ipos, mass, n, t.key, t.idx, &ctr->status);
     return cudaGetLastError();
 }
 
-__global__ void k_gather(const double* __restrict__ pos, const float* __restrict__ mass,
-                         const unsigned char* __restrict__ active, long long n, const unsigned int* __restrict__ idx,
+__global__ void k_gather(const double* __restrict__ pos, const unsigned int* __restrict__ ipos,
+                         const float* __restrict__ mass, const unsigned char* __restrict__ active, long long n,
+                         const unsigned int* __restrict__ idx,
                          double* __restrict__ sx, double* __restrict__ sy, double* __restrict__ sz,
                          float* __restrict__ sm, unsigned char* __restrict__ sact, float4* __restrict__ posf,
                          float4* __restrict__ plo, unsigned long long* __restrict__ n_active)
@@ -60,7 +69,7 @@ __global__ void k_gather(const double* __restrict__ pos, const float* __restrict
     bool act = false;
     if (i < n) {
         unsigned int p = idx[i];
-        double x = pos[p], y = pos[n + p], z = pos[2 * n + p];
+        double x = pos_at(pos, ipos, n, 0, p), y = pos_at(pos, ipos, n, 1, p), z = pos_at(pos, ipos, n, 2, p);
         sx[i] = x;
         sy[i] = y;
         sz[i] = z;
@@ -78,9 +87,9 @@ __global__ void k_gather(const double* __restrict__ pos, const float* __restrict
 }
 
 cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
-                              long long n, DevCounters* ctr, cudaStream_t s)
+                              long long n, DevCounters* ctr, cudaStream_t s, const unsigned int* ipos)
 {
-    k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, mass, active, n, t.idx, t.sx, t.sy, t.sz, t.sm,
+    k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, ipos, mass, active, n, t.idx, t.sx, t.sy, t.sz, t.sm,
                                                            t.sact, t.posf, t.plo, &ctr->n_active);
     return cudaGetLastError();
 }
@@ -216,7 +225,8 @@ __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ 
                         const int* __restrict__ iright, const int* __restrict__ nparent,
                         const unsigned int* __restrict__ cid, int n, int bucket, const unsigned char* __restrict__ split,
                         int* __restrict__ cfirst, int* __restrict__ ccount, int* __restrict__ cparent,
-                        int* __restrict__ cchild, unsigned int* __restrict__ bflag, unsigned char* __restrict__ nogroup)
+                        int* __restrict__ cchild, unsigned int* __restrict__ bflag, unsigned char* __restrict__ nogroup,
+                        long long cap)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= 2 * n - 1) return;
@@ -229,6 +239,7 @@ __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ 
     }
     if (!kept) return;
     int c = (int)cid[x];
+    if ((long long)c >= cap) return;  // never taken: the host sizes the cells from the count first
     int first = x < n - 1 ? ifirst[x] : x - (n - 1);
     int count = node_count(ifirst, ilast, n, x);
     cfirst[c] = first;
@@ -237,8 +248,9 @@ __global__ void k_cells(const int* __restrict__ ifirst, const int* __restrict__ 
     cparent[c] = p < 0 ? -1 : (int)cid[p];
     if (split) nogroup[c] = (unsigned char)((split[x] >> 1) & 1u);
     if (node_splits(ifirst, ilast, n, bucket, split, x)) {
-        cchild[2 * c] = (int)cid[ileft[x]];
-        cchild[2 * c + 1] = (int)cid[iright[x]];
+        const long long l = cid[ileft[x]], r = cid[iright[x]];
+        cchild[2 * c] = l < cap ? (int)l : -1;
+        cchild[2 * c + 1] = r < cap ? (int)r : -1;
     } else {
         cchild[2 * c] = -1;
         cchild[2 * c + 1] = -1;
@@ -541,7 +553,8 @@ cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s
     const unsigned char* split = (t.grade_key && ni > 1) ? t.split : nullptr;
     k_cells<<<(unsigned)fmm_ceil_div(2 * ni - 1, TB), TB, 0, s>>>(t.ifirst, t.ilast, t.ileft, t.iright, t.nparent,
                                                                   t.keep, ni, bucket, split, t.cfirst, t.ccount,
-                                                                  t.cparent, t.cchild, t.bflag, t.nogroup);
+                                                                  t.cparent, t.cchild, t.bflag, t.nogroup,
+                                                                  t.cap_cells);
     return cudaGetLastError();
 }
 

@@ -566,6 +566,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    if (fmm_overflowed(ctr)) return;
     const long long total = min((long long)*(volatile unsigned long long*)&ctr->cc_len, cap_cc);
     const long long nranges = fmm_ceil_div(total, LF_ENTRIES);
     const int c0 = lane, c1 = lane + 32;  // this lane's coefficients in the reduction
@@ -637,7 +638,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
 #define LG_MAX_ANC FMM_MAX_LEVELS
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
     const Group* __restrict__ groups, const int* __restrict__ cparent, const int* __restrict__ lcc_len,
-    const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg,
+    const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg, long long cap_groups,
     DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
@@ -645,7 +646,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long ng = (long long)*(volatile unsigned long long*)&ctr->n_groups;
+    if (fmm_overflowed(ctr)) return;
+    const long long ng = min((long long)*(volatile unsigned long long*)&ctr->n_groups, cap_groups);
     for (long long gi = gw; gi < ng; gi += nw) {
         const int g = groups[gi].cell;
         int na = 0;
@@ -811,6 +813,7 @@ cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps
     const int blocks = w.n_warps / LOCAL_WPB;
     k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.cen, t.posf,
                                                    t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
-    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, ctr);
+    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, w.cap_groups,
+                                                     ctr);
     return cudaGetLastError();
 }

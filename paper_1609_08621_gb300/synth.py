@@ -33,6 +33,7 @@ __all__ = [
     "coincident",
     "batch_boxes",
     "make",
+    "to_fixed",
     "WORKLOADS",
 ]
 
@@ -202,6 +203,7 @@ WORKLOADS = {
     "rungs16m": dict(n=256 ** 3, kind="plummer", seed=4, eps=paper_softening(256 ** 3), theta=0.55),
     "learned134m": dict(n=512 ** 3, kind="plummer", seed=5, eps=paper_softening(512 ** 3), theta=0.55),
     "periodic2m": dict(n=128 ** 3, kind="nfw", seed=2, eps=paper_softening(128 ** 3), theta=0.55, nrep=1),
+    "compressed704": dict(n=704 ** 3, kind="plummer", seed=6, eps=paper_softening(704 ** 3), theta=0.55),
 }
 
 
@@ -216,3 +218,10 @@ def make(kind: str, n: int, seed: int):
     if kind == "coincident":
         return coincident(n, seed)
     raise ValueError(f"unknown structure {kind!r}")
+
+
+def to_fixed(pos: np.ndarray) -> np.ndarray:
+    """Positions in [0, 1) as 32-bit fixed-point coordinates u (x ~ u 2^-32, nearest, capped at
+    2^32 - 1): the compressed storage of Sec. 3.4, an input format."""
+    u = np.rint(np.asarray(pos, dtype=np.float64) * 4294967296.0)
+    return np.minimum(u, 4294967295.0).astype(np.uint32)

@@ -103,3 +103,45 @@ def test_failed_allocation_reports_oom_and_the_context_recovers(dev, after):
     finally:
         binding.debug_fail_allocations(-1)
         ctx.close()
+
+
+def test_replay_whose_walk_overflows_is_repeated_eagerly(dev):
+    """A graph captured while 0.2% of the particles were active holds walk lists sized for them
+    (one entry per particle and list, 8192 scratch entries per warp: no regrow for them); with
+    every particle active the same replay overflows them (the PP list alone needs 2.3 entries per
+    particle).  The kernels after the walk then
+    read none of the partly written lists, the solve is repeated eagerly with grown lists, and the
+    result is bit for bit that of a context that never overflowed."""
+    n = 20000
+    pos, mass = synth.make("nfw", n, 93)
+    eps, theta = synth.paper_softening(n), 0.55
+    few = (np.random.default_rng(3).random(n) < 0.002).astype(np.uint8)
+    c = binding.Context(0)
+    try:
+        c.debug_walk_capacity(8192, 1)
+        c.set_graphs(True)
+        tp, tm, ta = t(pos, torch.float64), t(mass, torch.float32), t(few, torch.uint8)
+        acc = torch.zeros(3 * n, dtype=torch.float32, device="cuda:0")
+        pot = torch.zeros(n, dtype=torch.float32, device="cuda:0")
+        c.compute_forces(tp, tm, eps, theta, acc, pot, ta)  # eager, then captured
+        assert c.graph_info()["captured"] and c.stats()["retries"] == 0
+        r0 = c.graph_info()["replays"]
+        ta.fill_(1)
+        c.compute_forces(tp, tm, eps, theta, acc, pot, ta)  # the replay overflows
+        torch.cuda.synchronize()
+        assert c.graph_info()["replays"] == r0 and c.stats()["retries"] >= 1
+        a1, p1 = acc.cpu().numpy(), pot.cpu().numpy()
+        acc.fill_(float("nan"))
+        c.compute_forces(tp, tm, eps, theta, acc, pot, ta)  # captured again after the eager repeat
+        torch.cuda.synchronize()
+        assert c.graph_info()["replays"] == r0 + 1
+        assert np.array_equal(acc.cpu().numpy(), a1)
+    finally:
+        c.close()
+    ref = binding.Context(0)
+    try:
+        a0, p0 = solve(ref, pos, mass, eps, theta)
+        assert ref.stats()["retries"] == 0
+    finally:
+        ref.close()
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)

@@ -91,3 +91,62 @@ def test_rung_thresholds_and_synchronisation():
     assert rung[0] == 2 and act[0] == False  # rung 2 is next active at substep 4
     _, _, rung, act = kdk.kick_drift(pos, vel, np.zeros((3, 1), np.float32), np.array([3]), eps, 1.0, 3, 4, True)
     assert rung[0] == 1
+
+
+# ---------------------------------------------------------------- compressed storage (Sec. 3.4)
+
+
+def test_compressed_substep_is_the_fp64_substep_rounded():
+    """One substep on 32-bit positions and FP32 velocities lands within the rounding of that storage
+    of the FP64 substep: |dx| <= |v64 - v32| h + 2^-33 (the drift's rounding to the grid) + 2^-52 (the
+    FP64 substep's own rounding of x + v h, x < 1), and the velocity is the FP64 one rounded to FP32."""
+    rng = np.random.default_rng(3)
+    n = 500
+    pos = kdk.from_fixed(kdk.to_fixed(0.2 + 0.6 * rng.random((3, n))))
+    vel32 = (0.3 * rng.standard_normal((3, n))).astype(np.float32)
+    acc = (5.0 * rng.standard_normal((3, n))).astype(np.float32)
+    rung = rng.integers(0, 4, n)
+    eps, dt0, R = 1e-3, 1e-3, 3
+    for s in range(8):
+        p64, v64, r64, a64 = kdk.kick_drift(pos, vel32.astype(np.float64), acc, rung, eps, dt0, R, s, s > 0)
+        u, v, r, a, out = kdk.kick_drift_i32(kdk.to_fixed(pos), vel32, acc, rung, eps, dt0, R, s, s > 0)
+        assert not out.any() and np.array_equal(r, r64) and np.array_equal(a, a64)
+        assert np.array_equal(v, v64.astype(np.float32))
+        h = math.ldexp(dt0, -R)
+        bound = np.abs(v64 - v.astype(np.float64)) * h + 2.0 ** -33 + 2.0 ** -52
+        assert np.all(np.abs(kdk.from_fixed(u) - p64) <= bound)
+
+
+def test_compressed_drift_wraps_in_the_periodic_box_and_stops_at_the_isolated_walls():
+    # u = 2^32 - 10 moving by +25 units of 2^-32 per substep: 15 in the periodic box
+    h = 2.0 ** -30  # dt0 with R = 0
+    ipos = np.array([[2 ** 32 - 10], [7], [2 ** 31]], dtype=np.uint32)
+    vel = np.array([[25.0 * 2.0 ** -32 / h], [-8.0 * 2.0 ** -32 / h], [0.0]], dtype=np.float32)
+    acc = np.zeros((3, 1), np.float32)
+    u, v, r, a, out = kdk.kick_drift_i32(ipos, vel, acc, np.zeros(1, int), 1e-3, h, 0, 0, False, periodic=True)
+    assert list(u[:, 0]) == [15, 2 ** 32 - 1, 2 ** 31] and not out[0]
+    u, v, r, a, out = kdk.kick_drift_i32(ipos, vel, acc, np.zeros(1, int), 1e-3, h, 0, 0, False, periodic=False)
+    assert out[0] and np.array_equal(u, ipos)
+
+
+def test_compressed_storage_keeps_the_two_body_orbit():
+    """The paper checked that the compression does not affect trajectories significantly: over one
+    period of the softened circular orbit, 32-bit positions and FP32 velocities stay within 1e-6 of
+    the box of the FP64 integration, and the energy error stays the leapfrog's."""
+    pos, vel, mass, eps, period = _two_body()
+    steps = 256
+    dt0 = period / steps
+    f = _direct_force(mass, eps)
+    p64, v64, r, acc = kdk.run(pos, vel, mass, eps, dt0, 0, steps, f, rung=np.zeros(2, int))
+    u = kdk.to_fixed(pos)
+    v = vel.astype(np.float32)
+    rung = np.zeros(2, int)
+    a = f(kdk.from_fixed(u), None)
+    for k in range(steps):
+        u, v, rung, act, out = kdk.kick_drift_i32(u, v, a, rung, eps, dt0, 0, 0, k > 0)
+        assert not out.any()
+        a = f(kdk.from_fixed(u), None)
+    assert np.abs(kdk.from_fixed(u) - p64).max() < 1e-6
+    e0 = _energy(pos, vel, mass, eps)
+    vc = kdk.close(v.astype(np.float64), a, rung, dt0)
+    assert abs(_energy(kdk.from_fixed(u), vc, mass, eps) / e0 - 1) < 1e-4
