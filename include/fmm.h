@@ -204,10 +204,12 @@ fmm_status fmm_compute_forces_batch(fmm_ctx *ctx, const double *pos, const float
 
 /* CUDA graphs (not in the paper).  With enable = 1, a force solve (fmm_compute_forces, _batch,
  * _host, and the autotuner's solves) that repeats the previous call's buffers (pos, mass,
- * active, acc, pot pointers), n, box offsets, eps, theta and parameters replays a CUDA graph of
- * the whole solve: one launch, no host synchronisation inside, one at the end.  The first call of
- * a new combination runs eagerly and captures the graph (on the context's stream, in thread-local
- * capture mode) for the next.  A replay that finds a buffer or the walk's level count too small
+ * active, acc, pot pointers), n, box offsets, eps, theta and parameters replays the solve as two
+ * CUDA graphs: the first builds the keys, the sorted particles and the radix tree and reads back
+ * the tree's cell count; the host checks it against the cell buffers and launches the second
+ * (everything else), then synchronises once at the end.  The first call of a new combination runs
+ * eagerly and captures the graphs (on the context's stream, in thread-local capture mode) for the
+ * next.  A replay that finds the cell buffers, another buffer or the walk's level count too small
  * repeats the solve eagerly, which grows what it must, and recaptures.  Results are identical to
  * eager solves.  enable = 0 (the default) drops the graph.  The contents of the buffers may change
  * between calls; their addresses may not (a new address means a new capture). */
@@ -488,7 +490,7 @@ fmm_status fmm_debug_walk_capacity(fmm_ctx *ctx, long long scratch_entries, long
  *         thread's current device; the call returns after that stream has finished the work.
  *
  * The first call on each device looks up the scratch array's device address (and sets a kernel
- * attribute) with that device current; make that first call before any stream capture begins.
+ * attribute) with that device current.
  * One scratch array serves all calls on a device: calls that overlap in time (from several
  * threads, or on several streams) race on it and must be serialised by the caller.
  * Errors: FMM_ERR_ARG for NULL pointers, n out of range or a position outside [0, 1) (keys and

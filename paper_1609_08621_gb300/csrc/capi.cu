@@ -253,7 +253,7 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
             t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
             w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
-            w.lcells, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
+            w.lcp_off, w.lcp_len, w.cp, w.cp_sink, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
             w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch,
             f.cfirst, f.ccount, f.cchild, f.cparent, f.bucket_cell, f.com, f.clo, f.chi, f.bmax, f.rec, f.posf, f.plo,
             f.off, f.bucket_of, f.key, f.member, c->d_flag, c->d_at, c->d_idx, c->d_perm, c->d_act, c->d_pos, c->d_mass};
@@ -603,8 +603,9 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
     const long long cells = c->t.cap_cells;
     const long long need_front = cells;
     // Capacities per particle, from the NFW and clustered boxes measured here (per particle:
-    // PP entries 1.8, PC 5.2, local 7.9, a level's checklists under 5): checklists 8, PP 3, PC 8,
-    // local entries 12, and 8192 scratch entries per warp and list (fmm_debug_walk_capacity may
+    // PP entries 1.8, PC 5.2, local 7.9 (4.4 multipole and 3.4 point sources in the NFW halo), a
+    // level's checklists under 5): checklists 8, PP 3, PC 8, local entries 6 of each kind, and
+    // 8192 scratch entries per warp and list (fmm_debug_walk_capacity may
     // start them smaller).  Groups: in a plain tree they are one more than the cells with more
     // than g particles, which no multiple of n / (g + 1) bounds (a chain of such cells may shed a
     // few particles per level); measured 2.3 n / (g + 1) in a 20000-particle NFW halo and 1.7 in
@@ -615,10 +616,14 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
     long long need_cl = (long long)scale * (ls * n + floor);
     long long need_pp = (long long)scale * ((c->dbg_list_scale > 0 ? (ls + 1) / 2 : 3) * n + floor);
     long long need_pc = (long long)scale * (ls * n + floor);
-    long long need_cc = (long long)scale * ((c->dbg_list_scale > 0 ? ls : 12) * n + floor);
+    long long need_cc = (long long)scale * ((c->dbg_list_scale > 0 ? ls : 6) * n + floor);
     long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * scale;
     long long need_groups = c->t.graded ? cells : (long long)scale * (4 * n / (group + 1) + 64 + 2LL * c->t.nbox);
     if (need_groups > cells) need_groups = cells;
+    // the device counters hold these lists' lengths in 32 bits
+    if (std::max(need_cc, std::max(need_pp, need_pc)) >= (1LL << 32))
+        return fail(FMM_ERR_OOM, "walk lists of %lld entries exceed the 2^32 the counters hold",
+                    std::max(need_cc, std::max(need_pp, need_pc)));
     if (need_front > w.cap_front) {
         w.cap_front = 0;
         for (int i = 0; i < 2; i++) {
@@ -628,7 +633,8 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
         }
         CK(alloc(&w.lcc_off, need_front));
         CK(alloc(&w.lcc_len, need_front));
-        CK(alloc(&w.lcells, need_front));
+        CK(alloc(&w.lcp_off, need_front));
+        CK(alloc(&w.lcp_len, need_front));
         w.cap_front = need_front;
     }
     if (need_groups > w.cap_groups) {
@@ -662,6 +668,12 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
         CK(alloc(&w.cc, need_cc));
         CK(alloc(&w.cc_sink, need_cc));
         w.cap_cc = need_cc;
+    }
+    if (need_cc > w.cap_cp) {
+        w.cap_cp = 0;
+        CK(alloc(&w.cp, need_cc));
+        CK(alloc(&w.cp_sink, need_cc));
+        w.cap_cp = need_cc;
     }
     if (need_scr > w.cap_scratch) {
         w.cap_scratch = 0;
@@ -767,6 +779,7 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
         CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
         // cells above a box's root are never walked: their local lists must read as empty
         CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.n_cells, s));
+        CK(cudaMemsetAsync(w.lcp_len, 0, sizeof(int) * (size_t)t.n_cells, s));
         CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
         CK(fmm_launch_walk_seed(t, w, c->ctr, s, c->second_root));
         c->launches += 1;
@@ -790,9 +803,10 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
             while (used < levels && c->ctr_h->lv_front[used] > 0) used++;
             w.n_levels = used;
             w.n_groups = (long long)c->ctr_h->n_groups;
-            w.pp_len = (long long)c->ctr_h->pp_len;
-            w.pc_len = (long long)c->ctr_h->pc_len;
-            w.cc_len = (long long)c->ctr_h->cc_len;
+            w.pp_len = (long long)fmm_lo32(c->ctr_h->src_len);
+            w.pc_len = (long long)fmm_hi32(c->ctr_h->src_len);
+            w.cc_len = (long long)fmm_lo32(c->ctr_h->loc_len);
+            w.cp_len = (long long)fmm_hi32(c->ctr_h->loc_len);
             c->stats.retries = attempt;
             return FMM_OK;
         }
@@ -1020,6 +1034,7 @@ static fmm_status enqueue_graph_rest(fmm_ctx* c, long long n, const fmm_params& 
     a.audit_cap = c->audit_cap;
     // the overflow flag is not cleared here: the b_max items may have set it (the head cleared it)
     CK(cudaMemsetAsync(w.lcc_len, 0, sizeof(int) * (size_t)t.cap_cells, s));
+    CK(cudaMemsetAsync(w.lcp_len, 0, sizeof(int) * (size_t)t.cap_cells, s));
     CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
     CK(fmm_launch_walk_seed(t, w, c->ctr, s));
     c->launches += 1;
@@ -1181,9 +1196,10 @@ static fmm_status replay_graph(fmm_ctx* c, long long n, int* outcome)
     while (used < c->graph_levels && h.lv_front[used] > 0) used++;
     w.n_levels = used;
     w.n_groups = (long long)h.n_groups;
-    w.pp_len = (long long)h.pp_len;
-    w.pc_len = (long long)h.pc_len;
-    w.cc_len = (long long)h.cc_len;
+    w.pp_len = (long long)fmm_lo32(h.src_len);
+    w.pc_len = (long long)fmm_hi32(h.src_len);
+    w.cc_len = (long long)fmm_lo32(h.loc_len);
+    w.cp_len = (long long)fmm_hi32(h.loc_len);
     c->have_tree = true;
     c->theta_nodes = -1.0f;
     memset(&c->stats, 0, sizeof c->stats);
@@ -1667,7 +1683,7 @@ extern "C" fmm_status fmm_tree_info(const fmm_ctx* c, long long* n_cells, long l
     if (n_groups) *n_groups = c->have_solve ? c->w.n_groups : 0;
     if (n_pp) *n_pp = c->have_solve ? c->w.pp_len : 0;
     if (n_pc) *n_pc = c->have_solve ? c->w.pc_len : 0;
-    if (n_local) *n_local = c->have_solve ? c->w.cc_len : 0;
+    if (n_local) *n_local = c->have_solve ? c->w.cc_len + c->w.cp_len : 0;
     return FMM_OK;
 }
 
@@ -1764,16 +1780,14 @@ static fmm_status collect_lists(const fmm_ctx* c, int kind, std::vector<long lon
             for (int i = 0; i < l; i++) push(G.cell, L[o + i]);
         }
     } else {
-        std::vector<unsigned int> L((size_t)w.cc_len);
-        std::vector<int> sk((size_t)w.cc_len);
-        CK(d2h(L.data(), w.cc, w.cc_len, s));
-        CK(d2h(sk.data(), w.cc_sink, w.cc_len, s));
+        // kind 2 (CC): the multipole-source list; kind 3 (CP): the point-source list
+        const long long len = kind == 2 ? w.cc_len : w.cp_len;
+        std::vector<unsigned int> L((size_t)len);
+        std::vector<int> sk((size_t)len);
+        CK(d2h(L.data(), kind == 2 ? w.cc : w.cp, len, s));
+        CK(d2h(sk.data(), kind == 2 ? w.cc_sink : w.cp_sink, len, s));
         CK(cudaStreamSynchronize(s));
-        for (long long i = 0; i < w.cc_len; i++) {
-            unsigned int e = L[i];
-            bool pointlike = (e & FMM_PARTICLE_BIT) || cn[entry_index(e, ib)] == 1;
-            if ((kind == 3) == pointlike) push(sk[i], e);
-        }
+        for (long long i = 0; i < len; i++) push(sk[i], L[i]);
     }
     return FMM_OK;
 }

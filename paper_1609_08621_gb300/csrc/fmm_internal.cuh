@@ -128,8 +128,11 @@ struct DevCounters {
                               // isolated box (kept across solves until a solve reports it)
     unsigned long long n_active;
     // walk totals
-    unsigned long long n_groups, n_lcells;
-    unsigned long long pp_len, pc_len, cc_len;
+    unsigned long long n_groups;
+    // list lengths, two to a word (one atomic per sink allocates both): the local entries of
+    // multipole sources (low 32 bits) and point sources (high 32 bits), and the groups' PP (low)
+    // and PC (high) entries; the capacities stay below 2^32
+    unsigned long long loc_len, src_len;
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
@@ -152,6 +155,9 @@ __device__ __forceinline__ bool fmm_overflowed(const DevCounters* ctr)
 {
     return *(const volatile unsigned int*)&ctr->overflow != 0u;
 }
+
+__host__ __device__ __forceinline__ unsigned long long fmm_lo32(unsigned long long v) { return v & 0xffffffffull; }
+__host__ __device__ __forceinline__ unsigned long long fmm_hi32(unsigned long long v) { return v >> 32; }
 
 // Device buffers of a context.  Capacities are in elements.
 struct DevTree {
@@ -244,15 +250,16 @@ __host__ __forceinline__ PeriodicArgs periodic_args(const DevTree& t)
 }
 
 struct DevWalk {
-    long long cap_front = 0, cap_cl = 0, cap_pp = 0, cap_pc = 0, cap_cc = 0, cap_groups = 0;
+    long long cap_front = 0, cap_cl = 0, cap_pp = 0, cap_pc = 0, cap_cc = 0, cap_cp = 0, cap_groups = 0;
     long long cap_scratch = 0;  // entries per list per warp
     int n_warps = 0;
     int *f_cell[2] = {nullptr, nullptr};
     unsigned long long *f_cloff[2] = {nullptr, nullptr};
     int *f_cllen[2] = {nullptr, nullptr};
-    unsigned long long *lcc_off = nullptr;  // per cell: its local (CC/CP) list
-    int *lcc_len = nullptr;
-    int *lcells = nullptr;                  // cells with a non-empty local list
+    // per cell: its local-expansion entries, multipole sources (lcc, list cc) and point sources
+    // (lcp, list cp: particles and one-particle cells)
+    unsigned long long *lcc_off = nullptr, *lcp_off = nullptr;
+    int *lcc_len = nullptr, *lcp_len = nullptr;
     float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
     // work items of the interaction kernels: group g's PP list is cut into chunks of list_chunk
     // entries (items base_pp[g] ..), its PC list into chunks of list_chunk cells;
@@ -262,12 +269,12 @@ struct DevWalk {
     float4 *part_pp = nullptr, *part_pc = nullptr;
     long long cap_item_pp = 0, cap_item_pc = 0;
     unsigned int *cl[2] = {nullptr, nullptr};
-    unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr;
-    int *cc_sink = nullptr;   // sink cell of every local (CC/CP) entry
+    unsigned int *pp = nullptr, *pc = nullptr, *cc = nullptr, *cp = nullptr;
+    int *cc_sink = nullptr, *cp_sink = nullptr;  // sink cell of every local entry
     Group *groups = nullptr;
     unsigned int *scratch = nullptr;
     // levels kept for export of the local lists
-    long long n_groups = 0, pp_len = 0, pc_len = 0, cc_len = 0, n_levels = 0;
+    long long n_groups = 0, pp_len = 0, pc_len = 0, cc_len = 0, cp_len = 0, n_levels = 0;
 };
 
 // The fixed tree of the dual-tree scheme (dual.cu): a copy of the source-side arrays of a tree

@@ -73,23 +73,26 @@ __device__ __forceinline__ float gap_axis(float lo_s, float hi_s, float lo_k, fl
 #define FMM_WALK_SLOTS 1  // entries per lane and step
 #endif
 #ifndef FMM_WALK_MINB
-#define FMM_WALK_MINB 6  // resident blocks per SM the fixed-theta walk is compiled for
+#define FMM_WALK_MINB 5  // resident blocks per SM the fixed-theta walk is compiled for (96 registers, no spills)
 #endif
 template <int MODE>
 struct WalkSlots {
     static constexpr int E = FMM_WALK_SLOTS;
 };
 
-template <int MODE>
+// PER: a periodic box (list entries carry a copy code above their index bits); the isolated walk is
+// compiled without the decoding.
+template <int MODE, bool PER>
 __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k_walk_level(
     const WalkNode* __restrict__ node, const float4* __restrict__ posf, const int* __restrict__ cnact,
     const int* __restrict__ f_cell, const unsigned long long* __restrict__ f_cloff, const int* __restrict__ f_cllen,
     int level, const unsigned int* __restrict__ cl_cur, int* __restrict__ f_cell_next,
     unsigned long long* __restrict__ f_cloff_next, int* __restrict__ f_cllen_next, long long cap_front,
     unsigned int* __restrict__ cl_next, long long cap_cl, unsigned long long* __restrict__ lcc_off,
-    int* __restrict__ lcc_len, int* __restrict__ lcells, unsigned int* __restrict__ pp, long long cap_pp,
-    unsigned int* __restrict__ pc,
+    int* __restrict__ lcc_len, unsigned long long* __restrict__ lcp_off, int* __restrict__ lcp_len,
+    unsigned int* __restrict__ pp, long long cap_pp, unsigned int* __restrict__ pc,
     long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
+    unsigned int* __restrict__ cp, int* __restrict__ cp_sink, long long cap_cp,
     Group* __restrict__ groups, long long cap_groups, unsigned int* __restrict__ scratch, long long cap_scr,
     DevCounters* __restrict__ ctr, int bucket, int group, float four_eps2, const float4* __restrict__ mnorm,
     const float* __restrict__ amin,
@@ -97,7 +100,8 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
     int2* __restrict__ audit_pairs, long long audit_cap, const unsigned char* __restrict__ nogroup, PeriodicArgs pa)
 {
     constexpr int E = WalkSlots<MODE>::E;
-    const unsigned int q0 = copy_centre(pa.R);
+    const unsigned int q0 = PER ? copy_centre(pa.R) : 0u;
+    const int ib = PER ? pa.ib : 31;  // index bits of a list entry
     extern __shared__ __align__(16) unsigned char walk_smem[];
     if (MODE == 1) {
         mlp_load_smem(mlp_packed, walk_smem);
@@ -113,11 +117,12 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned int* Q = scratch + gw * 5 * cap_scr;
     unsigned int* D = Q + cap_scr;
-    unsigned int* A = Q + 2 * cap_scr;
+    unsigned int* A = Q + 2 * cap_scr;  // accepted: multipole sources from the front, point sources from the back
     unsigned int* P = Q + 3 * cap_scr;
     unsigned int* C = Q + 4 * cap_scr;
     const unsigned int lt = fmm_lanemask_lt();
     const unsigned long long n_front = *(volatile unsigned long long*)&ctr->lv_front[level];
+    unsigned long long w_entries = 0, w_max = 0;  // this warp's statistics, added once at the end
 
     for (;;) {
         unsigned long long fi = 0;
@@ -133,7 +138,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         const float ak = MODE == 1 ? amin[k] : 0.0f;
         const unsigned long long cl0 = f_cloff[fi];
         const long long ncl = f_cllen[fi];
-        long long nq = 0, nd = 0, na = 0, npp = 0, npc = 0;
+        long long nq = 0, nd = 0, na = 0, nap = 0, npp = 0, npc = 0;
         int npend = 0;  // learned criterion: pairs waiting for the network
         int srcpp = 0;  // this lane's PP source particles
         bool overflow = false;
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
 #pragma unroll
             for (int s = 0; s < E; s++) {
                 if (valid[s]) {
-                    const unsigned int j = entry_index(e[s], pa.ib);
+                    const unsigned int j = entry_index(e[s], ib);
                     if (e[s] & FMM_PARTICLE_BIT) S[s].a = posf[j];
                     else S[s] = node[j];
                 }
@@ -171,10 +176,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
             // the tables of those values (the axes with a non-zero shift)
 #pragma unroll
             for (int s = 0; s < E; s++) {
-                if (valid[s] && entry_copy(e[s], pa.ib) != q0) {
-                    const unsigned int j = entry_index(e[s], pa.ib);
+                if (PER && valid[s] && entry_copy(e[s], ib) != q0) {
+                    const unsigned int j = entry_index(e[s], ib);
                     int nv[3];
-                    copy_shift(entry_copy(e[s], pa.ib), pa.R, nv[0], nv[1], nv[2]);
+                    copy_shift(entry_copy(e[s], ib), pa.R, nv[0], nv[1], nv[2]);
                     const int w2 = 2 * pa.R;
 #pragma unroll
                     for (int ax = 0; ax < 3; ax++) {
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 }
             }
             int out[E], nadd[E], sfirst[E], c0[E], c1[E], nsrc_cell[E];
-            bool sleaf[E];
+            bool sleaf[E], ptl[E];
 #pragma unroll
             for (int s = 0; s < E; s++) {
                 out[s] = OUT_NONE;
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 c0[s] = c1[s] = -1;
                 nsrc_cell[s] = 0;
                 sleaf[s] = false;
+                ptl[s] = false;
                 if (s >= ns) continue;
                 float f[MLP_F];  // learned criterion: the pair's features (set for band pairs)
                 bool pointlike = false, acc = false, need = false;
@@ -255,7 +261,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                             } else if (band == 3 && !(ak > 0.0f)) {
                                 band = acc ? 1 : 2;  // no acceleration estimate: the fixed criterion decides
                             } else if (band == 3) {
-                                mlp_pair_features(K, S[s], mnorm[entry_index(e[s], pa.ib)], ak, eps, f);
+                                mlp_pair_features(K, S[s], mnorm[entry_index(e[s], ib)], ak, eps, f);
                                 band = mlp_surrogate(reinterpret_cast<const float*>(walk_smem + MLPP_SUR), f, te, tau,
                                                      margin);
                             }
@@ -282,6 +288,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                         nadd[s] = 0;
                     }
                 }
+                ptl[s] = pointlike;
                 if (valid[s]) {
                     if (acc) {
                         out[s] = OUT_ACCEPT;
@@ -298,15 +305,16 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 }
             }
             // ranks in queue order: slot by slot, lanes in order within a slot
-            unsigned int mA[E], mD[E], mC[E], mP[E];
+            unsigned int mA[E], mAp[E], mD[E], mC[E], mP[E];
             int incl[E], tot[E];
-            long long tA = 0, tD = 0, tC = 0, tP = 0, tQ = 0;
+            long long tA = 0, tAp = 0, tD = 0, tC = 0, tP = 0, tQ = 0;
 #pragma unroll
             for (int s = 0; s < E; s++) {
-                mA[s] = mD[s] = mC[s] = mP[s] = 0u;
+                mA[s] = mAp[s] = mD[s] = mC[s] = mP[s] = 0u;
                 incl[s] = tot[s] = 0;
                 if (s >= ns) continue;
-                mA[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_ACCEPT);
+                mA[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_ACCEPT && !ptl[s]);
+                mAp[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_ACCEPT && ptl[s]);
                 mD[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_DEFER);
                 mC[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_PC);
                 mP[s] = __ballot_sync(FMM_FULL_MASK, out[s] == OUT_PP);
@@ -319,12 +327,13 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 incl[s] = v;
                 tot[s] = __shfl_sync(FMM_FULL_MASK, v, 31);
                 tA += __popc(mA[s]);
+                tAp += __popc(mAp[s]);
                 tD += __popc(mD[s]);
                 tC += __popc(mC[s]);
                 tP += __popc(mP[s]);
                 tQ += tot[s];
             }
-            if (na + tA > cap_scr || nd + tD > cap_scr || npc + tC > cap_scr || npp + tP > cap_scr ||
+            if (na + nap + tA + tAp > cap_scr || nd + tD > cap_scr || npc + tC > cap_scr || npp + tP > cap_scr ||
                 nq + tQ > cap_scr) {
                 overflow = true;
                 break;
@@ -332,7 +341,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
 #pragma unroll
             for (int s = 0; s < E; s++) {
                 if (s >= ns) continue;
-                if (out[s] == OUT_ACCEPT) A[na + __popc(mA[s] & lt)] = e[s];
+                if (out[s] == OUT_ACCEPT) {
+                    if (ptl[s]) A[cap_scr - 1 - (nap + __popc(mAp[s] & lt))] = e[s];
+                    else A[na + __popc(mA[s] & lt)] = e[s];
+                }
                 if (out[s] == OUT_DEFER) D[nd + __popc(mD[s] & lt)] = e[s];
                 if (out[s] == OUT_PC) C[npc + __popc(mC[s] & lt)] = e[s];
                 if (out[s] == OUT_PP) {
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                 if (out[s] == OUT_OPEN) {
                     // the children, or a leaf's particles, stay in the source's copy
                     const long long pos = nq + incl[s] - nadd[s];
-                    const unsigned int qb = entry_copy(e[s], pa.ib) << pa.ib;
+                    const unsigned int qb = PER ? entry_copy(e[s], ib) << ib : 0u;
                     if (sleaf[s]) {
                         for (int j = 0; j < nadd[s]; j++)
                             Q[pos + j] = ((unsigned int)(sfirst[s] + j) | qb) | FMM_PARTICLE_BIT;
@@ -352,6 +364,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
                     }
                 }
                 na += __popc(mA[s]);
+                nap += __popc(mAp[s]);
                 nd += __popc(mD[s]);
                 npc += __popc(mC[s]);
                 npp += __popc(mP[s]);
@@ -402,16 +415,15 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
             if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
         }
-        if (lane == 0) {
-            atomicAdd(&ctr->lv_entries[level], (unsigned long long)(ncl + nq));
-            atomicMax(&ctr->lv_max_entries[level], (unsigned long long)(ncl + nq));
-        }
-        __syncwarp();
-        // local-expansion entries of this sink
-        unsigned long long off = 0;
-        if (lane == 0) off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
-        off = __shfl_sync(FMM_FULL_MASK, off, 0);
-        if ((long long)(off + na) > cap_cc) {
+        w_entries += (unsigned long long)(ncl + nq);
+        w_max = max(w_max, (unsigned long long)(ncl + nq));
+        // local-expansion entries of this sink: multipole sources (M2L) and point sources (P2L) in
+        // two lists, each in queue order
+        unsigned long long lo = 0;
+        if (lane == 0 && (na | nap)) lo = atomicAdd(&ctr->loc_len, (unsigned long long)na | ((unsigned long long)nap << 32));
+        lo = __shfl_sync(FMM_FULL_MASK, lo, 0);
+        const unsigned long long off = fmm_lo32(lo), offp = fmm_hi32(lo);
+        if ((long long)(off + na) > cap_cc || (long long)(offp + nap) > cap_cp) {
             if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
         }
@@ -419,18 +431,24 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
             cc[off + i] = A[i];
             cc_sink[off + i] = k;
         }
+        for (long long i = lane; i < nap; i += 32) {
+            cp[offp + i] = A[cap_scr - 1 - i];
+            cp_sink[offp + i] = k;
+        }
         if (lane == 0) {
             lcc_off[k] = off;
             lcc_len[k] = (int)na;
-            if (na > 0) lcells[atomicAdd(&ctr->n_lcells, 1ull)] = k;
+            lcp_off[k] = offp;
+            lcp_len[k] = (int)nap;
         }
         if (kg) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) srcpp += __shfl_xor_sync(FMM_FULL_MASK, srcpp, o);
             unsigned long long po = 0, co = 0, gi = 0;
             if (lane == 0) {
-                po = atomicAdd(&ctr->pp_len, (unsigned long long)npp);
-                co = atomicAdd(&ctr->pc_len, (unsigned long long)npc);
+                const unsigned long long so = atomicAdd(&ctr->src_len, (unsigned long long)npp | ((unsigned long long)npc << 32));
+                po = fmm_lo32(so);
+                co = fmm_hi32(so);
                 gi = atomicAdd(&ctr->n_groups, 1ull);
             }
             po = __shfl_sync(FMM_FULL_MASK, po, 0);
@@ -479,6 +497,10 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         }
     }
     if (MODE == 1 && lane == 0 && n_mlp) atomicAdd(&ctr->n_mlp, n_mlp);
+    if (lane == 0 && w_entries) {
+        atomicAdd(&ctr->lv_entries[level], w_entries);
+        atomicMax(&ctr->lv_max_entries[level], w_max);
+    }
 }
 
 #define LOCAL_WPB 2
@@ -496,11 +518,12 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
 // Centres enter as float pairs (cen_diff): the sink's (hk, lk), a cell's from cen, a particle's
 // from posf (hi, and its mass) and plo (lo); a source in a periodic copy has its pair shifted
 // (cen_shift) by the copy's integer offset.
+// KIND 0: a cell of several particles (M2L); KIND 1: a particle, or a cell of one (P2L).
+template <int KIND>
 __device__ __forceinline__ void local_entry(unsigned int e, const float4& hk, const float4& lk,
-                                            const int* __restrict__ ccount, const float4* __restrict__ cen,
+                                            const float4* __restrict__ cen,
                                             const float4* __restrict__ posf, const float4* __restrict__ plo,
-                                            const float* __restrict__ rec, float eps2, int ib, int R, float* acc,
-                                            int& ncc, int& ncp)
+                                            const float* __restrict__ rec, float eps2, int ib, int R, float* acc)
 {
     const unsigned int j = entry_index(e, ib);
     const unsigned int q = entry_copy(e, ib);
@@ -522,12 +545,9 @@ __device__ __forceinline__ void local_entry(unsigned int e, const float4& hk, co
     }
     const float rx = cen_diff(hk.x, lk.x, hs.x, ls.x), ry = cen_diff(hk.y, lk.y, hs.y, ls.y),
                 rz = cen_diff(hk.z, lk.z, hs.z, ls.z);
-    if (e & FMM_PARTICLE_BIT) {
-        fmm_p2l_acc(hs.w, rx, ry, rz, eps2, acc);
-        ncp++;
-    } else if (ccount[j] == 1) {  // a one-particle cell: its particle (mass = moment M[0]) -> local expansion
-        fmm_p2l_acc(rec[(long long)j * FMM_NREC], rx, ry, rz, eps2, acc);
-        ncp++;
+    if (KIND == 1) {
+        // a one-particle cell: its particle (mass = moment M[0]) -> local expansion
+        fmm_p2l_acc((e & FMM_PARTICLE_BIT) ? hs.w : rec[(long long)j * FMM_NREC], rx, ry, rz, eps2, acc);
     } else {
         float M[FMM_NMOM];
         const float4* r4 = reinterpret_cast<const float4*>(rec + (long long)j * FMM_NREC);
@@ -540,7 +560,6 @@ __device__ __forceinline__ void local_entry(unsigned int e, const float4& hk, co
             M[4 * q4 + 3] = v.w;
         }
         fmm_m2l_acc(M, rx, ry, rz, eps2, acc);
-        ncc++;
     }
 }
 
@@ -555,9 +574,13 @@ __device__ __forceinline__ long long local_boundary(long long p, long long total
     return f == p ? p : f + lcc_len[k];
 }
 
+// Two launches, one per list: KIND 0 the multipole sources (M2L), which write each sink's sum;
+// KIND 1 the point sources (P2L), which add theirs to it (or write it, for a sink with no
+// multipole source).  Every warp of a launch runs one kind of interaction.
+template <int KIND>
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
-    const int* __restrict__ lcc_len, const int* __restrict__ ccount, const float4* __restrict__ cen,
+    const int* __restrict__ lcc_len, const int* __restrict__ lm2l_len, const float4* __restrict__ cen,
     const float4* __restrict__ posf, const float4* __restrict__ plo,
     const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
     float eps2, int ib, int R, DevCounters* __restrict__ ctr)
@@ -567,10 +590,11 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (fmm_overflowed(ctr)) return;
-    const long long total = min((long long)*(volatile unsigned long long*)&ctr->cc_len, cap_cc);
+    const unsigned long long ll = *(volatile unsigned long long*)&ctr->loc_len;
+    const long long total = min((long long)(KIND == 0 ? fmm_lo32(ll) : fmm_hi32(ll)), cap_cc);
     const long long nranges = fmm_ceil_div(total, LF_ENTRIES);
     const int c0 = lane, c1 = lane + 32;  // this lane's coefficients in the reduction
-    int ncc = 0, ncp = 0;
+    int nent = 0;
     for (long long r = gw; r < nranges; r += nw) {
         const long long r0 = local_boundary(r * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
         const long long r1 = local_boundary((r + 1) * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
@@ -585,8 +609,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
             for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
             if (valid) {
                 sink = cc_sink[idx];
-                local_entry(cc[idx], cen[2 * sink], cen[2 * sink + 1], ccount, cen, posf, plo, rec, eps2, ib, R, acc,
-                            ncc, ncp);
+                local_entry<KIND>(cc[idx], cen[2 * sink], cen[2 * sink + 1], cen, posf, plo, rec, eps2, ib, R, acc);
+                nent++;
             }
 #pragma unroll
             for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
@@ -614,6 +638,10 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
                     continue;
                 }
                 float* dst = Lown + (long long)s_sink * FMM_NL;
+                if (KIND == 1 && lm2l_len[s_sink] > 0) {
+                    sum0 = dst[c0] + sum0;
+                    if (c1 < FMM_NL) sum1 = dst[c1] + sum1;
+                }
                 dst[c0] = sum0;
                 if (c1 < FMM_NL) dst[c1] = sum1;
             }
@@ -621,14 +649,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ncc += __shfl_xor_sync(FMM_FULL_MASK, ncc, o);
-        ncp += __shfl_xor_sync(FMM_FULL_MASK, ncp, o);
-    }
-    if (lane == 0) {
-        if (ncc) atomicAdd(&ctr->n_cc, (unsigned long long)ncc);
-        if (ncp) atomicAdd(&ctr->n_cp, (unsigned long long)ncp);
-    }
+    for (int o = 16; o > 0; o >>= 1) nent += __shfl_xor_sync(FMM_FULL_MASK, nent, o);
+    if (lane == 0 && nent) atomicAdd(KIND == 0 ? &ctr->n_cc : &ctr->n_cp, (unsigned long long)nent);
 }
 
 // Local expansion of each group about its centre of mass: the own expansions of the group and
@@ -638,7 +660,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
 #define LG_MAX_ANC FMM_MAX_LEVELS
 __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
     const Group* __restrict__ groups, const int* __restrict__ cparent, const int* __restrict__ lcc_len,
-    const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg, long long cap_groups,
+    const int* __restrict__ lcp_len, const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg, long long cap_groups,
     DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
@@ -653,7 +675,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
         int na = 0;
         if (lane == 0) {
             for (int a = g; a >= 0 && na < LG_MAX_ANC; a = cparent[a])
-                if (lcc_len[a] > 0) anc[wl][na++] = a;
+                if (lcc_len[a] > 0 || lcp_len[a] > 0) anc[wl][na++] = a;
         }
         na = __shfl_sync(FMM_FULL_MASK, na, 0);
         __syncwarp();
@@ -779,7 +801,7 @@ int fmm_walk_warps(int device)
 {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return sms * 24;  // 6 resident blocks of 4 warps per SM
+    return sms * 24;  // warps per SM of the walk and local-expansion grids (measured better than 20 or 16)
 }
 
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s)
@@ -789,20 +811,24 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     const int blocks = w.n_warps / WALK_WPB;
 #define WALK_ARGS                                                                                                   \
     t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],      \
-        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcells, w.pp,     \
-        w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
+        w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcp_off,          \
+        w.lcp_len, w.pp, w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.cp, w.cp_sink, w.cap_cp, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
         a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.margin, a.mlp_packed, a.audit_pairs, \
         a.audit_cap, t.graded ? t.nogroup : nullptr, periodic_args(t)
+    // the learned and audit walks take isolated boxes only (the host refuses the combinations)
+    if (a.mode != 0 && t.per_R > 0) return cudaErrorInvalidValue;
     if (a.mode == 1) {
         const size_t smem = MLPP_SIZE + (size_t)WALK_WPB * (MLP_WARP_SCRATCH + WALK_PEND_BYTES);
         static std::atomic<unsigned long long> attr{0};
-        cudaError_t e = fmm_smem_attr_once(k_walk_level<1>, (int)smem, attr);
+        cudaError_t e = fmm_smem_attr_once(k_walk_level<1, false>, (int)smem, attr);
         if (e != cudaSuccess) return e;
-        k_walk_level<1><<<blocks, WALK_THREADS, smem, s>>>(WALK_ARGS);
+        k_walk_level<1, false><<<blocks, WALK_THREADS, smem, s>>>(WALK_ARGS);
     } else if (a.mode == 2) {
-        k_walk_level<2><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
+        k_walk_level<2, false><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
+    } else if (t.per_R > 0) {
+        k_walk_level<0, true><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
     } else {
-        k_walk_level<0><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
+        k_walk_level<0, false><<<blocks, WALK_THREADS, 0, s>>>(WALK_ARGS);
     }
 #undef WALK_ARGS
     return cudaGetLastError();
@@ -811,9 +837,11 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
 cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s)
 {
     const int blocks = w.n_warps / LOCAL_WPB;
-    k_local_flat<<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, t.ccount, t.cen, t.posf,
-                                                   t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
-    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, t.com, t.L, w.Lg, w.cap_groups,
-                                                     ctr);
+    k_local_flat<0><<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, w.lcc_len, t.cen, t.posf,
+                                                      t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
+    k_local_flat<1><<<blocks, LOCAL_THREADS, 0, s>>>(w.cp, w.cp_sink, w.lcp_off, w.lcp_len, w.lcc_len, t.cen, t.posf,
+                                                      t.plo, t.rec, t.L, w.cap_cp, eps2, t.per_ib, t.per_R, ctr);
+    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, w.lcp_len, t.com, t.L, w.Lg,
+                                                     w.cap_groups, ctr);
     return cudaGetLastError();
 }
