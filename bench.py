@@ -55,8 +55,29 @@ PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul,
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), not measured by this run.  Reported,
 # labelled as stored, only for runs with those settings; set back to None whenever a kernel
 # changes after that capture.
-NCU_TRAFFIC = {"k_pc": 255633664, "k_pp": 121505280}
+NCU_TRAFFIC = {"k_pc": 202016000 + 53694208, "k_pp": 94603776 + 24113152}
 NCU_TRAFFIC_PARAMS = (16, 64, 128)
+
+# Algorithmic DRAM bytes of the tree phase (keys, radix sort, gather, radix tree, cells, upward
+# pass, exact b_max, walk nodes), the reads and writes a streaming implementation cannot avoid:
+# per particle keys 40 (positions and mass in, key and index out), 8 sort passes of 24 (key and
+# index in and out), gather 89 (positions and mass in; sorted FP64 positions, mass, active flag and
+# the FP32 pairs out), radix tree 40 (keys in, nodes out), bucket flags 4, upward 44 (sorted
+# positions and mass in, FP32 offsets out), b_max 16 (FP32 positions in); per cell 500: the cell
+# arrays 20, the upward pass's centre, box, b_max, active count and 44-float record (268), and the
+# walk node, centre pair and multipole norms with their inputs (212).
+TREE_BYTES_PER_PARTICLE = 40 + 8 * 24 + 89 + 40 + 4 + 44 + 16
+TREE_BYTES_PER_CELL = 20 + 268 + 212
+
+
+def measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json at the repository root (written by the harness that
+    measured the GB300s), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
 
 
 def parse():
@@ -75,6 +96,9 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="solve eagerly instead of replaying a CUDA graph")
     ap.add_argument("--params", default=None, help="bucket,group,list_chunk instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--levels", action="store_true",
+                    help="add the walk's counts per level of the last timed solve (sinks, checklist entries, "
+                         "largest of one sink)")
     ap.add_argument("--cpu-sample", type=float, default=None, help="active fraction of the CPU sample")
     ap.add_argument("--dual", type=int, default=None,
                     help="rungs16m: fixed rung of the dual-tree scheme (rungs <= it form the fixed tree)")
@@ -910,7 +934,16 @@ def main():
             if pp_ms + pc_ms > 0 else 0.0}
     roof["traffic_source"] = ("stored from an earlier ncu capture of this kernel and these settings, not measured "
                               "in this run" if roof["traffic"] is not None else
-                              "no ncu capture of this kernel at these settings")
+                              "no ncu capture of the current kernel at these settings")
+    # the tree phase against the HBM roofline (algorithmic bytes; CUDA events of the phase)
+    hbm, hbm_src = measured_peak("hbm_gbs", 6800.0)
+    tree_ms = kt["tree"] / args.steps
+    n_tree = int(wl.config.get("n", 0) or 0)
+    tree_bytes = TREE_BYTES_PER_PARTICLE * n_tree + TREE_BYTES_PER_CELL * int(st["n_cells"])
+    tree_gbs = tree_bytes / (tree_ms * 1e-3) / 1e9 if tree_ms > 0 else 0.0
+    tree_hbm = {"bound": "hbm", "bytes": tree_bytes, "ms": tree_ms, "achieved": tree_gbs, "peak": hbm,
+                "unit": "GB/s", "frac": tree_gbs / hbm, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_particle": TREE_BYTES_PER_PARTICLE, "bytes_per_cell": TREE_BYTES_PER_CELL}
     line = {"metric": "interactions/s (PP + PC) per force solve", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -918,8 +951,11 @@ def main():
             "phase_ms": {k: v / args.steps for k, v in kt.items()},
             "interactions_per_step": inter_job, "n_pp_pairs": st["n_pp_pairs"], "n_pc_pairs": st["n_pc_pairs"],
             "n_cc": st["n_cc"], "n_cp": st["n_cp"], "n_groups": st["n_groups"], "n_levels": st["n_levels"],
-            "active_per_step": float(np.mean(active)), "walk_retries": retries, "roofline": roof, "clocks": ck,
+            "active_per_step": float(np.mean(active)), "walk_retries": retries, "roofline": roof,
+            "tree_hbm": tree_hbm, "tree_hbm_frac": tree_hbm["frac"], "clocks": ck,
             "gpu_launches": launches}
+    if args.levels:
+        line["walk_levels"] = [[int(v) for v in row] for row in ctx.export_walk_levels()]
     if hasattr(wl, "learned"):
         line["learned"] = wl.learned
     if not args.no_e2e:

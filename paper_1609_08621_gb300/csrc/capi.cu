@@ -247,10 +247,10 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
     const DevTree& t = c->t;
     const DevWalk& w = c->w;
     const FixedTree& f = c->fx;
-    return {t.key, t.key_alt, t.idx, t.idx_alt, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
+    return {t.key, t.key_alt, t.idx, t.idx_alt, t.src, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
             t.bucket_of, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
             t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
-            t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.L, t.scan_part,
+            t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.bm_order, t.bm_bin, t.bm_binbase, t.L, t.scan_part,
             t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
             w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
             w.lcp_off, w.lcp_len, w.cp, w.cp_sink, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
@@ -375,6 +375,9 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.key_alt, cap));
         CK(alloc(&t.idx, cap));
         CK(alloc(&t.idx_alt, cap));
+        CK(alloc(&t.src, cap));
+        CK(alloc(&t.bm_bin, fmm_bmax_bins(cap)));
+        CK(alloc(&t.bm_binbase, fmm_bmax_bins(cap)));
         CK(alloc(&t.sx, cap));
         CK(alloc(&t.sy, cap));
         CK(alloc(&t.sz, cap));
@@ -515,7 +518,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
     if (st != FMM_OK) return st;
     c->have_tree = false;
     CK(clear_counters(c, s));
-    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s, c->cur_ipos));
+    CK(fmm_launch_keys(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
     if (nbox > 1) {
         CK(fmm_launch_box_sort(t, n, s));
         c->launches += 8 * 5 + 1 + 2 * 5 + 1;
@@ -523,7 +526,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
         CK(fmm_radix_sort(t, n, s));
         c->launches += 8 * 5;
     }
-    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
+    CK(fmm_launch_gather(t, n, c->ctr, s));
     CK(fmm_launch_radix_tree(t, n, bucket, s));
     CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
     // the cell count, then cell arrays for it (a small margin lets graph replays of a slowly
@@ -557,6 +560,7 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
             t.cap_bm_items = 0;
             CK(alloc(&t.bm_item, need));
             CK(alloc(&t.bm_imax, need));
+            CK(alloc(&t.bm_order, need));
             t.cap_bm_items = need;
         }
     }
@@ -566,8 +570,8 @@ static fmm_status build_tree(fmm_ctx* c, const double* pos, const float* mass, c
         c->launches += 1;
     }
     // keys, gather, radix tree + keep, scan, cells, scan, bucket index, depth, bucket cells,
-    // upward, exact b_max (count, scan, expand, two passes, final)
-    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 8;
+    // upward, exact b_max (count, scan, expand, item order: count, scan, place; two passes, final)
+    c->launches += 1 + 1 + (n > 1 ? 2 : 1) + 3 + 1 + 3 + 1 + 1 + 2 + 13;
     t.depth = (int)c->ctr_h->depth;
     t.graded = t.grade_key != nullptr && n > 1;
     c->have_tree = true;
@@ -964,7 +968,7 @@ static fmm_status enqueue_graph_head(fmm_ctx* c, const double* pos, const float*
     st = set_periodic(c, q, n, nbox);
     if (st != FMM_OK) return st;
     CK(clear_counters(c, s));
-    CK(fmm_launch_keys(t, pos, mass, n, c->ctr, s, c->cur_ipos));
+    CK(fmm_launch_keys(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
     if (nbox > 1) {
         CK(fmm_launch_box_sort(t, n, s));
         c->launches += 8 * 5 + 1 + 2 * 5 + 1;
@@ -972,7 +976,7 @@ static fmm_status enqueue_graph_head(fmm_ctx* c, const double* pos, const float*
         CK(fmm_radix_sort(t, n, s));
         c->launches += 8 * 5;
     }
-    CK(fmm_launch_gather(t, pos, mass, active, n, c->ctr, s, c->cur_ipos));
+    CK(fmm_launch_gather(t, n, c->ctr, s));
     CK(fmm_launch_radix_tree(t, n, q.bucket, s));
     CK(fmm_scan_exclusive(t.keep, t.keep, 2 * n - 1, c->totals, t, s));
     CK(cudaMemcpyAsync(c->totals_h, c->totals, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
@@ -1000,7 +1004,7 @@ static fmm_status enqueue_graph_rest(fmm_ctx* c, long long n, const fmm_params& 
         CK(fmm_launch_box_roots(t, s));
         c->launches += 1;
     }
-    c->launches += 1 + 3 + 1 + 1 + 2 + 8;
+    c->launches += 1 + 3 + 1 + 1 + 2 + 13;
     CK(fmm_launch_nodes(t, q.theta, s));
     c->launches += 1;
     if (t.per_R > 0) {

@@ -159,6 +159,14 @@ __device__ __forceinline__ bool fmm_overflowed(const DevCounters* ctr)
 __host__ __device__ __forceinline__ unsigned long long fmm_lo32(unsigned long long v) { return v & 0xffffffffull; }
 __host__ __device__ __forceinline__ unsigned long long fmm_hi32(unsigned long long v) { return v >> 32; }
 
+// One particle of the input as the key kernel copies it, in input order, for the gather after
+// the sort: a single aligned 32-byte sector per particle instead of one per coordinate.
+struct __align__(32) SrcRec {
+    double x, y, z;
+    float m;
+    unsigned int act;
+};
+
 // Device buffers of a context.  Capacities are in elements.
 struct DevTree {
     long long n = 0, cap_n = 0;
@@ -174,11 +182,14 @@ struct DevTree {
     unsigned int *bm_cnt = nullptr, *bm_base = nullptr, *bm32 = nullptr;
     unsigned long long* bm64 = nullptr;
     int* bm_item = nullptr;
+    unsigned int* bm_order = nullptr;  // the items by the particle they start at
+    unsigned int *bm_bin = nullptr, *bm_binbase = nullptr;  // items per chunk of particles, and their scan
     float* bm_imax = nullptr;  // FP32 maximum of each item
     long long cap_bm_items = 0;
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;
     unsigned int *idx = nullptr, *idx_alt = nullptr;
+    SrcRec *src = nullptr;  // the input particles in input order (key kernel to gather)
     // sorted particles
     double *sx = nullptr, *sy = nullptr, *sz = nullptr;
     float *sm = nullptr;
@@ -316,15 +327,16 @@ cudaError_t fmm_radix_sort_kv_scratch(unsigned long long* ka, unsigned long long
 
 // tree.cu
 // positions: pos (FP64 SoA) or, when ipos is given, 32-bit fixed-point coordinates x = u 2^-32
-cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
+cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
+                            long long n, DevCounters* ctr,
                             cudaStream_t s, const unsigned int* ipos = nullptr);
-cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
-                              long long n, DevCounters* ctr, cudaStream_t s, const unsigned int* ipos = nullptr);
+cudaError_t fmm_launch_gather(DevTree& t, long long n, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_bucket_index(DevTree& t, long long n, cudaStream_t s);
 cudaError_t fmm_launch_radix_tree(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_cells(DevTree& t, long long n, int bucket, cudaStream_t s);
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s);
 long long fmm_bmax_items_bound(long long n, int depth, long long n_cells);
+long long fmm_bmax_bins(long long n);
 cudaError_t fmm_launch_nodes(DevTree& t, double theta, cudaStream_t s);
 cudaError_t fmm_launch_depth(DevTree& t, const unsigned int* ncell_dev, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_box_sort(DevTree& t, long long n, cudaStream_t s);

@@ -37,13 +37,21 @@ __device__ __forceinline__ double pos_at(const double* __restrict__ pos, const u
 }
 
 __global__ void k_keys(const double* __restrict__ pos, const unsigned int* __restrict__ ipos,
-                       const float* __restrict__ mass, long long n, unsigned long long* __restrict__ key,
-                       unsigned int* __restrict__ idx, unsigned int* __restrict__ status)
+                       const float* __restrict__ mass, const unsigned char* __restrict__ active, long long n,
+                       unsigned long long* __restrict__ key, unsigned int* __restrict__ idx,
+                       SrcRec* __restrict__ src, unsigned int* __restrict__ status)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double x = pos_at(pos, ipos, n, 0, i), y = pos_at(pos, ipos, n, 1, i), z = pos_at(pos, ipos, n, 2, i);
     float m = mass[i];
+    SrcRec r;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+    r.m = m;
+    r.act = active ? (active[i] != 0 ? 1u : 0u) : 1u;
+    src[i] = r;
     bool ok = (x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0 && m > 0.0f && isfinite(m));
     if (!ok) atomicOr(status, FMM_DEV_ERR_ARG);
     // axis x owns the highest bit of each level triple: key bit 62 - l for level l
@@ -51,16 +59,15 @@ __global__ void k_keys(const double* __restrict__ pos, const unsigned int* __res
     idx[i] = (unsigned int)i;
 }
 
-cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, long long n, DevCounters* ctr,
-                            cudaStream_t s, const unsigned int* ipos)
+cudaError_t fmm_launch_keys(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
+                            long long n, DevCounters* ctr, cudaStream_t s, const unsigned int* ipos)
 {
-    k_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, ipos, mass, n, t.key, t.idx, &ctr->status);
+    k_keys<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, ipos, mass, active, n, t.key, t.idx, t.src,
+                                                         &ctr->status);
     return cudaGetLastError();
 }
 
-__global__ void k_gather(const double* __restrict__ pos, const unsigned int* __restrict__ ipos,
-                         const float* __restrict__ mass, const unsigned char* __restrict__ active, long long n,
-                         const unsigned int* __restrict__ idx,
+__global__ void k_gather(const SrcRec* __restrict__ src, long long n, const unsigned int* __restrict__ idx,
                          double* __restrict__ sx, double* __restrict__ sy, double* __restrict__ sz,
                          float* __restrict__ sm, unsigned char* __restrict__ sact, float4* __restrict__ posf,
                          float4* __restrict__ plo, unsigned long long* __restrict__ n_active)
@@ -68,14 +75,14 @@ __global__ void k_gather(const double* __restrict__ pos, const unsigned int* __r
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
     if (i < n) {
-        unsigned int p = idx[i];
-        double x = pos_at(pos, ipos, n, 0, p), y = pos_at(pos, ipos, n, 1, p), z = pos_at(pos, ipos, n, 2, p);
+        const SrcRec r = src[idx[i]];
+        const double x = r.x, y = r.y, z = r.z;
         sx[i] = x;
         sy[i] = y;
         sz[i] = z;
-        float m = mass[p];
+        const float m = r.m;
         sm[i] = m;
-        act = active ? (active[p] != 0) : true;
+        act = r.act != 0u;
         sact[i] = act ? 1 : 0;
         const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
         posf[i] = make_float4(hx, hy, hz, m);
@@ -86,11 +93,10 @@ __global__ void k_gather(const double* __restrict__ pos, const unsigned int* __r
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, (unsigned long long)__popc(b));
 }
 
-cudaError_t fmm_launch_gather(DevTree& t, const double* pos, const float* mass, const unsigned char* active,
-                              long long n, DevCounters* ctr, cudaStream_t s, const unsigned int* ipos)
+cudaError_t fmm_launch_gather(DevTree& t, long long n, DevCounters* ctr, cudaStream_t s)
 {
-    k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(pos, ipos, mass, active, n, t.idx, t.sx, t.sy, t.sz, t.sm,
-                                                           t.sact, t.posf, t.plo, &ctr->n_active);
+    k_gather<<<(unsigned)fmm_ceil_div(n, TB), TB, 0, s>>>(t.src, n, t.idx, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf,
+                                                           t.plo, &ctr->n_active);
     return cudaGetLastError();
 }
 
@@ -436,6 +442,41 @@ long long fmm_bmax_items_bound(long long n, int depth, long long n_cells)
     return fmm_ceil_div(n * (long long)(depth + 1), BM_CHUNK) + n_cells + 1;
 }
 
+// The passes take the items ordered by the particle they start at (counted per BM_CHUNK particles,
+// then placed): the warps in flight then read the same particles for the cells of every level
+// around them, from L2, instead of streaming all particles once per level.  Every item keeps its
+// index (its FP32 maximum is stored under it), and the maxima are order-independent.
+long long fmm_bmax_bins(long long n) { return fmm_ceil_div(n, BM_CHUNK) + 1; }
+
+__device__ __forceinline__ unsigned int bm_bin_of(long long i, const int* __restrict__ item,
+                                                  const unsigned int* __restrict__ ncell,
+                                                  const unsigned int* __restrict__ base, const int* __restrict__ cfirst)
+{
+    const int c = item[i];
+    if (c < 0 || c >= (int)*ncell) return 0u;  // an item the expansion could not write: skipped by the passes
+    const long long k = i - (long long)base[c];
+    return (unsigned int)(((long long)cfirst[c] + k * BM_CHUNK) / BM_CHUNK);
+}
+
+__global__ void k_bm_bin_count(const int* __restrict__ item, const unsigned int* __restrict__ n_items, long long cap,
+                               const unsigned int* __restrict__ ncell, const unsigned int* __restrict__ base,
+                               const int* __restrict__ cfirst, unsigned int* __restrict__ bin)
+{
+    const long long ni = min((long long)*n_items, cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(bin + bm_bin_of(i, item, ncell, base, cfirst), 1u);
+}
+
+__global__ void k_bm_place(const int* __restrict__ item, const unsigned int* __restrict__ n_items, long long cap,
+                           const unsigned int* __restrict__ ncell, const unsigned int* __restrict__ base,
+                           const int* __restrict__ cfirst, unsigned int* __restrict__ cursor,
+                           unsigned int* __restrict__ order)
+{
+    const long long ni = min((long long)*n_items, cap);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += (long long)gridDim.x * blockDim.x)
+        order[atomicAdd(cursor + bm_bin_of(i, item, ncell, base, cfirst), 1u)] = (unsigned int)i;
+}
+
 __global__ void k_bm_count(const unsigned int* __restrict__ ncell, long long grid, const int* __restrict__ ccount,
                            const int* __restrict__ cchild, unsigned int* __restrict__ cnt, unsigned int* __restrict__ bm32,
                            unsigned long long* __restrict__ bm64)
@@ -462,10 +503,15 @@ __global__ void k_bm_expand(long long grid, const unsigned int* __restrict__ cnt
     for (long long i = 0; i < k; i++) item[b + i] = (int)c;
 }
 
+// the FP32 squared distance, in a fixed order of roundings, and the distance
+__device__ __forceinline__ float bm_d2_32(const float4 v, float px, float py, float pz)
+{
+    const float dx = __fsub_rn(v.x, px), dy = __fsub_rn(v.y, py), dz = __fsub_rn(v.z, pz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
 __device__ __forceinline__ float bm_d32(const float4 v, float px, float py, float pz)
 {
-    const float dx = v.x - px, dy = v.y - py, dz = v.z - pz;
-    return sqrtf(dx * dx + dy * dy + dz * dz);
+    return sqrtf(bm_d2_32(v, px, py, pz));
 }
 
 // the largest FP64 squared distance from p among the particles [j0, j1) whose FP32 distance
@@ -493,7 +539,8 @@ __device__ __forceinline__ float bm_threshold(float top) { return top - (4e-7f +
 // a cell of several items records the item's maximum and raises the cell's.  PASS 2: the items of
 // multi-item cells whose maximum reaches the cell's threshold look for FP64 candidates.
 template <int PASS>
-__global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, const unsigned int* __restrict__ n_items,
+__global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict__ order,
+                                                 const int* __restrict__ item, const unsigned int* __restrict__ n_items,
                                                  long long cap, const unsigned int* __restrict__ ncell,
                                                  const unsigned int* __restrict__ cnt, const unsigned int* __restrict__ base,
                                                  const int* __restrict__ cfirst, const int* __restrict__ ccount,
@@ -506,7 +553,8 @@ __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, c
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long ni = min((long long)*n_items, cap);
-    for (long long i = gw; i < ni; i += nw) {
+    for (long long ii = gw; ii < ni; ii += nw) {
+        const long long i = order[ii];
         // an item the expansion could not write (capacity overflow, reported to the host) is skipped
         const int c = item[i];
         if (c < 0 || c >= (int)*ncell) continue;
@@ -519,10 +567,13 @@ __global__ void __launch_bounds__(256) k_bm_pass(const int* __restrict__ item, c
         const Com4 p = com[c];
         const float px = __double2float_rn(p.x), py = __double2float_rn(p.y), pz = __double2float_rn(p.z);
         if (PASS == 1) {
-            float m = 0.0f;
-            for (long long j = j0 + lane; j < j1; j += 32) m = fmaxf(m, bm_d32(posf[j], px, py, pz));
+            // the largest FP32 distance, as the square root of the largest square (the same value:
+            // the square root is monotonic and correctly rounded)
+            float m2 = 0.0f;
+            for (long long j = j0 + lane; j < j1; j += 32) m2 = fmaxf(m2, bm_d2_32(posf[j], px, py, pz));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FMM_FULL_MASK, m, o));
+            for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(FMM_FULL_MASK, m2, o));
+            const float m = sqrtf(m2);
             if (nk == 1) {
                 const double best = bm_candidates(j0, j1, p, px, py, pz, bm_threshold(m), posf, sx, sy, sz, lane);
                 if (lane == 0) bm64[c] = (unsigned long long)__double_as_longlong(best);
@@ -565,7 +616,6 @@ static long long grid_buckets(const DevTree& t) { return t.cap_grid ? t.cap_cell
 cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* ctr, cudaStream_t s)
 {
     (void)bucket;
-    (void)n;
     const long long nc = grid_cells(t), nb = grid_buckets(t);
     k_bucket_cells<<<(unsigned)fmm_ceil_div(nc, TB), TB, 0, s>>>(t.cfirst, t.cchild, t.dcount, t.bucket_of,
                                                                  t.bucket_cell);
@@ -580,15 +630,26 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
     cudaError_t e = fmm_scan_exclusive(t.bm_cnt, t.bm_base, nc, &ctr->n_bm_items, t, s);
     if (e != cudaSuccess) return e;
     k_bm_expand<<<gb, TB, 0, s>>>(nc, t.bm_cnt, t.bm_base, t.bm_item, t.cap_bm_items, &ctr->overflow);
+    {
+        const long long nbins = fmm_bmax_bins(n);
+        const unsigned ob = (unsigned)std::max(1LL, std::min(fmm_ceil_div(t.cap_bm_items, TB), 152LL * 32));
+        cudaMemsetAsync(t.bm_bin, 0, sizeof(unsigned int) * (size_t)nbins, s);
+        k_bm_bin_count<<<ob, TB, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_base, t.cfirst,
+                                          t.bm_bin);
+        e = fmm_scan_exclusive(t.bm_bin, t.bm_binbase, nbins, &ctr->pad1, t, s);
+        if (e != cudaSuccess) return e;
+        k_bm_place<<<ob, TB, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_base, t.cfirst,
+                                      t.bm_binbase, t.bm_order);
+    }
     int sms = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long want = fmm_ceil_div(t.cap_bm_items, 8);
     const unsigned pb = (unsigned)std::max(1LL, std::min(want, (long long)sms * 8));
-    k_bm_pass<1><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
+    k_bm_pass<1><<<pb, 256, 0, s>>>(t.bm_order, t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
                                     t.cfirst, t.ccount,
                                     t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64, t.bm_imax);
-    k_bm_pass<2><<<pb, 256, 0, s>>>(t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
+    k_bm_pass<2><<<pb, 256, 0, s>>>(t.bm_order, t.bm_item, &ctr->n_bm_items, t.cap_bm_items, t.dcount, t.bm_cnt, t.bm_base,
                                     t.cfirst, t.ccount,
                                     t.com, t.posf, t.sx, t.sy, t.sz, t.bm32, t.bm64, t.bm_imax);
     k_bm_final<<<gb, TB, 0, s>>>(t.dcount, t.cchild, t.bm64, t.bmax);

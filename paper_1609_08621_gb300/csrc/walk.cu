@@ -577,8 +577,11 @@ __device__ __forceinline__ long long local_boundary(long long p, long long total
 // Two launches, one per list: KIND 0 the multipole sources (M2L), which write each sink's sum;
 // KIND 1 the point sources (P2L), which add theirs to it (or write it, for a sink with no
 // multipole source).  Every warp of a launch runs one kind of interaction.
+#ifndef FMM_LOCAL_MINB
+#define FMM_LOCAL_MINB 1  // resident blocks per SM the M2L pass is compiled for (1: no register limit)
+#endif
 template <int KIND>
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
+__global__ void __launch_bounds__(LOCAL_THREADS, KIND == 0 ? FMM_LOCAL_MINB : 1) k_local_flat(
     const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
     const int* __restrict__ lcc_len, const int* __restrict__ lm2l_len, const float4* __restrict__ cen,
     const float4* __restrict__ posf, const float4* __restrict__ plo,
