@@ -253,7 +253,7 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.bm_order, t.bm_bin, t.bm_binbase, t.L, t.scan_part,
             t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
             w.f_cell[0], w.f_cell[1], w.f_cloff[0], w.f_cloff[1], w.f_cllen[0], w.f_cllen[1], w.lcc_off, w.lcc_len,
-            w.lcp_off, w.lcp_len, w.cp, w.cp_sink, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
+            w.lcp_off, w.lcp_len, w.wcells, w.cp, w.cp_sink, w.Lg, w.cnt_pp, w.cnt_pc, w.base_pp, w.base_pc, w.item_pp, w.item_pc, w.part_pp, w.part_pc,
             w.cl[0], w.cl[1], w.pp, w.pc, w.cc, w.cc_sink, w.groups, w.scratch,
             f.cfirst, f.ccount, f.cchild, f.cparent, f.bucket_cell, f.com, f.clo, f.chi, f.bmax, f.rec, f.posf, f.plo,
             f.off, f.bucket_of, f.key, f.member, c->d_flag, c->d_at, c->d_idx, c->d_perm, c->d_act, c->d_pos, c->d_mass};
@@ -639,6 +639,7 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
         CK(alloc(&w.lcc_len, need_front));
         CK(alloc(&w.lcp_off, need_front));
         CK(alloc(&w.lcp_len, need_front));
+        CK(alloc(&w.wcells, need_front));
         w.cap_front = need_front;
     }
     if (need_groups > w.cap_groups) {
@@ -793,8 +794,8 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
             CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
             c->launches += 1;
         }
-        CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
-        c->launches += 2;
+        CK(fmm_launch_local(t, w, c->ctr, a.eps2, levels, s));
+        c->launches += 3 + levels;
         {
             const fmm_status se = ewald_join(c, c->params.terms);
             if (se != FMM_OK) return se;
@@ -1048,8 +1049,8 @@ static fmm_status enqueue_graph_rest(fmm_ctx* c, long long n, const fmm_params& 
         CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
         c->launches += 1;
     }
-    CK(fmm_launch_local(t, w, c->ctr, a.eps2, s));
-    c->launches += 2;
+    CK(fmm_launch_local(t, w, c->ctr, a.eps2, c->graph_levels, s));
+    c->launches += 3 + c->graph_levels;
     st = ewald_join(c, q.terms);
     if (st != FMM_OK) return st;
     CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));

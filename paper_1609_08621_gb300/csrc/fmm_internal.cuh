@@ -147,6 +147,7 @@ struct DevCounters {
     unsigned long long lv_cl[FMM_MAX_LEVELS];
     unsigned long long lv_entries[FMM_MAX_LEVELS];      // checklist entries examined (incl. opened)
     unsigned long long lv_max_entries[FMM_MAX_LEVELS];  // largest per-sink count
+    unsigned long long lv_base[FMM_MAX_LEVELS + 1];     // first walked cell of each level in DevWalk::wcells
 };
 
 // A walk (or the b_max items before it) that ran past a capacity left holes in the lists: the
@@ -271,6 +272,7 @@ struct DevWalk {
     // (lcp, list cp: particles and one-particle cells)
     unsigned long long *lcc_off = nullptr, *lcp_off = nullptr;
     int *lcc_len = nullptr, *lcp_len = nullptr;
+    int *wcells = nullptr;  // the walked cells in level order (level l at ctr->lv_base[l])
     float *Lg = nullptr;                    // FMM_NL per group: the group's local expansion
     // work items of the interaction kernels: group g's PP list is cut into chunks of list_chunk
     // entries (items base_pp[g] ..), its PC list into chunks of list_chunk cells;
@@ -358,7 +360,7 @@ struct WalkArgs {
     long long audit_cap;
 };
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
-cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s);
+cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int levels, cudaStream_t s);
 cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root = -1);
 cudaError_t fmm_launch_shift_tables(DevTree& t, cudaStream_t s);
 int fmm_walk_warps(int device);

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
     unsigned long long* __restrict__ f_cloff_next, int* __restrict__ f_cllen_next, long long cap_front,
     unsigned int* __restrict__ cl_next, long long cap_cl, unsigned long long* __restrict__ lcc_off,
     int* __restrict__ lcc_len, unsigned long long* __restrict__ lcp_off, int* __restrict__ lcp_len,
+    int* __restrict__ wcells,
     unsigned int* __restrict__ pp, long long cap_pp, unsigned int* __restrict__ pc,
     long long cap_pc, unsigned int* __restrict__ cc, int* __restrict__ cc_sink, long long cap_cc,
     unsigned int* __restrict__ cp, int* __restrict__ cp_sink, long long cap_cp,
@@ -122,6 +123,9 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
     unsigned int* C = Q + 4 * cap_scr;
     const unsigned int lt = fmm_lanemask_lt();
     const unsigned long long n_front = *(volatile unsigned long long*)&ctr->lv_front[level];
+    // this level's sinks go to the walked-cell list after the levels before it
+    const unsigned long long wbase = *(volatile unsigned long long*)&ctr->lv_base[level];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->lv_base[level + 1] = wbase + n_front;
     unsigned long long w_entries = 0, w_max = 0;  // this warp's statistics, added once at the end
 
     for (;;) {
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         fi = __shfl_sync(FMM_FULL_MASK, fi, 0);
         if (fi >= n_front) break;
         const int k = f_cell[fi];
+        if (lane == 0 && (long long)(wbase + fi) < cap_front) wcells[wbase + fi] = k;
         const WalkNode K = node[k];
         // a group holds <= g particles; in a graded tree (dual trees) it is also no larger than the
         // fixed tree's groups around it
@@ -577,11 +582,8 @@ __device__ __forceinline__ long long local_boundary(long long p, long long total
 // Two launches, one per list: KIND 0 the multipole sources (M2L), which write each sink's sum;
 // KIND 1 the point sources (P2L), which add theirs to it (or write it, for a sink with no
 // multipole source).  Every warp of a launch runs one kind of interaction.
-#ifndef FMM_LOCAL_MINB
-#define FMM_LOCAL_MINB 1  // resident blocks per SM the M2L pass is compiled for (1: no register limit)
-#endif
 template <int KIND>
-__global__ void __launch_bounds__(LOCAL_THREADS, KIND == 0 ? FMM_LOCAL_MINB : 1) k_local_flat(
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
     const int* __restrict__ lcc_len, const int* __restrict__ lm2l_len, const float4* __restrict__ cen,
     const float4* __restrict__ posf, const float4* __restrict__ plo,
@@ -656,61 +658,59 @@ __global__ void __launch_bounds__(LOCAL_THREADS, KIND == 0 ? FMM_LOCAL_MINB : 1)
     if (lane == 0 && nent) atomicAdd(KIND == 0 ? &ctr->n_cc : &ctr->n_cp, (unsigned long long)nent);
 }
 
-// Local expansion of each group about its centre of mass: the own expansions of the group and
-// of all its ancestors, each re-expanded (L2L) at the group's centre.  A local expansion is a
-// polynomial of degree 5, so one re-expansion from an ancestor equals the chain of L2L steps
-// down the tree.  One warp per group, lanes take ancestors.
-#define LG_MAX_ANC FMM_MAX_LEVELS
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local_groups(
-    const Group* __restrict__ groups, const int* __restrict__ cparent, const int* __restrict__ lcc_len,
-    const int* __restrict__ lcp_len, const Com4* __restrict__ com, const float* __restrict__ Lown, float* __restrict__ Lg, long long cap_groups,
-    DevCounters* __restrict__ ctr)
+// The local expansion of every walked cell about its centre of mass, top-down one level per
+// launch: L(c) = L2L(L(parent), com(c) - com(parent)) + L_own(c), with L_own the sum of c's own
+// M2L and P2L terms (zero for a cell with empty lists) and a level-0 cell taking its own terms
+// only.  Written in place over L_own.  A local expansion is a polynomial of degree 5, so the chain
+// of re-expansions equals re-expanding every ancestor's own terms to the cell directly.  One
+// thread per cell.
+#define LD_THREADS 128
+__global__ void __launch_bounds__(LD_THREADS) k_local_down(int level, const int* __restrict__ wcells, long long cap,
+                                                          const int* __restrict__ cparent,
+                                                          const int* __restrict__ lcc_len,
+                                                          const int* __restrict__ lcp_len,
+                                                          const Com4* __restrict__ com, float* __restrict__ L,
+                                                          const DevCounters* __restrict__ ctr)
 {
-    __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
-    __shared__ int anc[LOCAL_WPB][LG_MAX_ANC];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (fmm_overflowed(ctr)) return;
-    const long long ng = min((long long)*(volatile unsigned long long*)&ctr->n_groups, cap_groups);
-    for (long long gi = gw; gi < ng; gi += nw) {
-        const int g = groups[gi].cell;
-        int na = 0;
-        if (lane == 0) {
-            for (int a = g; a >= 0 && na < LG_MAX_ANC; a = cparent[a])
-                if (lcc_len[a] > 0 || lcp_len[a] > 0) anc[wl][na++] = a;
-        }
-        na = __shfl_sync(FMM_FULL_MASK, na, 0);
-        __syncwarp();
-        const Com4 cg = com[g];
+    const long long b0 = min((long long)ctr->lv_base[level], cap);
+    const long long b1 = min((long long)ctr->lv_base[level + 1], cap);
+    for (long long i = b0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b1;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = wcells[i];
+        float* Lc = L + (long long)c * FMM_NL;
         float acc[FMM_NL];
+        if (lcc_len[c] > 0 || lcp_len[c] > 0) {
 #pragma unroll
-        for (int i = 0; i < FMM_NL; i++) acc[i] = 0.0f;
-        for (int i = lane; i < na; i += 32) {
-            const int a = anc[wl][i];
-            const float* La = Lown + (long long)a * FMM_NL;
-            if (a == g) {
+            for (int q = 0; q < FMM_NL; q++) acc[q] = Lc[q];
+        } else {
 #pragma unroll
-                for (int q = 0; q < FMM_NL; q++) acc[q] += La[q];
-            } else {
-                const Com4 ca = com[a];
-                float Lo[FMM_NL];
-                fmm_l2l(La, __double2float_rn(cg.x - ca.x), __double2float_rn(cg.y - ca.y),
-                        __double2float_rn(cg.z - ca.z), Lo);
+            for (int q = 0; q < FMM_NL; q++) acc[q] = 0.0f;
+        }
+        if (level > 0) {
+            const int p = cparent[c];
+            const Com4 cc = com[c], cp = com[p];
+            float Lo[FMM_NL];
+            fmm_l2l(L + (long long)p * FMM_NL, __double2float_rn(cc.x - cp.x), __double2float_rn(cc.y - cp.y),
+                    __double2float_rn(cc.z - cp.z), Lo);
 #pragma unroll
-                for (int q = 0; q < FMM_NL; q++) acc[q] += Lo[q];
-            }
+            for (int q = 0; q < FMM_NL; q++) acc[q] = Lo[q] + acc[q];
         }
 #pragma unroll
-        for (int i = 0; i < FMM_NL; i++) red[wl][lane][i] = acc[i];
-        __syncwarp();
-        float* out = Lg + gi * FMM_NL;
-        for (int c = lane; c < FMM_NL; c += 32) {
-            float sum = 0.0f;
-            for (int r = 0; r < 32; r++) sum += red[wl][r][c];
-            out[c] = sum;
-        }
-        __syncwarp();
+        for (int q = 0; q < FMM_NL; q++) Lc[q] = acc[q];
+    }
+}
+
+// Each group's local expansion: its cell's, after the top-down pass.
+__global__ void k_local_groups(const Group* __restrict__ groups, const float* __restrict__ L, float* __restrict__ Lg,
+                               long long cap_groups, const DevCounters* __restrict__ ctr)
+{
+    if (fmm_overflowed(ctr)) return;
+    const long long ng = min((long long)*(volatile const unsigned long long*)&ctr->n_groups, cap_groups);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ng * FMM_NL;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long gi = i / FMM_NL;
+        Lg[i] = L[(long long)groups[gi].cell * FMM_NL + (i - gi * FMM_NL)];
     }
 }
 
@@ -815,7 +815,7 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
 #define WALK_ARGS                                                                                                   \
     t.node, t.posf, t.cnact, w.f_cell[cur], w.f_cloff[cur], w.f_cllen[cur], a.level, w.cl[cur], w.f_cell[nxt],      \
         w.f_cloff[nxt], w.f_cllen[nxt], w.cap_front, w.cl[nxt], w.cap_cl, w.lcc_off, w.lcc_len, w.lcp_off,          \
-        w.lcp_len, w.pp, w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.cp, w.cp_sink, w.cap_cp, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
+        w.lcp_len, w.wcells, w.pp, w.cap_pp, w.pc, w.cap_pc, w.cc, w.cc_sink, w.cap_cc, w.cp, w.cp_sink, w.cap_cp, w.groups, w.cap_groups, w.scratch, w.cap_scratch, ctr, \
         a.bucket, a.group, a.four_eps2, t.mnorm, t.amin, a.eps, a.band_lo, a.band_hi, a.tau, a.margin, a.mlp_packed, a.audit_pairs, \
         a.audit_cap, t.graded ? t.nogroup : nullptr, periodic_args(t)
     // the learned and audit walks take isolated boxes only (the host refuses the combinations)
@@ -837,14 +837,19 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     return cudaGetLastError();
 }
 
-cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, cudaStream_t s)
+cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int levels, cudaStream_t s)
 {
     const int blocks = w.n_warps / LOCAL_WPB;
     k_local_flat<0><<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, w.lcc_len, t.cen, t.posf,
                                                       t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
     k_local_flat<1><<<blocks, LOCAL_THREADS, 0, s>>>(w.cp, w.cp_sink, w.lcp_off, w.lcp_len, w.lcc_len, t.cen, t.posf,
                                                       t.plo, t.rec, t.L, w.cap_cp, eps2, t.per_ib, t.per_R, ctr);
-    k_local_groups<<<blocks, LOCAL_THREADS, 0, s>>>(w.groups, t.cparent, w.lcc_len, w.lcp_len, t.com, t.L, w.Lg,
-                                                     w.cap_groups, ctr);
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int l = 0; l < levels; l++)
+        k_local_down<<<(unsigned)(sms * 8), LD_THREADS, 0, s>>>(l, w.wcells, w.cap_front, t.cparent, w.lcc_len,
+                                                                 w.lcp_len, t.com, t.L, ctr);
+    k_local_groups<<<(unsigned)(sms * 8), 256, 0, s>>>(w.groups, t.L, w.Lg, w.cap_groups, ctr);
     return cudaGetLastError();
 }
