@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="solve eagerly instead of replaying a CUDA graph")
     ap.add_argument("--params", default=None, help="bucket,group,list_chunk instead of autotuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fixed", action="store_true",
+                    help="learned134m: time the fixed-theta solve of the same box only (no training, no judge)")
     ap.add_argument("--levels", action="store_true",
                     help="add the walk's counts per level of the last timed solve (sinks, checklist entries, "
                          "largest of one sink)")
@@ -859,7 +861,12 @@ def main():
     ctx = binding.Context(local, stream)
     kind = {"batch64": Batch, "rungs16m": Rungs, "learned134m": Learned, "periodic2m": Periodic,
             "compressed704": Compressed}.get(args.workload, Box)
+    if args.fixed and args.workload == "learned134m":
+        kind = Box  # the same box and settings, fixed theta only (a profiling aid: no judge, no baseline)
+        args.no_cpu_baseline = True
     wl = kind(args, rank, dev, ctx)
+    if kind is Box and args.workload == "learned134m":
+        wl.config["criterion"] = "fixed theta 0.55 only (--fixed)"
     ctx.set_graphs(not args.no_graphs)
     wl.tuning["cuda_graph"] = not args.no_graphs
 

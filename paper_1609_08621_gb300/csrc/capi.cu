@@ -247,8 +247,8 @@ static std::vector<void*> tree_walk_buffers(const fmm_ctx* c)
     const DevTree& t = c->t;
     const DevWalk& w = c->w;
     const FixedTree& f = c->fx;
-    return {t.key, t.key_alt, t.idx, t.idx_alt, t.src, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
-            t.bucket_of, t.act, t.ifirst, t.ilast, t.ileft, t.iright, t.nparent, t.keep, t.bflag, t.cfirst,
+    return {t.key, t.key_alt, t.idx, t.idx_alt, t.radix, t.sx, t.sy, t.sz, t.sm, t.sact, t.posf, t.plo, t.cen, t.off,
+            t.bucket_of, t.act, t.bflag, t.cfirst,
             t.ccount, t.cparent, t.cchild, t.cnact, t.bucket_cell, t.arrive, t.com, t.clo, t.chi, t.bmax, t.rec,
             t.node, t.mnorm, t.amin, t.bm_cnt, t.bm_base, t.bm32, t.bm64, t.bm_item, t.bm_imax, t.bm_order, t.bm_bin, t.bm_binbase, t.L, t.scan_part,
             t.hist, t.box_off, t.box_root, t.sbox, t.key_orig, t.split, t.nogroup, t.ewald_L, t.cshift, t.pshift,
@@ -375,7 +375,6 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.key_alt, cap));
         CK(alloc(&t.idx, cap));
         CK(alloc(&t.idx_alt, cap));
-        CK(alloc(&t.src, cap));
         CK(alloc(&t.bm_bin, fmm_bmax_bins(cap)));
         CK(alloc(&t.bm_binbase, fmm_bmax_bins(cap)));
         CK(alloc(&t.sx, cap));
@@ -389,12 +388,16 @@ static fmm_status ensure_tree(fmm_ctx* c, long long n, int bucket, int nbox = 1,
         CK(alloc(&t.act, cap));
         CK(alloc(&t.bucket_of, cap));
         CK(alloc(&t.bflag, cap));
-        CK(alloc(&t.ifirst, cap));
-        CK(alloc(&t.ilast, cap));
-        CK(alloc(&t.ileft, cap));
-        CK(alloc(&t.iright, cap));
-        CK(alloc(&t.nparent, 2 * cap));
-        CK(alloc(&t.keep, 2 * cap));
+        // the radix tree's arrays share one block of 32 bytes per particle with the input records,
+        // which the gather reads before the radix tree writes them
+        CK(alloc(&t.radix, 8 * cap));
+        t.ifirst = t.radix;
+        t.ilast = t.radix + cap;
+        t.ileft = t.radix + 2 * cap;
+        t.iright = t.radix + 3 * cap;
+        t.nparent = t.radix + 4 * cap;
+        t.keep = reinterpret_cast<unsigned int*>(t.radix + 6 * cap);
+        t.src = reinterpret_cast<SrcRec*>(t.radix);
         t.cap_n = cap;
     }
     // the cells themselves are sized by build_tree once the tree's cell count is known; callers
@@ -601,33 +604,39 @@ extern "C" fmm_status fmm_build_tree(fmm_ctx* c, const double* pos, const float*
     return build_tree(c, pos, mass, active, n, q->bucket);
 }
 
-static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
+// What a walk asks of its buffers beyond their starting sizes: per list a minimum capacity in
+// entries (0: the starting size), and a factor on the per-warp scratch.
+struct WalkNeed {
+    long long cl = 0, pp = 0, pc = 0, cc = 0, cp = 0, groups = 0;
+    long long scratch_scale = 1;
+};
+
+static fmm_status ensure_walk(fmm_ctx* c, long long n, int group, const WalkNeed& more)
 {
     DevWalk& w = c->w;
     const long long cells = c->t.cap_cells;
     const long long need_front = cells;
-    // Capacities per particle, from the NFW and clustered boxes measured here (per particle:
-    // PP entries 1.8, PC 5.2, local 7.9 (4.4 multipole and 3.4 point sources in the NFW halo), a
-    // level's checklists under 5): checklists 8, PP 3, PC 8, local entries 6 of each kind, and
-    // 8192 scratch entries per warp and list (fmm_debug_walk_capacity may
-    // start them smaller).  Groups: in a plain tree they are one more than the cells with more
-    // than g particles, which no multiple of n / (g + 1) bounds (a chain of such cells may shed a
-    // few particles per level); measured 2.3 n / (g + 1) in a 20000-particle NFW halo and 1.7 in
-    // one of 2^21, so they start at 4 n / (g + 1) (graded trees take the cell count).  A walk that
-    // overflows any of them doubles them all and runs again.
+    // Starting capacities per particle, from the NFW and clustered boxes measured here (per
+    // particle: PP entries 1.8, PC 5.2; local entries 4.4 multipole and 3.4 point sources in the
+    // NFW halo, 7.8 and none in the clustered 512^3 box; a level's checklists under 5):
+    // checklists 8, PP 3, PC 8, local entries 8 multipole and 4 point sources, and 8192 scratch
+    // entries per warp and list (fmm_debug_walk_capacity may start them smaller).  Groups: in a
+    // plain tree they are one more than the cells with more than g particles, which no multiple of
+    // n / (g + 1) bounds (a chain of such cells may shed a few particles per level); measured
+    // 2.3 n / (g + 1) in a 20000-particle NFW halo and 1.7 in one of 2^21, so they start at
+    // 4 n / (g + 1) (graded trees take the cell count).  A walk that overflows asks for what its
+    // counters show it needed (run_walk).
     const long long ls = c->dbg_list_scale > 0 ? c->dbg_list_scale : 8;
     const long long floor = c->dbg_list_scale > 0 ? 4096 : 65536;  // small boxes have longer lists per particle
-    long long need_cl = (long long)scale * (ls * n + floor);
-    long long need_pp = (long long)scale * ((c->dbg_list_scale > 0 ? (ls + 1) / 2 : 3) * n + floor);
-    long long need_pc = (long long)scale * (ls * n + floor);
-    long long need_cc = (long long)scale * ((c->dbg_list_scale > 0 ? ls : 6) * n + floor);
-    long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * scale;
-    long long need_groups = c->t.graded ? cells : (long long)scale * (4 * n / (group + 1) + 64 + 2LL * c->t.nbox);
+    long long need_cl = std::max(ls * n + floor, more.cl);
+    long long need_pp = std::max((c->dbg_list_scale > 0 ? (ls + 1) / 2 : 3) * n + floor, more.pp);
+    long long need_pc = std::max(ls * n + floor, more.pc);
+    long long need_cc = std::max((c->dbg_list_scale > 0 ? ls : 8) * n + floor, more.cc);
+    long long need_cp = std::max((c->dbg_list_scale > 0 ? ls : 4) * n + floor, more.cp);
+    long long need_scr = (c->dbg_scratch > 0 ? c->dbg_scratch : 8192LL) * more.scratch_scale;
+    long long need_groups =
+        std::max(c->t.graded ? cells : 4 * n / (group + 1) + 64 + 2LL * c->t.nbox, more.groups);
     if (need_groups > cells) need_groups = cells;
-    // the device counters hold these lists' lengths in 32 bits
-    if (std::max(need_cc, std::max(need_pp, need_pc)) >= (1LL << 32))
-        return fail(FMM_ERR_OOM, "walk lists of %lld entries exceed the 2^32 the counters hold",
-                    std::max(need_cc, std::max(need_pp, need_pc)));
     if (need_front > w.cap_front) {
         w.cap_front = 0;
         for (int i = 0; i < 2; i++) {
@@ -674,11 +683,11 @@ static fmm_status ensure_walk(fmm_ctx* c, long long n, int scale, int group)
         CK(alloc(&w.cc_sink, need_cc));
         w.cap_cc = need_cc;
     }
-    if (need_cc > w.cap_cp) {
+    if (need_cp > w.cap_cp) {
         w.cap_cp = 0;
-        CK(alloc(&w.cp, need_cc));
-        CK(alloc(&w.cp_sink, need_cc));
-        w.cap_cp = need_cc;
+        CK(alloc(&w.cp, need_cp));
+        CK(alloc(&w.cp_sink, need_cp));
+        w.cap_cp = need_cp;
     }
     if (need_scr > w.cap_scratch) {
         w.cap_scratch = 0;
@@ -777,9 +786,9 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
     // groups sit at most at the deepest cell level: depth + 1 levels, no host round trip between them
     const int levels = t.depth + 1;
     if (levels + 1 > FMM_MAX_LEVELS) return fail(FMM_ERR_STATE, "tree depth %d exceeds the walk's levels", t.depth);
-    int scale = 1;
+    WalkNeed more;
     for (int attempt = 0;; attempt++) {
-        fmm_status st = ensure_walk(c, n, scale, group);
+        fmm_status st = ensure_walk(c, n, group, more);
         if (st != FMM_OK) return st;
         CK(cudaMemsetAsync(&c->ctr->overflow, 0, sizeof(unsigned int), s));
         // cells above a box's root are never walked: their local lists must read as empty
@@ -808,15 +817,37 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
             while (used < levels && c->ctr_h->lv_front[used] > 0) used++;
             w.n_levels = used;
             w.n_groups = (long long)c->ctr_h->n_groups;
-            w.pp_len = (long long)fmm_lo32(c->ctr_h->src_len);
-            w.pc_len = (long long)fmm_hi32(c->ctr_h->src_len);
-            w.cc_len = (long long)fmm_lo32(c->ctr_h->loc_len);
-            w.cp_len = (long long)fmm_hi32(c->ctr_h->loc_len);
+            w.pp_len = (long long)c->ctr_h->pp_len;
+            w.pc_len = (long long)c->ctr_h->pc_len;
+            w.cc_len = (long long)c->ctr_h->cc_len;
+            w.cp_len = (long long)c->ctr_h->cp_len;
             c->stats.retries = attempt;
             return FMM_OK;
         }
         if (attempt >= 8) return fail(FMM_ERR_OOM, "walk lists keep overflowing after %d grows", attempt);
-        scale *= 2;
+        // The list counters kept counting past the capacities: a list that overflowed grows to what
+        // this walk asked of it plus an eighth, and at least doubles (a checklist or scratch
+        // overflow hides the sinks below it, so the next walk may ask for much more); the lists
+        // that fitted keep their size.  An overflow that no counter shows was the per-warp scratch,
+        // which doubles; scratch started below its default size (fmm_debug_walk_capacity) doubles
+        // at every overflow.
+        {
+            const DevCounters& h = *c->ctr_h;
+            bool seen = false;
+            auto grow_to = [&](unsigned long long used, long long cap, long long& need) {
+                if ((long long)used > cap) {
+                    need = std::max(need, std::max((long long)used + (long long)used / 8 + 4096, 2 * cap));
+                    seen = true;
+                }
+            };
+            grow_to(h.pp_len, w.cap_pp, more.pp);
+            grow_to(h.pc_len, w.cap_pc, more.pc);
+            grow_to(h.cc_len, w.cap_cc, more.cc);
+            grow_to(h.cp_len, w.cap_cp, more.cp);
+            grow_to(h.n_groups, w.cap_groups, more.groups);
+            for (int l = 0; l <= levels; l++) grow_to(h.lv_cl[l], w.cap_cl, more.cl);
+            if (!seen || w.cap_scratch < 8192) more.scratch_scale *= 2;
+        }
     }
 }
 
@@ -1201,10 +1232,10 @@ static fmm_status replay_graph(fmm_ctx* c, long long n, int* outcome)
     while (used < c->graph_levels && h.lv_front[used] > 0) used++;
     w.n_levels = used;
     w.n_groups = (long long)h.n_groups;
-    w.pp_len = (long long)fmm_lo32(h.src_len);
-    w.pc_len = (long long)fmm_hi32(h.src_len);
-    w.cc_len = (long long)fmm_lo32(h.loc_len);
-    w.cp_len = (long long)fmm_hi32(h.loc_len);
+    w.pp_len = (long long)h.pp_len;
+    w.pc_len = (long long)h.pc_len;
+    w.cc_len = (long long)h.cc_len;
+    w.cp_len = (long long)h.cp_len;
     c->have_tree = true;
     c->theta_nodes = -1.0f;
     memset(&c->stats, 0, sizeof c->stats);

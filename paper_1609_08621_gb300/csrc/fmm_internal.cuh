@@ -128,11 +128,8 @@ struct DevCounters {
                               // isolated box (kept across solves until a solve reports it)
     unsigned long long n_active;
     // walk totals
-    unsigned long long n_groups;
-    // list lengths, two to a word (one atomic per sink allocates both): the local entries of
-    // multipole sources (low 32 bits) and point sources (high 32 bits), and the groups' PP (low)
-    // and PC (high) entries; the capacities stay below 2^32
-    unsigned long long loc_len, src_len;
+    unsigned long long n_groups, cp_len;  // cp_len: entries of the point-source local list
+    unsigned long long pp_len, pc_len, cc_len;
     unsigned long long n_pp_pairs, n_pc_pairs, n_cc, n_cp;
     unsigned long long pp_work, pc_work;  // work counters of the persistent interaction kernels
     unsigned int n_item_pp, n_item_pc;    // work items of the interaction kernels
@@ -157,9 +154,6 @@ __device__ __forceinline__ bool fmm_overflowed(const DevCounters* ctr)
     return *(const volatile unsigned int*)&ctr->overflow != 0u;
 }
 
-__host__ __device__ __forceinline__ unsigned long long fmm_lo32(unsigned long long v) { return v & 0xffffffffull; }
-__host__ __device__ __forceinline__ unsigned long long fmm_hi32(unsigned long long v) { return v >> 32; }
-
 // One particle of the input as the key kernel copies it, in input order, for the gather after
 // the sort: a single aligned 32-byte sector per particle instead of one per coordinate.
 struct __align__(32) SrcRec {
@@ -167,6 +161,7 @@ struct __align__(32) SrcRec {
     float m;
     unsigned int act;
 };
+static_assert(sizeof(SrcRec) == 8 * sizeof(int), "an input record spans the 8 ints per particle of the radix block");
 
 // Device buffers of a context.  Capacities are in elements.
 struct DevTree {
@@ -190,7 +185,8 @@ struct DevTree {
     // sorting
     unsigned long long *key = nullptr, *key_alt = nullptr;
     unsigned int *idx = nullptr, *idx_alt = nullptr;
-    SrcRec *src = nullptr;  // the input particles in input order (key kernel to gather)
+    SrcRec *src = nullptr;  // the input particles in input order (key kernel to gather), a view of radix
+    int *radix = nullptr;   // one block of 8 ints per particle: src, then the radix tree's arrays
     // sorted particles
     double *sx = nullptr, *sy = nullptr, *sz = nullptr;
     float *sm = nullptr;
@@ -201,7 +197,7 @@ struct DevTree {
     int *bucket_of = nullptr;
     int *act = nullptr;      // per group, its active particles compacted (see k_group_active)
     // radix tree (nodes 0..n-2 internal, leaf p is node n-1+p)
-    int *ifirst = nullptr, *ilast = nullptr, *ileft = nullptr, *iright = nullptr;  // child node ids
+    int *ifirst = nullptr, *ilast = nullptr, *ileft = nullptr, *iright = nullptr;  // child node ids (views of radix)
     int *nparent = nullptr;  // parent internal node of every node (2n-1)
     unsigned int *keep = nullptr;  // 2n-1 flags, scanned to cell ids
     unsigned int *bflag = nullptr; // n flags, scanned to bucket ids

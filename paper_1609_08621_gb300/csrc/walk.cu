@@ -424,10 +424,13 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         w_max = max(w_max, (unsigned long long)(ncl + nq));
         // local-expansion entries of this sink: multipole sources (M2L) and point sources (P2L) in
         // two lists, each in queue order
-        unsigned long long lo = 0;
-        if (lane == 0 && (na | nap)) lo = atomicAdd(&ctr->loc_len, (unsigned long long)na | ((unsigned long long)nap << 32));
-        lo = __shfl_sync(FMM_FULL_MASK, lo, 0);
-        const unsigned long long off = fmm_lo32(lo), offp = fmm_hi32(lo);
+        unsigned long long off = 0, offp = 0;
+        if (lane == 0) {
+            if (na) off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
+            if (nap) offp = atomicAdd(&ctr->cp_len, (unsigned long long)nap);
+        }
+        off = __shfl_sync(FMM_FULL_MASK, off, 0);
+        offp = __shfl_sync(FMM_FULL_MASK, offp, 0);
         if ((long long)(off + na) > cap_cc || (long long)(offp + nap) > cap_cp) {
             if (lane == 0) atomicOr(&ctr->overflow, 1u);
             continue;
@@ -451,9 +454,8 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
             for (int o = 16; o > 0; o >>= 1) srcpp += __shfl_xor_sync(FMM_FULL_MASK, srcpp, o);
             unsigned long long po = 0, co = 0, gi = 0;
             if (lane == 0) {
-                const unsigned long long so = atomicAdd(&ctr->src_len, (unsigned long long)npp | ((unsigned long long)npc << 32));
-                po = fmm_lo32(so);
-                co = fmm_hi32(so);
+                po = atomicAdd(&ctr->pp_len, (unsigned long long)npp);
+                co = atomicAdd(&ctr->pc_len, (unsigned long long)npc);
                 gi = atomicAdd(&ctr->n_groups, 1ull);
             }
             po = __shfl_sync(FMM_FULL_MASK, po, 0);
@@ -595,8 +597,8 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (fmm_overflowed(ctr)) return;
-    const unsigned long long ll = *(volatile unsigned long long*)&ctr->loc_len;
-    const long long total = min((long long)(KIND == 0 ? fmm_lo32(ll) : fmm_hi32(ll)), cap_cc);
+    const long long total =
+        min((long long)*(volatile unsigned long long*)(KIND == 0 ? &ctr->cc_len : &ctr->cp_len), cap_cc);
     const long long nranges = fmm_ceil_div(total, LF_ENTRIES);
     const int c0 = lane, c1 = lane + 32;  // this lane's coefficients in the reduction
     int nent = 0;
