@@ -38,6 +38,7 @@
 #include <algorithm>
 
 #include "expansions.cuh"
+#include "f64bits.cuh"
 #include "fmm_internal.cuh"
 
 #define IW 4  // warps per block
@@ -478,6 +479,14 @@ __global__ void __launch_bounds__(ITHREADS, 4) k_pc(const Group* __restrict__ gr
     if (lane == 0 && pairs) atomicAdd(&ctr->n_pc_pairs, pairs);
 }
 
+// The partial sums as the accumulator type: FP64 values are formed from the FP32 encodings and
+// rounded back the same way (f64bits.cuh), so the FP64 pipe, at 1/64 of the FP32 rate on this GPU,
+// runs only the additions.
+__device__ __forceinline__ float acc_widen(float x, float) { return x; }
+__device__ __forceinline__ double acc_widen(float x, double) { return fmm_f2d(x); }
+__device__ __forceinline__ float acc_round(float x) { return x; }
+__device__ __forceinline__ float acc_round(double x) { return fmm_d2f_rn(x); }
+
 // Per group: each sink adds its PP partials and PC partials in item order, then the group's
 // local expansion, and the result goes to the caller's order (active particles only).
 // T = float: partial sums added in FP32; T = double: added in FP64 (accumulate = 1)
@@ -522,34 +531,34 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
             T ax = 0, ay = 0, az = 0, aw = 0;
             for (unsigned int k = 0; k < npp; k++) {
                 const float4 p = part_pp[(unsigned long long)(bpp + k) * FMM_GMAX + i];
-                ax += p.x;
-                ay += p.y;
-                az += p.z;
-                aw += p.w;
+                ax += acc_widen(p.x, ax);
+                ay += acc_widen(p.y, ay);
+                az += acc_widen(p.z, az);
+                aw += acc_widen(p.w, aw);
             }
             for (unsigned int k = 0; k < npc; k++) {
                 const float4 p = part_pc[(unsigned long long)(bpc + k) * FMM_GMAX + i];
-                ax += p.x;
-                ay += p.y;
-                az += p.z;
-                aw += p.w;
+                ax += acc_widen(p.x, ax);
+                ay += acc_widen(p.y, ay);
+                az += acc_widen(p.z, az);
+                aw += acc_widen(p.w, aw);
             }
             if (terms & 4) {
                 float ux, uy, uz, m;
                 load_sink(s, hk, lk, bucket_of, bucket_cell, cen, off, ux, uy, uz, m);
                 float lx = 0.f, ly = 0.f, lz = 0.f, lw = 0.f;
                 fmm_l2p_acc(Ls[wl], ux, uy, uz, lx, ly, lz, lw);
-                ax += lx;
-                ay += ly;
-                az += lz;
-                aw += lw;
+                ax += acc_widen(lx, ax);
+                ay += acc_widen(ly, ay);
+                az += acc_widen(lz, az);
+                aw += acc_widen(lw, aw);
             }
             {
                 const unsigned int p = perm[s];
-                acc[p] = (float)ax;
-                acc[n + p] = (float)ay;
-                acc[2 * n + p] = (float)az;
-                if (pot) pot[p] = (float)aw;
+                acc[p] = acc_round(ax);
+                acc[n + p] = acc_round(ay);
+                acc[2 * n + p] = acc_round(az);
+                if (pot) pot[p] = acc_round(aw);
             }
         }
         __syncwarp();

@@ -15,6 +15,7 @@
 // is synchronised.
 #include <math.h>
 
+#include "f64bits.cuh"
 #include "fmm_internal.cuh"
 
 __device__ __forceinline__ int target_rung(float ax, float ay, float az, double eps, double dt0, int R)
@@ -38,6 +39,15 @@ __global__ void k_assign_rungs(const float* __restrict__ acc, unsigned char* __r
     rung[i] = (unsigned char)target_rung(acc[i], acc[n + i], acc[2 * n + i], eps, dt0, R);
 }
 
+// dt0 2^-k as ldexp gives it, by one exact multiplication with the power of two built from its bits
+__device__ __forceinline__ double pow2_scale(double dt0, int k)
+{
+    return __dmul_rn(dt0, fmm_dfrom((unsigned long long)(1023 - k) << 52));
+}
+
+// FP64 issues at 1/64 of the FP32 rate on this GPU: the kicks and the drift are FP64 arithmetic, while
+// the widening of the FP32 accelerations and the box check of the new position use the encodings
+// (f64bits.cuh) and give the same values.
 __global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel, const float* __restrict__ acc,
                              unsigned char* __restrict__ rung, unsigned char* __restrict__ active_next, long long n,
                              double eps, double dt0, int R, long long s, int closing, unsigned int* __restrict__ status)
@@ -48,9 +58,9 @@ __global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel,
     double vx = vel[i], vy = vel[n + i], vz = vel[2 * n + i];
     if ((s & ((1LL << (R - r)) - 1)) == 0) {
         float fx = acc[i], fy = acc[n + i], fz = acc[2 * n + i];
-        double ax = fx, ay = fy, az = fz;
+        double ax = fmm_f2d(fx), ay = fmm_f2d(fy), az = fmm_f2d(fz);
         if (closing) {
-            double hk = ldexp(dt0, -r - 1);
+            double hk = pow2_scale(dt0, r + 1);
             vx += ax * hk;
             vy += ay * hk;
             vz += az * hk;
@@ -63,7 +73,7 @@ __global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel,
         }
         r = rn;
         rung[i] = (unsigned char)r;
-        double hk = ldexp(dt0, -r - 1);
+        double hk = pow2_scale(dt0, r + 1);
         vx += ax * hk;
         vy += ay * hk;
         vz += az * hk;
@@ -71,9 +81,9 @@ __global__ void k_kick_drift(double* __restrict__ pos, double* __restrict__ vel,
         vel[n + i] = vy;
         vel[2 * n + i] = vz;
     }
-    double h = ldexp(dt0, -R);
+    double h = pow2_scale(dt0, R);
     double x = pos[i] + vx * h, y = pos[n + i] + vy * h, z = pos[2 * n + i] + vz * h;
-    if (!(x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0)) atomicOr(status, FMM_DEV_ERR_ARG);
+    if (!(fmm_in_unit(x) && fmm_in_unit(y) && fmm_in_unit(z))) atomicOr(status, FMM_DEV_ERR_ARG);
     pos[i] = x;
     pos[n + i] = y;
     pos[2 * n + i] = z;

@@ -2,6 +2,8 @@
 // unit box, interleaved with x owning the highest bit of each level triple.
 #pragma once
 
+#include "f64bits.cuh"
+
 __device__ __forceinline__ unsigned long long spread3(unsigned int v)
 {
     // place the 21 bits of v at every third bit position
@@ -14,10 +16,5 @@ __device__ __forceinline__ unsigned long long spread3(unsigned int v)
     return x;
 }
 
-__device__ __forceinline__ unsigned int quantise21(double v)
-{
-    double s = v * 2097152.0;  // 2^21, exact
-    if (!(s >= 0.0)) s = 0.0;
-    unsigned int u = (unsigned int)s;
-    return u > 2097151u ? 2097151u : u;
-}
+// floor(v 2^21) clamped to the 21-bit range, from the bits of v (no FP64 instruction)
+__device__ __forceinline__ unsigned int quantise21(double v) { return fmm_quantise21(v); }

@@ -52,7 +52,8 @@ __global__ void k_keys(const double* __restrict__ pos, const unsigned int* __res
     r.m = m;
     r.act = active ? (active[i] != 0 ? 1u : 0u) : 1u;
     src[i] = r;
-    bool ok = (x >= 0.0 && x < 1.0 && y >= 0.0 && y < 1.0 && z >= 0.0 && z < 1.0 && m > 0.0f && isfinite(m));
+    // 0 <= x < 1 per axis, tested on the encodings (FP64 comparisons issue at 1/64 of the FP32 rate)
+    bool ok = (fmm_in_unit(x) && fmm_in_unit(y) && fmm_in_unit(z) && m > 0.0f && isfinite(m));
     if (!ok) atomicOr(status, FMM_DEV_ERR_ARG);
     // axis x owns the highest bit of each level triple: key bit 62 - l for level l
     key[i] = (spread3(quantise21(x)) << 2) | (spread3(quantise21(y)) << 1) | spread3(quantise21(z));
@@ -84,10 +85,13 @@ __global__ void k_gather(const SrcRec* __restrict__ src, long long n, const unsi
         sm[i] = m;
         act = r.act != 0u;
         sact[i] = act ? 1 : 0;
-        const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
+        // (fl(x), fl(x - fl(x))) per axis, from the encodings
+        float hx, hy, hz, lx, ly, lz;
+        fmm_split_f32(x, hx, lx);
+        fmm_split_f32(y, hy, ly);
+        fmm_split_f32(z, hz, lz);
         posf[i] = make_float4(hx, hy, hz, m);
-        plo[i] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
-                             __double2float_rn(z - (double)hz), 0.0f);
+        plo[i] = make_float4(lx, ly, lz, 0.0f);
     }
     unsigned int b = __ballot_sync(FMM_FULL_MASK, act);
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, (unsigned long long)__popc(b));
@@ -332,12 +336,29 @@ __device__ __forceinline__ double dist2_ordered(double dx, double dy, double dz)
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// the FP32 squared distance, in a fixed order of roundings, and the distance
+__device__ __forceinline__ float bm_d2_32(const float4 v, float px, float py, float pz)
+{
+    const float dx = __fsub_rn(v.x, px), dy = __fsub_rn(v.y, py), dz = __fsub_rn(v.z, pz);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+__device__ __forceinline__ float bm_d32(const float4 v, float px, float py, float pz)
+{
+    return sqrtf(bm_d2_32(v, px, py, pz));
+}
+
+// The FP32 distance of a particle from an FP32-rounded centre differs from the exact one by less
+// than about 1.1e-7 + 1.3e-7 d (positions in [0, 1), one subtraction and the norm), so every particle
+// within twice that margin of the largest FP32 distance is a candidate for the farthest one.
+__device__ __forceinline__ float bm_threshold(float top) { return top - (4e-7f + 6e-7f * top); }
+
 __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__ nbucket, const int* __restrict__ bucket_cell,
                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                                 const int* __restrict__ cparent, const int* __restrict__ cchild,
                                                 const double* __restrict__ sx, const double* __restrict__ sy,
                                                 const double* __restrict__ sz, const float* __restrict__ sm,
-                                                const unsigned char* __restrict__ sact, Com4* com, double* clo,
+                                                const unsigned char* __restrict__ sact,
+                                                const float4* __restrict__ posf, Com4* com, double* clo,
                                                 double* chi, double* bmax, int* cnact, float* rec,
                                                 float4* __restrict__ off, unsigned int* arrive)
 {
@@ -345,41 +366,61 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
     if (b >= (int)*nbucket) return;
     int c = bucket_cell[b];
     int f = cfirst[c], cnt = ccount[c];
+    // FP64 issues at 1/64 of the FP32 rate here: the sums stay FP64, while the box is a minimum and
+    // maximum of the positions' order keys, the widening of the mass and the rounding of the offsets
+    // work on the encodings (f64bits.cuh), and the exact squared distances are evaluated only for
+    // the particles that can be the farthest
     double M = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
     int na = 0;
     for (int j = f; j < f + cnt; j++) {
-        double m = (double)sm[j], x = sx[j], y = sy[j], z = sz[j];
+        double m = fmm_f2d(sm[j]), x = sx[j], y = sy[j], z = sz[j];
         M += m;
         mx += m * x;
         my += m * y;
         mz += m * z;
-        lo[0] = fmin(lo[0], x);
-        hi[0] = fmax(hi[0], x);
-        lo[1] = fmin(lo[1], y);
-        hi[1] = fmax(hi[1], y);
-        lo[2] = fmin(lo[2], z);
-        hi[2] = fmax(hi[2], z);
+        const unsigned long long kx = fmm_nonneg_key(x), ky = fmm_nonneg_key(y), kz = fmm_nonneg_key(z);
+        lo[0] = min(lo[0], kx);
+        hi[0] = max(hi[0], kx);
+        lo[1] = min(lo[1], ky);
+        hi[1] = max(hi[1], ky);
+        lo[2] = min(lo[2], kz);
+        hi[2] = max(hi[2], kz);
         na += sact[j] ? 1 : 0;
     }
     const double iM = 1.0 / M;  // one FP64 division (a software sequence on this part) instead of three
     double cx = mx * iM, cy = my * iM, cz = mz * iM;
-    double b2 = 0.0;
     float Mo[FMM_NMOM];
 #pragma unroll
     for (int i = 0; i < FMM_NMOM; i++) Mo[i] = 0.0f;
+    // the FP32 distances from the rounded centre single out the candidates for the farthest particle
+    // (the margin of the exact b_max passes below), at most 32 of them in a bit mask
+    const float pcx = fmm_d2f_rn(cx), pcy = fmm_d2f_rn(cy), pcz = fmm_d2f_rn(cz);
+    float m2 = 0.0f;
     for (int j = f; j < f + cnt; j++) {
         double dx = sx[j] - cx, dy = sy[j] - cy, dz = sz[j] - cz;
-        b2 = fmax(b2, dist2_ordered(dx, dy, dz));
         float m = sm[j];
-        float fx = __double2float_rn(dx), fy = __double2float_rn(dy), fz = __double2float_rn(dz);
+        float fx = fmm_d2f_rn(dx), fy = fmm_d2f_rn(dy), fz = fmm_d2f_rn(dz);
         fmm_p2m_acc(m, fx, fy, fz, Mo);
         off[j] = make_float4(fx, fy, fz, m);
+        m2 = fmaxf(m2, bm_d2_32(posf[j], pcx, pcy, pcz));
+    }
+    const float thr = bm_threshold(sqrtf(m2));
+    double b2 = 0.0;
+    for (int j0 = f; j0 < f + cnt; j0 += 32) {
+        unsigned int cand = 0u;
+        for (int t = 0; t < 32 && j0 + t < f + cnt; t++)
+            if (bm_d32(posf[j0 + t], pcx, pcy, pcz) >= thr) cand |= 1u << t;
+        while (cand) {
+            const int j = j0 + __ffs(cand) - 1;
+            cand &= cand - 1;
+            b2 = fmax(b2, dist2_ordered(sx[j] - cx, sy[j] - cy, sz[j] - cz));
+        }
     }
     com[c] = make_com4(cx, cy, cz, M);
     for (int a = 0; a < 3; a++) {
-        clo[3 * c + a] = lo[a];
-        chi[3 * c + a] = hi[a];
+        clo[3 * c + a] = fmm_dfrom(lo[a]);
+        chi[3 * c + a] = fmm_dfrom(hi[a]);
     }
     bmax[c] = __dsqrt_rn(b2);
     cnact[c] = na;
@@ -409,12 +450,12 @@ __global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__
 #pragma unroll
             for (int i = 0; i < FMM_NMOM; i++) Mc[i] = __ldcg(src + i);
             double tx = ac.x - px, ty = ac.y - py, tz = ac.z - pz;
-            fmm_m2m_acc(Mc, __double2float_rn(tx), __double2float_rn(ty), __double2float_rn(tz), Mq);
+            fmm_m2m_acc(Mc, fmm_d2f_rn(tx), fmm_d2f_rn(ty), fmm_d2f_rn(tz), Mq);
         }
         com[p] = make_com4(px, py, pz, Mp);
         for (int a = 0; a < 3; a++) {
-            clo[3 * p + a] = fmin(__ldcg(&clo[3 * c0 + a]), __ldcg(&clo[3 * c1 + a]));
-            chi[3 * p + a] = fmax(__ldcg(&chi[3 * c0 + a]), __ldcg(&chi[3 * c1 + a]));
+            clo[3 * p + a] = fmm_dfrom(min(fmm_nonneg_key(__ldcg(&clo[3 * c0 + a])), fmm_nonneg_key(__ldcg(&clo[3 * c1 + a]))));
+            chi[3 * p + a] = fmm_dfrom(max(fmm_nonneg_key(__ldcg(&chi[3 * c0 + a])), fmm_nonneg_key(__ldcg(&chi[3 * c1 + a]))));
         }
         cnact[p] = __ldcg(&cnact[c0]) + __ldcg(&cnact[c1]);
         write_record(rec + (long long)p * FMM_NREC, Mq);
@@ -503,37 +544,69 @@ __global__ void k_bm_expand(long long grid, const unsigned int* __restrict__ cnt
     for (long long i = 0; i < k; i++) item[b + i] = (int)c;
 }
 
-// the FP32 squared distance, in a fixed order of roundings, and the distance
-__device__ __forceinline__ float bm_d2_32(const float4 v, float px, float py, float pz)
+// FP64 candidates: (cell, particle) pairs whose FP32 distance reaches the cell's threshold wait in
+// a per-warp buffer and are evaluated 32 at a time, one per lane.  FP64 issues at 1/64 of the FP32
+// rate and a warp instruction costs the same with one active lane as with 32, so evaluating the
+// few candidates of each item as they are found kept the FP64 pipe busy on mostly idle lanes.
+#define BM_PEND 64
+struct BmPend {
+    int c[BM_PEND];
+    int j[BM_PEND];
+};
+
+// the exact squared distance of each of the first cnt waiting pairs, raised into its cell's maximum
+// (the bits of non-negative doubles order as unsigned integers)
+__device__ __forceinline__ void bm_eval(const BmPend& B, int cnt, const Com4* __restrict__ com,
+                                        const double* __restrict__ sx, const double* __restrict__ sy,
+                                        const double* __restrict__ sz, unsigned long long* __restrict__ bm64, int lane)
 {
-    const float dx = __fsub_rn(v.x, px), dy = __fsub_rn(v.y, py), dz = __fsub_rn(v.z, pz);
-    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-}
-__device__ __forceinline__ float bm_d32(const float4 v, float px, float py, float pz)
-{
-    return sqrtf(bm_d2_32(v, px, py, pz));
+    if (lane < cnt) {
+        const int c = B.c[lane], j = B.j[lane];
+        const Com4 p = com[c];
+        const double d2 = dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z);
+        atomicMax(bm64 + c, (unsigned long long)__double_as_longlong(d2));
+    }
 }
 
-// the largest FP64 squared distance from p among the particles [j0, j1) whose FP32 distance
-// reaches thr (warp-wide; FP64 runs at a small fraction of the FP32 rate, so only warp steps that
-// hold a candidate enter the FP64 branch)
-__device__ __forceinline__ double bm_candidates(long long j0, long long j1, const Com4& p, float px, float py,
-                                                float pz, float thr, const float4* __restrict__ posf,
-                                                const double* __restrict__ sx, const double* __restrict__ sy,
-                                                const double* __restrict__ sz, int lane)
+// queue the particles [j0, j1) of cell c whose FP32 distance from (px, py, pz) reaches thr;
+// evaluate whenever 32 wait
+__device__ __forceinline__ void bm_candidates(int c, long long j0, long long j1, float px, float py, float pz, float thr,
+                                              const float4* __restrict__ posf, BmPend& B, int& npend,
+                                              const Com4* __restrict__ com, const double* __restrict__ sx,
+                                              const double* __restrict__ sy, const double* __restrict__ sz,
+                                              unsigned long long* __restrict__ bm64, int lane)
 {
-    double best = 0.0;
+    const unsigned int lt = fmm_lanemask_lt();
     for (long long jb = j0; jb < j1; jb += 32) {
         const long long j = jb + lane;
         const bool cand = j < j1 && bm_d32(posf[j], px, py, pz) >= thr;
-        if (__any_sync(FMM_FULL_MASK, cand) && cand) best = fmax(best, dist2_ordered(sx[j] - p.x, sy[j] - p.y, sz[j] - p.z));
+        const unsigned int m = __ballot_sync(FMM_FULL_MASK, cand);
+        if (cand) {
+            const int slot = npend + __popc(m & lt);
+            B.c[slot] = c;
+            B.j[slot] = (int)j;
+        }
+        npend += __popc(m);
+        __syncwarp();
+        if (npend >= 32) {
+            bm_eval(B, 32, com, sx, sy, sz, bm64, lane);
+            const int rest = npend - 32;
+            int rc = 0, rj = 0;
+            if (lane < rest) {
+                rc = B.c[32 + lane];
+                rj = B.j[32 + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                B.c[lane] = rc;
+                B.j[lane] = rj;
+            }
+            npend = rest;
+            __syncwarp();
+        }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(FMM_FULL_MASK, best, o));
-    return best;
 }
 
-__device__ __forceinline__ float bm_threshold(float top) { return top - (4e-7f + 6e-7f * top); }
 
 // PASS 1: per item the FP32 maximum; a cell of one item finishes at once (its FP64 candidates),
 // a cell of several items records the item's maximum and raises the cell's.  PASS 2: the items of
@@ -549,7 +622,10 @@ __global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict_
                                                  const double* __restrict__ sz, unsigned int* __restrict__ bm32,
                                                  unsigned long long* __restrict__ bm64, float* __restrict__ imax)
 {
+    __shared__ BmPend pend[8];
     const int lane = threadIdx.x & 31;
+    BmPend& B = pend[threadIdx.x >> 5];
+    int npend = 0;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long ni = min((long long)*n_items, cap);
@@ -565,7 +641,7 @@ __global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict_
         const long long f = cfirst[c], e = f + ccount[c];
         const long long j0 = f + k * BM_CHUNK, j1 = min(j0 + BM_CHUNK, e);
         const Com4 p = com[c];
-        const float px = __double2float_rn(p.x), py = __double2float_rn(p.y), pz = __double2float_rn(p.z);
+        const float px = fmm_d2f_rn(p.x), py = fmm_d2f_rn(p.y), pz = fmm_d2f_rn(p.z);
         if (PASS == 1) {
             // the largest FP32 distance, as the square root of the largest square (the same value:
             // the square root is monotonic and correctly rounded)
@@ -575,8 +651,7 @@ __global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict_
             for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(FMM_FULL_MASK, m2, o));
             const float m = sqrtf(m2);
             if (nk == 1) {
-                const double best = bm_candidates(j0, j1, p, px, py, pz, bm_threshold(m), posf, sx, sy, sz, lane);
-                if (lane == 0) bm64[c] = (unsigned long long)__double_as_longlong(best);
+                bm_candidates(c, j0, j1, px, py, pz, bm_threshold(m), posf, B, npend, com, sx, sy, sz, bm64, lane);
             } else if (lane == 0) {
                 imax[i] = m;
                 atomicMax(bm32 + c, __float_as_uint(m));
@@ -584,10 +659,10 @@ __global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict_
         } else {
             const float thr = bm_threshold(__uint_as_float(bm32[c]));
             if (imax[i] < thr) continue;  // no particle of this item can be the farthest
-            const double best = bm_candidates(j0, j1, p, px, py, pz, thr, posf, sx, sy, sz, lane);
-            if (lane == 0 && best > 0.0) atomicMax(bm64 + c, (unsigned long long)__double_as_longlong(best));
+            bm_candidates(c, j0, j1, px, py, pz, thr, posf, B, npend, com, sx, sy, sz, bm64, lane);
         }
     }
+    bm_eval(B, npend, com, sx, sy, sz, bm64, lane);
 }
 
 __global__ void k_bm_final(const unsigned int* __restrict__ ncell, const int* __restrict__ cchild,
@@ -622,7 +697,7 @@ cudaError_t fmm_launch_upward(DevTree& t, long long n, int bucket, DevCounters* 
     cudaMemsetAsync(t.arrive, 0, sizeof(unsigned int) * (size_t)nc, s);
     k_upward<<<(unsigned)fmm_ceil_div(nb, 128), 128, 0, s>>>(t.dcount + 1, t.bucket_cell, t.cfirst, t.ccount,
                                                               t.cparent, t.cchild, t.sx, t.sy, t.sz, t.sm, t.sact,
-                                                              t.com, t.clo, t.chi, t.bmax, t.cnact, t.rec, t.off,
+                                                              t.posf, t.com, t.clo, t.chi, t.bmax, t.cnact, t.rec, t.off,
                                                               t.arrive);
     // exact b_max of the internal cells: items, then the two passes
     const unsigned gb = (unsigned)fmm_ceil_div(nc, TB);
@@ -667,26 +742,28 @@ __global__ void k_nodes(const unsigned int* __restrict__ ncell, float theta, con
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (int)*ncell) return;
     Com4 cm = com[c];
-    float bm = __double2float_rn(bmax[c]);
+    // every rounding to single precision from the encodings (f64bits.cuh), no FP64 instruction
+    float bm = fmm_d2f_rn(bmax[c]);
     int cnt = ccount[c];
     float ro = (cnt == 1) ? 0.0f : __fdiv_rn(bm, theta);
     WalkNode w;
-    const float hx = __double2float_rn(cm.x), hy = __double2float_rn(cm.y), hz = __double2float_rn(cm.z);
+    float hx, hy, hz, lx, ly, lz;
+    fmm_split_f32(cm.x, hx, lx);
+    fmm_split_f32(cm.y, hy, ly);
+    fmm_split_f32(cm.z, hz, lz);
     w.a = make_float4(hx, hy, hz, ro);
     cen[2 * c] = make_float4(hx, hy, hz, 0.0f);
-    cen[2 * c + 1] = make_float4(__double2float_rn(cm.x - (double)hx), __double2float_rn(cm.y - (double)hy),
-                                 __double2float_rn(cm.z - (double)hz), 0.0f);
-    w.b = make_float4(__double2float_rn(clo[3 * c]), __double2float_rn(clo[3 * c + 1]),
-                      __double2float_rn(clo[3 * c + 2]), bm);
-    w.c = make_float4(__double2float_rn(chi[3 * c]), __double2float_rn(chi[3 * c + 1]),
-                      __double2float_rn(chi[3 * c + 2]), 0.0f);
+    cen[2 * c + 1] = make_float4(lx, ly, lz, 0.0f);
+    w.b = make_float4(fmm_d2f_rn(clo[3 * c]), fmm_d2f_rn(clo[3 * c + 1]), fmm_d2f_rn(clo[3 * c + 2]), bm);
+    w.c = make_float4(fmm_d2f_rn(chi[3 * c]), fmm_d2f_rn(chi[3 * c + 1]), fmm_d2f_rn(chi[3 * c + 2]), 0.0f);
     w.d = make_int4(cchild[2 * c], cchild[2 * c + 1], cfirst[c], cnt);
     node[c] = w;
     // multipole norms for the learned criterion: |M2|_F / (M b^2), |M4|_F / (M b^4), both in [0, 1];
     // cells smaller than 1e-7 of the box (coincident particles) report 0
-    float4 mn = make_float4(0.0f, 0.0f, (float)cm.w, 0.0f);
+    const float mass32 = fmm_d2f_rn(cm.w);
+    float4 mn = make_float4(0.0f, 0.0f, mass32, 0.0f);
     if (bm > 1e-7f && cnt > 1) {
-        const float b2 = bm * bm, s2 = 1.0f / ((float)cm.w * b2), s4 = s2 / b2;
+        const float b2 = bm * bm, s2 = 1.0f / (mass32 * b2), s4 = s2 / b2;
         float n2, n4;
         fmm_moment_norms2(rec + (long long)c * FMM_NREC, s2, s4, n2, n4);
         mn.x = fminf(sqrtf(n2), 1.0f);
