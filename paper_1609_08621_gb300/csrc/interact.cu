@@ -487,6 +487,34 @@ __device__ __forceinline__ double acc_widen(float x, double) { return fmm_f2d(x)
 __device__ __forceinline__ float acc_round(float x) { return x; }
 __device__ __forceinline__ float acc_round(double x) { return fmm_d2f_rn(x); }
 
+// nk partials of slot i from item b on, added in item order; the loads of four items are issued
+// before their additions
+template <typename T>
+__device__ __forceinline__ void sum_partials(const float4* __restrict__ part, unsigned int b, unsigned int nk, int i,
+                                             T& ax, T& ay, T& az, T& aw)
+{
+    unsigned int k = 0;
+    for (; k + 4 <= nk; k += 4) {
+        float4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) p[u] = part[(unsigned long long)(b + k + u) * FMM_GMAX + i];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            ax += acc_widen(p[u].x, ax);
+            ay += acc_widen(p[u].y, ay);
+            az += acc_widen(p[u].z, az);
+            aw += acc_widen(p[u].w, aw);
+        }
+    }
+    for (; k < nk; k++) {
+        const float4 p = part[(unsigned long long)(b + k) * FMM_GMAX + i];
+        ax += acc_widen(p.x, ax);
+        ay += acc_widen(p.y, ay);
+        az += acc_widen(p.z, az);
+        aw += acc_widen(p.w, aw);
+    }
+}
+
 // Per group: each sink adds its PP partials and PC partials in item order, then the group's
 // local expansion, and the result goes to the caller's order (active particles only).
 // T = float: partial sums added in FP32; T = double: added in FP64 (accumulate = 1)
@@ -528,24 +556,15 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
         const int nact = cnact[G.cell];
         for (int i = lane; i < nact; i += 32) {
             const int s = act[G.first + i];
+            // the sink's geometry and output slot first, so their loads overlap the partials'
+            const unsigned int po = perm[s];
+            float ux = 0.f, uy = 0.f, uz = 0.f, m;
+            if (terms & 4) load_sink(s, hk, lk, bucket_of, bucket_cell, cen, off, ux, uy, uz, m);
             T ax = 0, ay = 0, az = 0, aw = 0;
-            for (unsigned int k = 0; k < npp; k++) {
-                const float4 p = part_pp[(unsigned long long)(bpp + k) * FMM_GMAX + i];
-                ax += acc_widen(p.x, ax);
-                ay += acc_widen(p.y, ay);
-                az += acc_widen(p.z, az);
-                aw += acc_widen(p.w, aw);
-            }
-            for (unsigned int k = 0; k < npc; k++) {
-                const float4 p = part_pc[(unsigned long long)(bpc + k) * FMM_GMAX + i];
-                ax += acc_widen(p.x, ax);
-                ay += acc_widen(p.y, ay);
-                az += acc_widen(p.z, az);
-                aw += acc_widen(p.w, aw);
-            }
+            // partials in item order, four loads in flight at a time
+            sum_partials(part_pp, bpp, npp, i, ax, ay, az, aw);
+            sum_partials(part_pc, bpc, npc, i, ax, ay, az, aw);
             if (terms & 4) {
-                float ux, uy, uz, m;
-                load_sink(s, hk, lk, bucket_of, bucket_cell, cen, off, ux, uy, uz, m);
                 float lx = 0.f, ly = 0.f, lz = 0.f, lw = 0.f;
                 fmm_l2p_acc(Ls[wl], ux, uy, uz, lx, ly, lz, lw);
                 ax += acc_widen(lx, ax);
@@ -553,13 +572,10 @@ __global__ void __launch_bounds__(ITHREADS) k_l2p_out(const Group* __restrict__ 
                 az += acc_widen(lz, az);
                 aw += acc_widen(lw, aw);
             }
-            {
-                const unsigned int p = perm[s];
-                acc[p] = acc_round(ax);
-                acc[n + p] = acc_round(ay);
-                acc[2 * n + p] = acc_round(az);
-                if (pot) pot[p] = acc_round(aw);
-            }
+            acc[po] = acc_round(ax);
+            acc[n + po] = acc_round(ay);
+            acc[2 * n + po] = acc_round(az);
+            if (pot) pot[po] = acc_round(aw);
         }
         __syncwarp();
     }
