@@ -467,9 +467,17 @@ fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
  * sized yet: scratch_entries per warp and list (default 8192) and list_scale checklist, local and
  * PC entries per particle (defaults 8, 12 and 8; PP half of list_scale, rounded up, default 3);
  * 0 keeps the defaults.  Each overflow doubles them and repeats the walk, up to 8 times, so small
- * values exercise that path.  Returns FMM_ERR_ARG for ctx == NULL or negative values. */
+ * values exercise that path.  Returns FMM_ERR_ARG for ctx == NULL or negative values.
+ *
+ * fmm_debug_local_side: the walk size, in sinks walked by the context's previous solve, from which
+ * each walk level's local expansions (M2L, P2L, L2L) run on a side stream beside the levels below
+ * instead of after the last level (default 2^22; a first solve never uses it).  Both orders give
+ * the same bits, since every sink's terms are added in its own list order; 0 takes the side stream
+ * whenever a previous solve exists, so tests can compare the two.  A negative value restores the
+ * default.  Returns FMM_ERR_ARG for ctx == NULL. */
 fmm_status fmm_debug_fail_allocations(long long after);
 fmm_status fmm_debug_walk_capacity(fmm_ctx *ctx, long long scratch_entries, long long list_scale);
+fmm_status fmm_debug_local_side(fmm_ctx *ctx, long long min_sinks);
 
 /* ---------------------------------------------------------------- allocation-free Morton order
  *

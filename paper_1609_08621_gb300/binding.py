@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
         "fmm_kick_drift_i32": (i, [vp, vp, vp, vp, vp, vp, ll, d, d, i, i, i]),
         "fmm_memory_info": (i, [vp, C.POINTER(ll), C.POINTER(ll)]),
         "fmm_debug_walk_capacity": (i, [vp, ll, ll]),
+        "fmm_debug_local_side": (i, [vp, ll]),
         "fmm_set_graphs": (i, [vp, i]),
         "fmm_graph_info": (i, [vp, C.POINTER(i), C.POINTER(ll)]),
         "fmm_autotune": (i, [vp, vp, vp, ll, vp, i, d, d, vp, i, i, vp, C.POINTER(fmm_params), C.POINTER(C.c_float)]),
@@ -519,6 +520,11 @@ class Context:
         """fmm_debug_walk_capacity: the walk's first scratch and list capacities (0: default), a
         test hook that makes the walk overflow and regrow."""
         _check(load().fmm_debug_walk_capacity(self.h, int(scratch_entries), int(list_scale)))
+
+    def debug_local_side(self, min_sinks=-1):
+        """fmm_debug_local_side: walks of at least min_sinks sinks (in the previous solve) run their
+        local expansions on a side stream (0: always after a first solve; negative: the default)."""
+        _check(load().fmm_debug_local_side(self.h, int(min_sinks)))
 
     def export_list_shifts(self, kind):
         """fmm_export_list_shifts: the periodic copy (n_x, n_y, n_z) of each entry's source, rows in

@@ -168,9 +168,16 @@ struct fmm_ctx {
     // the tree, join before the groups add them)
     cudaStream_t ew_stream = nullptr;
     cudaEvent_t ew_fork = nullptr, ew_join = nullptr;
+    // the local expansions of each walk level run on a side stream while the walk goes on (a fork
+    // after every level, a join before the groups take their expansions)
+    cudaStream_t loc_stream = nullptr;
+    cudaEvent_t loc_fork = nullptr, loc_join = nullptr;
     // positions of the current call as 32-bit fixed-point coordinates (fmm_compute_forces_i32), else
     // NULL and the call's FP64 positions are used
     const unsigned int* cur_ipos = nullptr;
+    // walks of at least this many sinks (previous solve) run the local expansions on a side stream
+    // (fmm_debug_local_side; FMM_LOCAL_SIDE_SINKS by default)
+    long long side_sinks = -1;
     // test hook (fmm_debug_walk_capacity): the walk's first per-warp scratch and list capacities
     long long dbg_scratch = 0, dbg_list_scale = 0;
     // staging for the host-buffer entry point
@@ -230,6 +237,13 @@ extern "C" fmm_status fmm_debug_fail_allocations(long long after)
     return FMM_OK;
 }
 
+extern "C" fmm_status fmm_debug_local_side(fmm_ctx* c, long long min_sinks)
+{
+    if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
+    c->side_sinks = min_sinks < 0 ? -1 : min_sinks;
+    return FMM_OK;
+}
+
 extern "C" fmm_status fmm_debug_walk_capacity(fmm_ctx* c, long long scratch_entries, long long list_scale)
 {
     if (!c) return fail(FMM_ERR_ARG, "ctx is NULL");
@@ -280,6 +294,11 @@ static void free_all(fmm_ctx* c)
     c->gexec = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
+    if (c->loc_stream) cudaStreamDestroy(c->loc_stream);
+    if (c->loc_fork) cudaEventDestroy(c->loc_fork);
+    if (c->loc_join) cudaEventDestroy(c->loc_join);
+    c->loc_stream = nullptr;
+    c->loc_fork = c->loc_join = nullptr;
     if (c->ew_stream) cudaStreamDestroy(c->ew_stream);
     if (c->ew_fork) cudaEventDestroy(c->ew_fork);
     if (c->ew_join) cudaEventDestroy(c->ew_join);
@@ -322,6 +341,10 @@ extern "C" fmm_status fmm_create(fmm_ctx** out, int device, void* cuda_stream)
     for (auto& ev : c->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaMemset(c->seed, 0, 8 * sizeof(unsigned int));
+    // the side stream of the walk levels' local expansions, made here so that no capture creates it
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->loc_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->loc_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->loc_join, cudaEventDisableTiming);
     // every counter starts at zero, the compressed kick-drift's status word included (it is kept
     // across solves, so memory left by an earlier context must not read as a report)
     if (e == cudaSuccess) e = cudaMemset(c->ctr, 0, sizeof(DevCounters));
@@ -763,6 +786,62 @@ static fmm_status ewald_join(fmm_ctx* c, int terms)
     return FMM_OK;
 }
 
+// The walk's levels on the context's stream, and the local expansions of every level.
+//
+// A walk of many sinks (at least FMM_LOCAL_SIDE_SINKS in the previous solve) forks each level's
+// expansions onto a side stream as soon as the level's walk kernel ends, to run beside the levels
+// below; the context's stream joins the side stream before the groups take their expansions.
+// There the walk warps leave the FMA pipes idle while they wait on loads.  A smaller walk is bound
+// by its longest chains of dependent steps instead, and kernels running beside it lengthen them:
+// measured on one GB300, the side stream took the 512^3 box's walk phase from 155.6 to 144.8 ms
+// (6.8 M sinks) and the 128^3 NFW box's from 4.1 to 5.2 ms (0.1 M sinks), so a smaller walk runs
+// the expansions after its last level.  Grids follow the previous solve's counts (full persistent
+// grids for the first solve).
+#ifndef FMM_LOCAL_SIDE_SINKS
+#define FMM_LOCAL_SIDE_SINKS (1LL << 22)
+#endif
+static fmm_status walk_levels(fmm_ctx* c, WalkArgs& a, int levels)
+{
+    DevTree& t = c->t;
+    DevWalk& w = c->w;
+    cudaStream_t s = c->stream;
+    const DevCounters* prev = c->have_solve ? c->ctr_h : nullptr;
+    long long prev_sinks = 0;
+    if (prev)
+        for (int L = 0; L < FMM_MAX_LEVELS; L++) prev_sinks += (long long)prev->lv_front[L];
+    const long long side_from = c->side_sinks >= 0 ? c->side_sinks : FMM_LOCAL_SIDE_SINKS;
+    if (!prev || prev_sinks < side_from) {
+        for (int L = 0; L < levels; L++) {
+            a.level = L;
+            a.level_parity = L & 1;
+            CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
+            c->launches += 1;
+        }
+        const LocalGrids g =
+            fmm_local_grids(w, prev ? (long long)prev->cc_len : -1, prev ? (long long)prev->cp_len : -1, -1);
+        CK(fmm_launch_local_level(t, w, c->ctr, a.eps2, -1, levels, g, s));
+        c->launches += 2 + levels;
+    } else {
+        for (int L = 0; L < levels; L++) {
+            a.level = L;
+            a.level_parity = L & 1;
+            CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
+            CK(cudaEventRecord(c->loc_fork, s));
+            CK(cudaStreamWaitEvent(c->loc_stream, c->loc_fork, 0));
+            const LocalGrids g = fmm_local_grids(w, prev ? (long long)prev->lv_cc[L] : -1,
+                                                 prev ? (long long)prev->lv_cp[L] : -1,
+                                                 prev ? (long long)prev->lv_front[L] : -1);
+            CK(fmm_launch_local_level(t, w, c->ctr, a.eps2, L, levels, g, c->loc_stream));
+            c->launches += 1 + 3;
+        }
+        CK(cudaEventRecord(c->loc_join, c->loc_stream));
+        CK(cudaStreamWaitEvent(s, c->loc_join, 0));
+    }
+    CK(fmm_launch_local_groups(w, t, c->ctr, s));
+    c->launches += 1;
+    return FMM_OK;
+}
+
 static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int group, int mode = 0)
 {
     DevTree& t = c->t;
@@ -797,14 +876,10 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
         CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
         CK(fmm_launch_walk_seed(t, w, c->ctr, s, c->second_root));
         c->launches += 1;
-        for (int L = 0; L < levels; L++) {
-            a.level = L;
-            a.level_parity = L & 1;
-            CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
-            c->launches += 1;
+        {
+            const fmm_status sw = walk_levels(c, a, levels);
+            if (sw != FMM_OK) return sw;
         }
-        CK(fmm_launch_local(t, w, c->ctr, a.eps2, levels, s));
-        c->launches += 3 + levels;
         {
             const fmm_status se = ewald_join(c, c->params.terms);
             if (se != FMM_OK) return se;
@@ -1074,14 +1149,8 @@ static fmm_status enqueue_graph_rest(fmm_ctx* c, long long n, const fmm_params& 
     CK(cudaMemsetAsync(&c->ctr->n_groups, 0, sizeof(DevCounters) - offsetof(DevCounters, n_groups), s));
     CK(fmm_launch_walk_seed(t, w, c->ctr, s));
     c->launches += 1;
-    for (int L = 0; L < c->graph_levels; L++) {
-        a.level = L;
-        a.level_parity = L & 1;
-        CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
-        c->launches += 1;
-    }
-    CK(fmm_launch_local(t, w, c->ctr, a.eps2, c->graph_levels, s));
-    c->launches += 3 + c->graph_levels;
+    st = walk_levels(c, a, c->graph_levels);
+    if (st != FMM_OK) return st;
     st = ewald_join(c, q.terms);
     if (st != FMM_OK) return st;
     CK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));

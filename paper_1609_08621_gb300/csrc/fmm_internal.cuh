@@ -145,6 +145,10 @@ struct DevCounters {
     unsigned long long lv_entries[FMM_MAX_LEVELS];      // checklist entries examined (incl. opened)
     unsigned long long lv_max_entries[FMM_MAX_LEVELS];  // largest per-sink count
     unsigned long long lv_base[FMM_MAX_LEVELS + 1];     // first walked cell of each level in DevWalk::wcells
+    // local-list entries (multipole and point sources) of each level's sinks: a level's entries
+    // follow those of the levels before it in the flat lists
+    unsigned long long lv_cc[FMM_MAX_LEVELS];
+    unsigned long long lv_cp[FMM_MAX_LEVELS];
 };
 
 // A walk (or the b_max items before it) that ran past a capacity left holes in the lists: the
@@ -356,7 +360,13 @@ struct WalkArgs {
     long long audit_cap;
 };
 cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, const WalkArgs& a, cudaStream_t s);
-cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int levels, cudaStream_t s);
+struct LocalGrids {
+    unsigned cc, cp, down;  // blocks of the M2L, P2L and top-down kernels
+};
+LocalGrids fmm_local_grids(const DevWalk& w, long long n_cc, long long n_cp, long long n_cells);
+cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int level, int levels,
+                                   const LocalGrids& g, cudaStream_t s);
+cudaError_t fmm_launch_local_groups(DevWalk& w, DevTree& t, DevCounters* ctr, cudaStream_t s);
 cudaError_t fmm_launch_walk_seed(DevTree& t, DevWalk& w, DevCounters* ctr, cudaStream_t s, int second_root = -1);
 cudaError_t fmm_launch_shift_tables(DevTree& t, cudaStream_t s);
 int fmm_walk_warps(int device);

@@ -36,6 +36,7 @@
 // per warp in shared memory.
 // L2P: the group's order-5 local coefficients evaluated at u_i.
 #include <algorithm>
+#include <atomic>
 
 #include "expansions.cuh"
 #include "f64bits.cuh"
@@ -595,16 +596,26 @@ static unsigned grid_for(long long n_groups)
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-// resident blocks of a kernel on the whole GPU (persistent grids)
+// resident blocks of a kernel on the current device (persistent grids), looked up once per device
+// and kernel: a table of atomics, 0 until the first launch on that device
 template <typename K>
-static int persistent_blocks(K kernel)
+static int persistent_blocks(K kernel, std::atomic<int>* table)
 {
-    int per_sm = 1, sms = 152, device = 0;
+    int device = 0;
     cudaGetDevice(&device);
+    const bool cached = device >= 0 && device < 64;
+    if (cached) {
+        const int b = table[device].load(std::memory_order_relaxed);
+        if (b > 0) return b;
+    }
+    int per_sm = 1, sms = 152;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ITHREADS, 0);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    return (per_sm < 1 ? 1 : per_sm) * sms;
+    const int b = (per_sm < 1 ? 1 : per_sm) * sms;
+    if (cached) table[device].store(b, std::memory_order_relaxed);
+    return b;
 }
+static std::atomic<int> g_pp_blocks[64], g_pc_blocks[64];
 
 // Active sinks of every group, compacted in particle order: act[G.first + i] = the group's i-th
 // active particle (with no inactive particles, the identity).  One warp per group.
@@ -685,8 +696,7 @@ cudaError_t fmm_launch_items(DevTree& t, DevWalk& w, DevCounters* ctr, int chunk
 cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s)
 {
     if (!(a.terms & 1)) return cudaSuccess;
-    static int blocks = 0;
-    if (!blocks) blocks = persistent_blocks(k_pp);
+    const int blocks = persistent_blocks(k_pp, g_pp_blocks);
     cudaMemsetAsync(&ctr->pp_work, 0, sizeof(unsigned long long), s);
     k_pp<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pp, w.base_pp, w.pp, t.cfirst, t.ccount, t.cnact, t.cen,
                                      t.bucket_of, t.bucket_cell, t.off, w.part_pp, t.act, a.eps2, a.chunk, w.cap_item_pp,
@@ -697,8 +707,7 @@ cudaError_t fmm_launch_pp(DevTree& t, DevWalk& w, DevCounters* ctr, const Intera
 cudaError_t fmm_launch_pc(DevTree& t, DevWalk& w, DevCounters* ctr, const InteractArgs& a, cudaStream_t s)
 {
     if (!(a.terms & 2)) return cudaSuccess;
-    static int blocks = 0;
-    if (!blocks) blocks = persistent_blocks(k_pc);
+    const int blocks = persistent_blocks(k_pc, g_pc_blocks);
     cudaMemsetAsync(&ctr->pc_work, 0, sizeof(unsigned long long), s);
     k_pc<<<blocks, ITHREADS, 0, s>>>(w.groups, w.item_pc, w.base_pc, w.pc, t.cnact, t.cen, t.bucket_of,
                                      t.bucket_cell, t.off, t.rec, w.part_pc, t.act, a.eps2, a.chunk, w.cap_item_pc,

@@ -352,7 +352,10 @@ __device__ __forceinline__ float bm_d32(const float4 v, float px, float py, floa
 // within twice that margin of the largest FP32 distance is a candidate for the farthest one.
 __device__ __forceinline__ float bm_threshold(float top) { return top - (4e-7f + 6e-7f * top); }
 
-__global__ void __launch_bounds__(128) k_upward(const unsigned int* __restrict__ nbucket, const int* __restrict__ bucket_cell,
+#ifndef FMM_UPWARD_MINB
+#define FMM_UPWARD_MINB 5  // resident blocks per SM the upward pass is compiled for (96 registers; 4: 128)
+#endif
+__global__ void __launch_bounds__(128, FMM_UPWARD_MINB) k_upward(const unsigned int* __restrict__ nbucket, const int* __restrict__ bucket_cell,
                                                 const int* __restrict__ cfirst, const int* __restrict__ ccount,
                                                 const int* __restrict__ cparent, const int* __restrict__ cchild,
                                                 const double* __restrict__ sx, const double* __restrict__ sy,
@@ -629,37 +632,66 @@ __global__ void __launch_bounds__(256) k_bm_pass(const unsigned int* __restrict_
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long ni = min((long long)*n_items, cap);
-    for (long long ii = gw; ii < ni; ii += nw) {
-        const long long i = order[ii];
-        // an item the expansion could not write (capacity overflow, reported to the host) is skipped
-        const int c = item[i];
-        if (c < 0 || c >= (int)*ncell) continue;
-        const long long k = i - (long long)base[c];
-        const long long nk = cnt[c];
-        if (k < 0 || k >= nk) continue;
-        if (PASS == 2 && nk == 1) continue;
-        const long long f = cfirst[c], e = f + ccount[c];
-        const long long j0 = f + k * BM_CHUNK, j1 = min(j0 + BM_CHUNK, e);
-        const Com4 p = com[c];
-        const float px = fmm_d2f_rn(p.x), py = fmm_d2f_rn(p.y), pz = fmm_d2f_rn(p.z);
-        if (PASS == 1) {
-            // the largest FP32 distance, as the square root of the largest square (the same value:
-            // the square root is monotonic and correctly rounded)
-            float m2 = 0.0f;
-            for (long long j = j0 + lane; j < j1; j += 32) m2 = fmaxf(m2, bm_d2_32(posf[j], px, py, pz));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(FMM_FULL_MASK, m2, o));
-            const float m = sqrtf(m2);
-            if (nk == 1) {
-                bm_candidates(c, j0, j1, px, py, pz, bm_threshold(m), posf, B, npend, com, sx, sy, sz, bm64, lane);
-            } else if (lane == 0) {
-                imax[i] = m;
-                atomicMax(bm32 + c, __float_as_uint(m));
+    const int nc = (int)*ncell;
+    // A warp takes 32 consecutive items at a time: lane q looks up item q's cell, chunk and centre
+    // (one chain of dependent loads for all 32), then the warp runs the items one by one.
+    for (long long ib = gw * 32; ib < ni; ib += nw * 32) {
+        const long long ii = ib + lane;
+        long long i = 0, j0 = 0, j1 = 0, nk = 0;
+        int c = -1;
+        float px = 0.0f, py = 0.0f, pz = 0.0f, thr = 0.0f;
+        bool ok = false;
+        if (ii < ni) {
+            i = order[ii];
+            // an item the expansion could not write (capacity overflow, reported to the host) is skipped
+            c = item[i];
+            if (c >= 0 && c < nc) {
+                const long long k = i - (long long)base[c];
+                nk = cnt[c];
+                ok = k >= 0 && k < nk && !(PASS == 2 && nk == 1);
+                if (ok) {
+                    const long long f = cfirst[c], e = f + ccount[c];
+                    j0 = f + k * BM_CHUNK;
+                    j1 = min(j0 + BM_CHUNK, e);
+                    const Com4 p = com[c];
+                    px = fmm_d2f_rn(p.x);
+                    py = fmm_d2f_rn(p.y);
+                    pz = fmm_d2f_rn(p.z);
+                    if (PASS == 2) {
+                        thr = bm_threshold(__uint_as_float(bm32[c]));
+                        ok = imax[i] >= thr;  // else no particle of this item can be the farthest
+                    }
+                }
             }
-        } else {
-            const float thr = bm_threshold(__uint_as_float(bm32[c]));
-            if (imax[i] < thr) continue;  // no particle of this item can be the farthest
-            bm_candidates(c, j0, j1, px, py, pz, thr, posf, B, npend, com, sx, sy, sz, bm64, lane);
+        }
+        unsigned int todo = __ballot_sync(FMM_FULL_MASK, ok);
+        while (todo) {
+            const int q = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const long long iq = __shfl_sync(FMM_FULL_MASK, i, q), a0 = __shfl_sync(FMM_FULL_MASK, j0, q),
+                            a1 = __shfl_sync(FMM_FULL_MASK, j1, q), nkq = __shfl_sync(FMM_FULL_MASK, nk, q);
+            const int cq = __shfl_sync(FMM_FULL_MASK, c, q);
+            const float qx = __shfl_sync(FMM_FULL_MASK, px, q), qy = __shfl_sync(FMM_FULL_MASK, py, q),
+                        qz = __shfl_sync(FMM_FULL_MASK, pz, q);
+            if (PASS == 1) {
+                // the largest FP32 distance, as the square root of the largest square (the same
+                // value: the square root is monotonic and correctly rounded)
+                float m2 = 0.0f;
+                for (long long j = a0 + lane; j < a1; j += 32) m2 = fmaxf(m2, bm_d2_32(posf[j], qx, qy, qz));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m2 = fmaxf(m2, __shfl_xor_sync(FMM_FULL_MASK, m2, o));
+                const float m = sqrtf(m2);
+                if (nkq == 1) {
+                    bm_candidates(cq, a0, a1, qx, qy, qz, bm_threshold(m), posf, B, npend, com, sx, sy, sz, bm64,
+                                  lane);
+                } else if (lane == 0) {
+                    imax[iq] = m;
+                    atomicMax(bm32 + cq, __float_as_uint(m));
+                }
+            } else {
+                const float tq = __shfl_sync(FMM_FULL_MASK, thr, q);
+                bm_candidates(cq, a0, a1, qx, qy, qz, tq, posf, B, npend, com, sx, sy, sz, bm64, lane);
+            }
         }
     }
     bm_eval(B, npend, com, sx, sy, sz, bm64, lane);

@@ -20,7 +20,9 @@
 // cell's lists are in a deterministic order whatever the scheduling.
 //
 // The local expansion of a walked cell is L_k = L2L(L_parent) + sum of M2L (CC) and P2L
-// (CP) terms, computed by a second kernel per level after the walk kernel of that level.
+// (CP) terms.  A level's local lists are complete when its walk kernel ends, so a large walk runs
+// their M2L and P2L terms and the level's top-down pass on a side stream while the walk goes on
+// below; a small one runs them after its last level.
 #include <algorithm>
 
 #include "expansions.cuh"
@@ -426,8 +428,14 @@ __global__ void __launch_bounds__(WALK_THREADS, MODE == 1 ? 4 : FMM_WALK_MINB) k
         // two lists, each in queue order
         unsigned long long off = 0, offp = 0;
         if (lane == 0) {
-            if (na) off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
-            if (nap) offp = atomicAdd(&ctr->cp_len, (unsigned long long)nap);
+            if (na) {
+                off = atomicAdd(&ctr->cc_len, (unsigned long long)na);
+                atomicAdd(&ctr->lv_cc[level], (unsigned long long)na);
+            }
+            if (nap) {
+                offp = atomicAdd(&ctr->cp_len, (unsigned long long)nap);
+                atomicAdd(&ctr->lv_cp[level], (unsigned long long)nap);
+            }
         }
         off = __shfl_sync(FMM_FULL_MASK, off, 0);
         offp = __shfl_sync(FMM_FULL_MASK, offp, 0);
@@ -584,27 +592,39 @@ __device__ __forceinline__ long long local_boundary(long long p, long long total
 // Two launches, one per list: KIND 0 the multipole sources (M2L), which write each sink's sum;
 // KIND 1 the point sources (P2L), which add theirs to it (or write it, for a sink with no
 // multipole source).  Every warp of a launch runs one kind of interaction.
+// One level's entries: those of the sinks of walk level `level`, [sum of the earlier levels' counts,
+// plus this level's), all of them complete when the level's walk kernel has ended; level -1: all.
+#ifndef FMM_LOCAL_MINB
+#define FMM_LOCAL_MINB 8  // resident blocks per SM the local-expansion kernels are compiled for (128 registers)
+#endif
 template <int KIND>
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local_flat(
+__global__ void __launch_bounds__(LOCAL_THREADS, FMM_LOCAL_MINB) k_local_flat(
     const unsigned int* __restrict__ cc, const int* __restrict__ cc_sink, const unsigned long long* __restrict__ lcc_off,
     const int* __restrict__ lcc_len, const int* __restrict__ lm2l_len, const float4* __restrict__ cen,
     const float4* __restrict__ posf, const float4* __restrict__ plo,
     const float* __restrict__ rec, float* __restrict__ Lown, long long cap_cc,
-    float eps2, int ib, int R, DevCounters* __restrict__ ctr)
+    float eps2, int ib, int R, int level, DevCounters* __restrict__ ctr)
 {
     __shared__ float red[LOCAL_WPB][32][FMM_NL + 1];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (fmm_overflowed(ctr)) return;
-    const long long total =
-        min((long long)*(volatile unsigned long long*)(KIND == 0 ? &ctr->cc_len : &ctr->cp_len), cap_cc);
-    const long long nranges = fmm_ceil_div(total, LF_ENTRIES);
+    long long start = 0, total;
+    if (level < 0) {  // every level's entries
+        total = min((long long)*(volatile unsigned long long*)(KIND == 0 ? &ctr->cc_len : &ctr->cp_len), cap_cc);
+    } else {
+        const unsigned long long* lv = KIND == 0 ? ctr->lv_cc : ctr->lv_cp;
+        for (int l = 0; l < level; l++) start += (long long)__ldcg(lv + l);
+        total = min(start + (long long)__ldcg(lv + level), cap_cc);
+    }
+    if (start >= total) return;
+    const long long nranges = fmm_ceil_div(total - start, LF_ENTRIES);
     const int c0 = lane, c1 = lane + 32;  // this lane's coefficients in the reduction
     int nent = 0;
     for (long long r = gw; r < nranges; r += nw) {
-        const long long r0 = local_boundary(r * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
-        const long long r1 = local_boundary((r + 1) * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
+        const long long r0 = local_boundary(start + r * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
+        const long long r1 = local_boundary(start + (r + 1) * LF_ENTRIES, total, cc_sink, lcc_off, lcc_len);
         float carry0 = 0.0f, carry1 = 0.0f;
         int carry_sink = -1;
         for (long long base = r0; base < r1; base += 32) {
@@ -839,19 +859,51 @@ cudaError_t fmm_launch_walk_level(DevTree& t, DevWalk& w, DevCounters* ctr, cons
     return cudaGetLastError();
 }
 
-cudaError_t fmm_launch_local(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int levels, cudaStream_t s)
+// The local expansions of walk level `level` (-1: the whole lists, then every level's top-down
+// pass): its own M2L terms, then its P2L terms, then the top-down pass of its cells (which reads the
+// level above, done by an earlier call on the same stream).  The grids are the caller's: every
+// kernel takes its work with grid-stride loops, so any size gives the same result.
+cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, float eps2, int level, int levels,
+                                   const LocalGrids& g, cudaStream_t s)
 {
-    const int blocks = w.n_warps / LOCAL_WPB;
-    k_local_flat<0><<<blocks, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, w.lcc_len, t.cen, t.posf,
-                                                      t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, ctr);
-    k_local_flat<1><<<blocks, LOCAL_THREADS, 0, s>>>(w.cp, w.cp_sink, w.lcp_off, w.lcp_len, w.lcc_len, t.cen, t.posf,
-                                                      t.plo, t.rec, t.L, w.cap_cp, eps2, t.per_ib, t.per_R, ctr);
+    k_local_flat<0><<<g.cc, LOCAL_THREADS, 0, s>>>(w.cc, w.cc_sink, w.lcc_off, w.lcc_len, w.lcc_len, t.cen, t.posf,
+                                                    t.plo, t.rec, t.L, w.cap_cc, eps2, t.per_ib, t.per_R, level, ctr);
+    k_local_flat<1><<<g.cp, LOCAL_THREADS, 0, s>>>(w.cp, w.cp_sink, w.lcp_off, w.lcp_len, w.lcc_len, t.cen, t.posf,
+                                                    t.plo, t.rec, t.L, w.cap_cp, eps2, t.per_ib, t.per_R, level, ctr);
+    const int l0 = level < 0 ? 0 : level, l1 = level < 0 ? levels : level + 1;
+    for (int l = l0; l < l1; l++)
+        k_local_down<<<g.down, LD_THREADS, 0, s>>>(l, w.wcells, w.cap_front, t.cparent, w.lcc_len, w.lcp_len, t.com,
+                                                   t.L, ctr);
+    return cudaGetLastError();
+}
+
+// Grid sizes for a level with about n_cc / n_cp local entries and n_cells walked cells (counts of
+// the previous solve; negative: unknown, the full persistent grids).
+LocalGrids fmm_local_grids(const DevWalk& w, long long n_cc, long long n_cp, long long n_cells)
+{
     int sms = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int l = 0; l < levels; l++)
-        k_local_down<<<(unsigned)(sms * 8), LD_THREADS, 0, s>>>(l, w.wcells, w.cap_front, t.cparent, w.lcc_len,
-                                                                 w.lcp_len, t.com, t.L, ctr);
+    const long long full = w.n_warps / LOCAL_WPB, full_down = (long long)sms * 8;
+    auto flat = [&](long long e) {
+        if (e < 0) return (unsigned)full;
+        // a quarter more warps than ranges, at least one block
+        const long long warps = fmm_ceil_div(e, LF_ENTRIES) * 5 / 4 + 1;
+        return (unsigned)std::max(1LL, std::min(full, fmm_ceil_div(warps, LOCAL_WPB)));
+    };
+    LocalGrids g;
+    g.cc = flat(n_cc);
+    g.cp = flat(n_cp);
+    g.down = n_cells < 0 ? (unsigned)full_down
+                         : (unsigned)std::max(1LL, std::min(full_down, fmm_ceil_div(n_cells * 5 / 4 + 1, LD_THREADS)));
+    return g;
+}
+
+cudaError_t fmm_launch_local_groups(DevWalk& w, DevTree& t, DevCounters* ctr, cudaStream_t s)
+{
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     k_local_groups<<<(unsigned)(sms * 8), 256, 0, s>>>(w.groups, t.L, w.Lg, w.cap_groups, ctr);
     return cudaGetLastError();
 }
