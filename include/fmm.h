@@ -469,12 +469,12 @@ fmm_status fmm_multi_index(int *local_idx, int *moment_idx);
  * 0 keeps the defaults.  Each overflow doubles them and repeats the walk, up to 8 times, so small
  * values exercise that path.  Returns FMM_ERR_ARG for ctx == NULL or negative values.
  *
- * fmm_debug_local_side: the walk size, in sinks walked by the context's previous solve, from which
- * each walk level's local expansions (M2L, P2L, L2L) run on a side stream beside the levels below
- * instead of after the last level (default 2^22; a first solve never uses it).  Both orders give
- * the same bits, since every sink's terms are added in its own list order; 0 takes the side stream
- * whenever a previous solve exists, so tests can compare the two.  A negative value restores the
- * default.  Returns FMM_ERR_ARG for ctx == NULL. */
+ * fmm_debug_local_side: the walk size, in sinks of the context's previous walk, from which each
+ * walk level's local expansions (M2L, P2L, L2L) run on a side stream beside the levels below
+ * instead of after the last level (default 2^22; a context's first walk never uses it).  Both
+ * orders give the same bits, since every sink's terms are added in its own list order; 0 takes the
+ * side stream whenever the context has walked before, so tests can compare the two.  A negative
+ * value restores the default.  Returns FMM_ERR_ARG for ctx == NULL. */
 fmm_status fmm_debug_fail_allocations(long long after);
 fmm_status fmm_debug_walk_capacity(fmm_ctx *ctx, long long scratch_entries, long long list_scale);
 fmm_status fmm_debug_local_side(fmm_ctx *ctx, long long min_sinks);

@@ -522,8 +522,9 @@ class Context:
         _check(load().fmm_debug_walk_capacity(self.h, int(scratch_entries), int(list_scale)))
 
     def debug_local_side(self, min_sinks=-1):
-        """fmm_debug_local_side: walks of at least min_sinks sinks (in the previous solve) run their
-        local expansions on a side stream (0: always after a first solve; negative: the default)."""
+        """fmm_debug_local_side: walks of at least min_sinks sinks (in the context's previous walk)
+        run their local expansions on a side stream (0: every walk after the first; negative: the
+        default)."""
         _check(load().fmm_debug_local_side(self.h, int(min_sinks)))
 
     def export_list_shifts(self, kind):

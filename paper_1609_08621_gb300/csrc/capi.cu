@@ -126,6 +126,11 @@ struct fmm_ctx {
     cudaEvent_t ev[8] = {};
     fmm_stats stats;
     bool have_tree = false, have_solve = false;
+    // the per-level counts of the context's last completed walk (size the next walk's local grids);
+    // kept apart from ctr_h, which later copies overwrite
+    bool have_counts = false;
+    long long prev_front[FMM_MAX_LEVELS] = {}, prev_cc[FMM_MAX_LEVELS] = {}, prev_cp[FMM_MAX_LEVELS] = {};
+    long long prev_cc_len = 0, prev_cp_len = 0;
     int launches = 0;  // kernels launched by the current solve
     float theta_nodes = -1.0f;
     // dual trees: the fixed tree, the subset scratch (flags, their scan, subset -> caller index,
@@ -788,15 +793,15 @@ static fmm_status ewald_join(fmm_ctx* c, int terms)
 
 // The walk's levels on the context's stream, and the local expansions of every level.
 //
-// A walk of many sinks (at least FMM_LOCAL_SIDE_SINKS in the previous solve) forks each level's
+// A walk of many sinks (at least FMM_LOCAL_SIDE_SINKS in the context's previous walk) forks each level's
 // expansions onto a side stream as soon as the level's walk kernel ends, to run beside the levels
 // below; the context's stream joins the side stream before the groups take their expansions.
 // There the walk warps leave the FMA pipes idle while they wait on loads.  A smaller walk is bound
 // by its longest chains of dependent steps instead, and kernels running beside it lengthen them:
 // measured on one GB300, the side stream took the 512^3 box's walk phase from 155.6 to 144.8 ms
 // (6.8 M sinks) and the 128^3 NFW box's from 4.1 to 5.2 ms (0.1 M sinks), so a smaller walk runs
-// the expansions after its last level.  Grids follow the previous solve's counts (full persistent
-// grids for the first solve).
+// the expansions after its last level.  Grids follow the previous walk's counts (full persistent
+// grids for the context's first walk).
 #ifndef FMM_LOCAL_SIDE_SINKS
 #define FMM_LOCAL_SIDE_SINKS (1LL << 22)
 #endif
@@ -805,10 +810,10 @@ static fmm_status walk_levels(fmm_ctx* c, WalkArgs& a, int levels)
     DevTree& t = c->t;
     DevWalk& w = c->w;
     cudaStream_t s = c->stream;
-    const DevCounters* prev = c->have_solve ? c->ctr_h : nullptr;
+    const bool prev = c->have_counts;
     long long prev_sinks = 0;
     if (prev)
-        for (int L = 0; L < FMM_MAX_LEVELS; L++) prev_sinks += (long long)prev->lv_front[L];
+        for (int L = 0; L < FMM_MAX_LEVELS; L++) prev_sinks += c->prev_front[L];
     const long long side_from = c->side_sinks >= 0 ? c->side_sinks : FMM_LOCAL_SIDE_SINKS;
     if (!prev || prev_sinks < side_from) {
         for (int L = 0; L < levels; L++) {
@@ -817,8 +822,7 @@ static fmm_status walk_levels(fmm_ctx* c, WalkArgs& a, int levels)
             CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
             c->launches += 1;
         }
-        const LocalGrids g =
-            fmm_local_grids(w, prev ? (long long)prev->cc_len : -1, prev ? (long long)prev->cp_len : -1, -1);
+        const LocalGrids g = fmm_local_grids(w, prev ? c->prev_cc_len : -1, prev ? c->prev_cp_len : -1, -1);
         CK(fmm_launch_local_level(t, w, c->ctr, a.eps2, -1, levels, g, s));
         c->launches += 2 + levels;
     } else {
@@ -828,9 +832,7 @@ static fmm_status walk_levels(fmm_ctx* c, WalkArgs& a, int levels)
             CK(fmm_launch_walk_level(t, w, c->ctr, a, s));
             CK(cudaEventRecord(c->loc_fork, s));
             CK(cudaStreamWaitEvent(c->loc_stream, c->loc_fork, 0));
-            const LocalGrids g = fmm_local_grids(w, prev ? (long long)prev->lv_cc[L] : -1,
-                                                 prev ? (long long)prev->lv_cp[L] : -1,
-                                                 prev ? (long long)prev->lv_front[L] : -1);
+            const LocalGrids g = fmm_local_grids(w, c->prev_cc[L], c->prev_cp[L], c->prev_front[L]);
             CK(fmm_launch_local_level(t, w, c->ctr, a.eps2, L, levels, g, c->loc_stream));
             c->launches += 1 + 3;
         }
@@ -897,6 +899,14 @@ static fmm_status run_walk(fmm_ctx* c, long long n, double eps, int bucket, int 
             w.cc_len = (long long)c->ctr_h->cc_len;
             w.cp_len = (long long)c->ctr_h->cp_len;
             c->stats.retries = attempt;
+            for (int L = 0; L < FMM_MAX_LEVELS; L++) {
+                c->prev_front[L] = (long long)c->ctr_h->lv_front[L];
+                c->prev_cc[L] = (long long)c->ctr_h->lv_cc[L];
+                c->prev_cp[L] = (long long)c->ctr_h->lv_cp[L];
+            }
+            c->prev_cc_len = w.cc_len;
+            c->prev_cp_len = w.cp_len;
+            c->have_counts = true;
             return FMM_OK;
         }
         if (attempt >= 8) return fail(FMM_ERR_OOM, "walk lists keep overflowing after %d grows", attempt);

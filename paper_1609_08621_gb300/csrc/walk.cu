@@ -878,24 +878,26 @@ cudaError_t fmm_launch_local_level(DevTree& t, DevWalk& w, DevCounters* ctr, flo
 }
 
 // Grid sizes for a level with about n_cc / n_cp local entries and n_cells walked cells (counts of
-// the previous solve; negative: unknown, the full persistent grids).
+// the context's previous walk; negative: unknown, the full persistent grids).  Never below two
+// blocks per SM: counts that changed since cost a level at most a few-fold, not its parallelism.
 LocalGrids fmm_local_grids(const DevWalk& w, long long n_cc, long long n_cp, long long n_cells)
 {
     int sms = 152, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long full = w.n_warps / LOCAL_WPB, full_down = (long long)sms * 8;
+    const long long full = w.n_warps / LOCAL_WPB, full_down = (long long)sms * 8, floor = 2LL * sms;
     auto flat = [&](long long e) {
         if (e < 0) return (unsigned)full;
-        // a quarter more warps than ranges, at least one block
+        // a quarter more warps than ranges
         const long long warps = fmm_ceil_div(e, LF_ENTRIES) * 5 / 4 + 1;
-        return (unsigned)std::max(1LL, std::min(full, fmm_ceil_div(warps, LOCAL_WPB)));
+        return (unsigned)std::max(std::min(floor, full), std::min(full, fmm_ceil_div(warps, LOCAL_WPB)));
     };
     LocalGrids g;
     g.cc = flat(n_cc);
     g.cp = flat(n_cp);
     g.down = n_cells < 0 ? (unsigned)full_down
-                         : (unsigned)std::max(1LL, std::min(full_down, fmm_ceil_div(n_cells * 5 / 4 + 1, LD_THREADS)));
+                         : (unsigned)std::max(std::min(floor, full_down),
+                                              std::min(full_down, fmm_ceil_div(n_cells * 5 / 4 + 1, LD_THREADS)));
     return g;
 }
 

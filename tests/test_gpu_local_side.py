@@ -4,7 +4,7 @@ large walks take), against the same expansions after the last level (the path sm
 Every sink's M2L and P2L terms are added in its own list order by one warp in both, and the top-down
 pass runs level by level in both, so the forces must agree bit for bit: eager solves, CUDA-graph
 replays, the periodic box and the learned criterion's walk.  fmm_debug_local_side(0) makes every
-solve after the first take the side stream.
+walk after a context's first take the side stream.
 """
 import numpy as np
 import pytest
@@ -60,6 +60,9 @@ def test_side_stream_gives_the_bits_of_the_in_order_path(dev, graphs, nrep):
         r = solves(ref, pos, mass, eps, theta, 4)
         s = solves(side, pos, mass, eps, theta, 4)
         assert side.stats()["n_cc"] > 0
+        if not graphs:
+            # the side stream launches M2L, P2L and L2L per level: more kernels than the in-order path
+            assert side.stats()["n_launches"] > ref.stats()["n_launches"]
         for (ra, rp), (sa, sp) in zip(r, s):
             assert np.array_equal(ra, sa) and np.array_equal(rp, sp)
         if graphs:
@@ -108,6 +111,7 @@ def test_side_stream_learned_walk(dev):
                 res.append(acc.cpu().numpy())
             outs[name] = res
             assert c.stats()["n_learned"] > 0
+        assert side.stats()["n_launches"] > ref.stats()["n_launches"]
         for ra, sa in zip(outs["ref"], outs["side"]):
             assert np.array_equal(ra, sa)
     finally:
