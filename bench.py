@@ -50,13 +50,37 @@ SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 PP_FLOPS = 19.0  # FP32 flops of one PP pair in the kernel (3 sub, 3 fma, 3 mul, 3 fma, 1 add)
 
-# DRAM bytes (read + write) per launch of the interaction kernels on the 128^3 NFW box with
-# buckets of 16, groups of 64 and work items of 128 list entries, stored from one earlier ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), not measured by this run.  Reported,
-# labelled as stored, only for runs with those settings; set back to None whenever a kernel
-# changes after that capture.
-NCU_TRAFFIC = {"k_pc": 202016000 + 53694208, "k_pp": 94603776 + 24113152}
+# DRAM bytes (read + write) of the interaction kernels with buckets of 16, groups of 64 and work
+# items of 128 list entries, stored from one earlier ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of the timed solve's launch), not measured by this run, and reported
+# labelled as stored only for runs with those settings; set back to None whenever a kernel changes
+# after that capture.
+# - the 128^3 NFW box: bytes per launch;
+# - the 512^3 box: bytes per (sink, source) pair of the kernel, from the full-size fixed-theta solve
+#   (k_pc 54,254,844,416 B for 31,659,347,808 PC pairs, k_pp 18,396,550,144 B for 128,335,887,451
+#   PP pairs); a learned solve runs the same kernels over fewer pairs, so its traffic is that rate
+#   times its own pair count.
+NCU_TRAFFIC = {"k_pc": 204893440 + 52785664, "k_pp": 94600448 + 20952576}
+NCU_TRAFFIC_PER_PAIR_512 = {"k_pc": 54254844416 / 31659347808, "k_pp": 18396550144 / 128335887451}
 NCU_TRAFFIC_PARAMS = (16, 64, 128)
+
+def stored_traffic(workload, n_override, tuning, kernel, stats):
+    """(DRAM bytes per launch of `kernel`, where the figure comes from) for the roofline: a stored ncu
+    capture for the 128^3 NFW box, a stored per-pair rate times this solve's pairs for the 512^3 box,
+    both only at the captured settings; else (None, why)."""
+    tun = tuning or {}
+    stored = (tun.get("bucket"), tun.get("group"), tun.get("list_chunk")) == NCU_TRAFFIC_PARAMS and n_override is None
+    if stored and workload == "nfw2m" and NCU_TRAFFIC and kernel in NCU_TRAFFIC:
+        return (NCU_TRAFFIC[kernel],
+                "stored from an earlier ncu capture of this kernel and these settings, not measured in this run")
+    if stored and workload == "learned134m" and NCU_TRAFFIC_PER_PAIR_512 and kernel in NCU_TRAFFIC_PER_PAIR_512:
+        pairs = int(stats.get("n_pc_pairs" if kernel == "k_pc" else "n_pp_pairs", 0) or 0)
+        if pairs > 0:
+            return (NCU_TRAFFIC_PER_PAIR_512[kernel] * pairs,
+                    "stored: bytes per pair from an earlier ncu capture of this kernel on the fixed-theta solve of "
+                    "this box at these settings, times this solve's pairs; not measured in this run")
+    return None, "no ncu capture of the current kernel at these settings"
+
 
 # Algorithmic DRAM bytes of the tree phase (keys, radix sort, gather, radix tree, cells, upward
 # pass, exact b_max, walk nodes), the reads and writes a streaming implementation cannot avoid:
@@ -933,15 +957,11 @@ def main():
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": NCU_TRAFFIC.get(dom) if NCU_TRAFFIC and args.workload == "nfw2m" and args.n is None and
-            (wl.config.get("bucket"), wl.config.get("group"), wl.config.get("list_chunk")) == NCU_TRAFFIC_PARAMS
-            else None,
+            "traffic": None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
             "pp_pc_frac": ((fpp + fpc) / ((pp_ms + pc_ms) * 1e-3) / 1e12) / FP32_PEAK_TFLOPS
             if pp_ms + pc_ms > 0 else 0.0}
-    roof["traffic_source"] = ("stored from an earlier ncu capture of this kernel and these settings, not measured "
-                              "in this run" if roof["traffic"] is not None else
-                              "no ncu capture of the current kernel at these settings")
+    roof["traffic"], roof["traffic_source"] = stored_traffic(args.workload, args.n, getattr(wl, "tuning", None), dom, st)
     # the tree phase against the HBM roofline (algorithmic bytes; CUDA events of the phase)
     hbm, hbm_src = measured_peak("hbm_gbs", 6800.0)
     tree_ms = kt["tree"] / args.steps
